@@ -1,0 +1,199 @@
+/*
+ * zbus.h -- C ABI of libzbus, a batched three-phase Z-bus power-flow solver
+ * for one NVIDIA GB300 (sm_103a).
+ *
+ * The method is the current-injection fixed point of arxiv 2605.14103,
+ * Sec. II-B:
+ *
+ *     v_b^{k+1} = Z i(v_b^k, S_b^wye, S_b^del) + w
+ *
+ * where Z is the reduced bus impedance of the non-slack phases, w the no-load
+ * voltage (the paper's v_0) and i(.) the current injection of constant-power
+ * wye and delta loads.  Many load scenarios b share one Z.
+ *
+ * Conventions shared by every call:
+ *   - Complex numbers are interleaved (re, im) doubles.
+ *   - Unknowns: the non-slack bus-phases of the admittance matrix, in
+ *     ascending global index order; n of them.  For a feeder whose bus k
+ *     occupies global indices 3k, 3k+1, 3k+2 with bus 0 the slack, unknown
+ *     j = 3(k-1) + phase.
+ *   - Loads are consumption (pu).  A wye slot j draws conj(S_wye_j / v_j).
+ *     A delta load of a bus sits in the bus's three slots in branch order
+ *     (ab, bc, ca); branch xy draws conj(S_xy / (v_x - v_y)) out of phase x
+ *     and returns it into phase y.  Delta loads require n to be a multiple
+ *     of 3 (three consecutive unknowns per bus).  A slot with S = 0 draws
+ *     nothing.
+ *   - Scenario arrays are scenario-major: element (b, j) of a [B][n] complex
+ *     array is at offset 2*(b*n + j) doubles.
+ *   - Device pointers are plain CUDA device addresses (for example a torch
+ *     tensor's data_ptr()); streams are cudaStream_t passed as void* (NULL is
+ *     the legacy default stream).
+ *   - Calls return a zbus_status; on an argument error nothing is launched and
+ *     outputs are untouched.  zbus_last_error() gives a message for the last
+ *     failing call of the calling thread.
+ *   - A network handle is not thread-safe: calls on one handle must not run
+ *     concurrently from several host threads.
+ */
+#ifndef ZBUS_H
+#define ZBUS_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct zbus_network_s* zbus_network;
+
+typedef enum {
+  ZBUS_OK = 0,
+  ZBUS_ERR_ARG = 1,         /* invalid argument; nothing was launched */
+  ZBUS_ERR_SINGULAR = 2,    /* Y_LL is singular to working precision */
+  ZBUS_ERR_OOM = 3,         /* device allocation failed or budget exceeded */
+  ZBUS_ERR_CUDA = 4,        /* a CUDA runtime call failed */
+  ZBUS_ERR_TIMEOUT = 5,     /* a bounded device wait gave up */
+  ZBUS_ERR_DEVICE = 6,      /* a kernel reported an internal error word */
+  ZBUS_ERR_UNSUPPORTED = 7  /* option not available for this network / device */
+} zbus_status;
+
+typedef enum {
+  ZBUS_FP64 = 0,              /* plain map, FP64 on the CUDA cores */
+  ZBUS_MIXED_BF16X2 = 1,      /* defect form, Z as BF16 hi+lo on tensor cores */
+  ZBUS_MIXED_FP16_SCALED = 2  /* defect form, Z as row-scaled FP16 hi+lo */
+} zbus_precision;
+
+typedef enum {
+  ZBUS_CONV_MAXABS = 0,  /* max_j |v_j^k - v_j^{k-1}| <= tol */
+  ZBUS_CONV_SUMMAG = 1   /* | sum_j |v_j^k| - sum_j |v_j^{k-1}| | <= tol (Sec. II-B) */
+} zbus_conv_rule;
+
+typedef struct {
+  int32_t precision;       /* zbus_precision */
+  int32_t conv_rule;       /* zbus_conv_rule */
+  double mismatch_tol;     /* mixed modes: a converged scenario must also have
+                              max_j |v_j conj(r_j)| <= mismatch_tol (FP64);
+                              <= 0 selects 1e-6 */
+  int32_t max_correction;  /* mixed modes: extra sweeps granted to scenarios
+                              that fail the mismatch test; < 0 selects 8 */
+  int32_t profile;         /* 1: run the sweeps from the host with CUDA events
+                              around every kernel on cuda_stream, for
+                              zbus_last_profile; 0: device-resident loop */
+  double reserved[4];
+} zbus_solve_opts;
+
+/* Fill *opts with the defaults (FP64, max-step rule). */
+void zbus_solve_opts_default(zbus_solve_opts* opts);
+
+/*
+ * zbus_network_create -- set up one network on the current CUDA device.
+ *
+ * Sec. II-B: separates slack and non-slack phases and precomputes the reduced
+ * bus impedance.  On the device, in FP64: dense Y_LL and Y_Ls from the COO
+ * entries (duplicates summed), Z = Y_LL^{-1} by Gauss-Jordan elimination with
+ * partial pivoting, w = -Z Y_Ls v_s, and the operand layouts of every
+ * precision.
+ *
+ *   n_total       number of bus-phases including the three slack phases (>= 4)
+ *   nnz           number of COO entries (>= 1)
+ *   row, col      host int32[nnz], 0 <= row, col < n_total
+ *   val_reim      host double[2*nnz], complex admittance entries (pu)
+ *   slack_idx     host int32[3], distinct global indices of the slack phases
+ *   v_slack_reim  host double[6], complex slack phase voltages (pu)
+ *   cuda_stream   stream for the setup work; the call returns after it finished
+ *   out           receives the handle (owned by the library until destroy)
+ *
+ * Returns ZBUS_ERR_SINGULAR if a pivot is zero or not finite, ZBUS_ERR_OOM if
+ * device memory runs out.
+ */
+zbus_status zbus_network_create(int32_t n_total, int64_t nnz,
+                                const int32_t* row, const int32_t* col,
+                                const double* val_reim,
+                                const int32_t* slack_idx,
+                                const double* v_slack_reim,
+                                void* cuda_stream, zbus_network* out);
+
+/* Release a network and every device buffer it owns.  NULL is ignored.  The
+ * caller must make sure no work of this handle is still running. */
+void zbus_network_destroy(zbus_network net);
+
+/* Number of unknowns n (non-slack bus-phases) of a network; -1 for NULL. */
+int32_t zbus_network_size(zbus_network net);
+
+/*
+ * zbus_network_get_z -- copy the device-formed Z (row-major [n][n] complex)
+ * and w ([n] complex) into caller device buffers, on cuda_stream.  Either
+ * output may be NULL.
+ */
+zbus_status zbus_network_get_z(zbus_network net, double* Z_out, double* w_out,
+                               void* cuda_stream);
+
+/*
+ * zbus_network_reserve -- grow the handle's scratch space for batches of up to
+ * B scenarios in the given precision, so that later zbus_solve calls of that
+ * size allocate nothing.  Synchronous.
+ */
+zbus_status zbus_network_reserve(zbus_network net, int64_t B, int32_t precision);
+
+/*
+ * zbus_solve -- batched fixed point over B scenarios (Sec. II-B).
+ *
+ *   S_wye, S_delta  device, [B][n] complex, consumption (pu); either may be
+ *                   NULL for "no loads of that kind"
+ *   V_init          device [B][n] complex warm start, or NULL for v^0 = w
+ *   tol             stop tolerance of the chosen rule (pu), >= 0
+ *   max_iter        iteration cap, >= 1
+ *   opts            NULL for the defaults
+ *   V_out           device [B][n] complex, the last iterate of every scenario
+ *   iters           device int32[B], maps performed (including the one that
+ *                   met tol)
+ *   converged       device uint8[B], 1 if the rule was met (and, in the mixed
+ *                   modes, the FP64 mismatch test passed)
+ *   cuda_stream     all work is enqueued on this stream; results are valid
+ *                   after it synchronises.  Scratch grows on demand (a
+ *                   synchronous allocation) unless reserved beforehand.
+ *
+ * Non-convergence is reported by the flags, not by the status.  V_out may
+ * alias V_init.  B = 0 is a no-op.
+ */
+zbus_status zbus_solve(zbus_network net, int64_t B,
+                       const double* S_wye, const double* S_delta,
+                       const double* V_init, double tol, int32_t max_iter,
+                       const zbus_solve_opts* opts,
+                       double* V_out, int32_t* iters, uint8_t* converged,
+                       void* cuda_stream);
+
+/*
+ * zbus_power_mismatch -- per-scenario FP64 power mismatch of given voltages,
+ * max_j |v_j conj((Y_LL v + Y_Ls v_s)_j - i_j(v))|, computed with the sparse
+ * admittance matrix (never with Z).  V, S_* device [B][n] complex; out device
+ * double[B].
+ */
+zbus_status zbus_power_mismatch(zbus_network net, int64_t B, const double* V,
+                                const double* S_wye, const double* S_delta,
+                                double* out, void* cuda_stream);
+
+/*
+ * zbus_last_profile -- per-sweep kernel times of the last zbus_solve on this
+ * handle that ran with opts.profile = 1.  Call after that solve's stream has
+ * synchronised.  For sweep k < min(max_n, sweeps): ms[3k + 0..2] receive the
+ * durations (milliseconds, CUDA events) of the load-current / residual
+ * kernel, the contraction and the convergence kernel; active[k] the number of
+ * scenarios the sweep processed.  *sweeps receives the number of sweeps
+ * launched (the loop runs max_iter sweeps; those after the last active one
+ * have active[k] = 0).  Any output may be NULL.
+ */
+zbus_status zbus_last_profile(zbus_network net, int32_t max_n, float* ms, int32_t* active,
+                              int32_t* sweeps);
+
+/* Human-readable name of a status code (static storage). */
+const char* zbus_status_string(zbus_status s);
+
+/* Message of the last failing call on the calling thread ("" if none). */
+const char* zbus_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* ZBUS_H */

@@ -1,0 +1,393 @@
+// C ABI of libzbus: argument checks, handle lifetime, scratch space and the
+// device-resident iteration loop (a CUDA graph whose WHILE node repeats one
+// sweep until no scenario is active).
+#include <cmath>
+#include <cstdlib>
+#include <cstring>
+#include <algorithm>
+#include <set>
+
+#include "zbus_internal.cuh"
+
+namespace zbus {
+
+static thread_local std::string g_last_error;
+
+void set_error(const std::string& msg) { g_last_error = msg; }
+
+zbus_status fail(zbus_status s, const std::string& msg) {
+  g_last_error = msg;
+  return s;
+}
+
+zbus_status cuda_fail(cudaError_t e, const char* what, const char* file, int line) {
+  g_last_error = std::string(what) + ": " + cudaGetErrorString(e) + " (" + file + ":" +
+                 std::to_string(line) + ")";
+  cudaGetLastError();  // clear a sticky launch error where possible
+  return e == cudaErrorMemoryAllocation ? ZBUS_ERR_OOM : ZBUS_ERR_CUDA;
+}
+
+namespace {
+
+size_t align256(size_t x) { return (x + 255) & ~size_t(255); }
+
+void drop_graphs(zbus_network net) {
+  for (auto& g : net->graphs) {
+    if (g.exec) cudaGraphExecDestroy(g.exec);
+    if (g.graph) cudaGraphDestroy(g.graph);
+  }
+  net->graphs.clear();
+}
+
+// Scratch of one solve: context, active list, per-tile partials and the
+// contraction operand of the active scenarios.
+size_t workspace_bytes(const zbus_network net, int64_t B) {
+  const int ntn = net->n_pad / F64_BN;
+  size_t b = align256(sizeof(SolveCtx));
+  b += align256((size_t)B * sizeof(int32_t));
+  b += align256((size_t)B * ntn * 2 * sizeof(double));
+  b += align256((size_t)3 * B * net->n_pad * sizeof(double));
+  return b;
+}
+
+zbus_status ensure_workspace(zbus_network net, int64_t B) {
+  Workspace& ws = net->ws;
+  if (ws.base && ws.cap_B >= B) return ZBUS_OK;
+  const size_t bytes = workspace_bytes(net, B);
+  if (ws.base) {
+    ZB_CUDA(cudaDeviceSynchronize());
+    drop_graphs(net);
+    cudaFree(ws.base);
+    ws = Workspace();
+  }
+  void* base = nullptr;
+  ZB_CUDA(cudaMalloc(&base, bytes));
+  char* p = (char*)base;
+  const int ntn = net->n_pad / F64_BN;
+  ws.base = base;
+  ws.bytes = bytes;
+  ws.cap_B = B;
+  ws.ctx = (SolveCtx*)p;
+  p += align256(sizeof(SolveCtx));
+  ws.list = (int32_t*)p;
+  p += align256((size_t)B * sizeof(int32_t));
+  ws.part = (double*)p;
+  p += align256((size_t)B * ntn * 2 * sizeof(double));
+  ws.Iop = (double*)p;
+  return ZBUS_OK;
+}
+
+bool use_graphs() {
+  const char* e = std::getenv("ZBUS_NO_GRAPH");
+  return !(e && e[0] == '1');
+}
+
+// One sweep of the plain FP64 method on stream st.
+void enqueue_sweep_f64(zbus_network net, int64_t B, int grid, cudaGraphConditionalHandle h,
+                       bool use_handle, cudaStream_t st) {
+  launch_currents_f64(net->ws.ctx, net->n, net->n_pad, (int)B, st);
+  launch_gemm_f64(net->ws.ctx, net->Zr, net->Zi, net->Zs, net->w, net->n, net->n_pad, grid, st);
+  launch_converge(net->ws.ctx, h, use_handle, st);
+}
+
+zbus_status get_loop_graph(zbus_network net, int64_t B, int32_t precision, GraphEntry** out) {
+  for (auto& g : net->graphs)
+    if (g.B == B && g.precision == precision) {
+      *out = &g;
+      return ZBUS_OK;
+    }
+  GraphEntry e;
+  e.B = B;
+  e.precision = precision;
+  e.grid_gemm = gemm_f64_grid((int)B, net->n_pad);
+  if (!net->cap_stream) ZB_CUDA(cudaStreamCreateWithFlags(&net->cap_stream, cudaStreamNonBlocking));
+  ZB_CUDA(cudaGraphCreate(&e.graph, 0));
+  cudaGraphConditionalHandle h;
+  ZB_CUDA(cudaGraphConditionalHandleCreate(&h, e.graph, 1, cudaGraphCondAssignDefault));
+  cudaGraphNodeParams cp = {cudaGraphNodeTypeConditional};
+  cp.conditional.handle = h;
+  cp.conditional.type = cudaGraphCondTypeWhile;
+  cp.conditional.size = 1;
+  cudaGraphNode_t node;
+  ZB_CUDA(cudaGraphAddNode(&node, e.graph, nullptr, nullptr, 0, &cp));
+  cudaGraph_t body = cp.conditional.phGraph_out[0];
+  ZB_CUDA(cudaStreamBeginCaptureToGraph(net->cap_stream, body, nullptr, nullptr, 0,
+                                        cudaStreamCaptureModeThreadLocal));
+  enqueue_sweep_f64(net, B, e.grid_gemm, h, true, net->cap_stream);
+  cudaGraph_t captured = nullptr;
+  cudaError_t ce = cudaStreamEndCapture(net->cap_stream, &captured);
+  if (ce != cudaSuccess) {
+    cudaGraphDestroy(e.graph);
+    return cuda_fail(ce, "cudaStreamEndCapture(sweep)", __FILE__, __LINE__);
+  }
+  ce = cudaGraphInstantiate(&e.exec, e.graph, 0);
+  if (ce != cudaSuccess) {
+    cudaGraphDestroy(e.graph);
+    return cuda_fail(ce, "cudaGraphInstantiate(solve loop)", __FILE__, __LINE__);
+  }
+  net->graphs.push_back(e);
+  *out = &net->graphs.back();
+  return ZBUS_OK;
+}
+
+zbus_status check_device(zbus_network net) {
+  int dev = -1;
+  ZB_CUDA(cudaGetDevice(&dev));
+  if (dev != net->device)
+    return fail(ZBUS_ERR_ARG, "current CUDA device " + std::to_string(dev) +
+                                  " differs from the network's device " +
+                                  std::to_string(net->device));
+  return ZBUS_OK;
+}
+
+}  // namespace
+}  // namespace zbus
+
+using namespace zbus;
+
+extern "C" {
+
+void zbus_solve_opts_default(zbus_solve_opts* o) {
+  if (!o) return;
+  std::memset(o, 0, sizeof(*o));
+  o->precision = ZBUS_FP64;
+  o->conv_rule = ZBUS_CONV_MAXABS;
+  o->mismatch_tol = 1e-6;
+  o->max_correction = 8;
+}
+
+const char* zbus_status_string(zbus_status s) {
+  switch (s) {
+    case ZBUS_OK: return "ZBUS_OK";
+    case ZBUS_ERR_ARG: return "ZBUS_ERR_ARG";
+    case ZBUS_ERR_SINGULAR: return "ZBUS_ERR_SINGULAR";
+    case ZBUS_ERR_OOM: return "ZBUS_ERR_OOM";
+    case ZBUS_ERR_CUDA: return "ZBUS_ERR_CUDA";
+    case ZBUS_ERR_TIMEOUT: return "ZBUS_ERR_TIMEOUT";
+    case ZBUS_ERR_DEVICE: return "ZBUS_ERR_DEVICE";
+    case ZBUS_ERR_UNSUPPORTED: return "ZBUS_ERR_UNSUPPORTED";
+  }
+  return "ZBUS_UNKNOWN_STATUS";
+}
+
+const char* zbus_last_error(void) { return g_last_error.c_str(); }
+
+zbus_status zbus_network_create(int32_t n_total, int64_t nnz, const int32_t* row,
+                                const int32_t* col, const double* val_reim,
+                                const int32_t* slack_idx, const double* v_slack_reim,
+                                void* cuda_stream, zbus_network* out) {
+  g_last_error.clear();
+  if (!out) return fail(ZBUS_ERR_ARG, "out is NULL");
+  *out = nullptr;
+  if (n_total < 4) return fail(ZBUS_ERR_ARG, "n_total must be >= 4 (three slack phases + 1)");
+  if (nnz < 1) return fail(ZBUS_ERR_ARG, "nnz must be >= 1");
+  if (!row || !col || !val_reim || !slack_idx || !v_slack_reim)
+    return fail(ZBUS_ERR_ARG, "a required host array is NULL");
+  std::set<int32_t> sl;
+  for (int p = 0; p < 3; ++p) {
+    if (slack_idx[p] < 0 || slack_idx[p] >= n_total)
+      return fail(ZBUS_ERR_ARG, "slack index out of range");
+    sl.insert(slack_idx[p]);
+  }
+  if (sl.size() != 3) return fail(ZBUS_ERR_ARG, "slack indices must be distinct");
+  for (int p = 0; p < 6; ++p)
+    if (!std::isfinite(v_slack_reim[p])) return fail(ZBUS_ERR_ARG, "slack voltage not finite");
+  for (int64_t t = 0; t < nnz; ++t) {
+    if (row[t] < 0 || row[t] >= n_total || col[t] < 0 || col[t] >= n_total)
+      return fail(ZBUS_ERR_ARG, "COO index out of range at entry " + std::to_string(t));
+    if (!std::isfinite(val_reim[2 * t]) || !std::isfinite(val_reim[2 * t + 1]))
+      return fail(ZBUS_ERR_ARG, "COO value not finite at entry " + std::to_string(t));
+  }
+  auto* net = new zbus_network_s();
+  cudaError_t ce = cudaGetDevice(&net->device);
+  if (ce != cudaSuccess) {
+    delete net;
+    return cuda_fail(ce, "cudaGetDevice", __FILE__, __LINE__);
+  }
+  zbus_status s = build_network(net, n_total, nnz, row, col, val_reim, slack_idx, v_slack_reim,
+                                (cudaStream_t)cuda_stream);
+  if (s != ZBUS_OK) {
+    std::string msg = g_last_error;
+    cudaStreamSynchronize((cudaStream_t)cuda_stream);
+    zbus_network_destroy(net);
+    g_last_error = msg;
+    return s;
+  }
+  *out = net;
+  return ZBUS_OK;
+}
+
+void zbus_network_destroy(zbus_network net) {
+  if (!net) return;
+  drop_graphs(net);
+  if (net->cap_stream) cudaStreamDestroy(net->cap_stream);
+  for (auto e : net->prof.ev) cudaEventDestroy(e);
+  cudaFree(net->prof.d_hist);
+  cudaFree(net->ws.base);
+  cudaFree(net->Z);
+  cudaFree(net->w);
+  cudaFree(net->ys);
+  cudaFree(net->Zr);
+  cudaFree(net->Zi);
+  cudaFree(net->Zs);
+  cudaFree(net->csr_ptr);
+  cudaFree(net->csr_col);
+  cudaFree(net->csr_val);
+  delete net;
+}
+
+int32_t zbus_network_size(zbus_network net) { return net ? net->n : -1; }
+
+zbus_status zbus_network_get_z(zbus_network net, double* Z_out, double* w_out, void* cuda_stream) {
+  g_last_error.clear();
+  if (!net) return fail(ZBUS_ERR_ARG, "network is NULL");
+  ZB_CHECK(check_device(net));
+  cudaStream_t st = (cudaStream_t)cuda_stream;
+  if (Z_out)
+    ZB_CUDA(cudaMemcpyAsync(Z_out, net->Z, (size_t)net->n * net->n * sizeof(double2),
+                            cudaMemcpyDeviceToDevice, st));
+  if (w_out)
+    ZB_CUDA(cudaMemcpyAsync(w_out, net->w, (size_t)net->n * sizeof(double2),
+                            cudaMemcpyDeviceToDevice, st));
+  return ZBUS_OK;
+}
+
+zbus_status zbus_network_reserve(zbus_network net, int64_t B, int32_t precision) {
+  g_last_error.clear();
+  if (!net) return fail(ZBUS_ERR_ARG, "network is NULL");
+  if (B < 0 || B > INT32_MAX / 4) return fail(ZBUS_ERR_ARG, "B out of range");
+  if (precision != ZBUS_FP64)
+    return fail(ZBUS_ERR_UNSUPPORTED, "precision not available in this build");
+  ZB_CHECK(check_device(net));
+  return ensure_workspace(net, B);
+}
+
+zbus_status zbus_solve(zbus_network net, int64_t B, const double* S_wye, const double* S_delta,
+                       const double* V_init, double tol, int32_t max_iter,
+                       const zbus_solve_opts* opts, double* V_out, int32_t* iters,
+                       uint8_t* converged, void* cuda_stream) {
+  g_last_error.clear();
+  if (!net) return fail(ZBUS_ERR_ARG, "network is NULL");
+  if (B < 0 || B > INT32_MAX / 4) return fail(ZBUS_ERR_ARG, "B out of range");
+  if (!(tol >= 0.0) || !std::isfinite(tol)) return fail(ZBUS_ERR_ARG, "tol must be finite, >= 0");
+  if (max_iter < 1) return fail(ZBUS_ERR_ARG, "max_iter must be >= 1");
+  zbus_solve_opts o;
+  zbus_solve_opts_default(&o);
+  if (opts) o = *opts;
+  if (o.conv_rule != ZBUS_CONV_MAXABS && o.conv_rule != ZBUS_CONV_SUMMAG)
+    return fail(ZBUS_ERR_ARG, "unknown convergence rule");
+  if (o.precision != ZBUS_FP64 && o.precision != ZBUS_MIXED_BF16X2 &&
+      o.precision != ZBUS_MIXED_FP16_SCALED)
+    return fail(ZBUS_ERR_ARG, "unknown precision");
+  if (B == 0) return ZBUS_OK;
+  if (!V_out || !iters || !converged) return fail(ZBUS_ERR_ARG, "an output pointer is NULL");
+  if (S_delta && !net->bus_aligned)
+    return fail(ZBUS_ERR_ARG, "delta loads need three unknowns per bus (n % 3 == 0)");
+  if (o.precision != ZBUS_FP64)
+    return fail(ZBUS_ERR_UNSUPPORTED, "precision not available in this build");
+  ZB_CHECK(check_device(net));
+  cudaStream_t st = (cudaStream_t)cuda_stream;
+  ZB_CHECK(ensure_workspace(net, B));
+
+  SolveCtx h;
+  std::memset(&h, 0, sizeof(h));
+  h.S_wye = (const double2*)S_wye;
+  h.S_del = (const double2*)S_delta;
+  h.V_init = (const double2*)V_init;
+  h.V = (double2*)V_out;
+  h.iters = iters;
+  h.conv = converged;
+  h.list = net->ws.list;
+  h.part = net->ws.part;
+  h.Iop = net->ws.Iop;
+  h.tol = tol;
+  h.mismatch_tol = o.mismatch_tol > 0 ? o.mismatch_tol : 1e-6;
+  h.B = (int32_t)B;
+  h.max_iter = max_iter;
+  h.rule = o.conv_rule;
+  h.ntn = net->n_pad / F64_BN;
+  if (o.profile == 1) {
+    Profile& P = net->prof;
+    if (P.cap < max_iter) {
+      for (auto e : P.ev) cudaEventDestroy(e);
+      P.ev.clear();
+      cudaFree(P.d_hist);
+      P.d_hist = nullptr;
+      P.cap = 0;
+      ZB_CUDA(cudaMalloc((void**)&P.d_hist, (size_t)max_iter * sizeof(int32_t)));
+      P.ev.resize((size_t)4 * max_iter);
+      for (auto& e : P.ev) ZB_CUDA(cudaEventCreate(&e));
+      P.cap = max_iter;
+    }
+    ZB_CUDA(cudaMemsetAsync(P.d_hist, 0, (size_t)max_iter * sizeof(int32_t), st));
+    h.hist = P.d_hist;
+    h.hist_n = max_iter;
+    launch_init(net->ws.ctx, h, net->w, net->n, (int)B, st);
+    const int grid = gemm_f64_grid((int)B, net->n_pad);
+    for (int k = 0; k < max_iter; ++k) {
+      cudaEvent_t* e = &P.ev[(size_t)4 * k];
+      ZB_CUDA(cudaEventRecord(e[0], st));
+      launch_currents_f64(net->ws.ctx, net->n, net->n_pad, (int)B, st);
+      ZB_CUDA(cudaEventRecord(e[1], st));
+      launch_gemm_f64(net->ws.ctx, net->Zr, net->Zi, net->Zs, net->w, net->n, net->n_pad, grid,
+                      st);
+      ZB_CUDA(cudaEventRecord(e[2], st));
+      launch_converge(net->ws.ctx, 0, false, st);
+      ZB_CUDA(cudaEventRecord(e[3], st));
+    }
+    P.sweeps = max_iter;
+    ZB_CUDA(cudaGetLastError());
+    return ZBUS_OK;
+  }
+  launch_init(net->ws.ctx, h, net->w, net->n, (int)B, st);
+  ZB_CUDA(cudaGetLastError());
+  if (use_graphs()) {
+    GraphEntry* g = nullptr;
+    ZB_CHECK(get_loop_graph(net, B, o.precision, &g));
+    ZB_CUDA(cudaGraphLaunch(g->exec, st));
+  } else {
+    const int grid = gemm_f64_grid((int)B, net->n_pad);
+    for (int k = 0; k < max_iter; ++k) enqueue_sweep_f64(net, B, grid, 0, false, st);
+    ZB_CUDA(cudaGetLastError());
+  }
+  return ZBUS_OK;
+}
+
+zbus_status zbus_last_profile(zbus_network net, int32_t max_n, float* ms, int32_t* active,
+                              int32_t* sweeps) {
+  g_last_error.clear();
+  if (!net) return fail(ZBUS_ERR_ARG, "network is NULL");
+  Profile& P = net->prof;
+  if (sweeps) *sweeps = P.sweeps;
+  const int m = std::min(max_n, P.sweeps);
+  if (m <= 0) return ZBUS_OK;
+  if (ms) {
+    for (int k = 0; k < m; ++k)
+      for (int q = 0; q < 3; ++q)
+        ZB_CUDA(cudaEventElapsedTime(&ms[3 * k + q], P.ev[(size_t)4 * k + q],
+                                     P.ev[(size_t)4 * k + q + 1]));
+  }
+  if (active) ZB_CUDA(cudaMemcpy(active, P.d_hist, (size_t)m * sizeof(int32_t),
+                                 cudaMemcpyDeviceToHost));
+  return ZBUS_OK;
+}
+
+zbus_status zbus_power_mismatch(zbus_network net, int64_t B, const double* V,
+                                const double* S_wye, const double* S_delta, double* out,
+                                void* cuda_stream) {
+  g_last_error.clear();
+  if (!net) return fail(ZBUS_ERR_ARG, "network is NULL");
+  if (B < 0 || B > INT32_MAX) return fail(ZBUS_ERR_ARG, "B out of range");
+  if (B == 0) return ZBUS_OK;
+  if (!V || !out) return fail(ZBUS_ERR_ARG, "V or out is NULL");
+  if (S_delta && !net->bus_aligned)
+    return fail(ZBUS_ERR_ARG, "delta loads need three unknowns per bus (n % 3 == 0)");
+  ZB_CHECK(check_device(net));
+  launch_mismatch((const double2*)V, (const double2*)S_wye, (const double2*)S_delta,
+                  net->csr_ptr, net->csr_col, net->csr_val, net->ys, net->n, (int)B, out,
+                  (cudaStream_t)cuda_stream);
+  ZB_CUDA(cudaGetLastError());
+  return ZBUS_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,428 @@
+// Plain FP64 Z-bus sweep (Sec. II-B):
+//   K1  load currents i(v) of wye and delta constant-power loads,
+//   K2  D = Z i with the three-real-product (3M) complex scheme, epilogue
+//       v <- w + D and per-tile step partials,
+//   K3  per-scenario stop test, freeze and stable compaction of the active
+//       list; sets the graph's loop condition.
+// Plus the run start (v^0) and the FP64 power-mismatch check.
+#include <cmath>
+
+#include "zbus_internal.cuh"
+
+namespace zbus {
+namespace {
+
+// conj(S / v) = conj(S) v / |v|^2; zero when the slot has no load.
+__device__ __forceinline__ double2 load_draw(double2 S, double2 v) {
+  if (S.x == 0.0 && S.y == 0.0) return make_double2(0.0, 0.0);
+  const double inv = 1.0 / (v.x * v.x + v.y * v.y);
+  return make_double2((S.x * v.x + S.y * v.y) * inv, (S.x * v.y - S.y * v.x) * inv);
+}
+
+}  // namespace
+
+// Current injection of one bus (three consecutive unknowns).  Wye slot p draws
+// conj(S_wye_p / v_p); delta branch xy in order (ab, bc, ca) draws
+// conj(S_xy / (v_x - v_y)) from phase x and returns it into phase y.
+// Injection = -(drawn).  `m` = number of valid slots (3 unless the network
+// ends inside a bus, which only wye loads allow).
+__device__ __forceinline__ void bus_injection(const double2* v, const double2* sw,
+                                              const double2* sd, int m, double2* inj) {
+  double2 d[3];
+#pragma unroll
+  for (int p = 0; p < 3; ++p) d[p] = (p < m && sw) ? load_draw(sw[p], v[p]) : make_double2(0.0, 0.0);
+  if (sd && m == 3) {
+    const double2 vab = make_double2(v[0].x - v[1].x, v[0].y - v[1].y);
+    const double2 vbc = make_double2(v[1].x - v[2].x, v[1].y - v[2].y);
+    const double2 vca = make_double2(v[2].x - v[0].x, v[2].y - v[0].y);
+    const double2 iab = load_draw(sd[0], vab);
+    const double2 ibc = load_draw(sd[1], vbc);
+    const double2 ica = load_draw(sd[2], vca);
+    d[0].x += iab.x - ica.x; d[0].y += iab.y - ica.y;
+    d[1].x += ibc.x - iab.x; d[1].y += ibc.y - iab.y;
+    d[2].x += ica.x - ibc.x; d[2].y += ica.y - ibc.y;
+  }
+#pragma unroll
+  for (int p = 0; p < 3; ++p) inj[p] = make_double2(-d[p].x, -d[p].y);
+}
+
+namespace {
+
+// ---------------------------------------------------------------------------
+// Run start: v^0 = w (or the warm start), flags cleared, every scenario active.
+// ---------------------------------------------------------------------------
+// The solve's context arrives by value and is stored for the later kernels;
+// this kernel itself only uses the by-value copy.
+__global__ void k_init(SolveCtx* ctx, SolveCtx h, const double2* __restrict__ w, int n, int B) {
+  const double2* Vi = h.V_init;
+  double2* V = h.V;
+  const int64_t tot = (int64_t)B * n;
+  for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < tot;
+       t += (int64_t)gridDim.x * blockDim.x) {
+    const int j = (int)(t % n);
+    V[t] = Vi ? Vi[t] : w[j];
+  }
+  for (int64_t b = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; b < B;
+       b += (int64_t)gridDim.x * blockDim.x) {
+    h.iters[b] = 0;
+    h.conv[b] = 0;
+    h.list[b] = (int32_t)b;
+  }
+  if (blockIdx.x == 0 && threadIdx.x == 0) {
+    h.count = B;
+    h.iter = 0;
+    h.err = 0;
+    *ctx = h;
+  }
+}
+
+// ---------------------------------------------------------------------------
+// K1: i(v) for the active scenarios into the 3M operands Ir, Ii, Ir + Ii,
+// [slot][n_pad] each, zero in the padding.  One thread per (slot, bus).
+// ---------------------------------------------------------------------------
+__global__ void k_currents_f64(const SolveCtx* __restrict__ ctx, int n, int n_pad) {
+  const int count = ctx->count;
+  const int nbp = n_pad / 3;
+  const int64_t tot = (int64_t)count * nbp;
+  const int64_t plane = (int64_t)ctx->B * n_pad;
+  double* Ir = ctx->Iop;
+  double* Ii = Ir + plane;
+  double* Is = Ii + plane;
+  const double2* __restrict__ V = ctx->V;
+  const double2* __restrict__ Sw = ctx->S_wye;
+  const double2* __restrict__ Sd = ctx->S_del;
+  for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < tot;
+       t += (int64_t)gridDim.x * blockDim.x) {
+    const int slot = (int)(t / nbp);
+    const int k = (int)(t % nbp);
+    const int j0 = 3 * k;
+    const int64_t o = (int64_t)slot * n_pad + j0;
+    double2 inj[3] = {make_double2(0.0, 0.0), make_double2(0.0, 0.0), make_double2(0.0, 0.0)};
+    if (j0 < n) {
+      const int b = ctx->list[slot];
+      const int m = min(3, n - j0);
+      const int64_t e = (int64_t)b * n + j0;
+      double2 v[3], sw[3], sd[3];
+#pragma unroll
+      for (int p = 0; p < 3; ++p) {
+        v[p] = p < m ? V[e + p] : make_double2(1.0, 0.0);
+        sw[p] = (Sw && p < m) ? Sw[e + p] : make_double2(0.0, 0.0);
+        sd[p] = (Sd && p < m) ? Sd[e + p] : make_double2(0.0, 0.0);
+      }
+      bus_injection(v, Sw ? sw : nullptr, Sd ? sd : nullptr, m, inj);
+      for (int p = m; p < 3; ++p) inj[p] = make_double2(0.0, 0.0);
+    }
+#pragma unroll
+    for (int p = 0; p < 3; ++p) {
+      Ir[o + p] = inj[p].x;
+      Ii[o + p] = inj[p].y;
+      Is[o + p] = inj[p].x + inj[p].y;
+    }
+  }
+}
+
+// ---------------------------------------------------------------------------
+// K2: FP64 3M contraction over active scenarios.
+//   T1 = Zr Ir, T2 = Zi Ii, T3 = (Zr + Zi)(Ir + Ii);  D = (T1 - T2, T3 - T1 - T2)
+// Tile: BM scenarios x BN outputs, k in steps of BK, each thread TM x TN.
+// Epilogue: v <- w + D in place, partials (max |dv|, sum |v_new| - |v_old|)
+// per (slot, N-tile), summed in a fixed order.
+// ---------------------------------------------------------------------------
+constexpr int TM = 2, TN = 4;
+constexpr int THR_M = F64_BM / TM;   // 16
+constexpr int THR_N = F64_BN / TN;   // 12
+constexpr int GEMM_THREADS = THR_M * THR_N;  // 192
+
+__global__ void __launch_bounds__(GEMM_THREADS)
+k_gemm3m_f64(const SolveCtx* __restrict__ ctx, const double* __restrict__ Zr,
+             const double* __restrict__ Zi, const double* __restrict__ Zs,
+             const double2* __restrict__ w, int n, int n_pad) {
+  __shared__ double sZ[3][F64_BK][F64_BN];
+  __shared__ double sI[3][F64_BK][F64_BM];
+  __shared__ double sred[2][F64_BM][THR_N];
+
+  const int count = ctx->count;
+  const int ntn = n_pad / F64_BN;
+  const int mtiles = (count + F64_BM - 1) / F64_BM;
+  const int total = mtiles * ntn;
+  const int64_t plane = (int64_t)ctx->B * n_pad;
+  const double* Ir = ctx->Iop;
+  const double* Ii = Ir + plane;
+  const double* Is = Ii + plane;
+  double2* V = ctx->V;
+  const int32_t* list = ctx->list;
+  double* part = ctx->part;
+
+  const int tid = threadIdx.x;
+  const int tm = tid / THR_N;   // 0..15
+  const int tn = tid % THR_N;   // 0..11
+
+  for (int tile = blockIdx.x; tile < total; tile += gridDim.x) {
+    const int mt = tile / ntn;
+    const int nt = tile % ntn;
+    const int row0 = nt * F64_BN;
+    const int slot0 = mt * F64_BM;
+    double a1[TM][TN], a2[TM][TN], a3[TM][TN];
+#pragma unroll
+    for (int a = 0; a < TM; ++a)
+#pragma unroll
+      for (int c = 0; c < TN; ++c) a1[a][c] = a2[a][c] = a3[a][c] = 0.0;
+
+    for (int k0 = 0; k0 < n_pad; k0 += F64_BK) {
+      // Z tile: BN rows x BK, stored k-major in shared memory
+      for (int e = tid; e < F64_BN * F64_BK; e += GEMM_THREADS) {
+        const int r = e / F64_BK, c = e % F64_BK;
+        const int64_t g = (int64_t)(row0 + r) * n_pad + k0 + c;
+        sZ[0][c][r] = Zr[g];
+        sZ[1][c][r] = Zi[g];
+        sZ[2][c][r] = Zs[g];
+      }
+      for (int e = tid; e < F64_BM * F64_BK; e += GEMM_THREADS) {
+        const int r = e / F64_BK, c = e % F64_BK;
+        const int slot = slot0 + r;
+        double x = 0.0, y = 0.0, s = 0.0;
+        if (slot < count) {
+          const int64_t g = (int64_t)slot * n_pad + k0 + c;
+          x = Ir[g];
+          y = Ii[g];
+          s = Is[g];
+        }
+        sI[0][c][r] = x;
+        sI[1][c][r] = y;
+        sI[2][c][r] = s;
+      }
+      __syncthreads();
+#pragma unroll
+      for (int kk = 0; kk < F64_BK; ++kk) {
+        double i1[TM], i2[TM], i3[TM], z1[TN], z2[TN], z3[TN];
+#pragma unroll
+        for (int a = 0; a < TM; ++a) {
+          i1[a] = sI[0][kk][tm * TM + a];
+          i2[a] = sI[1][kk][tm * TM + a];
+          i3[a] = sI[2][kk][tm * TM + a];
+        }
+#pragma unroll
+        for (int c = 0; c < TN; ++c) {
+          z1[c] = sZ[0][kk][tn + THR_N * c];
+          z2[c] = sZ[1][kk][tn + THR_N * c];
+          z3[c] = sZ[2][kk][tn + THR_N * c];
+        }
+#pragma unroll
+        for (int a = 0; a < TM; ++a)
+#pragma unroll
+          for (int c = 0; c < TN; ++c) {
+            a1[a][c] = fma(z1[c], i1[a], a1[a][c]);
+            a2[a][c] = fma(z2[c], i2[a], a2[a][c]);
+            a3[a][c] = fma(z3[c], i3[a], a3[a][c]);
+          }
+      }
+      __syncthreads();
+    }
+
+    // epilogue
+#pragma unroll
+    for (int a = 0; a < TM; ++a) {
+      const int r = tm * TM + a;
+      const int slot = slot0 + r;
+      double dmax = 0.0, dsum = 0.0;
+      if (slot < count) {
+        const int b = list[slot];
+#pragma unroll
+        for (int c = 0; c < TN; ++c) {
+          const int i = row0 + tn + THR_N * c;
+          if (i < n) {
+            const double dr = a1[a][c] - a2[a][c];
+            const double di = a3[a][c] - a1[a][c] - a2[a][c];
+            const double2 wi = w[i];
+            const int64_t g = (int64_t)b * n + i;
+            const double2 vo = V[g];
+            const double2 vn = make_double2(wi.x + dr, wi.y + di);
+            V[g] = vn;
+            double step = hypot(vn.x - vo.x, vn.y - vo.y);
+            if (step != step) step = INFINITY;
+            dmax = fmax(dmax, step);
+            dsum += hypot(vn.x, vn.y) - hypot(vo.x, vo.y);
+          }
+        }
+      }
+      sred[0][r][tn] = dmax;
+      sred[1][r][tn] = dsum;
+    }
+    __syncthreads();
+    if (tid < F64_BM) {
+      const int slot = slot0 + tid;
+      if (slot < count) {
+        double dmax = 0.0, dsum = 0.0;
+        for (int c = 0; c < THR_N; ++c) {
+          dmax = fmax(dmax, sred[0][tid][c]);
+          dsum += sred[1][tid][c];
+        }
+        part[((int64_t)slot * ntn + nt) * 2 + 0] = dmax;
+        part[((int64_t)slot * ntn + nt) * 2 + 1] = dsum;
+      }
+    }
+    __syncthreads();
+  }
+}
+
+// ---------------------------------------------------------------------------
+// K3: stop test per active scenario, stable in-place compaction of the list.
+// One block of 1024 threads.
+// ---------------------------------------------------------------------------
+constexpr int CONV_THREADS = 1024;
+
+__global__ void __launch_bounds__(CONV_THREADS)
+k_converge(SolveCtx* ctx, cudaGraphConditionalHandle h, int use_handle) {
+  __shared__ int swarp[CONV_THREADS / 32];
+  __shared__ int sbase, stotal;
+  const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
+  const int count = ctx->count;
+  const int it = ctx->iter + 1;
+  const int ntn = ctx->ntn;
+  const double tol = ctx->tol;
+  const int rule = ctx->rule;
+  const int max_iter = ctx->max_iter;
+  int32_t* list = ctx->list;
+  const double* part = ctx->part;
+  if (tid == 0) {
+    sbase = 0;
+    if (ctx->hist && it - 1 < ctx->hist_n) ctx->hist[it - 1] = count;
+  }
+  __syncthreads();
+  for (int base = 0; base < count; base += CONV_THREADS) {
+    const int slot = base + tid;
+    int keep = 0, b = -1;
+    if (slot < count) {
+      b = list[slot];
+      double dmax = 0.0, dsum = 0.0;
+      for (int t = 0; t < ntn; ++t) {
+        dmax = fmax(dmax, part[((int64_t)slot * ntn + t) * 2 + 0]);
+        dsum += part[((int64_t)slot * ntn + t) * 2 + 1];
+      }
+      const double delta = rule == ZBUS_CONV_SUMMAG ? fabs(dsum) : dmax;
+      ctx->iters[b] = it;
+      if (!isfinite(delta)) {
+        ctx->conv[b] = 0;
+      } else if (delta <= tol) {
+        ctx->conv[b] = 1;
+      } else if (it < max_iter) {
+        keep = 1;
+      }
+    }
+    // block-wide exclusive scan of keep, then an in-place stable write: every
+    // read of this chunk happened before the first barrier and every write
+    // lands at or before its writer's own slot.
+    const unsigned bal = __ballot_sync(0xffffffffu, keep);
+    const int wpre = __popc(bal & ((1u << lane) - 1u));
+    if (lane == 0) swarp[wid] = __popc(bal);
+    __syncthreads();
+    if (wid == 0) {
+      const int x = swarp[lane];
+      int incl = x;
+      for (int o = 1; o < 32; o <<= 1) {
+        const int y = __shfl_up_sync(0xffffffffu, incl, o);
+        if (lane >= o) incl += y;
+      }
+      swarp[lane] = incl - x;
+      if (lane == 31) stotal = incl;
+    }
+    __syncthreads();
+    if (keep) list[sbase + swarp[wid] + wpre] = b;
+    __syncthreads();
+    if (tid == 0) sbase += stotal;
+    __syncthreads();
+  }
+  if (tid == 0) {
+    ctx->count = sbase;
+    ctx->iter = it;
+    if (use_handle) cudaGraphSetConditional(h, sbase > 0 ? 1u : 0u);
+  }
+}
+
+// ---------------------------------------------------------------------------
+// FP64 power mismatch with the sparse admittance matrix:
+//   max_j | v_j conj( sum_c Y_LL[j][c] v_c + ys_j - i_j(v) ) |
+// One block per scenario, one thread per bus.
+// ---------------------------------------------------------------------------
+__global__ void k_mismatch(const double2* __restrict__ V, const double2* __restrict__ Sw,
+                           const double2* __restrict__ Sd, const int32_t* __restrict__ ptr,
+                           const int32_t* __restrict__ col, const double2* __restrict__ val,
+                           const double2* __restrict__ ys, int n, double* out) {
+  __shared__ double sm[32];
+  const int b = blockIdx.x;
+  const double2* v = V + (int64_t)b * n;
+  double worst = 0.0;
+  const int nb = (n + 2) / 3;
+  for (int k = threadIdx.x; k < nb; k += blockDim.x) {
+    const int j0 = 3 * k;
+    const int m = min(3, n - j0);
+    double2 vv[3], sw[3], sd[3], inj[3];
+    for (int p = 0; p < 3; ++p) {
+      vv[p] = p < m ? v[j0 + p] : make_double2(1.0, 0.0);
+      sw[p] = (Sw && p < m) ? Sw[(int64_t)b * n + j0 + p] : make_double2(0.0, 0.0);
+      sd[p] = (Sd && p < m) ? Sd[(int64_t)b * n + j0 + p] : make_double2(0.0, 0.0);
+    }
+    bus_injection(vv, Sw ? sw : nullptr, Sd ? sd : nullptr, m, inj);
+    for (int p = 0; p < m; ++p) {
+      const int j = j0 + p;
+      double2 acc = ys[j];
+      for (int t = ptr[j]; t < ptr[j + 1]; ++t) {
+        const double2 y = val[t], x = v[col[t]];
+        acc.x += y.x * x.x - y.y * x.y;
+        acc.y += y.x * x.y + y.y * x.x;
+      }
+      const double rx = acc.x - inj[p].x, ry = acc.y - inj[p].y;
+      // |v conj(r)| = |v| |r|
+      double e = hypot(vv[p].x, vv[p].y) * hypot(rx, ry);
+      if (e != e) e = INFINITY;
+      worst = fmax(worst, e);
+    }
+  }
+  for (int o = 16; o > 0; o >>= 1) worst = fmax(worst, __shfl_xor_sync(0xffffffffu, worst, o));
+  if ((threadIdx.x & 31) == 0) sm[threadIdx.x >> 5] = worst;
+  __syncthreads();
+  if (threadIdx.x < 32) {
+    double x = threadIdx.x < (blockDim.x >> 5) ? sm[threadIdx.x] : 0.0;
+    for (int o = 16; o > 0; o >>= 1) x = fmax(x, __shfl_xor_sync(0xffffffffu, x, o));
+    if (threadIdx.x == 0) out[b] = x;
+  }
+}
+
+}  // namespace
+
+void launch_init(SolveCtx* ctx, const SolveCtx& h, const double2* w, int n, int B,
+                 cudaStream_t st) {
+  int64_t tot = (int64_t)B * n;
+  int grid = (int)std::min<int64_t>(4096, std::max<int64_t>(1, (tot + 255) / 256));
+  k_init<<<grid, 256, 0, st>>>(ctx, h, w, n, B);
+}
+
+void launch_currents_f64(SolveCtx* ctx, int n, int n_pad, int B, cudaStream_t st) {
+  int64_t tot = (int64_t)B * (n_pad / 3);
+  int grid = (int)std::min<int64_t>(152 * 16, std::max<int64_t>(1, (tot + 255) / 256));
+  k_currents_f64<<<grid, 256, 0, st>>>(ctx, n, n_pad);
+}
+
+int gemm_f64_grid(int B, int n_pad) {
+  const int tiles = ((B + F64_BM - 1) / F64_BM) * (n_pad / F64_BN);
+  return std::max(1, std::min(tiles, 152 * 4));
+}
+
+void launch_gemm_f64(SolveCtx* ctx, const double* Zr, const double* Zi, const double* Zs,
+                     const double2* w, int n, int n_pad, int grid, cudaStream_t st) {
+  k_gemm3m_f64<<<grid, GEMM_THREADS, 0, st>>>(ctx, Zr, Zi, Zs, w, n, n_pad);
+}
+
+void launch_converge(SolveCtx* ctx, cudaGraphConditionalHandle h, bool use_handle,
+                     cudaStream_t st) {
+  k_converge<<<1, CONV_THREADS, 0, st>>>(ctx, h, use_handle ? 1 : 0);
+}
+
+void launch_mismatch(const double2* V, const double2* S_wye, const double2* S_del,
+                     const int32_t* ptr, const int32_t* col, const double2* val,
+                     const double2* ys, int n, int B, double* out, cudaStream_t st) {
+  if (B <= 0) return;
+  k_mismatch<<<B, 256, 0, st>>>(V, S_wye, S_del, ptr, col, val, ys, n, out);
+}
+
+}  // namespace zbus

@@ -1,0 +1,320 @@
+// Network setup (Sec. II-B: slack / non-slack separation and the precomputed
+// reduced bus impedance), all arithmetic in FP64 on the device:
+//   dense Y_LL, Y_Ls v_s from the coalesced COO entries,
+//   Z = Y_LL^{-1} by Gauss-Jordan elimination with partial pivoting,
+//   w = -Z (Y_Ls v_s),
+//   FP64 contraction operands Zr, Zi, Zr + Zi (zero-padded, row-major).
+#include <algorithm>
+#include <cmath>
+#include <numeric>
+
+#include "zbus_internal.cuh"
+
+namespace zbus {
+namespace {
+
+__device__ __forceinline__ double2 cmul(double2 a, double2 b) {
+  return make_double2(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x);
+}
+
+// Scatter coalesced Y_LL entries (no duplicates) into a zeroed dense matrix.
+__global__ void k_scatter(double2* A, int n, const int32_t* r, const int32_t* c,
+                          const double2* v, int64_t m) {
+  for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < m;
+       t += (int64_t)gridDim.x * blockDim.x)
+    A[(int64_t)r[t] * n + c[t]] = v[t];
+}
+
+// ys[j] = sum_p Y_Ls[j][p] v_s[p] from the slack-column entries (row-sorted,
+// so each row's terms are summed in a fixed order by one thread).
+__global__ void k_slack_injection(double2* ys, int n, const int32_t* ptr, const int32_t* sp,
+                                  const double2* sv, double2 v0, double2 v1, double2 v2) {
+  int j = blockIdx.x * blockDim.x + threadIdx.x;
+  if (j >= n) return;
+  double2 acc = make_double2(0.0, 0.0);
+  for (int t = ptr[j]; t < ptr[j + 1]; ++t) {
+    double2 vs = sp[t] == 0 ? v0 : (sp[t] == 1 ? v1 : v2);
+    double2 p = cmul(sv[t], vs);
+    acc.x += p.x;
+    acc.y += p.y;
+  }
+  ys[j] = acc;
+}
+
+// Gauss-Jordan step k, part 1 (one block): choose the pivot row, swap it into
+// row k, save column k, scale the pivot row.  info records the first bad pivot.
+__global__ void k_gj_pivot(double2* A, int n, int k, int32_t* perm, double2* colk, int32_t* info) {
+  __shared__ double sbest[1024];
+  __shared__ int sidx[1024];
+  const int tid = threadIdx.x;
+  double best = -1.0;
+  int bi = k;
+  for (int i = k + tid; i < n; i += blockDim.x) {
+    double2 a = A[(int64_t)i * n + k];
+    double m = a.x * a.x + a.y * a.y;
+    if (m > best) { best = m; bi = i; }
+  }
+  sbest[tid] = best;
+  sidx[tid] = bi;
+  __syncthreads();
+  for (int s = blockDim.x / 2; s > 0; s >>= 1) {
+    if (tid < s) {
+      double o = sbest[tid + s];
+      int oi = sidx[tid + s];
+      if (o > sbest[tid] || (o == sbest[tid] && oi < sidx[tid])) { sbest[tid] = o; sidx[tid] = oi; }
+    }
+    __syncthreads();
+  }
+  const int p = sidx[0];
+  const double pm = sbest[0];
+  if (tid == 0) {
+    perm[k] = p;
+    if (!(pm > 0.0) || !isfinite(pm)) {
+      if (*info == 0) *info = k + 1;
+    }
+  }
+  if (p != k) {
+    for (int j = tid; j < n; j += blockDim.x) {
+      double2 a = A[(int64_t)k * n + j];
+      A[(int64_t)k * n + j] = A[(int64_t)p * n + j];
+      A[(int64_t)p * n + j] = a;
+    }
+  }
+  __syncthreads();
+  for (int i = tid; i < n; i += blockDim.x) colk[i] = A[(int64_t)i * n + k];
+  __syncthreads();
+  double2 piv = colk[k];
+  double d = piv.x * piv.x + piv.y * piv.y;
+  double2 inv = (d > 0.0) ? make_double2(piv.x / d, -piv.y / d) : make_double2(0.0, 0.0);
+  for (int j = tid; j < n; j += blockDim.x) {
+    if (j == k) A[(int64_t)k * n + j] = inv;
+    else A[(int64_t)k * n + j] = cmul(A[(int64_t)k * n + j], inv);
+  }
+}
+
+// Gauss-Jordan step k, part 2: eliminate column k from every other row.
+// A[i][j] <- (j == k ? 0 : A[i][j]) - colk[i] * A[k][j]
+__global__ void k_gj_update(double2* A, int n, int k, const double2* colk) {
+  const int j = blockIdx.x * blockDim.x + threadIdx.x;
+  if (j >= n) return;
+  const double2 akj = A[(int64_t)k * n + j];
+  for (int i = blockIdx.y; i < n; i += gridDim.y) {
+    if (i == k) continue;
+    const double2 f = colk[i];
+    if (f.x == 0.0 && f.y == 0.0) continue;
+    double2 a = (j == k) ? make_double2(0.0, 0.0) : A[(int64_t)i * n + j];
+    a.x -= f.x * akj.x - f.y * akj.y;
+    a.y -= f.x * akj.y + f.y * akj.x;
+    A[(int64_t)i * n + j] = a;
+  }
+}
+
+// Undo the row interchanges of the elimination as column interchanges of the
+// inverse, last step first.  One thread per row.
+__global__ void k_gj_unpermute(double2* A, int n, const int32_t* perm) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  double2* row = A + (int64_t)i * n;
+  for (int k = n - 1; k >= 0; --k) {
+    const int p = perm[k];
+    if (p != k) {
+      double2 t = row[k];
+      row[k] = row[p];
+      row[p] = t;
+    }
+  }
+}
+
+// w[i] = -sum_j Z[i][j] ys[j], one warp per row, fixed summation order.
+__global__ void k_noload(const double2* Z, const double2* ys, double2* w, int n) {
+  const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int lane = threadIdx.x & 31;
+  if (warp >= n) return;
+  double2 acc = make_double2(0.0, 0.0);
+  for (int j = lane; j < n; j += 32) {
+    double2 p = cmul(Z[(int64_t)warp * n + j], ys[j]);
+    acc.x += p.x;
+    acc.y += p.y;
+  }
+  for (int o = 16; o > 0; o >>= 1) {
+    acc.x += __shfl_xor_sync(0xffffffffu, acc.x, o);
+    acc.y += __shfl_xor_sync(0xffffffffu, acc.y, o);
+  }
+  if (lane == 0) w[warp] = make_double2(-acc.x, -acc.y);
+}
+
+// Real operand layouts of the FP64 contraction: Zr, Zi, Zr + Zi, zero padded
+// to n_pad x n_pad.
+__global__ void k_pack_f64(const double2* Z, int n, int n_pad, double* Zr, double* Zi, double* Zs) {
+  const int64_t tot = (int64_t)n_pad * n_pad;
+  for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < tot;
+       t += (int64_t)gridDim.x * blockDim.x) {
+    const int i = (int)(t / n_pad), j = (int)(t % n_pad);
+    double2 z = (i < n && j < n) ? Z[(int64_t)i * n + j] : make_double2(0.0, 0.0);
+    Zr[t] = z.x;
+    Zi[t] = z.y;
+    Zs[t] = z.x + z.y;
+  }
+}
+
+__global__ void k_check_finite(const double2* w, int n, int32_t* info) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n && !(isfinite(w[i].x) && isfinite(w[i].y))) atomicCAS(info, 0, -1);
+}
+
+struct Entry {
+  int32_t r, c;
+  double re, im;
+};
+
+template <class T>
+zbus_status upload(T** dst, const std::vector<T>& src, cudaStream_t st) {
+  size_t bytes = std::max<size_t>(1, src.size()) * sizeof(T);
+  ZB_CUDA(cudaMalloc((void**)dst, bytes));
+  if (!src.empty()) ZB_CUDA(cudaMemcpyAsync(*dst, src.data(), src.size() * sizeof(T),
+                                            cudaMemcpyHostToDevice, st));
+  return ZBUS_OK;
+}
+
+}  // namespace
+
+zbus_status build_network(zbus_network net, int32_t n_total, int64_t nnz, const int32_t* row,
+                          const int32_t* col, const double* val, const int32_t* slack,
+                          const double* vs, cudaStream_t st) {
+  const int n = n_total - 3;
+  net->n_total = n_total;
+  net->n = n;
+  net->n_pad = round_up(n, F64_PAD);
+  net->bus_aligned = (n % 3) == 0;
+  for (int p = 0; p < 3; ++p) net->v_slack[p] = make_double2(vs[2 * p], vs[2 * p + 1]);
+
+  // global index -> unknown index (>= 0) or slack phase (-1 - p)
+  std::vector<int32_t> pos(n_total, 0);
+  for (int p = 0; p < 3; ++p) pos[slack[p]] = -1 - p;
+  int j = 0;
+  for (int g = 0; g < n_total; ++g)
+    if (pos[g] >= 0) pos[g] = j++;
+
+  // coalesce the COO entries of the non-slack rows (sorted, duplicates summed
+  // in input order)
+  std::vector<Entry> e;
+  e.reserve((size_t)nnz);
+  for (int64_t t = 0; t < nnz; ++t) {
+    if (pos[row[t]] < 0) continue;
+    e.push_back({pos[row[t]], pos[col[t]], val[2 * t], val[2 * t + 1]});
+  }
+  std::stable_sort(e.begin(), e.end(), [](const Entry& a, const Entry& b) {
+    return a.r != b.r ? a.r < b.r : a.c < b.c;  // slack columns (< 0) first, then ascending
+  });
+  std::vector<Entry> u;
+  for (const Entry& x : e) {
+    if (!u.empty() && u.back().r == x.r && u.back().c == x.c) {
+      u.back().re += x.re;
+      u.back().im += x.im;
+    } else {
+      u.push_back(x);
+    }
+  }
+  // split: Y_LL (c >= 0) as CSR with ascending columns, Y_Ls (c < 0) per row
+  std::vector<int32_t> lp(n + 1, 0), sp(n + 1, 0);
+  for (const Entry& x : u) {
+    if (x.c >= 0) lp[x.r + 1]++;
+    else sp[x.r + 1]++;
+  }
+  for (int i = 0; i < n; ++i) {
+    lp[i + 1] += lp[i];
+    sp[i + 1] += sp[i];
+  }
+  std::vector<int32_t> lr(lp[n]), lc(lp[n]), sc(sp[n]);
+  std::vector<double2> lv(lp[n]), sv(sp[n]);
+  std::vector<int32_t> fl(lp.begin(), lp.end() - 1), fs(sp.begin(), sp.end() - 1);
+  for (const Entry& x : u) {
+    if (x.c >= 0) {
+      int t = fl[x.r]++;
+      lr[t] = x.r;
+      lc[t] = x.c;
+      lv[t] = make_double2(x.re, x.im);
+    } else {
+      int t = fs[x.r]++;
+      sc[t] = -1 - x.c;
+      sv[t] = make_double2(x.re, x.im);
+    }
+  }
+  net->nnz_ll = lp[n];
+  int mr = 0;
+  for (int i = 0; i < n; ++i) mr = std::max(mr, lp[i + 1] - lp[i]);
+  net->max_row_nnz = mr;
+
+  const size_t zb = (size_t)n * n * sizeof(double2);
+  const size_t pb = (size_t)net->n_pad * net->n_pad * sizeof(double);
+  ZB_CUDA(cudaMalloc((void**)&net->Z, zb));
+  ZB_CUDA(cudaMalloc((void**)&net->w, n * sizeof(double2)));
+  ZB_CUDA(cudaMalloc((void**)&net->ys, n * sizeof(double2)));
+  ZB_CUDA(cudaMalloc((void**)&net->Zr, pb));
+  ZB_CUDA(cudaMalloc((void**)&net->Zi, pb));
+  ZB_CUDA(cudaMalloc((void**)&net->Zs, pb));
+  ZB_CHECK(upload(&net->csr_ptr, lp, st));
+  ZB_CHECK(upload(&net->csr_col, lc, st));
+  ZB_CHECK(upload(&net->csr_val, lv, st));
+
+  int32_t *d_lr = nullptr, *d_sp = nullptr, *d_sc = nullptr, *d_perm = nullptr, *d_info = nullptr;
+  double2 *d_sv = nullptr, *d_colk = nullptr;
+  zbus_status s = ZBUS_OK;
+  do {
+    if ((s = upload(&d_lr, lr, st)) != ZBUS_OK) break;
+    if ((s = upload(&d_sp, sp, st)) != ZBUS_OK) break;
+    if ((s = upload(&d_sc, sc, st)) != ZBUS_OK) break;
+    if ((s = upload(&d_sv, sv, st)) != ZBUS_OK) break;
+    cudaError_t ce;
+    if ((ce = cudaMalloc((void**)&d_perm, n * sizeof(int32_t))) != cudaSuccess ||
+        (ce = cudaMalloc((void**)&d_info, sizeof(int32_t))) != cudaSuccess ||
+        (ce = cudaMalloc((void**)&d_colk, n * sizeof(double2))) != cudaSuccess) {
+      s = cuda_fail(ce, "cudaMalloc(setup scratch)", __FILE__, __LINE__);
+      break;
+    }
+    cudaMemsetAsync(d_info, 0, sizeof(int32_t), st);
+    cudaMemsetAsync(net->Z, 0, zb, st);
+    if (lp[n] > 0)
+      k_scatter<<<std::min<int64_t>(4096, (lp[n] + 255) / 256), 256, 0, st>>>(
+          net->Z, n, d_lr, net->csr_col, net->csr_val, lp[n]);
+    k_slack_injection<<<(n + 255) / 256, 256, 0, st>>>(net->ys, n, d_sp, d_sc, d_sv,
+                                                        net->v_slack[0], net->v_slack[1],
+                                                        net->v_slack[2]);
+    const int gy = std::min(n, 256);
+    for (int k = 0; k < n; ++k) {
+      k_gj_pivot<<<1, 1024, 0, st>>>(net->Z, n, k, d_perm, d_colk, d_info);
+      k_gj_update<<<dim3((n + 127) / 128, gy), 128, 0, st>>>(net->Z, n, k, d_colk);
+    }
+    k_gj_unpermute<<<(n + 127) / 128, 128, 0, st>>>(net->Z, n, d_perm);
+    k_noload<<<(n * 32 + 255) / 256, 256, 0, st>>>(net->Z, net->ys, net->w, n);
+    k_check_finite<<<(n + 255) / 256, 256, 0, st>>>(net->w, n, d_info);
+    k_pack_f64<<<2048, 256, 0, st>>>(net->Z, n, net->n_pad, net->Zr, net->Zi, net->Zs);
+    if ((ce = cudaGetLastError()) != cudaSuccess) {
+      s = cuda_fail(ce, "setup kernel launch", __FILE__, __LINE__);
+      break;
+    }
+    int32_t info = 0;
+    if ((ce = cudaMemcpyAsync(&info, d_info, sizeof(int32_t), cudaMemcpyDeviceToHost, st)) !=
+            cudaSuccess ||
+        (ce = cudaStreamSynchronize(st)) != cudaSuccess) {
+      s = cuda_fail(ce, "setup synchronize", __FILE__, __LINE__);
+      break;
+    }
+    if (info > 0) {
+      s = fail(ZBUS_ERR_SINGULAR, "Y_LL is singular: zero pivot at elimination step " +
+                                      std::to_string(info - 1));
+    } else if (info < 0) {
+      s = fail(ZBUS_ERR_SINGULAR, "no-load voltage is not finite (Y_LL numerically singular)");
+    }
+  } while (0);
+  cudaFree(d_lr);
+  cudaFree(d_sp);
+  cudaFree(d_sc);
+  cudaFree(d_sv);
+  cudaFree(d_perm);
+  cudaFree(d_info);
+  cudaFree(d_colk);
+  return s;
+}
+
+}  // namespace zbus

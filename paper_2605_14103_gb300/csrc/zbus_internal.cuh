@@ -1,0 +1,146 @@
+// Internal declarations of libzbus (not part of the C ABI).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <string>
+#include <vector>
+
+#include "zbus.h"
+
+namespace zbus {
+
+// ---------------------------------------------------------------------------
+// Error plumbing: a thread-local message plus status codes.
+// ---------------------------------------------------------------------------
+void set_error(const std::string& msg);
+zbus_status fail(zbus_status s, const std::string& msg);
+zbus_status cuda_fail(cudaError_t e, const char* what, const char* file, int line);
+
+#define ZB_CUDA(call)                                                        \
+  do {                                                                       \
+    cudaError_t _e = (call);                                                 \
+    if (_e != cudaSuccess) return ::zbus::cuda_fail(_e, #call, __FILE__, __LINE__); \
+  } while (0)
+
+#define ZB_CHECK(call)                        \
+  do {                                        \
+    zbus_status _s = (call);                  \
+    if (_s != ZBUS_OK) return _s;             \
+  } while (0)
+
+// ---------------------------------------------------------------------------
+// Tiling constants of the FP64 path.
+// ---------------------------------------------------------------------------
+constexpr int F64_BM = 32;   // scenarios per tile
+constexpr int F64_BN = 48;   // outputs (16 buses) per tile
+constexpr int F64_BK = 16;   // k step
+constexpr int F64_PAD = 48;  // n is padded to a multiple of this
+
+inline int round_up(int x, int m) { return (x + m - 1) / m * m; }
+
+// ---------------------------------------------------------------------------
+// Per-solve device context.  Kernels read pointers and sizes from it, so a
+// captured graph does not depend on the caller's buffers.
+// ---------------------------------------------------------------------------
+struct SolveCtx {
+  const double2* S_wye;   // [B][n] or nullptr
+  const double2* S_del;   // [B][n] or nullptr
+  const double2* V_init;  // [B][n] or nullptr
+  double2* V;             // [B][n]
+  int32_t* iters;         // [B]
+  uint8_t* conv;          // [B]
+  int32_t* list;          // [B] active slot -> scenario
+  double* part;           // [B][ntn][2] per-tile partials (max step, sum-magnitude change)
+  double* Iop;            // FP64: 3 x [B][n_pad] (Ir, Ii, Ir+Ii)
+  double tol;
+  double mismatch_tol;
+  int32_t B;
+  int32_t count;          // active scenarios
+  int32_t iter;           // maps performed so far
+  int32_t max_iter;
+  int32_t rule;
+  int32_t ntn;            // N-tiles of the contraction
+  int32_t phase;          // mixed modes: 0 = sweeping, 1 = correction
+  int32_t corr_left;
+  int32_t err;            // device error word (0 = fine)
+  int32_t* hist;          // profile mode: active count of sweep k (else nullptr)
+  int32_t hist_n;
+};
+
+struct Workspace {
+  int64_t cap_B = 0;
+  int32_t precision = -1;
+  size_t bytes = 0;
+  void* base = nullptr;
+  SolveCtx* ctx = nullptr;   // device
+  int32_t* list = nullptr;
+  double* part = nullptr;
+  double* Iop = nullptr;
+};
+
+// Host-driven profiling run: 4 events per sweep around the three kernels.
+struct Profile {
+  std::vector<cudaEvent_t> ev;
+  int32_t* d_hist = nullptr;
+  int32_t cap = 0;
+  int32_t sweeps = 0;
+};
+
+struct GraphEntry {
+  int64_t B = 0;
+  int32_t precision = -1;
+  int32_t grid_gemm = 0;
+  cudaGraph_t graph = nullptr;
+  cudaGraphExec_t exec = nullptr;
+};
+
+}  // namespace zbus
+
+struct zbus_network_s {
+  int device = 0;
+  int n = 0;         // unknowns
+  int n_total = 0;
+  int n_pad = 0;     // FP64 operand padding
+  bool bus_aligned = false;  // n % 3 == 0: delta loads allowed
+  double2 v_slack[3];
+  // device data
+  double2* Z = nullptr;      // [n][n]
+  double2* w = nullptr;      // [n]
+  double2* ys = nullptr;     // [n]  Y_Ls v_s
+  double* Zr = nullptr;      // [n_pad][n_pad] row-major, zero padded
+  double* Zi = nullptr;
+  double* Zs = nullptr;      // Zr + Zi
+  int32_t* csr_ptr = nullptr;   // Y_LL rows (n + 1)
+  int32_t* csr_col = nullptr;
+  double2* csr_val = nullptr;
+  int64_t nnz_ll = 0;
+  int max_row_nnz = 0;
+  zbus::Workspace ws;
+  std::vector<zbus::GraphEntry> graphs;
+  cudaStream_t cap_stream = nullptr;  // private stream used only to capture graphs
+  zbus::Profile prof;
+};
+
+namespace zbus {
+
+// setup.cu
+zbus_status build_network(zbus_network net, int32_t n_total, int64_t nnz, const int32_t* row,
+                          const int32_t* col, const double* val, const int32_t* slack,
+                          const double* vs, cudaStream_t st);
+
+// kernels_f64.cu
+void launch_init(SolveCtx* ctx, const SolveCtx& h, const double2* w, int n, int B,
+                 cudaStream_t st);
+void launch_currents_f64(SolveCtx* ctx, int n, int n_pad, int B, cudaStream_t st);
+void launch_gemm_f64(SolveCtx* ctx, const double* Zr, const double* Zi, const double* Zs,
+                     const double2* w, int n, int n_pad, int grid, cudaStream_t st);
+int gemm_f64_grid(int B, int n_pad);
+void launch_converge(SolveCtx* ctx, cudaGraphConditionalHandle h, bool use_handle,
+                     cudaStream_t st);
+void launch_mismatch(const double2* V, const double2* S_wye, const double2* S_del,
+                     const int32_t* ptr, const int32_t* col, const double2* val,
+                     const double2* ys, int n, int B, double* out, cudaStream_t st);
+
+}  // namespace zbus

@@ -1,0 +1,256 @@
+"""Thin ctypes binding of libzbus (include/zbus.h).
+
+Argument marshalling only: every step of the solve runs in the library's CUDA
+kernels.  Device buffers are torch tensors (complex128 for complex arrays),
+streams are torch.cuda streams.  If libzbus.so is missing or cannot be loaded
+every call raises; there is no fallback.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libzbus.so")
+
+ZBUS_OK = 0
+STATUS = {0: "ZBUS_OK", 1: "ZBUS_ERR_ARG", 2: "ZBUS_ERR_SINGULAR", 3: "ZBUS_ERR_OOM",
+          4: "ZBUS_ERR_CUDA", 5: "ZBUS_ERR_TIMEOUT", 6: "ZBUS_ERR_DEVICE",
+          7: "ZBUS_ERR_UNSUPPORTED"}
+PRECISION = {"fp64": 0, "bf16x2": 1, "fp16_scaled": 2}
+RULE = {"maxabs": 0, "summag": 1}
+
+
+class ZbusError(RuntimeError):
+    def __init__(self, status: int, message: str):
+        super().__init__(f"{STATUS.get(status, status)}: {message}")
+        self.status = status
+
+
+class zbus_solve_opts(C.Structure):
+    _fields_ = [("precision", C.c_int32), ("conv_rule", C.c_int32),
+                ("mismatch_tol", C.c_double), ("max_correction", C.c_int32),
+                ("profile", C.c_int32), ("reserved", C.c_double * 4)]
+
+
+_lib = None
+
+_P = C.c_void_p
+_SIGS = {
+    "zbus_solve_opts_default": (None, [C.POINTER(zbus_solve_opts)]),
+    "zbus_network_create": (C.c_int, [C.c_int32, C.c_int64, _P, _P, _P, _P, _P, _P,
+                                      C.POINTER(_P)]),
+    "zbus_network_destroy": (None, [_P]),
+    "zbus_network_size": (C.c_int32, [_P]),
+    "zbus_network_get_z": (C.c_int, [_P, _P, _P, _P]),
+    "zbus_network_reserve": (C.c_int, [_P, C.c_int64, C.c_int32]),
+    "zbus_solve": (C.c_int, [_P, C.c_int64, _P, _P, _P, C.c_double, C.c_int32,
+                             C.POINTER(zbus_solve_opts), _P, _P, _P, _P]),
+    "zbus_power_mismatch": (C.c_int, [_P, C.c_int64, _P, _P, _P, _P, _P]),
+    "zbus_last_profile": (C.c_int, [_P, C.c_int32, _P, _P, _P]),
+    "zbus_status_string": (C.c_char_p, [C.c_int]),
+    "zbus_last_error": (C.c_char_p, []),
+}
+
+
+def lib():
+    """The loaded libzbus (raises if it has not been built)."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise RuntimeError(f"libzbus.so not found at {LIB_PATH}; build it with "
+                               "paper_2605_14103_gb300.build.build()")
+        L = C.CDLL(LIB_PATH)
+        for name, (res, args) in _SIGS.items():
+            f = getattr(L, name)
+            f.restype = res
+            f.argtypes = args
+        _lib = L
+    return _lib
+
+
+def _check(status: int):
+    if status != ZBUS_OK:
+        msg = lib().zbus_last_error().decode(errors="replace")
+        raise ZbusError(status, msg)
+
+
+def _stream(stream) -> int | None:
+    import torch
+    s = stream if stream is not None else torch.cuda.current_stream()
+    return s.cuda_stream or None
+
+
+def _dptr(t, name, dtype=None, shape=None):
+    """Device pointer of a contiguous CUDA tensor (None passes through)."""
+    if t is None:
+        return None
+    if not t.is_cuda:
+        raise ValueError(f"{name} must be a CUDA tensor")
+    if not t.is_contiguous():
+        raise ValueError(f"{name} must be contiguous")
+    if dtype is not None and t.dtype != dtype:
+        raise ValueError(f"{name} must have dtype {dtype}, got {t.dtype}")
+    if shape is not None and tuple(t.shape) != tuple(shape):
+        raise ValueError(f"{name} must have shape {tuple(shape)}, got {tuple(t.shape)}")
+    return t.data_ptr()
+
+
+# ---------------------------------------------------------------------------
+# Functions with the C ABI's names.
+# ---------------------------------------------------------------------------
+
+def zbus_solve_opts_default() -> zbus_solve_opts:
+    o = zbus_solve_opts()
+    lib().zbus_solve_opts_default(C.byref(o))
+    return o
+
+
+def zbus_network_create(n_total, row, col, val, slack_idx, v_slack, stream=None) -> int:
+    """Host COO (numpy) -> network handle (an integer)."""
+    row = np.ascontiguousarray(row, dtype=np.int32)
+    col = np.ascontiguousarray(col, dtype=np.int32)
+    val = np.ascontiguousarray(val, dtype=np.complex128)
+    sl = np.ascontiguousarray(slack_idx, dtype=np.int32)
+    vs = np.ascontiguousarray(v_slack, dtype=np.complex128)
+    if not (row.shape == col.shape == val.shape) or sl.shape != (3,) or vs.shape != (3,):
+        raise ValueError("row/col/val must have equal length; slack_idx and v_slack 3 entries")
+    h = _P()
+    _check(lib().zbus_network_create(int(n_total), int(row.size), row.ctypes.data,
+                                     col.ctypes.data, val.ctypes.data, sl.ctypes.data,
+                                     vs.ctypes.data, _stream(stream), C.byref(h)))
+    return h.value
+
+
+def zbus_network_destroy(h):
+    if h:
+        lib().zbus_network_destroy(h)
+
+
+def zbus_network_size(h) -> int:
+    return int(lib().zbus_network_size(h))
+
+
+def zbus_network_get_z(h, Z_out=None, w_out=None, stream=None):
+    import torch
+    n = zbus_network_size(h)
+    _check(lib().zbus_network_get_z(h, _dptr(Z_out, "Z_out", torch.complex128, (n, n)),
+                                    _dptr(w_out, "w_out", torch.complex128, (n,)),
+                                    _stream(stream)))
+
+
+def zbus_network_reserve(h, B, precision="fp64"):
+    _check(lib().zbus_network_reserve(h, int(B), PRECISION[precision]))
+
+
+def zbus_solve(h, S_wye, S_delta, V_init, tol, max_iter, opts, V_out, iters, converged,
+               stream=None):
+    import torch
+    n = zbus_network_size(h)
+    B = V_out.shape[0]
+    c128 = torch.complex128
+    _check(lib().zbus_solve(
+        h, int(B), _dptr(S_wye, "S_wye", c128, (B, n)), _dptr(S_delta, "S_delta", c128, (B, n)),
+        _dptr(V_init, "V_init", c128, (B, n)), float(tol), int(max_iter),
+        C.byref(opts) if opts is not None else None,
+        _dptr(V_out, "V_out", c128, (B, n)), _dptr(iters, "iters", torch.int32, (B,)),
+        _dptr(converged, "converged", torch.uint8, (B,)), _stream(stream)))
+
+
+def zbus_power_mismatch(h, V, S_wye, S_delta, out, stream=None):
+    import torch
+    n = zbus_network_size(h)
+    B = V.shape[0]
+    c128 = torch.complex128
+    _check(lib().zbus_power_mismatch(
+        h, int(B), _dptr(V, "V", c128, (B, n)), _dptr(S_wye, "S_wye", c128, (B, n)),
+        _dptr(S_delta, "S_delta", c128, (B, n)), _dptr(out, "out", torch.float64, (B,)),
+        _stream(stream)))
+
+
+def zbus_last_profile(h, max_n):
+    """(ms [sweeps, 3] float32, active [sweeps] int32) of the last profiled solve."""
+    ms = np.zeros((max_n, 3), dtype=np.float32)
+    act = np.zeros(max_n, dtype=np.int32)
+    sw = C.c_int32(0)
+    _check(lib().zbus_last_profile(h, int(max_n), ms.ctypes.data, act.ctypes.data,
+                                   C.byref(sw)))
+    m = min(max_n, sw.value)
+    return ms[:m], act[:m]
+
+
+def zbus_status_string(s: int) -> str:
+    return lib().zbus_status_string(int(s)).decode()
+
+
+def zbus_last_error() -> str:
+    return lib().zbus_last_error().decode(errors="replace")
+
+
+# ---------------------------------------------------------------------------
+# Convenience wrapper.
+# ---------------------------------------------------------------------------
+
+class Network:
+    """One feeder's Z-bus data on the current CUDA device."""
+
+    def __init__(self, n_total, row, col, val, slack_idx, v_slack, stream=None):
+        self.handle = zbus_network_create(n_total, row, col, val, slack_idx, v_slack, stream)
+        self.n = zbus_network_size(self.handle)
+
+    @classmethod
+    def from_feeder(cls, f, stream=None):
+        return cls(f.n_total, f.Y_row, f.Y_col, f.Y_val, f.slack_idx, f.v_slack, stream)
+
+    def close(self):
+        if self.handle:
+            zbus_network_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def get_z(self, stream=None):
+        import torch
+        Z = torch.empty((self.n, self.n), dtype=torch.complex128, device="cuda")
+        w = torch.empty((self.n,), dtype=torch.complex128, device="cuda")
+        zbus_network_get_z(self.handle, Z, w, stream)
+        return Z, w
+
+    def reserve(self, B, precision="fp64"):
+        zbus_network_reserve(self.handle, B, precision)
+
+    def solve(self, S_wye, S_delta=None, V_init=None, tol=1e-8, max_iter=50,
+              precision="fp64", rule="maxabs", mismatch_tol=1e-6, max_correction=8,
+              profile=False, out=None, stream=None):
+        """Returns (V [B,n] complex128, iters int32[B], converged uint8[B]) on the device."""
+        import torch
+        B = (S_wye if S_wye is not None else S_delta).shape[0]
+        dev = (S_wye if S_wye is not None else S_delta).device
+        if out is None:
+            out = (torch.empty((B, self.n), dtype=torch.complex128, device=dev),
+                   torch.empty((B,), dtype=torch.int32, device=dev),
+                   torch.empty((B,), dtype=torch.uint8, device=dev))
+        o = zbus_solve_opts_default()
+        o.precision = PRECISION[precision]
+        o.conv_rule = RULE[rule]
+        o.mismatch_tol = mismatch_tol
+        o.max_correction = max_correction
+        o.profile = 1 if profile else 0
+        V, it, cv = out
+        zbus_solve(self.handle, S_wye, S_delta, V_init, tol, max_iter, o, V, it, cv, stream)
+        return V, it, cv
+
+    def last_profile(self, max_n=1024):
+        return zbus_last_profile(self.handle, max_n)
+
+    def power_mismatch(self, V, S_wye=None, S_delta=None, stream=None):
+        import torch
+        out = torch.empty((V.shape[0],), dtype=torch.float64, device=V.device)
+        zbus_power_mismatch(self.handle, V, S_wye, S_delta, out, stream)
+        return out

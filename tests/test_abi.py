@@ -1,0 +1,91 @@
+"""The C-ABI library loads on a CPU-only host and exports every declared symbol;
+argument errors are reported before any CUDA work."""
+import ctypes as C
+import os
+import re
+
+import numpy as np
+import pytest
+
+from paper_2605_14103_gb300 import build as B
+from paper_2605_14103_gb300 import zbus
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def lib():
+    B.build()
+    return zbus.lib()
+
+
+def declared_functions():
+    names = set()
+    inc = os.path.join(ROOT, "include")
+    for f in os.listdir(inc):
+        if f.endswith(".h"):
+            txt = open(os.path.join(inc, f)).read()
+            txt = re.sub(r"/\*.*?\*/", "", txt, flags=re.S)
+            names |= set(re.findall(r"\b(zbus_\w+)\s*\(", txt))
+    return sorted(names)
+
+
+def test_header_declares_the_boundary():
+    names = declared_functions()
+    for must in ("zbus_network_create", "zbus_solve", "zbus_network_destroy",
+                 "zbus_status_string"):
+        assert must in names
+
+
+def test_every_declared_symbol_is_exported(lib):
+    missing = [n for n in declared_functions() if not hasattr(lib, n)]
+    assert not missing, missing
+
+
+def test_status_strings(lib):
+    for code, name in zbus.STATUS.items():
+        assert zbus.zbus_status_string(code) == name
+
+
+def test_opts_default(lib):
+    o = zbus.zbus_solve_opts_default()
+    assert o.precision == 0 and o.conv_rule == 0
+    assert o.mismatch_tol == 1e-6 and o.max_correction == 8
+
+
+def _create(lib, n_total, row, col, val, slack, vs):
+    h = C.c_void_p()
+    row = np.ascontiguousarray(row, dtype=np.int32)
+    col = np.ascontiguousarray(col, dtype=np.int32)
+    val = np.ascontiguousarray(val, dtype=np.complex128)
+    slack = np.ascontiguousarray(slack, dtype=np.int32)
+    vs = np.ascontiguousarray(vs, dtype=np.complex128)
+    st = lib.zbus_network_create(n_total, row.size, row.ctypes.data, col.ctypes.data,
+                                 val.ctypes.data, slack.ctypes.data, vs.ctypes.data, None,
+                                 C.byref(h))
+    return st, h.value
+
+
+def test_create_rejects_bad_arguments(lib):
+    vs = np.ones(3, dtype=np.complex128)
+    ok_row, ok_col, ok_val = [0, 1, 2, 3], [0, 1, 2, 3], [1, 1, 1, 1]
+    cases = [
+        (3, ok_row, ok_col, ok_val, [0, 1, 2]),            # too small
+        (4, [0, 9], [0, 0], [1, 1], [0, 1, 2]),            # row out of range
+        (4, ok_row, ok_col, ok_val, [0, 1, 1]),            # repeated slack
+        (4, ok_row, ok_col, ok_val, [0, 1, 7]),            # slack out of range
+        (4, [0], [0], [np.nan], [0, 1, 2]),                # non-finite value
+    ]
+    for n_total, r, c, v, s in cases:
+        st, h = _create(lib, n_total, r, c, v, s, vs)
+        assert st == 1, (n_total, r, s, zbus.zbus_last_error())
+        assert not h
+        assert zbus.zbus_last_error()
+
+
+def test_solve_rejects_null_network(lib):
+    st = lib.zbus_solve(None, 4, None, None, None, 1e-8, 50, None, None, None, None, None)
+    assert st == 1
+    assert "NULL" in zbus.zbus_last_error()
+    assert lib.zbus_network_size(None) == -1
+    lib.zbus_network_destroy(None)   # ignored
