@@ -186,6 +186,40 @@ zbus_status zbus_power_mismatch(zbus_network net, int64_t B, const double* V,
 zbus_status zbus_last_profile(zbus_network net, int32_t max_n, float* ms, int32_t* active,
                               int32_t* sweeps);
 
+/*
+ * zbus_solve_noalloc -- the plain FP64 solve (same results as zbus_solve with
+ * precision ZBUS_FP64) for callers that cannot allocate device memory while
+ * they solve: processes whose device memory is owned by another allocator,
+ * real-time loops that forbid allocation after start-up, plug-in hosts that do
+ * not let plug-ins allocate.  The paper has no counterpart; this is a
+ * property of this library's interface.
+ *
+ * It calls no cudaMalloc, cudaFree or allocating library routine: its scratch
+ * (solve context, active list, per-tile partials, contraction operands) lives
+ * in one static 16 MiB device array that every GPU loading the library holds
+ * until the process exits.  The network must exist already (create it at
+ * start-up).  The sweeps are launched from the host (max_iter sweeps; once no
+ * scenario is active the remaining launches return at once).
+ *
+ *   arguments as zbus_solve, with conv_rule (zbus_conv_rule) in place of opts.
+ *   Returns ZBUS_ERR_ARG, launching nothing, when the batch needs more than
+ *   the 16 MiB: about 16 MiB / (24 n_pad + 16 ceil(n/48) + 4) bytes per
+ *   scenario, n_pad = n rounded up to a multiple of 48 (about 1790 scenarios
+ *   for n = 381).
+ *
+ * The first call on a device looks up the array's device address (with that
+ * device current) and caches it; make that first call before any stream
+ * capture.  All calls share the array and it keeps the last call's contents;
+ * every call rewrites what it reads, but calls that overlap on the GPU (other
+ * streams or other host threads) race on it.
+ */
+zbus_status zbus_solve_noalloc(zbus_network net, int64_t B,
+                               const double* S_wye, const double* S_delta,
+                               const double* V_init, double tol, int32_t max_iter,
+                               int32_t conv_rule,
+                               double* V_out, int32_t* iters, uint8_t* converged,
+                               void* cuda_stream);
+
 /* Human-readable name of a status code (static storage). */
 const char* zbus_status_string(zbus_status s);
 

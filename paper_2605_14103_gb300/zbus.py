@@ -50,6 +50,8 @@ _SIGS = {
                              C.POINTER(zbus_solve_opts), _P, _P, _P, _P]),
     "zbus_power_mismatch": (C.c_int, [_P, C.c_int64, _P, _P, _P, _P, _P]),
     "zbus_last_profile": (C.c_int, [_P, C.c_int32, _P, _P, _P]),
+    "zbus_solve_noalloc": (C.c_int, [_P, C.c_int64, _P, _P, _P, C.c_double, C.c_int32,
+                                     C.c_int32, _P, _P, _P, _P]),
     "zbus_status_string": (C.c_char_p, [C.c_int]),
     "zbus_last_error": (C.c_char_p, []),
 }
@@ -155,6 +157,20 @@ def zbus_solve(h, S_wye, S_delta, V_init, tol, max_iter, opts, V_out, iters, con
         h, int(B), _dptr(S_wye, "S_wye", c128, (B, n)), _dptr(S_delta, "S_delta", c128, (B, n)),
         _dptr(V_init, "V_init", c128, (B, n)), float(tol), int(max_iter),
         C.byref(opts) if opts is not None else None,
+        _dptr(V_out, "V_out", c128, (B, n)), _dptr(iters, "iters", torch.int32, (B,)),
+        _dptr(converged, "converged", torch.uint8, (B,)), _stream(stream)))
+
+
+def zbus_solve_noalloc(h, S_wye, S_delta, V_init, tol, max_iter, rule, V_out, iters, converged,
+                       stream=None):
+    """The FP64 solve with library-static scratch (no device allocation)."""
+    import torch
+    n = zbus_network_size(h)
+    B = V_out.shape[0]
+    c128 = torch.complex128
+    _check(lib().zbus_solve_noalloc(
+        h, int(B), _dptr(S_wye, "S_wye", c128, (B, n)), _dptr(S_delta, "S_delta", c128, (B, n)),
+        _dptr(V_init, "V_init", c128, (B, n)), float(tol), int(max_iter), RULE[rule],
         _dptr(V_out, "V_out", c128, (B, n)), _dptr(iters, "iters", torch.int32, (B,)),
         _dptr(converged, "converged", torch.uint8, (B,)), _stream(stream)))
 
