@@ -46,6 +46,8 @@ def parse():
     p.add_argument("--precision", default="fp64")
     p.add_argument("--cpu-seconds", type=float, default=10.0)
     p.add_argument("--no-cpu-baseline", action="store_true")
+    p.add_argument("--forms", default="all", choices=["all", "one"])
+    p.add_argument("--batch", type=int, default=0, help="override the scenario count")
     return p.parse_args()
 
 
@@ -230,6 +232,124 @@ def run_reference(args):
 # ---------------------------------------------------------------------------
 # our arm
 # ---------------------------------------------------------------------------
+KERNELS = {"fp64": ("k_currents_f64", "k_gemm3m_f64", "k_converge"),
+           "fp16_scaled": ("k_residual_mixed", "k_contract_tc", "k_converge"),
+           "bf16x2": ("k_residual_mixed", "k_contract_tc", "k_converge")}
+
+
+def kernel_roofline(form, name, n, B_act_sweeps, ms, peaks, K_pad=None, N_pad=None):
+    """Roofline entry of one kernel from its summed launch time over active sweeps.
+
+    B_act_sweeps: sum over the profiled sweeps of the active scenario count.
+    Algorithmic work per scenario-sweep: contraction 8 n^2 flop (complex n x n
+    times n); residual / currents: the bytes they must move (v, loads, output).
+    """
+    t = ms / 1e3
+    if name == "k_gemm3m_f64":
+        ach = 8.0 * n * n * B_act_sweeps / t / 1e12
+        return {"bound": "alu", "achieved": ach, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
+                "frac": ach / FP64_PEAK_TFLOPS,
+                "peak_src": "nominal FP64 1.25 TFLOP/s (DFMA probe: 1.197 measured)"}
+    if name == "k_contract_tc":
+        ach = 8.0 * n * n * B_act_sweeps / t / 1e12
+        zp = 2 if form == "bf16x2" else 1
+        byts = (B_act_sweeps * (K_pad * 2 + 32.0 * n)) / t / 1e9   # R rows + v read/write
+        tf = {"bound": "tensor", "achieved": ach, "peak": peaks["bf16_tflops"], "unit": "TFLOP/s",
+              "frac": ach / peaks["bf16_tflops"], "executed_tflops": ach * zp,
+              "peak_src": "MEASURED_PEAKS bf16 burst (fp16 same rate)"}
+        hb = {"bound": "hbm", "achieved": byts, "peak": peaks["hbm_gbs"], "unit": "GB/s",
+              "frac": byts / peaks["hbm_gbs"], "peak_src": "MEASURED_PEAKS hbm copy"}
+        return tf if tf["frac"] >= hb["frac"] else hb
+    # residual / load-current kernels: bytes of v (16 n), two load arrays
+    # (32 n) and the operand row they write (mixed: 4 n; FP64: 24 n)
+    out_b = 4.0 * n if form != "fp64" else 24.0 * n
+    byts = B_act_sweeps * (48.0 * n + out_b) / t / 1e9
+    return {"bound": "hbm", "achieved": byts, "peak": peaks["hbm_gbs"], "unit": "GB/s",
+            "frac": byts / peaks["hbm_gbs"], "peak_src": "MEASURED_PEAKS hbm copy"}
+
+
+def load_peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        d = json.load(open(p))
+        return {"hbm_gbs": d["hbm_gbs"], "bf16_tflops": d["bf16_tflops"], "src": "measured"}
+    return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "src": "fallback"}
+
+
+def measure(net, form, Sw, Sd, wl, n, steps, warmup, flush, ws, peaks):
+    """Timed solves of one precision form: value, step times, kernel shares, roofline."""
+    import torch
+    B = Sw.shape[0]
+    net.reserve(B, form)
+    V = torch.empty((B, n), dtype=torch.complex128, device="cuda")
+    it = torch.empty((B,), dtype=torch.int32, device="cuda")
+    cv = torch.empty((B,), dtype=torch.uint8, device="cuda")
+
+    def solve(profile=False):
+        net.solve(Sw, Sd, tol=wl.tol, max_iter=wl.max_iter, precision=form,
+                  profile=profile, out=(V, it, cv))
+
+    for _ in range(max(3, warmup)):
+        solve()
+    torch.cuda.synchronize()
+    evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+           for _ in range(steps)]
+    barrier(ws)
+    torch.cuda.synchronize()
+    for k in range(steps):
+        flush.zero_()
+        evs[k][0].record()
+        solve()
+        evs[k][1].record()
+    torch.cuda.synchronize()
+    barrier(ws)
+    step_ms = [a.elapsed_time(b) for a, b in evs]
+    mm = net.power_mismatch(V, Sw, Sd)
+    good = int(((cv == 1) & (mm <= 1e-6)).sum().item())
+    max_iters = int(it.max().item())
+    t_max = allreduce_max(sum(step_ms) / 1e3, ws)
+    value = allreduce_sum(good, ws) * steps / t_max
+
+    # profiled pass: CUDA events around every kernel of every sweep
+    k_ms = [0.0, 0.0, 0.0]
+    act_sum = 0
+    for _ in range(min(steps, 3)):
+        flush.zero_()
+        solve(profile=True)
+        torch.cuda.synchronize()
+        ms, act = net.last_profile(wl.max_iter)
+        for k in range(len(act)):
+            if act[k] > 0:
+                for q in range(3):
+                    k_ms[q] += float(ms[k, q])
+                act_sum += int(act[k])
+    names = KERNELS[form]
+    tot = sum(k_ms)
+    K_pad = (2 * n + 63) // 64 * 64
+    N_pad = (2 * n + 255) // 256 * 256
+    kernels = []
+    for q in range(3):
+        e = {"kernel": names[q], "share": k_ms[q] / tot if tot else 0.0,
+             "ms_per_sweep": k_ms[q] / max(1, act_sum) * B}
+        if q < 2:
+            e["roofline"] = kernel_roofline(form, names[q], n, act_sum, k_ms[q], peaks, K_pad,
+                                            N_pad)
+        kernels.append(e)
+    dom = max(kernels[:2], key=lambda e: e["share"])
+    roof = dict(dom["roofline"])
+    roof["kernel"] = dom["kernel"]
+    roof["traffic"] = TRAFFIC.get((form, dom["kernel"]))
+    return {"value": value, "ms_per_step": 1e3 * t_max / steps,
+            "step_ms_p50": statistics.median(step_ms), "converged_per_step": good,
+            "max_iters": max_iters, "mean_iters": float(it.float().mean().item()),
+            "gpu_launches": steps * (1 + 3 * max_iters + (1 if form != "fp64" else 0)),
+            "kernels": kernels, "roofline": roof}, (V, it, cv)
+
+
+# DRAM bytes per launch from ncu captures of the current kernels (None until captured)
+TRAFFIC = {}
+
+
 def run_ours(args):
     import numpy as np
     import torch
@@ -241,76 +361,32 @@ def run_ours(args):
     from paper_2605_14103_gb300 import zbus
 
     torch.cuda.set_device(local)
+    peaks = load_peaks()
     f, _, _, wl = F.make_workload(args.workload, B=1)
-    Sw_h, Sd_h = F.make_scenarios(f, wl.B, wl.mult[0], wl.mult[1], seed=f.seed + 1 + 7919 * rank)
+    Bw = args.batch if args.batch > 0 else wl.B
+    Sw_h, Sd_h = F.make_scenarios(f, Bw, wl.mult[0], wl.mult[1], seed=f.seed + 1 + 7919 * rank)
     B, n = Sw_h.shape
     Sw = torch.from_numpy(Sw_h).cuda()
     Sd = torch.from_numpy(Sd_h).cuda()
     net = zbus.Network.from_feeder(f)
-    net.reserve(B, args.precision)
-    V = torch.empty((B, n), dtype=torch.complex128, device="cuda")
-    it = torch.empty((B,), dtype=torch.int32, device="cuda")
-    cv = torch.empty((B,), dtype=torch.uint8, device="cuda")
     flush = torch.empty(512 * 1024 * 1024, dtype=torch.uint8, device="cuda")
 
-    def solve(profile=False):
-        net.solve(Sw, Sd, tol=wl.tol, max_iter=wl.max_iter, precision=args.precision,
-                  profile=profile, out=(V, it, cv))
-
-    for _ in range(max(3, args.warmup)):
-        solve()
-    torch.cuda.synchronize()
-
-    # ---- timed region: K solves through the device-resident loop ----
+    forms = [args.precision] + ([m for m in ("fp64", "fp16_scaled", "bf16x2")
+                                 if m != args.precision] if args.forms == "all" else [])
     clocks = Clocks(torch.cuda.current_device()) if rank == 0 else None
     if clocks:
         clocks.start()
-    evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
-           for _ in range(args.steps)]
-    barrier(ws)
-    torch.cuda.synchronize()
-    t0 = time.perf_counter()
-    for k in range(args.steps):
-        flush.zero_()
-        evs[k][0].record()
-        solve()
-        evs[k][1].record()
-    torch.cuda.synchronize()
-    barrier(ws)
-    wall = time.perf_counter() - t0
+    results = {}
+    head_out = None
+    for form in forms:
+        steps = args.steps if form == args.precision else max(3, args.steps // 2)
+        r, out = measure(net, form, Sw, Sd, wl, n, steps, args.warmup, flush, ws, peaks)
+        results[form] = r
+        if form == args.precision:
+            head_out = tuple(x.clone() for x in out)
     clk = clocks.stop() if clocks else None
-    step_ms = [a.elapsed_time(b) for a, b in evs]
-    t_dev = sum(step_ms) / 1e3
-
-    # ---- what was solved ----
-    mm = net.power_mismatch(V, Sw, Sd)
-    ok = (cv == 1) & (mm <= 1e-6)
-    good = int(ok.sum().item())
-    max_iters = int(it.max().item())
-    sweeps_total = int(it.sum().item())
-    t_max = allreduce_max(t_dev, ws)
-    good_all = allreduce_sum(good, ws)
-    value = good_all * args.steps / t_max
-    launches = args.steps * (1 + 3 * max_iters)
-
-    # ---- roofline of the contraction: profiled pass, events around each launch ----
-    prof_steps = min(args.steps, 3)
-    g_ms, g_flops = 0.0, 0.0
-    for _ in range(prof_steps):
-        flush.zero_()
-        solve(profile=True)
-        torch.cuda.synchronize()
-        ms, act = net.last_profile(wl.max_iter)
-        for k in range(len(act)):
-            if act[k] > 0:
-                g_ms += float(ms[k, 1])
-                g_flops += 8.0 * n * n * float(act[k])
-    achieved = g_flops / (g_ms / 1e3) / 1e12 if g_ms > 0 else 0.0
-    roofline = {"bound": "alu", "achieved": achieved, "peak": FP64_PEAK_TFLOPS,
-                "unit": "TFLOP/s", "frac": achieved / FP64_PEAK_TFLOPS,
-                "traffic": None, "kernel": "k_gemm3m_f64",
-                "note": "FP64 pipe; algorithmic 8 n^2 flop per scenario-sweep; peak is nominal "
-                        "FP64 (DFMA probe measured 1.197 TFLOP/s)"}
+    head = results[args.precision]
+    V, it, cv = head_out
 
     # ---- end to end through the public API, host buffers ----
     Sw_p = torch.from_numpy(Sw_h).pin_memory()
@@ -318,53 +394,58 @@ def run_ours(args):
     V_p = torch.empty((B, n), dtype=torch.complex128).pin_memory()
     it_p = torch.empty((B,), dtype=torch.int32).pin_memory()
     cv_p = torch.empty((B,), dtype=torch.uint8).pin_memory()
-    e2e_steps = args.steps
+    Vd = torch.empty_like(V)
+    itd = torch.empty_like(it)
+    cvd = torch.empty_like(cv)
     ev2 = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
-           for _ in range(e2e_steps)]
+           for _ in range(args.steps)]
     e2e_good = 0
-    for k in range(e2e_steps):
+    for k in range(args.steps):
         flush.zero_()
         ev2[k][0].record()
         Sw.copy_(Sw_p, non_blocking=True)
         Sd.copy_(Sd_p, non_blocking=True)
-        solve()
-        V_p.copy_(V, non_blocking=True)
-        it_p.copy_(it, non_blocking=True)
-        cv_p.copy_(cv, non_blocking=True)
+        net.solve(Sw, Sd, tol=wl.tol, max_iter=wl.max_iter, precision=args.precision,
+                  out=(Vd, itd, cvd))
+        V_p.copy_(Vd, non_blocking=True)
+        it_p.copy_(itd, non_blocking=True)
+        cv_p.copy_(cvd, non_blocking=True)
         ev2[k][1].record()
         torch.cuda.synchronize()
         e2e_good += int(cv_p.numpy().sum())
     e2e_t = allreduce_max(sum(a.elapsed_time(b) for a, b in ev2) / 1e3, ws)
     e2e_val = allreduce_sum(e2e_good, ws) / e2e_t
-    h2d = 2 * B * n * 16
-    d2h = B * n * 16 + B * 4 + B
 
-    # ---- CPU baseline (rank 0, one GPU) ----
     cpu, parity = None, None
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
         cpu, parity = cpu_baseline(f, Sw_h, Sd_h, wl, args.cpu_seconds, V.cpu().numpy(),
                                    it.cpu().numpy(), cv.cpu().numpy())
 
     if rank == 0:
-        out = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws,
-               "steps": args.steps, "warmup": args.warmup,
-               "ms_per_step": 1e3 * t_max / args.steps, "higher_is_better": True,
-               "scaling": "weak", "vs_baseline": None,
+        forms_out = {}
+        for k, r in results.items():
+            forms_out[k] = {x: r[x] for x in ("value", "ms_per_step", "mean_iters", "max_iters",
+                                               "converged_per_step")}
+            forms_out[k]["vs_plain_fp64"] = r["value"] / results["fp64"]["value"] \
+                if "fp64" in results else None
+            forms_out[k]["kernels"] = r["kernels"]
+        out = {"metric": METRIC, "value": head["value"], "unit": UNIT, "n_gpus": ws,
+               "steps": args.steps, "warmup": args.warmup, "ms_per_step": head["ms_per_step"],
+               "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
                "dtype": "f64" if args.precision == "fp64" else args.precision + "+f64",
                "data": "synthetic",
                "config": {"workload": args.workload, "feeder_buses": wl.N, "unknowns": n,
                           "scenarios_per_gpu": B, "tol": wl.tol, "max_iter": wl.max_iter,
-                          "precision": args.precision, "l2": "flushed between steps (512 MiB write)",
+                          "precision": args.precision,
+                          "l2": "flushed between steps (512 MiB write)",
                           "parallelism": f"replicas x{ws}"},
-               "converged_per_step": good, "max_iters": max_iters,
-               "mean_iters": sweeps_total / B,
-               "step_ms": {"p50": statistics.median(step_ms), "max": max(step_ms),
-                           "wall_s_incl_flush": wall},
-               "gpu_launches": launches,
-               "roofline": roofline,
-               "e2e": {"value": e2e_val, "unit": UNIT, "h2d_bytes_per_step": h2d,
-                       "d2h_bytes_per_step": d2h},
-               "clocks": clk, "cpu_baseline": cpu, "parity": parity}
+               "converged_per_step": head["converged_per_step"], "max_iters": head["max_iters"],
+               "mean_iters": head["mean_iters"], "gpu_launches": head["gpu_launches"],
+               "roofline": head["roofline"],
+               "e2e": {"value": e2e_val, "unit": UNIT, "h2d_bytes_per_step": 2 * B * n * 16,
+                       "d2h_bytes_per_step": B * n * 16 + B * 4 + B},
+               "clocks": clk, "cpu_baseline": cpu, "parity": parity,
+               "peaks": peaks["src"], "forms": forms_out}
         print(json.dumps(out), flush=True)
     if ws > 1:
         import torch.distributed as dist

@@ -39,21 +39,42 @@ void drop_graphs(zbus_network net) {
   net->graphs.clear();
 }
 
-// Scratch of one solve: context, active list, per-tile partials and the
-// contraction operand of the active scenarios.
-size_t workspace_bytes(const zbus_network net, int64_t B) {
-  const int ntn = net->n_pad / F64_BN;
-  size_t b = align256(sizeof(SolveCtx));
-  b += align256((size_t)B * sizeof(int32_t));
-  b += align256((size_t)B * ntn * 2 * sizeof(double));
-  b += align256((size_t)3 * B * net->n_pad * sizeof(double));
-  return b;
+int max_ntn(const zbus_network net) {
+  // the FP64 contraction tiles outputs by 48, the tensor-core one by >= 128 reals
+  return std::max(net->n_pad / F64_BN, round_up(2 * net->n, 256) / 128);
+}
+
+int k_pad_tc(const zbus_network net) { return round_up(2 * net->n, 64); }
+
+// Scratch of one solve: context, active list, per-tile partials, the FP64
+// contraction operands and the low-precision residual rows.
+struct WsLayout {
+  size_t list, part, iop, R, rinv, mm, total;
+};
+
+WsLayout workspace_layout(const zbus_network net, int64_t B) {
+  WsLayout L;
+  size_t o = align256(sizeof(SolveCtx));
+  L.list = o;
+  o += align256((size_t)B * sizeof(int32_t));
+  L.part = o;
+  o += align256((size_t)B * max_ntn(net) * 2 * sizeof(double));
+  L.iop = o;
+  o += align256((size_t)3 * B * net->n_pad * sizeof(double));
+  L.R = o;
+  o += align256((size_t)B * k_pad_tc(net) * 2);
+  L.rinv = o;
+  o += align256((size_t)B * sizeof(float));
+  L.mm = o;
+  o += align256((size_t)B * sizeof(double));
+  L.total = o;
+  return L;
 }
 
 zbus_status ensure_workspace(zbus_network net, int64_t B) {
   Workspace& ws = net->ws;
   if (ws.base && ws.cap_B >= B) return ZBUS_OK;
-  const size_t bytes = workspace_bytes(net, B);
+  const WsLayout L = workspace_layout(net, B);
   if (ws.base) {
     ZB_CUDA(cudaDeviceSynchronize());
     drop_graphs(net);
@@ -61,19 +82,29 @@ zbus_status ensure_workspace(zbus_network net, int64_t B) {
     ws = Workspace();
   }
   void* base = nullptr;
-  ZB_CUDA(cudaMalloc(&base, bytes));
+  ZB_CUDA(cudaMalloc(&base, L.total));
   char* p = (char*)base;
-  const int ntn = net->n_pad / F64_BN;
   ws.base = base;
-  ws.bytes = bytes;
+  ws.bytes = L.total;
   ws.cap_B = B;
   ws.ctx = (SolveCtx*)p;
-  p += align256(sizeof(SolveCtx));
-  ws.list = (int32_t*)p;
-  p += align256((size_t)B * sizeof(int32_t));
-  ws.part = (double*)p;
-  p += align256((size_t)B * ntn * 2 * sizeof(double));
-  ws.Iop = (double*)p;
+  ws.list = (int32_t*)(p + L.list);
+  ws.part = (double*)(p + L.part);
+  ws.Iop = (double*)(p + L.iop);
+  ws.R = (void*)(p + L.R);
+  ws.rinv = (float*)(p + L.rinv);
+  ws.mm = (double*)(p + L.mm);
+  ws.tmR_ready = false;
+  return ZBUS_OK;
+}
+
+// TMA map of the residual rows for the given operand type.
+zbus_status ensure_tmR(zbus_network net, bool bf16) {
+  Workspace& ws = net->ws;
+  if (ws.tmR_ready && ws.tmR_bf16 == bf16) return ZBUS_OK;
+  ZB_CHECK(make_tmap_2d(&ws.tmR, ws.R, bf16, (uint64_t)k_pad_tc(net), (uint64_t)ws.cap_B, 64, 128));
+  ws.tmR_bf16 = bf16;
+  ws.tmR_ready = true;
   return ZBUS_OK;
 }
 
@@ -82,12 +113,40 @@ bool use_graphs() {
   return !(e && e[0] == '1');
 }
 
-// One sweep of the plain FP64 method on stream st.
-void enqueue_sweep_f64(zbus_network net, int64_t B, int grid, cudaGraphConditionalHandle h,
-                       bool use_handle, cudaStream_t st) {
-  launch_currents_f64(net->ws.ctx, net->n, net->n_pad, (int)B, st);
-  launch_gemm_f64(net->ws.ctx, net->Zr, net->Zi, net->Zs, net->w, net->n, net->n_pad, grid, st);
+const MixedOperands& operands(zbus_network net, int32_t precision) {
+  return net->mixed[precision == ZBUS_MIXED_BF16X2 ? 1 : 0];
+}
+
+int ntn_for(zbus_network net, int32_t precision) {
+  if (precision == ZBUS_FP64) return net->n_pad / F64_BN;
+  const MixedOperands& op = operands(net, precision);
+  return op.N_pad / op.BN;
+}
+
+int contraction_grid(zbus_network net, int32_t precision, int64_t B) {
+  if (precision == ZBUS_FP64) return gemm_f64_grid((int)B, net->n_pad);
+  return tc_grid(operands(net, precision), (int)B);
+}
+
+// One sweep of the chosen method on stream st (up to three kernels).
+zbus_status enqueue_sweep(zbus_network net, int32_t precision, int64_t B, int grid,
+                          cudaGraphConditionalHandle h, bool use_handle, cudaStream_t st,
+                          cudaEvent_t* ev = nullptr) {
+  if (ev) ZB_CUDA(cudaEventRecord(ev[0], st));
+  if (precision == ZBUS_FP64) {
+    launch_currents_f64(net->ws.ctx, net->n, net->n_pad, (int)B, st);
+    if (ev) ZB_CUDA(cudaEventRecord(ev[1], st));
+    launch_gemm_f64(net->ws.ctx, net->Zr, net->Zi, net->Zs, net->w, net->n, net->n_pad, grid, st);
+  } else {
+    const MixedOperands& op = operands(net, precision);
+    ZB_CHECK(launch_residual_mixed(net, op, (int)B, net->ws.R, net->ws.rinv, st));
+    if (ev) ZB_CUDA(cudaEventRecord(ev[1], st));
+    ZB_CHECK(launch_contract_tc(net, op, net->ws.tmR, net->ws.rinv, grid, st));
+  }
+  if (ev) ZB_CUDA(cudaEventRecord(ev[2], st));
   launch_converge(net->ws.ctx, h, use_handle, st);
+  if (ev) ZB_CUDA(cudaEventRecord(ev[3], st));
+  return ZBUS_OK;
 }
 
 zbus_status get_loop_graph(zbus_network net, int64_t B, int32_t precision, GraphEntry** out) {
@@ -99,7 +158,7 @@ zbus_status get_loop_graph(zbus_network net, int64_t B, int32_t precision, Graph
   GraphEntry e;
   e.B = B;
   e.precision = precision;
-  e.grid_gemm = gemm_f64_grid((int)B, net->n_pad);
+  e.grid_gemm = contraction_grid(net, precision, B);
   if (!net->cap_stream) ZB_CUDA(cudaStreamCreateWithFlags(&net->cap_stream, cudaStreamNonBlocking));
   ZB_CUDA(cudaGraphCreate(&e.graph, 0));
   cudaGraphConditionalHandle h;
@@ -113,11 +172,12 @@ zbus_status get_loop_graph(zbus_network net, int64_t B, int32_t precision, Graph
   cudaGraph_t body = cp.conditional.phGraph_out[0];
   ZB_CUDA(cudaStreamBeginCaptureToGraph(net->cap_stream, body, nullptr, nullptr, 0,
                                         cudaStreamCaptureModeThreadLocal));
-  enqueue_sweep_f64(net, B, e.grid_gemm, h, true, net->cap_stream);
+  zbus_status s = enqueue_sweep(net, precision, B, e.grid_gemm, h, true, net->cap_stream);
   cudaGraph_t captured = nullptr;
   cudaError_t ce = cudaStreamEndCapture(net->cap_stream, &captured);
-  if (ce != cudaSuccess) {
+  if (s != ZBUS_OK || ce != cudaSuccess) {
     cudaGraphDestroy(e.graph);
+    if (s != ZBUS_OK) return s;
     return cuda_fail(ce, "cudaStreamEndCapture(sweep)", __FILE__, __LINE__);
   }
   ce = cudaGraphInstantiate(&e.exec, e.graph, 0);
@@ -224,6 +284,7 @@ void zbus_network_destroy(zbus_network net) {
   for (auto e : net->prof.ev) cudaEventDestroy(e);
   cudaFree(net->prof.d_hist);
   cudaFree(net->ws.base);
+  free_mixed(net);
   cudaFree(net->Z);
   cudaFree(net->w);
   cudaFree(net->ys);
@@ -256,10 +317,16 @@ zbus_status zbus_network_reserve(zbus_network net, int64_t B, int32_t precision)
   g_last_error.clear();
   if (!net) return fail(ZBUS_ERR_ARG, "network is NULL");
   if (B < 0 || B > INT32_MAX / 4) return fail(ZBUS_ERR_ARG, "B out of range");
-  if (precision != ZBUS_FP64)
-    return fail(ZBUS_ERR_UNSUPPORTED, "precision not available in this build");
+  if (precision != ZBUS_FP64 && precision != ZBUS_MIXED_BF16X2 &&
+      precision != ZBUS_MIXED_FP16_SCALED)
+    return fail(ZBUS_ERR_ARG, "unknown precision");
   ZB_CHECK(check_device(net));
-  return ensure_workspace(net, B);
+  ZB_CHECK(ensure_workspace(net, B));
+  if (precision != ZBUS_FP64) {
+    ZB_CHECK(prepare_mixed(net, precision, nullptr));
+    ZB_CHECK(ensure_tmR(net, precision == ZBUS_MIXED_BF16X2));
+  }
+  return ZBUS_OK;
 }
 
 zbus_status zbus_solve(zbus_network net, int64_t B, const double* S_wye, const double* S_delta,
@@ -283,11 +350,14 @@ zbus_status zbus_solve(zbus_network net, int64_t B, const double* S_wye, const d
   if (!V_out || !iters || !converged) return fail(ZBUS_ERR_ARG, "an output pointer is NULL");
   if (S_delta && !net->bus_aligned)
     return fail(ZBUS_ERR_ARG, "delta loads need three unknowns per bus (n % 3 == 0)");
-  if (o.precision != ZBUS_FP64)
-    return fail(ZBUS_ERR_UNSUPPORTED, "precision not available in this build");
   ZB_CHECK(check_device(net));
   cudaStream_t st = (cudaStream_t)cuda_stream;
   ZB_CHECK(ensure_workspace(net, B));
+  const bool mixed = o.precision != ZBUS_FP64;
+  if (mixed) {
+    ZB_CHECK(prepare_mixed(net, o.precision, st));
+    ZB_CHECK(ensure_tmR(net, o.precision == ZBUS_MIXED_BF16X2));
+  }
 
   SolveCtx h;
   std::memset(&h, 0, sizeof(h));
@@ -305,7 +375,7 @@ zbus_status zbus_solve(zbus_network net, int64_t B, const double* S_wye, const d
   h.B = (int32_t)B;
   h.max_iter = max_iter;
   h.rule = o.conv_rule;
-  h.ntn = net->n_pad / F64_BN;
+  h.ntn = ntn_for(net, o.precision);
   if (o.profile == 1) {
     Profile& P = net->prof;
     if (P.cap < max_iter) {
@@ -323,33 +393,25 @@ zbus_status zbus_solve(zbus_network net, int64_t B, const double* S_wye, const d
     h.hist = P.d_hist;
     h.hist_n = max_iter;
     launch_init(net->ws.ctx, h, net->w, net->n, (int)B, st);
-    const int grid = gemm_f64_grid((int)B, net->n_pad);
-    for (int k = 0; k < max_iter; ++k) {
-      cudaEvent_t* e = &P.ev[(size_t)4 * k];
-      ZB_CUDA(cudaEventRecord(e[0], st));
-      launch_currents_f64(net->ws.ctx, net->n, net->n_pad, (int)B, st);
-      ZB_CUDA(cudaEventRecord(e[1], st));
-      launch_gemm_f64(net->ws.ctx, net->Zr, net->Zi, net->Zs, net->w, net->n, net->n_pad, grid,
-                      st);
-      ZB_CUDA(cudaEventRecord(e[2], st));
-      launch_converge(net->ws.ctx, 0, false, st);
-      ZB_CUDA(cudaEventRecord(e[3], st));
-    }
+    const int grid = contraction_grid(net, o.precision, B);
+    for (int k = 0; k < max_iter; ++k)
+      ZB_CHECK(enqueue_sweep(net, o.precision, B, grid, 0, false, st, &P.ev[(size_t)4 * k]));
     P.sweeps = max_iter;
-    ZB_CUDA(cudaGetLastError());
-    return ZBUS_OK;
-  }
-  launch_init(net->ws.ctx, h, net->w, net->n, (int)B, st);
-  ZB_CUDA(cudaGetLastError());
-  if (use_graphs()) {
-    GraphEntry* g = nullptr;
-    ZB_CHECK(get_loop_graph(net, B, o.precision, &g));
-    ZB_CUDA(cudaGraphLaunch(g->exec, st));
   } else {
-    const int grid = gemm_f64_grid((int)B, net->n_pad);
-    for (int k = 0; k < max_iter; ++k) enqueue_sweep_f64(net, B, grid, 0, false, st);
+    launch_init(net->ws.ctx, h, net->w, net->n, (int)B, st);
     ZB_CUDA(cudaGetLastError());
+    if (use_graphs()) {
+      GraphEntry* g = nullptr;
+      ZB_CHECK(get_loop_graph(net, B, o.precision, &g));
+      ZB_CUDA(cudaGraphLaunch(g->exec, st));
+    } else {
+      const int grid = contraction_grid(net, o.precision, B);
+      for (int k = 0; k < max_iter; ++k)
+        ZB_CHECK(enqueue_sweep(net, o.precision, B, grid, 0, false, st));
+    }
   }
+  if (mixed) ZB_CHECK(launch_final_check(net, (int)B, net->ws.mm, st));
+  ZB_CUDA(cudaGetLastError());
   return ZBUS_OK;
 }
 

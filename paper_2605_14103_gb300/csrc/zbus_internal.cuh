@@ -1,6 +1,7 @@
 // Internal declarations of libzbus (not part of the C ABI).
 #pragma once
 
+#include <cuda.h>
 #include <cuda_runtime.h>
 #include <stdint.h>
 
@@ -71,13 +72,32 @@ struct SolveCtx {
 
 struct Workspace {
   int64_t cap_B = 0;
-  int32_t precision = -1;
   size_t bytes = 0;
   void* base = nullptr;
   SolveCtx* ctx = nullptr;   // device
   int32_t* list = nullptr;
-  double* part = nullptr;
-  double* Iop = nullptr;
+  double* part = nullptr;    // [cap_B][max N-tiles][2]
+  double* Iop = nullptr;     // FP64: 3 x [cap_B][n_pad]
+  void* R = nullptr;         // mixed: [cap_B][K_pad] fp16 / bf16 residual rows
+  float* rinv = nullptr;     // mixed: [cap_B] inverse residual scales
+  double* mm = nullptr;      // mixed: [cap_B] final FP64 mismatch (-1 if not checked)
+  CUtensorMap tmR;           // TMA map of R (box 64 x 128)
+  bool tmR_bf16 = false;
+  bool tmR_ready = false;
+};
+
+// Low-precision operands of Z for the tensor-core contraction.
+struct MixedOperands {
+  bool ready = false;
+  bool bf16 = false;
+  int zparts = 1;            // 1: FP16 row-scaled; 2: BF16 hi + lo
+  int K_pad = 0;             // 2n rounded up to 64
+  int N_pad = 0;             // 2n rounded up to 256
+  int BN = 128;              // N-tile of the contraction
+  void* Z0 = nullptr;        // [N_pad][K_pad] (hi part)
+  void* Z1 = nullptr;        // [N_pad][K_pad] (lo part, BF16 only)
+  float* zinv = nullptr;     // [N_pad / 2] inverse row scales per complex output
+  CUtensorMap tmZ0, tmZ1;
 };
 
 // Host-driven profiling run: 4 events per sweep around the three kernels.
@@ -118,6 +138,7 @@ struct zbus_network_s {
   int64_t nnz_ll = 0;
   int max_row_nnz = 0;
   zbus::Workspace ws;
+  zbus::MixedOperands mixed[2];   // [0] FP16 row-scaled, [1] BF16 hi + lo
   std::vector<zbus::GraphEntry> graphs;
   cudaStream_t cap_stream = nullptr;  // private stream used only to capture graphs
   zbus::Profile prof;
@@ -142,5 +163,18 @@ void launch_converge(SolveCtx* ctx, cudaGraphConditionalHandle h, bool use_handl
 void launch_mismatch(const double2* V, const double2* S_wye, const double2* S_del,
                      const int32_t* ptr, const int32_t* col, const double2* val,
                      const double2* ys, int n, int B, double* out, cudaStream_t st);
+
+
+// mixed.cu
+zbus_status make_tmap_2d(CUtensorMap* map, const void* base, bool bf16, uint64_t cols,
+                         uint64_t rows, uint32_t box_cols, uint32_t box_rows);
+zbus_status prepare_mixed(zbus_network net, int32_t precision, cudaStream_t st);
+void free_mixed(zbus_network net);
+int tc_grid(const MixedOperands& op, int B);
+zbus_status launch_residual_mixed(zbus_network net, const MixedOperands& op, int B, void* R,
+                                  float* rinv, cudaStream_t st);
+zbus_status launch_contract_tc(zbus_network net, const MixedOperands& op, const CUtensorMap& tmR,
+                               const float* rinv, int grid, cudaStream_t st);
+zbus_status launch_final_check(zbus_network net, int B, double* mm_out, cudaStream_t st);
 
 }  // namespace zbus

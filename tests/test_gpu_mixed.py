@@ -1,0 +1,149 @@
+"""GPU parity of the mixed-precision (tcgen05) defect form against the FP64 oracle.
+
+Bar (per scenario): identical converged flags, max |V_gpu - V_oracle| <= 1e-6 pu
+on converged scenarios, FP64 power mismatch <= 1e-6 pu, iteration counts
+within one of the oracle's.  A single sweep from a warm start isolates the
+residual, the tensor-core contraction and the epilogue: its step must match
+the FP64 step Z r(v) to the precision of the operands (FP16 row-scaled:
+relative 2^-10 of the step size; BF16 hi+lo with BF16 residual: 2^-7).
+"""
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+
+from oracle import zbus_oracle as O                      # noqa: E402
+from paper_2605_14103_gb300 import feeders as F          # noqa: E402
+from paper_2605_14103_gb300 import zbus                  # noqa: E402
+
+pytestmark = pytest.mark.gpu
+
+MODES = ["fp16_scaled", "bf16x2"]
+STEP_RTOL = {"fp16_scaled": 2.0 ** -10, "bf16x2": 2.0 ** -7}
+
+
+@pytest.fixture(scope="module", autouse=True)
+def built():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2605_14103_gb300 import build as B
+    B.build()
+    zbus.lib()
+
+
+def dev(x):
+    return torch.from_numpy(np.ascontiguousarray(x)).cuda()
+
+
+def oracle(f, Sw, Sd, tol=1e-8, max_iter=50, V0=None):
+    return O.solve_coo(f.n_total, f.Y_row, f.Y_col, f.Y_val, f.slack_idx, f.v_slack, Sw, Sd,
+                       tol=tol, max_iter=max_iter, V0=V0)
+
+
+def check(net, f, Sw, Sd, ref, V, it, cv):
+    V, it, cv = V.cpu().numpy(), it.cpu().numpy(), cv.cpu().numpy()
+    np.testing.assert_array_equal(cv, ref["converged"])
+    m = ref["converged"] == 1
+    if m.any():
+        err = np.abs(V[m] - ref["V"][m]).max()
+        assert err <= 1e-6, err
+        assert np.abs(it[m] - ref["iters"][m]).max() <= 1
+    mm = net.power_mismatch(dev(V), dev(Sw), dev(Sd)).cpu().numpy()
+    assert mm[m].max(initial=0.0) <= 1e-6
+
+
+@pytest.mark.parametrize("mode", MODES)
+@pytest.mark.parametrize("N,B,seed", [(13, 8, 101), (128, 200, 202), (700, 130, 7)])
+def test_one_defect_step_matches_fp64_step(mode, N, B, seed):
+    f = F.make_feeder(N, seed, delta_frac=0.3)
+    Sw, Sd = F.make_scenarios(f, B, 0.8, 1.2)
+    V0 = oracle(f, 0.7 * Sw, 0.7 * Sd)["V"]           # a warm start away from the solution
+    ref1 = oracle(f, Sw, Sd, tol=0.0, max_iter=1, V0=V0)["V"]   # v + Z r(v) = Z i(v) + w
+    net = zbus.Network.from_feeder(f)
+    V, it, cv = net.solve(dev(Sw), dev(Sd), V_init=dev(V0), tol=0.0, max_iter=1, precision=mode)
+    V = V.cpu().numpy()
+    step = np.abs(ref1 - V0).max(axis=1, keepdims=True)
+    err = np.abs(V - ref1) / step
+    assert err.max() <= STEP_RTOL[mode], err.max()
+    assert (it.cpu().numpy() == 1).all()
+
+
+@pytest.mark.parametrize("mode", MODES)
+@pytest.mark.parametrize("N,B,delta,seed", [(13, 8, 0.4, 101), (17, 1, 0.5, 3),
+                                             (40, 7, 0.3, 4), (128, 129, 0.3, 202),
+                                             (128, 512, 0.3, 202), (65, 33, 1.0, 8),
+                                             (300, 260, 0.4, 9)])
+def test_mixed_solve_parity(mode, N, B, delta, seed):
+    f = F.make_feeder(N, seed, delta_frac=delta, mult_hi=1.5)
+    Sw, Sd = F.make_scenarios(f, B, 0.5, 1.5)
+    ref = oracle(f, Sw, Sd)
+    net = zbus.Network.from_feeder(f)
+    V, it, cv = net.solve(dev(Sw), dev(Sd), tol=1e-8, max_iter=50, precision=mode)
+    check(net, f, Sw, Sd, ref, V, it, cv)
+
+
+@pytest.mark.parametrize("mode", MODES)
+def test_mixed_1024bus(mode):
+    f, Sw, Sd, w = F.make_workload("feeder1024_b16384", B=40)
+    ref = oracle(f, Sw, Sd)
+    net = zbus.Network.from_feeder(f)
+    V, it, cv = net.solve(dev(Sw), dev(Sd), precision=mode)
+    check(net, f, Sw, Sd, ref, V, it, cv)
+
+
+@pytest.mark.parametrize("mode", MODES)
+def test_mixed_full_size_128bus_sampled(mode):
+    f, Sw, Sd, w = F.make_workload("feeder128_b4096")
+    net = zbus.Network.from_feeder(f)
+    net.reserve(w.B, mode)
+    V, it, cv = net.solve(dev(Sw), dev(Sd), tol=w.tol, max_iter=w.max_iter, precision=mode)
+    assert cv.cpu().numpy().all()
+    mm = net.power_mismatch(V, dev(Sw), dev(Sd)).cpu().numpy()
+    assert mm.max() <= 1e-6
+    idx = np.random.default_rng(2).choice(w.B, 96, replace=False)
+    ref = oracle(f, Sw[idx], Sd[idx])
+    ti = torch.from_numpy(idx).cuda()
+    check(net, f, Sw[idx], Sd[idx], ref, V[ti].contiguous(), it[ti].contiguous(),
+          cv[ti].contiguous())
+
+
+@pytest.mark.parametrize("mode", MODES)
+def test_mixed_results_do_not_depend_on_the_batch(mode):
+    f, Sw, Sd, w = F.make_workload("feeder128_b4096", B=300)
+    net = zbus.Network.from_feeder(f)
+    V, it, cv = net.solve(dev(Sw), dev(Sd), precision=mode)
+    perm = np.random.default_rng(0).permutation(300)[:77]
+    V2, it2, cv2 = net.solve(dev(Sw[perm]), dev(Sd[perm]), precision=mode)
+    ti = torch.from_numpy(perm).cuda()
+    assert torch.equal(V2, V[ti])
+    assert torch.equal(it2, it[ti])
+
+
+@pytest.mark.parametrize("mode", MODES)
+def test_mixed_zero_load_and_divergence(mode):
+    f = F.make_feeder(30, 15, delta_frac=0.3)
+    z = np.zeros((5, f.n), dtype=np.complex128)
+    net = zbus.Network.from_feeder(f)
+    V, it, cv = net.solve(dev(z), dev(z), precision=mode)
+    _, w = net.get_z()
+    assert (cv.cpu().numpy() == 1).all() and (it.cpu().numpy() == 1).all()
+    # the FP64 residual of w is rounding noise, not exactly zero: V = w + O(1e-15)
+    assert (V - w.expand(5, -1)).abs().max().item() <= 1e-12
+    f, Sw, Sd, _ = F.make_workload("feeder128_b4096", B=6)
+    Sw, Sd = Sw * 60.0, Sd * 60.0
+    Sw[0] /= 60.0
+    Sd[0] /= 60.0
+    net = zbus.Network.from_feeder(f)
+    V, it, cv = net.solve(dev(Sw), dev(Sd), max_iter=40, precision=mode)
+    c = cv.cpu().numpy()
+    assert c[0] == 1 and not c[1:].any()
+    assert (it.cpu().numpy() <= 40).all()
+
+
+def test_modes_agree_with_each_other_and_fp64():
+    f, Sw, Sd, w = F.make_workload("feeder128_b4096", B=256)
+    net = zbus.Network.from_feeder(f)
+    outs = {m: net.solve(dev(Sw), dev(Sd), precision=m)[0].cpu().numpy()
+            for m in ["fp64", "fp16_scaled", "bf16x2"]}
+    for m in ("fp16_scaled", "bf16x2"):
+        assert np.abs(outs[m] - outs["fp64"]).max() <= 1e-6
