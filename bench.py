@@ -232,9 +232,9 @@ def run_reference(args):
 # ---------------------------------------------------------------------------
 # our arm
 # ---------------------------------------------------------------------------
-KERNELS = {"fp64": ("k_currents_f64", "k_gemm3m_f64", "k_converge"),
-           "fp16_scaled": ("k_residual_mixed", "k_contract_tc", "k_converge"),
-           "bf16x2": ("k_residual_mixed", "k_contract_tc", "k_converge")}
+KERNELS = {"fp64": ("k_currents_f64", "k_gemm3m_f64", "k_decide+k_compact"),
+           "fp16_scaled": ("k_residual_df", "k_contract_tc", "k_decide_mixed+k_finish_mixed"),
+           "bf16x2": ("k_residual_df", "k_contract_tc", "k_decide_mixed+k_finish_mixed")}
 
 
 def kernel_roofline(form, name, n, B_act_sweeps, ms, peaks, K_pad=None, N_pad=None):
@@ -260,10 +260,11 @@ def kernel_roofline(form, name, n, B_act_sweeps, ms, peaks, K_pad=None, N_pad=No
         hb = {"bound": "hbm", "achieved": byts, "peak": peaks["hbm_gbs"], "unit": "GB/s",
               "frac": byts / peaks["hbm_gbs"], "peak_src": "MEASURED_PEAKS hbm copy"}
         return tf if tf["frac"] >= hb["frac"] else hb
-    # residual / load-current kernels: bytes of v (16 n), two load arrays
-    # (32 n) and the operand row they write (mixed: 4 n; FP64: 24 n)
-    out_b = 4.0 * n if form != "fp64" else 24.0 * n
-    byts = B_act_sweeps * (48.0 * n + out_b) / t / 1e9
+    # residual / load-current kernels: bytes they must move per scenario-sweep:
+    # FP64: v (16 n) + two FP64 load arrays (32 n) + 3M operands written (24 n);
+    # mixed: double-float v (16 n) + two FP32 load arrays (16 n) + R row (4 n)
+    per = 72.0 * n if form == "fp64" else 36.0 * n
+    byts = B_act_sweeps * per / t / 1e9
     return {"bound": "hbm", "achieved": byts, "peak": peaks["hbm_gbs"], "unit": "GB/s",
             "frac": byts / peaks["hbm_gbs"], "peak_src": "MEASURED_PEAKS hbm copy"}
 

@@ -203,7 +203,7 @@ zbus_status zbus_last_profile(zbus_network net, int32_t max_n, float* ms, int32_
  *
  *   arguments as zbus_solve, with conv_rule (zbus_conv_rule) in place of opts.
  *   Returns ZBUS_ERR_ARG, launching nothing, when the batch needs more than
- *   the 16 MiB: about 16 MiB / (24 n_pad + 16 ceil(n/48) + 4) bytes per
+ *   the 16 MiB: about 16 MiB / (24 n_pad + 16 ceil(n/48) + 5) bytes per
  *   scenario, n_pad = n rounded up to a multiple of 48 (about 1790 scenarios
  *   for n = 381).
  *

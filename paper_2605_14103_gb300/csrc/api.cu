@@ -49,24 +49,44 @@ int k_pad_tc(const zbus_network net) { return round_up(2 * net->n, 64); }
 // Scratch of one solve: context, active list, per-tile partials, the FP64
 // contraction operands and the low-precision residual rows.
 struct WsLayout {
-  size_t list, part, iop, R, rinv, mm, total;
+  size_t list, keep, part, iop, R, rinv, mm, vh, vl, swf, sdf, st, amax, mt, total;
 };
 
 WsLayout workspace_layout(const zbus_network net, int64_t B) {
+  // per-scenario arrays of the mixed sweeps are sized for B rounded up to the
+  // 128-scenario tile of the tensor-core contraction
+  const size_t Bp = (size_t)round_up((int)B, 128);
   WsLayout L;
   size_t o = align256(sizeof(SolveCtx));
   L.list = o;
   o += align256((size_t)B * sizeof(int32_t));
+  L.keep = o;
+  o += align256((size_t)B);
   L.part = o;
-  o += align256((size_t)B * max_ntn(net) * 2 * sizeof(double));
+  o += align256(Bp * max_ntn(net) * 2 * sizeof(double));
   L.iop = o;
   o += align256((size_t)3 * B * net->n_pad * sizeof(double));
   L.R = o;
-  o += align256((size_t)B * k_pad_tc(net) * 2);
+  o += align256(Bp * k_pad_tc(net) * 2);
   L.rinv = o;
-  o += align256((size_t)B * sizeof(float));
+  o += align256(Bp * sizeof(float));
   L.mm = o;
   o += align256((size_t)B * sizeof(double));
+  const size_t f2 = align256(Bp * net->n * sizeof(float2));
+  L.vh = o;
+  o += f2;
+  L.vl = o;
+  o += f2;
+  L.swf = o;
+  o += f2;
+  L.sdf = o;
+  o += f2;
+  L.st = o;
+  o += align256(Bp);
+  L.amax = o;
+  o += align256(2 * Bp * sizeof(float));
+  L.mt = o;
+  o += align256(2 * (Bp / 128) * sizeof(int32_t));
   L.total = o;
   return L;
 }
@@ -94,6 +114,15 @@ zbus_status ensure_workspace(zbus_network net, int64_t B) {
   ws.R = (void*)(p + L.R);
   ws.rinv = (float*)(p + L.rinv);
   ws.mm = (double*)(p + L.mm);
+  ws.keep = (uint8_t*)(p + L.keep);
+  ws.Vh = (float2*)(p + L.vh);
+  ws.Vl = (float2*)(p + L.vl);
+  ws.Swf = (float2*)(p + L.swf);
+  ws.Sdf = (float2*)(p + L.sdf);
+  ws.st = (uint8_t*)(p + L.st);
+  ws.amax = (float*)(p + L.amax);
+  ws.mt = (int32_t*)(p + L.mt);
+  ws.cap_Bp = round_up((int)B, 128);
   ws.tmR_ready = false;
   return ZBUS_OK;
 }
@@ -102,7 +131,7 @@ zbus_status ensure_workspace(zbus_network net, int64_t B) {
 zbus_status ensure_tmR(zbus_network net, bool bf16) {
   Workspace& ws = net->ws;
   if (ws.tmR_ready && ws.tmR_bf16 == bf16) return ZBUS_OK;
-  ZB_CHECK(make_tmap_2d(&ws.tmR, ws.R, bf16, (uint64_t)k_pad_tc(net), (uint64_t)ws.cap_B, 64, 128));
+  ZB_CHECK(make_tmap_2d(&ws.tmR, ws.R, bf16, (uint64_t)k_pad_tc(net), (uint64_t)ws.cap_Bp, 64, 128));
   ws.tmR_bf16 = bf16;
   ws.tmR_ready = true;
   return ZBUS_OK;
@@ -144,7 +173,10 @@ zbus_status enqueue_sweep(zbus_network net, int32_t precision, int64_t B, int gr
     ZB_CHECK(launch_contract_tc(net, op, net->ws.tmR, net->ws.rinv, grid, st));
   }
   if (ev) ZB_CUDA(cudaEventRecord(ev[2], st));
-  launch_converge(net->ws.ctx, h, use_handle, st);
+  if (precision == ZBUS_FP64)
+    launch_converge(net->ws.ctx, (int)B, h, use_handle, st);
+  else
+    launch_converge_mixed(net->ws.ctx, (int)B, h, use_handle, st);
   if (ev) ZB_CUDA(cudaEventRecord(ev[3], st));
   return ZBUS_OK;
 }
@@ -294,6 +326,9 @@ void zbus_network_destroy(zbus_network net) {
   cudaFree(net->csr_ptr);
   cudaFree(net->csr_col);
   cudaFree(net->csr_val);
+  cudaFree(net->bsr_ptr);
+  cudaFree(net->bsr_col);
+  cudaFree(net->bsr_val);
   delete net;
 }
 
@@ -368,6 +403,19 @@ zbus_status zbus_solve(zbus_network net, int64_t B, const double* S_wye, const d
   h.iters = iters;
   h.conv = converged;
   h.list = net->ws.list;
+  h.keep = net->ws.keep;
+  if (mixed) {
+    h.Vh = net->ws.Vh;
+    h.Vl = net->ws.Vl;
+    h.Swf = S_wye ? net->ws.Swf : nullptr;
+    h.Sdf = S_delta ? net->ws.Sdf : nullptr;
+    h.st = net->ws.st;
+    h.amax_prev = net->ws.amax;
+    h.amax_cur = net->ws.amax + net->ws.cap_Bp;
+    h.B_pad = round_up((int)B, 128);
+    h.mt_list = net->ws.mt;
+    h.mt_flag = (uint32_t*)(net->ws.mt + net->ws.cap_Bp / 128);
+  }
   h.part = net->ws.part;
   h.Iop = net->ws.Iop;
   h.tol = tol;
@@ -393,12 +441,14 @@ zbus_status zbus_solve(zbus_network net, int64_t B, const double* S_wye, const d
     h.hist = P.d_hist;
     h.hist_n = max_iter;
     launch_init(net->ws.ctx, h, net->w, net->n, (int)B, st);
+    if (mixed) launch_init_df(net->ws.ctx, net->n, (int)B, h.B_pad, st);
     const int grid = contraction_grid(net, o.precision, B);
     for (int k = 0; k < max_iter; ++k)
       ZB_CHECK(enqueue_sweep(net, o.precision, B, grid, 0, false, st, &P.ev[(size_t)4 * k]));
     P.sweeps = max_iter;
   } else {
     launch_init(net->ws.ctx, h, net->w, net->n, (int)B, st);
+    if (mixed) launch_init_df(net->ws.ctx, net->n, (int)B, h.B_pad, st);
     ZB_CUDA(cudaGetLastError());
     if (use_graphs()) {
       GraphEntry* g = nullptr;
@@ -410,7 +460,10 @@ zbus_status zbus_solve(zbus_network net, int64_t B, const double* S_wye, const d
         ZB_CHECK(enqueue_sweep(net, o.precision, B, grid, 0, false, st));
     }
   }
-  if (mixed) ZB_CHECK(launch_final_check(net, (int)B, net->ws.mm, st));
+  if (mixed) {
+    launch_merge_df(net->ws.ctx, net->n, (int)B, h.B_pad, st);
+    ZB_CHECK(launch_final_check(net, (int)B, net->ws.mm, st));
+  }
   ZB_CUDA(cudaGetLastError());
   return ZBUS_OK;
 }

@@ -1,0 +1,43 @@
+// Double-float arithmetic: a value is the unevaluated sum hi + lo of two
+// FP32 numbers (about 48 significant bits).  Built from the error-free
+// transformations of Knuth (two-sum) and Dekker (two-product via FMA), so it
+// runs on the FP32 pipes, which on this GPU are ~64x faster than FP64.
+#pragma once
+
+#include <cuda_runtime.h>
+
+namespace zbus {
+
+// s + e == a + b exactly, s = fl(a + b).
+__device__ __forceinline__ void two_sum(float a, float b, float& s, float& e) {
+  s = __fadd_rn(a, b);
+  const float bb = __fsub_rn(s, a);
+  e = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb));
+}
+
+// Same for |a| >= |b| (or a == 0).
+__device__ __forceinline__ void fast_two_sum(float a, float b, float& s, float& e) {
+  s = __fadd_rn(a, b);
+  e = __fsub_rn(b, __fsub_rn(s, a));
+}
+
+// (sh, sl) += (ah + al) * (bh + bl), dropping al * bl; sl is left unnormalised.
+__device__ __forceinline__ void df_mac(float& sh, float& sl, float ah, float al, float bh,
+                                       float bl) {
+  const float p = __fmul_rn(ah, bh);
+  float e = __fmaf_rn(ah, bh, -p);
+  e = __fmaf_rn(ah, bl, e);
+  e = __fmaf_rn(al, bh, e);
+  float s, t;
+  two_sum(sh, p, s, t);
+  sh = s;
+  sl = __fadd_rn(sl, __fadd_rn(t, e));
+}
+
+// Split a double into hi + lo floats.
+__device__ __forceinline__ float2 df_split(double x) {
+  const float h = __double2float_rn(x);
+  return make_float2(h, __double2float_rn(x - (double)h));
+}
+
+}  // namespace zbus

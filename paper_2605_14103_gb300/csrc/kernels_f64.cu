@@ -231,24 +231,51 @@ k_gemm3m_f64(const SolveCtx* __restrict__ ctx, const double* __restrict__ Zr,
 }
 
 // ---------------------------------------------------------------------------
-// K3: stop test per active scenario, stable in-place compaction of the list.
-// One block of 1024 threads.
+// K3a: stop test per active scenario (many blocks): reduce the per-tile
+// partials in a fixed order, record iters / flags, mark the slots to keep.
+// ---------------------------------------------------------------------------
+__global__ void k_decide(SolveCtx* __restrict__ ctx) {
+  const int count = ctx->count;
+  const int slot = blockIdx.x * blockDim.x + threadIdx.x;
+  if (slot >= count) return;
+  const int it = ctx->iter + 1;
+  const int ntn = ctx->ntn;
+  const int b = ctx->list[slot];
+  const double* part = ctx->part + (int64_t)slot * ntn * 2;
+  double dmax = 0.0, dsum = 0.0;
+  for (int t = 0; t < ntn; ++t) {
+    dmax = fmax(dmax, part[2 * t]);
+    dsum += part[2 * t + 1];
+  }
+  const double delta = ctx->rule == ZBUS_CONV_SUMMAG ? fabs(dsum) : dmax;
+  ctx->iters[b] = it;
+  int keep = 0;
+  if (!isfinite(delta)) {
+    ctx->conv[b] = 0;
+  } else if (delta <= ctx->tol) {
+    ctx->conv[b] = 1;
+  } else if (it < ctx->max_iter) {
+    keep = 1;
+  }
+  ctx->keep[slot] = (uint8_t)keep;
+}
+
+// ---------------------------------------------------------------------------
+// K3b: stable in-place compaction of the active list by the keep marks, one
+// block of 1024 threads; advances the sweep counter and sets the loop
+// condition of the graph.
 // ---------------------------------------------------------------------------
 constexpr int CONV_THREADS = 1024;
 
 __global__ void __launch_bounds__(CONV_THREADS)
-k_converge(SolveCtx* ctx, cudaGraphConditionalHandle h, int use_handle) {
+k_compact(SolveCtx* ctx, cudaGraphConditionalHandle h, int use_handle) {
   __shared__ int swarp[CONV_THREADS / 32];
   __shared__ int sbase, stotal;
   const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
   const int count = ctx->count;
   const int it = ctx->iter + 1;
-  const int ntn = ctx->ntn;
-  const double tol = ctx->tol;
-  const int rule = ctx->rule;
-  const int max_iter = ctx->max_iter;
   int32_t* list = ctx->list;
-  const double* part = ctx->part;
+  const uint8_t* keepv = ctx->keep;
   if (tid == 0) {
     sbase = 0;
     if (ctx->hist && it - 1 < ctx->hist_n) ctx->hist[it - 1] = count;
@@ -258,21 +285,8 @@ k_converge(SolveCtx* ctx, cudaGraphConditionalHandle h, int use_handle) {
     const int slot = base + tid;
     int keep = 0, b = -1;
     if (slot < count) {
+      keep = keepv[slot];
       b = list[slot];
-      double dmax = 0.0, dsum = 0.0;
-      for (int t = 0; t < ntn; ++t) {
-        dmax = fmax(dmax, part[((int64_t)slot * ntn + t) * 2 + 0]);
-        dsum += part[((int64_t)slot * ntn + t) * 2 + 1];
-      }
-      const double delta = rule == ZBUS_CONV_SUMMAG ? fabs(dsum) : dmax;
-      ctx->iters[b] = it;
-      if (!isfinite(delta)) {
-        ctx->conv[b] = 0;
-      } else if (delta <= tol) {
-        ctx->conv[b] = 1;
-      } else if (it < max_iter) {
-        keep = 1;
-      }
     }
     // block-wide exclusive scan of keep, then an in-place stable write: every
     // read of this chunk happened before the first barrier and every write
@@ -378,9 +392,10 @@ void launch_gemm_f64(SolveCtx* ctx, const double* Zr, const double* Zi, const do
   k_gemm3m_f64<<<grid, GEMM_THREADS, 0, st>>>(ctx, Zr, Zi, Zs, w, n, n_pad);
 }
 
-void launch_converge(SolveCtx* ctx, cudaGraphConditionalHandle h, bool use_handle,
+void launch_converge(SolveCtx* ctx, int B, cudaGraphConditionalHandle h, bool use_handle,
                      cudaStream_t st) {
-  k_converge<<<1, CONV_THREADS, 0, st>>>(ctx, h, use_handle ? 1 : 0);
+  k_decide<<<(B + 255) / 256, 256, 0, st>>>(ctx);
+  k_compact<<<1, CONV_THREADS, 0, st>>>(ctx, h, use_handle ? 1 : 0);
 }
 
 void launch_mismatch(const double2* V, const double2* S_wye, const double2* S_del,

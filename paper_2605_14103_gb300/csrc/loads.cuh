@@ -39,4 +39,29 @@ __device__ __forceinline__ void bus_injection(const double2* v, const double2* s
   for (int p = 0; p < 3; ++p) inj[p] = make_double2(-d[p].x, -d[p].y);
 }
 
+// FP32 versions for the mixed sweeps: conj(S / v) with a rounded reciprocal.
+__device__ __forceinline__ float2 load_draw_f(float2 S, float2 v) {
+  if (S.x == 0.f && S.y == 0.f) return make_float2(0.f, 0.f);
+  const float inv = __frcp_rn(__fmaf_rn(v.x, v.x, v.y * v.y));
+  return make_float2((S.x * v.x + S.y * v.y) * inv, (S.x * v.y - S.y * v.x) * inv);
+}
+
+__device__ __forceinline__ void bus_injection_f(const float2* v, const float2* sw,
+                                                const float2* sd, int m, float2* inj) {
+  float2 d[3];
+#pragma unroll
+  for (int p = 0; p < 3; ++p)
+    d[p] = (p < m && sw) ? load_draw_f(sw[p], v[p]) : make_float2(0.f, 0.f);
+  if (sd && m == 3) {
+    const float2 iab = load_draw_f(sd[0], make_float2(v[0].x - v[1].x, v[0].y - v[1].y));
+    const float2 ibc = load_draw_f(sd[1], make_float2(v[1].x - v[2].x, v[1].y - v[2].y));
+    const float2 ica = load_draw_f(sd[2], make_float2(v[2].x - v[0].x, v[2].y - v[0].y));
+    d[0].x += iab.x - ica.x; d[0].y += iab.y - ica.y;
+    d[1].x += ibc.x - iab.x; d[1].y += ibc.y - iab.y;
+    d[2].x += ica.x - ibc.x; d[2].y += ica.y - ibc.y;
+  }
+#pragma unroll
+  for (int p = 0; p < 3; ++p) inj[p] = make_float2(-d[p].x, -d[p].y);
+}
+
 }  // namespace zbus

@@ -70,14 +70,15 @@ extern "C" zbus_status zbus_solve_noalloc(zbus_network net, int64_t B, const dou
   if (S_delta && !net->bus_aligned)
     return fail(ZBUS_ERR_ARG, "delta loads need three unknowns per bus (n % 3 == 0)");
 
-  // scratch layout: context | active list | per-tile partials | 3M operands
+  // scratch layout: context | active list | keep marks | per-tile partials | 3M operands
   const int ntn = net->n_pad / F64_BN;
   const size_t o_list = a256(sizeof(SolveCtx));
-  const size_t o_part = o_list + a256((size_t)B * sizeof(int32_t));
+  const size_t o_keep = o_list + a256((size_t)B * sizeof(int32_t));
+  const size_t o_part = o_keep + a256((size_t)B);
   const size_t o_iop = o_part + a256((size_t)B * ntn * 2 * sizeof(double));
   const size_t need = o_iop + (size_t)3 * B * net->n_pad * sizeof(double);
   if (need > STATIC_SCRATCH_BYTES) {
-    const size_t per = sizeof(int32_t) + (size_t)ntn * 2 * sizeof(double) +
+    const size_t per = sizeof(int32_t) + 1 + (size_t)ntn * 2 * sizeof(double) +
                        (size_t)3 * net->n_pad * sizeof(double);
     return fail(ZBUS_ERR_ARG, "batch too large for the static scratch: needs " +
                                   std::to_string(need) + " bytes, the maximum is " +
@@ -101,6 +102,7 @@ extern "C" zbus_status zbus_solve_noalloc(zbus_network net, int64_t B, const dou
   h.iters = iters;
   h.conv = converged;
   h.list = (int32_t*)(p + o_list);
+  h.keep = (uint8_t*)(p + o_keep);
   h.part = (double*)(p + o_part);
   h.Iop = (double*)(p + o_iop);
   h.tol = tol;
@@ -112,15 +114,15 @@ extern "C" zbus_status zbus_solve_noalloc(zbus_network net, int64_t B, const dou
   SolveCtx* ctx = (SolveCtx*)p;
   cudaStream_t st = (cudaStream_t)cuda_stream;
   // The run start writes the whole context, the active list, iters and flags,
-  // so nothing left in the array by an earlier call is read: every partial and
-  // every operand element (padding included) is written in a sweep before the
-  // kernels of that sweep read it.
+  // so nothing left in the array by an earlier call is read: every partial,
+  // keep mark and operand element (padding included) is written in a sweep
+  // before the kernels of that sweep read it.
   launch_init(ctx, h, net->w, net->n, (int)B, st);
   const int grid = gemm_f64_grid((int)B, net->n_pad);
   for (int k = 0; k < max_iter; ++k) {
     launch_currents_f64(ctx, net->n, net->n_pad, (int)B, st);
     launch_gemm_f64(ctx, net->Zr, net->Zi, net->Zs, net->w, net->n, net->n_pad, grid, st);
-    launch_converge(ctx, 0, false, st);
+    launch_converge(ctx, (int)B, 0, false, st);
   }
   ZB_CUDA(cudaGetLastError());
   return ZBUS_OK;

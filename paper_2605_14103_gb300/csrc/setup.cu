@@ -245,6 +245,36 @@ zbus_status build_network(zbus_network net, int32_t n_total, int64_t nnz, const 
   for (int i = 0; i < n; ++i) mr = std::max(mr, lp[i + 1] - lp[i]);
   net->max_row_nnz = mr;
 
+  // 3x3 bus-block form of Y_LL (block (a, b) holds rows 3a..3a+2, columns
+  // 3b..3b+2; absent entries are zero), for networks with three unknowns per bus
+  if (net->bus_aligned) {
+    const int nb = n / 3;
+    std::vector<int32_t> bp(nb + 1, 0), bc;
+    std::vector<double2> bv;
+    for (int a = 0; a < nb; ++a) {
+      std::vector<int32_t> cols;
+      for (int r = 3 * a; r < 3 * a + 3; ++r)
+        for (int t = lp[r]; t < lp[r + 1]; ++t) cols.push_back(lc[t] / 3);
+      std::sort(cols.begin(), cols.end());
+      cols.erase(std::unique(cols.begin(), cols.end()), cols.end());
+      const size_t base = bc.size();
+      for (int c : cols) bc.push_back(c);
+      bv.resize(bc.size() * 9, make_double2(0.0, 0.0));
+      for (int r = 3 * a; r < 3 * a + 3; ++r)
+        for (int t = lp[r]; t < lp[r + 1]; ++t) {
+          const int cb = lc[t] / 3;
+          const size_t k = base + (std::lower_bound(cols.begin(), cols.end(), cb) - cols.begin());
+          bv[k * 9 + (size_t)(r - 3 * a) * 3 + (lc[t] - 3 * cb)] = lv[t];
+        }
+      bp[a + 1] = (int32_t)bc.size();
+    }
+    net->nbus = nb;
+    net->nblk = (int64_t)bc.size();
+    ZB_CHECK(upload(&net->bsr_ptr, bp, st));
+    ZB_CHECK(upload(&net->bsr_col, bc, st));
+    ZB_CHECK(upload(&net->bsr_val, bv, st));
+  }
+
   const size_t zb = (size_t)n * n * sizeof(double2);
   const size_t pb = (size_t)net->n_pad * net->n_pad * sizeof(double);
   ZB_CUDA(cudaMalloc((void**)&net->Z, zb));

@@ -68,6 +68,20 @@ struct SolveCtx {
   int32_t err;            // device error word (0 = fine)
   int32_t* hist;          // profile mode: active count of sweep k (else nullptr)
   int32_t hist_n;
+  uint8_t* keep;          // [B] stop decision of the current sweep, by slot
+  // mixed modes: double-float state (hi + lo FP32 pairs) and FP32 loads
+  float2* Vh;             // [n][B_pad] (scenario-minor)
+  float2* Vl;             // [n][B_pad]
+  float2* Swf;            // [n][B_pad] or nullptr
+  float2* Sdf;            // [n][B_pad] or nullptr
+  uint8_t* st;            // mixed: [B_pad] 0 = active, 1 = stopped
+  float* amax_prev;       // mixed: [B_pad] max |r| of the previous sweep (scale)
+  float* amax_cur;        // mixed: [B_pad] max |r| of this sweep
+  int32_t count_next;     // mixed: active scenarios after this sweep
+  int32_t B_pad;          // mixed: B rounded up to the 128-row tile
+  int32_t* mt_list;       // mixed: [B_pad / 128] tiles holding an active scenario
+  uint32_t* mt_flag;      // mixed: [B_pad / 128] set by the stop test
+  int32_t mt_count;       // mixed: entries of mt_list
 };
 
 struct Workspace {
@@ -81,6 +95,15 @@ struct Workspace {
   void* R = nullptr;         // mixed: [cap_B][K_pad] fp16 / bf16 residual rows
   float* rinv = nullptr;     // mixed: [cap_B] inverse residual scales
   double* mm = nullptr;      // mixed: [cap_B] final FP64 mismatch (-1 if not checked)
+  uint8_t* keep = nullptr;   // [cap_B]
+  float2* Vh = nullptr;      // mixed: [n][cap_Bp] double-float state, hi
+  float2* Vl = nullptr;      // mixed: [n][cap_Bp] lo
+  float2* Swf = nullptr;     // mixed: [n][cap_Bp] FP32 wye loads
+  float2* Sdf = nullptr;     // mixed: [n][cap_Bp] FP32 delta loads
+  uint8_t* st = nullptr;     // mixed: [cap_Bp]
+  float* amax = nullptr;     // mixed: [2][cap_Bp]
+  int32_t* mt = nullptr;     // mixed: [2][cap_Bp / 128] tile list and flags
+  int64_t cap_Bp = 0;        // cap_B rounded up to 128
   CUtensorMap tmR;           // TMA map of R (box 64 x 128)
   bool tmR_bf16 = false;
   bool tmR_ready = false;
@@ -94,6 +117,7 @@ struct MixedOperands {
   int K_pad = 0;             // 2n rounded up to 64
   int N_pad = 0;             // 2n rounded up to 256
   int BN = 128;              // N-tile of the contraction
+  int num_sms = 148;         // persistent grid size
   void* Z0 = nullptr;        // [N_pad][K_pad] (hi part)
   void* Z1 = nullptr;        // [N_pad][K_pad] (lo part, BF16 only)
   float* zinv = nullptr;     // [N_pad / 2] inverse row scales per complex output
@@ -137,6 +161,15 @@ struct zbus_network_s {
   double2* csr_val = nullptr;
   int64_t nnz_ll = 0;
   int max_row_nnz = 0;
+  float4* csr_df = nullptr;  // Y_LL values as double-float (re hi, re lo, im hi, im lo)
+  float4* ys_df = nullptr;   // Y_Ls v_s as double-float
+  // Y_LL as 3x3 bus blocks (networks with n % 3 == 0): block rows per bus
+  int nbus = 0;
+  int32_t* bsr_ptr = nullptr;   // [nbus + 1]
+  int32_t* bsr_col = nullptr;   // [nblk] bus column
+  double2* bsr_val = nullptr;   // [nblk][3][3] row-major complex
+  int64_t nblk = 0;
+  float4* bsr_df = nullptr;     // [nblk][9] double-float copy (mixed sweeps)
   zbus::Workspace ws;
   zbus::MixedOperands mixed[2];   // [0] FP16 row-scaled, [1] BF16 hi + lo
   std::vector<zbus::GraphEntry> graphs;
@@ -158,7 +191,7 @@ void launch_currents_f64(SolveCtx* ctx, int n, int n_pad, int B, cudaStream_t st
 void launch_gemm_f64(SolveCtx* ctx, const double* Zr, const double* Zi, const double* Zs,
                      const double2* w, int n, int n_pad, int grid, cudaStream_t st);
 int gemm_f64_grid(int B, int n_pad);
-void launch_converge(SolveCtx* ctx, cudaGraphConditionalHandle h, bool use_handle,
+void launch_converge(SolveCtx* ctx, int B, cudaGraphConditionalHandle h, bool use_handle,
                      cudaStream_t st);
 void launch_mismatch(const double2* V, const double2* S_wye, const double2* S_del,
                      const int32_t* ptr, const int32_t* col, const double2* val,
@@ -176,5 +209,9 @@ zbus_status launch_residual_mixed(zbus_network net, const MixedOperands& op, int
 zbus_status launch_contract_tc(zbus_network net, const MixedOperands& op, const CUtensorMap& tmR,
                                const float* rinv, int grid, cudaStream_t st);
 zbus_status launch_final_check(zbus_network net, int B, double* mm_out, cudaStream_t st);
+void launch_init_df(SolveCtx* ctx, int n, int B, int B_pad, cudaStream_t st);
+void launch_merge_df(SolveCtx* ctx, int n, int B, int B_pad, cudaStream_t st);
+void launch_converge_mixed(SolveCtx* ctx, int B, cudaGraphConditionalHandle h, bool use_handle,
+                           cudaStream_t st);
 
 }  // namespace zbus
