@@ -163,6 +163,47 @@ zbus_status zbus_solve(zbus_network net, int64_t B,
                        double* V_out, int32_t* iters, uint8_t* converged,
                        void* cuda_stream);
 
+/* One feeder of a batched solve: its network, scenario count and buffers
+ * (same meaning and layout as the arguments of zbus_solve). */
+typedef struct {
+  zbus_network net;
+  int64_t B;
+  const double* S_wye;
+  const double* S_delta;
+  const double* V_init;
+  double* V_out;
+  int32_t* iters;
+  uint8_t* converged;
+} zbus_batch_item;
+
+/*
+ * zbus_solve_batched -- several feeders of uneven size and scenario count in
+ * one solve (Sec. II-B fixed point for each).  In the mixed precisions the
+ * sweeps of all feeders run as one set of kernels per sweep (one persistent
+ * tensor-core contraction over the tiles of every feeder) inside one CUDA
+ * graph WHILE loop; each feeder's scenarios stop independently.  In FP64 the
+ * feeders are solved one after another.  A network may appear at most once
+ * per call.  Results equal those of zbus_solve on each feeder alone.
+ */
+zbus_status zbus_solve_batched(const zbus_batch_item* items, int32_t n_items, double tol,
+                               int32_t max_iter, const zbus_solve_opts* opts,
+                               void* cuda_stream);
+
+/*
+ * zbus_autotune -- time every compiled tensor-core contraction variant (N-tile
+ * and pipeline depth) of opts->precision on this workload (reps timed solves
+ * each, after one warm-up) and record the fastest for its size bucket (next
+ * powers of two of the largest feeder's n and of the total scenario count).
+ * The table persists in $ZBUS_TUNE_CACHE, else zbus_tune.json beside the
+ * library, and is consulted by every later mixed-precision solve.  The
+ * winner is returned in *best_BN / *best_stages (either may be NULL).
+ * Project-written; the paper has no counterpart.
+ */
+zbus_status zbus_autotune(const zbus_batch_item* items, int32_t n_items,
+                          const zbus_solve_opts* opts, double tol, int32_t max_iter,
+                          int32_t reps, void* cuda_stream, int32_t* best_BN,
+                          int32_t* best_stages);
+
 /*
  * zbus_power_mismatch -- per-scenario FP64 power mismatch of given voltages,
  * max_j |v_j conj((Y_LL v + Y_Ls v_s)_j - i_j(v))|, computed with the sparse

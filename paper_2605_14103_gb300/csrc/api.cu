@@ -1,12 +1,14 @@
-// C ABI of libzbus: argument checks, handle lifetime, scratch space and the
-// device-resident iteration loop (a CUDA graph whose WHILE node repeats one
-// sweep until no scenario is active).
+// C ABI of libzbus: argument checks, handle lifetime, scratch space, the
+// device-resident iteration loop of the plain FP64 method (a CUDA graph whose
+// WHILE node repeats one sweep until no scenario is active) and the entry
+// points of the grouped mixed-precision engine (group.cu).
 #include <cmath>
 #include <cstdlib>
 #include <cstring>
 #include <algorithm>
 #include <set>
 
+#include "group.cuh"
 #include "zbus_internal.cuh"
 
 namespace zbus {
@@ -49,7 +51,7 @@ int k_pad_tc(const zbus_network net) { return round_up(2 * net->n, 64); }
 // Scratch of one solve: context, active list, per-tile partials, the FP64
 // contraction operands and the low-precision residual rows.
 struct WsLayout {
-  size_t list, keep, part, iop, R, rinv, mm, vh, vl, swf, sdf, st, amax, mt, total;
+  size_t list, keep, part, iop, R, rinv, mm, vh, vl, swf, sdf, st, amax, mt, sit, sconv, total;
 };
 
 WsLayout workspace_layout(const zbus_network net, int64_t B) {
@@ -87,14 +89,21 @@ WsLayout workspace_layout(const zbus_network net, int64_t B) {
   o += align256(2 * Bp * sizeof(float));
   L.mt = o;
   o += align256(2 * (Bp / 128) * sizeof(int32_t));
+  L.sit = o;
+  o += align256(Bp * sizeof(int32_t));
+  L.sconv = o;
+  o += align256(Bp);
   L.total = o;
   return L;
 }
+
+}  // namespace
 
 zbus_status ensure_workspace(zbus_network net, int64_t B) {
   Workspace& ws = net->ws;
   if (ws.base && ws.cap_B >= B) return ZBUS_OK;
   const WsLayout L = workspace_layout(net, B);
+  const uint64_t gen = ws.gen + 1;
   if (ws.base) {
     ZB_CUDA(cudaDeviceSynchronize());
     drop_graphs(net);
@@ -104,17 +113,19 @@ zbus_status ensure_workspace(zbus_network net, int64_t B) {
   void* base = nullptr;
   ZB_CUDA(cudaMalloc(&base, L.total));
   char* p = (char*)base;
+  ws.gen = gen;
   ws.base = base;
   ws.bytes = L.total;
   ws.cap_B = B;
+  ws.cap_Bp = round_up((int)B, 128);
   ws.ctx = (SolveCtx*)p;
   ws.list = (int32_t*)(p + L.list);
+  ws.keep = (uint8_t*)(p + L.keep);
   ws.part = (double*)(p + L.part);
   ws.Iop = (double*)(p + L.iop);
   ws.R = (void*)(p + L.R);
   ws.rinv = (float*)(p + L.rinv);
   ws.mm = (double*)(p + L.mm);
-  ws.keep = (uint8_t*)(p + L.keep);
   ws.Vh = (float2*)(p + L.vh);
   ws.Vl = (float2*)(p + L.vl);
   ws.Swf = (float2*)(p + L.swf);
@@ -122,75 +133,42 @@ zbus_status ensure_workspace(zbus_network net, int64_t B) {
   ws.st = (uint8_t*)(p + L.st);
   ws.amax = (float*)(p + L.amax);
   ws.mt = (int32_t*)(p + L.mt);
-  ws.cap_Bp = round_up((int)B, 128);
-  ws.tmR_ready = false;
+  ws.slot_it = (int32_t*)(p + L.sit);
+  ws.slot_conv = (uint8_t*)(p + L.sconv);
   return ZBUS_OK;
 }
 
-// TMA map of the residual rows for the given operand type.
-zbus_status ensure_tmR(zbus_network net, bool bf16) {
-  Workspace& ws = net->ws;
-  if (ws.tmR_ready && ws.tmR_bf16 == bf16) return ZBUS_OK;
-  ZB_CHECK(make_tmap_2d(&ws.tmR, ws.R, bf16, (uint64_t)k_pad_tc(net), (uint64_t)ws.cap_Bp, 64, 128));
-  ws.tmR_bf16 = bf16;
-  ws.tmR_ready = true;
-  return ZBUS_OK;
-}
+namespace {
 
 bool use_graphs() {
   const char* e = std::getenv("ZBUS_NO_GRAPH");
   return !(e && e[0] == '1');
 }
 
-const MixedOperands& operands(zbus_network net, int32_t precision) {
-  return net->mixed[precision == ZBUS_MIXED_BF16X2 ? 1 : 0];
-}
-
-int ntn_for(zbus_network net, int32_t precision) {
-  if (precision == ZBUS_FP64) return net->n_pad / F64_BN;
-  const MixedOperands& op = operands(net, precision);
-  return op.N_pad / op.BN;
-}
-
-int contraction_grid(zbus_network net, int32_t precision, int64_t B) {
-  if (precision == ZBUS_FP64) return gemm_f64_grid((int)B, net->n_pad);
-  return tc_grid(operands(net, precision), (int)B);
-}
-
-// One sweep of the chosen method on stream st (up to three kernels).
-zbus_status enqueue_sweep(zbus_network net, int32_t precision, int64_t B, int grid,
-                          cudaGraphConditionalHandle h, bool use_handle, cudaStream_t st,
-                          cudaEvent_t* ev = nullptr) {
+// One sweep of the plain FP64 method on stream st (optionally bracketed by
+// events for the profile mode).
+zbus_status enqueue_sweep_f64(zbus_network net, int64_t B, int grid, cudaGraphConditionalHandle h,
+                              bool use_handle, cudaStream_t st, cudaEvent_t* ev = nullptr) {
   if (ev) ZB_CUDA(cudaEventRecord(ev[0], st));
-  if (precision == ZBUS_FP64) {
-    launch_currents_f64(net->ws.ctx, net->n, net->n_pad, (int)B, st);
-    if (ev) ZB_CUDA(cudaEventRecord(ev[1], st));
-    launch_gemm_f64(net->ws.ctx, net->Zr, net->Zi, net->Zs, net->w, net->n, net->n_pad, grid, st);
-  } else {
-    const MixedOperands& op = operands(net, precision);
-    ZB_CHECK(launch_residual_mixed(net, op, (int)B, net->ws.R, net->ws.rinv, st));
-    if (ev) ZB_CUDA(cudaEventRecord(ev[1], st));
-    ZB_CHECK(launch_contract_tc(net, op, net->ws.tmR, net->ws.rinv, grid, st));
-  }
+  launch_currents_f64(net->ws.ctx, net->n, net->n_pad, (int)B, st);
+  if (ev) ZB_CUDA(cudaEventRecord(ev[1], st));
+  launch_gemm_f64(net->ws.ctx, net->Zr, net->Zi, net->Zs, net->w, net->n, net->n_pad, grid, st);
   if (ev) ZB_CUDA(cudaEventRecord(ev[2], st));
-  if (precision == ZBUS_FP64)
-    launch_converge(net->ws.ctx, (int)B, h, use_handle, st);
-  else
-    launch_converge_mixed(net->ws.ctx, (int)B, h, use_handle, st);
+  launch_converge(net->ws.ctx, (int)B, h, use_handle, st);
   if (ev) ZB_CUDA(cudaEventRecord(ev[3], st));
   return ZBUS_OK;
 }
 
-zbus_status get_loop_graph(zbus_network net, int64_t B, int32_t precision, GraphEntry** out) {
+zbus_status get_loop_graph(zbus_network net, int64_t B, GraphEntry** out) {
   for (auto& g : net->graphs)
-    if (g.B == B && g.precision == precision) {
+    if (g.B == B) {
       *out = &g;
       return ZBUS_OK;
     }
   GraphEntry e;
   e.B = B;
-  e.precision = precision;
-  e.grid_gemm = contraction_grid(net, precision, B);
+  e.precision = ZBUS_FP64;
+  e.grid_gemm = gemm_f64_grid((int)B, net->n_pad);
   if (!net->cap_stream) ZB_CUDA(cudaStreamCreateWithFlags(&net->cap_stream, cudaStreamNonBlocking));
   ZB_CUDA(cudaGraphCreate(&e.graph, 0));
   cudaGraphConditionalHandle h;
@@ -204,7 +182,7 @@ zbus_status get_loop_graph(zbus_network net, int64_t B, int32_t precision, Graph
   cudaGraph_t body = cp.conditional.phGraph_out[0];
   ZB_CUDA(cudaStreamBeginCaptureToGraph(net->cap_stream, body, nullptr, nullptr, 0,
                                         cudaStreamCaptureModeThreadLocal));
-  zbus_status s = enqueue_sweep(net, precision, B, e.grid_gemm, h, true, net->cap_stream);
+  zbus_status s = enqueue_sweep_f64(net, B, e.grid_gemm, h, true, net->cap_stream);
   cudaGraph_t captured = nullptr;
   cudaError_t ce = cudaStreamEndCapture(net->cap_stream, &captured);
   if (s != ZBUS_OK || ce != cudaSuccess) {
@@ -219,6 +197,75 @@ zbus_status get_loop_graph(zbus_network net, int64_t B, int32_t precision, Graph
   }
   net->graphs.push_back(e);
   *out = &net->graphs.back();
+  return ZBUS_OK;
+}
+
+// Profile buffers (events, per-sweep active counts) for up to max_iter sweeps.
+zbus_status ensure_profile(zbus_network net, int32_t max_iter) {
+  Profile& P = net->prof;
+  if (P.cap >= max_iter) return ZBUS_OK;
+  for (auto e : P.ev) cudaEventDestroy(e);
+  P.ev.clear();
+  cudaFree(P.d_hist);
+  P.d_hist = nullptr;
+  P.cap = 0;
+  ZB_CUDA(cudaMalloc((void**)&P.d_hist, (size_t)max_iter * sizeof(int32_t)));
+  P.ev.resize((size_t)4 * max_iter);
+  for (auto& e : P.ev) ZB_CUDA(cudaEventCreate(&e));
+  P.cap = max_iter;
+  return ZBUS_OK;
+}
+
+// Groups of the batched entry point, keyed by their networks, sizes, precision.
+std::vector<Group*> g_batch_groups;
+
+void drop_groups_of(zbus_network net) {
+  for (size_t i = 0; i < g_batch_groups.size();) {
+    Group* g = g_batch_groups[i];
+    if (std::find(g->nets.begin(), g->nets.end(), net) != g->nets.end()) {
+      group_free(g);
+      delete g;
+      g_batch_groups.erase(g_batch_groups.begin() + i);
+    } else {
+      ++i;
+    }
+  }
+}
+
+bool group_current(const Group* g, const std::vector<zbus_network>& nets,
+                   const std::vector<int64_t>& Bs, int32_t precision) {
+  if (!g || g->precision != precision || g->nets != nets) return false;
+  if (g->tune_gen != tune_generation()) return false;
+  for (size_t k = 0; k < nets.size(); ++k)
+    if (g->ws_gen[k] != nets[k]->ws.gen || g->h_items[k].Bp < Bs[k]) return false;
+  return true;
+}
+
+// Run a group of feeders from their admissions to their results on stream st.
+zbus_status run_group(Group* g, const std::vector<zbus_network>& nets, const std::vector<int64_t>& Bs,
+                      const std::vector<const double*>& Sw, const std::vector<const double*>& Sd,
+                      const std::vector<const double*>& V0, const std::vector<double*>& Vout,
+                      const std::vector<int32_t*>& iters, const std::vector<uint8_t*>& conv,
+                      double tol, int32_t max_iter, const zbus_solve_opts& o, cudaStream_t st) {
+  const double mtol = o.mismatch_tol > 0 ? o.mismatch_tol : 1e-6;
+  ZB_CHECK(group_reset(g, st));
+  for (size_t k = 0; k < nets.size(); ++k)
+    ZB_CHECK(group_admit(g, (int)k, 0, Bs[k], V0[k], Sw[k], Sd[k], st));
+  zbus_network pn = nets[0];
+  if (o.profile == 1) {
+    ZB_CHECK(ensure_profile(pn, max_iter));
+    ZB_CUDA(cudaMemsetAsync(pn->prof.d_hist, 0, (size_t)max_iter * sizeof(int32_t), st));
+    ZB_CHECK(group_start(g, tol, max_iter, o.conv_rule, pn->prof.d_hist, max_iter, st));
+    for (int k = 0; k < max_iter; ++k)
+      ZB_CHECK(group_sweep(g, 0, false, st, &pn->prof.ev[(size_t)4 * k]));
+    pn->prof.sweeps = max_iter;
+  } else {
+    ZB_CHECK(group_start(g, tol, max_iter, o.conv_rule, nullptr, 0, st));
+    ZB_CHECK(group_run(g, st));
+  }
+  for (size_t k = 0; k < nets.size(); ++k)
+    ZB_CHECK(group_collect(g, (int)k, 0, Bs[k], Vout[k], iters[k], conv[k], Sw[k], Sd[k], mtol,
+                           k == 0 ? nets[k]->ws.mm : nullptr, st));
   return ZBUS_OK;
 }
 
@@ -312,6 +359,11 @@ zbus_status zbus_network_create(int32_t n_total, int64_t nnz, const int32_t* row
 void zbus_network_destroy(zbus_network net) {
   if (!net) return;
   drop_graphs(net);
+  drop_groups_of(net);
+  if (net->group1) {
+    group_free(net->group1);
+    delete net->group1;
+  }
   if (net->cap_stream) cudaStreamDestroy(net->cap_stream);
   for (auto e : net->prof.ev) cudaEventDestroy(e);
   cudaFree(net->prof.d_hist);
@@ -357,10 +409,7 @@ zbus_status zbus_network_reserve(zbus_network net, int64_t B, int32_t precision)
     return fail(ZBUS_ERR_ARG, "unknown precision");
   ZB_CHECK(check_device(net));
   ZB_CHECK(ensure_workspace(net, B));
-  if (precision != ZBUS_FP64) {
-    ZB_CHECK(prepare_mixed(net, precision, nullptr));
-    ZB_CHECK(ensure_tmR(net, precision == ZBUS_MIXED_BF16X2));
-  }
+  if (precision != ZBUS_FP64) ZB_CHECK(prepare_mixed(net, precision, nullptr));
   return ZBUS_OK;
 }
 
@@ -388,10 +437,13 @@ zbus_status zbus_solve(zbus_network net, int64_t B, const double* S_wye, const d
   ZB_CHECK(check_device(net));
   cudaStream_t st = (cudaStream_t)cuda_stream;
   ZB_CHECK(ensure_workspace(net, B));
-  const bool mixed = o.precision != ZBUS_FP64;
-  if (mixed) {
-    ZB_CHECK(prepare_mixed(net, o.precision, st));
-    ZB_CHECK(ensure_tmR(net, o.precision == ZBUS_MIXED_BF16X2));
+  if (o.precision != ZBUS_FP64) {
+    // mixed precision: a group of one feeder
+    if (!net->group1) net->group1 = new Group();
+    if (!group_current(net->group1, {net}, {B}, o.precision))
+      ZB_CHECK(group_build(net->group1, {net}, {B}, o.precision, st));
+    return run_group(net->group1, {net}, {B}, {S_wye}, {S_delta}, {V_init}, {V_out}, {iters},
+                     {converged}, tol, max_iter, o, st);
   }
 
   SolveCtx h;
@@ -404,18 +456,6 @@ zbus_status zbus_solve(zbus_network net, int64_t B, const double* S_wye, const d
   h.conv = converged;
   h.list = net->ws.list;
   h.keep = net->ws.keep;
-  if (mixed) {
-    h.Vh = net->ws.Vh;
-    h.Vl = net->ws.Vl;
-    h.Swf = S_wye ? net->ws.Swf : nullptr;
-    h.Sdf = S_delta ? net->ws.Sdf : nullptr;
-    h.st = net->ws.st;
-    h.amax_prev = net->ws.amax;
-    h.amax_cur = net->ws.amax + net->ws.cap_Bp;
-    h.B_pad = round_up((int)B, 128);
-    h.mt_list = net->ws.mt;
-    h.mt_flag = (uint32_t*)(net->ws.mt + net->ws.cap_Bp / 128);
-  }
   h.part = net->ws.part;
   h.Iop = net->ws.Iop;
   h.tol = tol;
@@ -423,49 +463,100 @@ zbus_status zbus_solve(zbus_network net, int64_t B, const double* S_wye, const d
   h.B = (int32_t)B;
   h.max_iter = max_iter;
   h.rule = o.conv_rule;
-  h.ntn = ntn_for(net, o.precision);
+  h.ntn = net->n_pad / F64_BN;
+  const int grid = gemm_f64_grid((int)B, net->n_pad);
   if (o.profile == 1) {
+    ZB_CHECK(ensure_profile(net, max_iter));
     Profile& P = net->prof;
-    if (P.cap < max_iter) {
-      for (auto e : P.ev) cudaEventDestroy(e);
-      P.ev.clear();
-      cudaFree(P.d_hist);
-      P.d_hist = nullptr;
-      P.cap = 0;
-      ZB_CUDA(cudaMalloc((void**)&P.d_hist, (size_t)max_iter * sizeof(int32_t)));
-      P.ev.resize((size_t)4 * max_iter);
-      for (auto& e : P.ev) ZB_CUDA(cudaEventCreate(&e));
-      P.cap = max_iter;
-    }
     ZB_CUDA(cudaMemsetAsync(P.d_hist, 0, (size_t)max_iter * sizeof(int32_t), st));
     h.hist = P.d_hist;
     h.hist_n = max_iter;
     launch_init(net->ws.ctx, h, net->w, net->n, (int)B, st);
-    if (mixed) launch_init_df(net->ws.ctx, net->n, (int)B, h.B_pad, st);
-    const int grid = contraction_grid(net, o.precision, B);
     for (int k = 0; k < max_iter; ++k)
-      ZB_CHECK(enqueue_sweep(net, o.precision, B, grid, 0, false, st, &P.ev[(size_t)4 * k]));
+      ZB_CHECK(enqueue_sweep_f64(net, B, grid, 0, false, st, &P.ev[(size_t)4 * k]));
     P.sweeps = max_iter;
   } else {
     launch_init(net->ws.ctx, h, net->w, net->n, (int)B, st);
-    if (mixed) launch_init_df(net->ws.ctx, net->n, (int)B, h.B_pad, st);
     ZB_CUDA(cudaGetLastError());
     if (use_graphs()) {
       GraphEntry* g = nullptr;
-      ZB_CHECK(get_loop_graph(net, B, o.precision, &g));
+      ZB_CHECK(get_loop_graph(net, B, &g));
       ZB_CUDA(cudaGraphLaunch(g->exec, st));
     } else {
-      const int grid = contraction_grid(net, o.precision, B);
-      for (int k = 0; k < max_iter; ++k)
-        ZB_CHECK(enqueue_sweep(net, o.precision, B, grid, 0, false, st));
+      for (int k = 0; k < max_iter; ++k) ZB_CHECK(enqueue_sweep_f64(net, B, grid, 0, false, st));
     }
-  }
-  if (mixed) {
-    launch_merge_df(net->ws.ctx, net->n, (int)B, h.B_pad, st);
-    ZB_CHECK(launch_final_check(net, (int)B, net->ws.mm, st));
   }
   ZB_CUDA(cudaGetLastError());
   return ZBUS_OK;
+}
+
+zbus_status zbus_solve_batched(const zbus_batch_item* items, int32_t n_items, double tol,
+                               int32_t max_iter, const zbus_solve_opts* opts, void* cuda_stream) {
+  g_last_error.clear();
+  if (n_items < 0 || (n_items > 0 && !items)) return fail(ZBUS_ERR_ARG, "items is NULL");
+  if (n_items == 0) return ZBUS_OK;
+  if (!(tol >= 0.0) || !std::isfinite(tol)) return fail(ZBUS_ERR_ARG, "tol must be finite, >= 0");
+  if (max_iter < 1) return fail(ZBUS_ERR_ARG, "max_iter must be >= 1");
+  zbus_solve_opts o;
+  zbus_solve_opts_default(&o);
+  if (opts) o = *opts;
+  if (o.conv_rule != ZBUS_CONV_MAXABS && o.conv_rule != ZBUS_CONV_SUMMAG)
+    return fail(ZBUS_ERR_ARG, "unknown convergence rule");
+  if (o.precision != ZBUS_FP64 && o.precision != ZBUS_MIXED_BF16X2 &&
+      o.precision != ZBUS_MIXED_FP16_SCALED)
+    return fail(ZBUS_ERR_ARG, "unknown precision");
+  std::vector<zbus_network> nets;
+  std::vector<int64_t> Bs;
+  std::vector<const double*> Sw, Sd, V0;
+  std::vector<double*> Vo;
+  std::vector<int32_t*> it;
+  std::vector<uint8_t*> cv;
+  std::set<zbus_network> seen;
+  for (int32_t k = 0; k < n_items; ++k) {
+    const zbus_batch_item& x = items[k];
+    if (!x.net) return fail(ZBUS_ERR_ARG, "item " + std::to_string(k) + ": network is NULL");
+    if (!seen.insert(x.net).second)
+      return fail(ZBUS_ERR_ARG, "item " + std::to_string(k) + ": a network may appear once");
+    if (x.B < 0 || x.B > INT32_MAX / 4) return fail(ZBUS_ERR_ARG, "item B out of range");
+    if (x.B > 0 && (!x.V_out || !x.iters || !x.converged))
+      return fail(ZBUS_ERR_ARG, "item " + std::to_string(k) + ": an output pointer is NULL");
+    if (x.S_delta && !x.net->bus_aligned)
+      return fail(ZBUS_ERR_ARG, "delta loads need three unknowns per bus (n % 3 == 0)");
+    ZB_CHECK(check_device(x.net));
+    if (x.B == 0) continue;
+    nets.push_back(x.net);
+    Bs.push_back(x.B);
+    Sw.push_back(x.S_wye);
+    Sd.push_back(x.S_delta);
+    V0.push_back(x.V_init);
+    Vo.push_back(x.V_out);
+    it.push_back(x.iters);
+    cv.push_back(x.converged);
+  }
+  if (nets.empty()) return ZBUS_OK;
+  cudaStream_t st = (cudaStream_t)cuda_stream;
+  if (o.precision == ZBUS_FP64) {
+    // the plain method runs feeder after feeder
+    for (size_t k = 0; k < nets.size(); ++k)
+      ZB_CHECK(zbus_solve(nets[k], Bs[k], Sw[k], Sd[k], V0[k], tol, max_iter, &o, Vo[k], it[k],
+                          cv[k], cuda_stream));
+    return ZBUS_OK;
+  }
+  for (size_t k = 0; k < nets.size(); ++k) ZB_CHECK(ensure_workspace(nets[k], Bs[k]));
+  Group* g = nullptr;
+  for (Group* c : g_batch_groups)
+    if (group_current(c, nets, Bs, o.precision)) g = c;
+  if (!g) {
+    g = new Group();
+    zbus_status s = group_build(g, nets, Bs, o.precision, st);
+    if (s != ZBUS_OK) {
+      group_free(g);
+      delete g;
+      return s;
+    }
+    g_batch_groups.push_back(g);
+  }
+  return run_group(g, nets, Bs, Sw, Sd, V0, Vo, it, cv, tol, max_iter, o, st);
 }
 
 zbus_status zbus_last_profile(zbus_network net, int32_t max_n, float* ms, int32_t* active,

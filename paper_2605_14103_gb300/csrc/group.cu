@@ -1,0 +1,966 @@
+// Grouped mixed-precision defect sweep (Sec. II-B fixed point in the form
+// v <- v + Z_lp r(v)), for one or many feeders at once.
+//
+// Per sweep, four kernels cover every item of the group:
+//   k_residual_group   r(v) in double-float over 3x3 bus blocks, one slot per
+//                      lane, written as scaled FP16 / BF16 rows of R
+//   k_contract_group   persistent tcgen05 contraction D = R Z_emb^T over the
+//                      list of (item, 128-slot tile, N-tile) with an active
+//                      slot; double-float epilogue v += D and step partials
+//   k_decide_group     per-slot stop test (own sweep counter per slot)
+//   k_finish_group     list of tiles for the next sweep, loop condition
+// Slots are admitted (k_slot_init) and collected (k_slot_merge + k_check, the
+// FP64 power-mismatch test) outside the loop.
+#include <cuda_bf16.h>
+#include <cuda_fp16.h>
+
+#include <algorithm>
+#include <cstring>
+
+#include "df.cuh"
+#include "group.cuh"
+#include "loads.cuh"
+#include "tc_ptx.cuh"
+
+namespace zbus {
+namespace {
+
+using namespace tc;
+
+constexpr int RES_WARPS = 4;
+constexpr int CHUNK_BUS = 4;
+constexpr int CHUNK_ROWS = 3 * CHUNK_BUS;
+constexpr int DEC_THREADS = 256;
+
+// Item owning global index x, for a non-decreasing begin field.
+__device__ __forceinline__ int find_item(const ItemDesc* items, int n_items, int x, int which) {
+  int lo = 0, hi = n_items - 1;
+  while (lo < hi) {
+    const int mid = (lo + hi + 1) >> 1;
+    const int v = which == 0 ? items[mid].res_begin
+                             : (which == 1 ? items[mid].dec_begin : items[mid].mt_begin);
+    if (v <= x) lo = mid;
+    else hi = mid - 1;
+  }
+  return lo;
+}
+
+// ---------------------------------------------------------------------------
+// Admission: slots [s0, s0 + B) of item k take v^0 (V0, else w) and the loads
+// (FP64, [B][n]), transposed to the scenario-minor state through 32 x 32
+// shared-memory tiles.  Admitted slots become active.
+// ---------------------------------------------------------------------------
+__global__ void k_slot_init(GroupState* __restrict__ gs, const ItemDesc* __restrict__ items, int k,
+                            int s0, int B, const double2* __restrict__ V0,
+                            const double2* __restrict__ w, const double2* __restrict__ Sw,
+                            const double2* __restrict__ Sd) {
+  __shared__ double2 tv[32][33];
+  __shared__ double2 tw[32][33];
+  __shared__ double2 td[32][33];
+  const ItemDesc it = items[k];
+  const int n = it.n, Bp = it.Bp;
+  const int j0 = blockIdx.x * 32, b0 = blockIdx.y * 32;
+  const int tx = threadIdx.x, ty = threadIdx.y;
+  for (int r = ty; r < 32; r += 8) {
+    const int b = b0 + r, j = j0 + tx;
+    double2 v = make_double2(0.0, 0.0), a = v, d = v;
+    if (b < B && j < n) {
+      const int64_t g = (int64_t)b * n + j;
+      v = V0 ? V0[g] : w[j];
+      if (Sw) a = Sw[g];
+      if (Sd) d = Sd[g];
+    }
+    tv[r][tx] = v;
+    tw[r][tx] = a;
+    td[r][tx] = d;
+  }
+  __syncthreads();
+  for (int r = ty; r < 32; r += 8) {
+    const int j = j0 + r, b = b0 + tx;
+    if (j < n && b < B) {
+      const int64_t g = (int64_t)j * Bp + s0 + b;
+      const double2 v = tv[tx][r];
+      const float2 xr = df_split(v.x), xi = df_split(v.y);
+      it.Vh[g] = make_float2(xr.x, xi.x);
+      it.Vl[g] = make_float2(xr.y, xi.y);
+      it.Swf[g] = make_float2(__double2float_rn(tw[tx][r].x), __double2float_rn(tw[tx][r].y));
+      it.Sdf[g] = make_float2(__double2float_rn(td[tx][r].x), __double2float_rn(td[tx][r].y));
+    }
+  }
+  if (blockIdx.x == 0 && ty == 0) {
+    const int b = b0 + tx;
+    const bool adm = b < B;
+    if (adm) {
+      const int slot = s0 + b;
+      it.st[slot] = SLOT_ACTIVE;
+      it.it[slot] = 0;
+      it.conv[slot] = 0;
+      it.amax[slot] = 1.0f;
+      it.amax[Bp + slot] = 0.0f;
+      atomicOr(&it.mt_flag[slot / 128], 1u);
+    }
+    const unsigned bal = __ballot_sync(0xffffffffu, adm);
+    if (tx == 0) atomicAdd(&gs->active_next, __popc(bal));
+  }
+}
+
+// Every slot of every item free, tile flags cleared, loop state zeroed.
+__global__ void k_group_reset(GroupState* __restrict__ gs, const ItemDesc* __restrict__ items,
+                              int n_items) {
+  for (int k = blockIdx.y; k < n_items; k += gridDim.y) {
+    const ItemDesc it = items[k];
+    for (int b = blockIdx.x * blockDim.x + threadIdx.x; b < it.Bp; b += gridDim.x * blockDim.x) {
+      it.st[b] = SLOT_FREE;
+      if ((b & 127) == 0) it.mt_flag[b / 128] = 0;
+    }
+  }
+  if (blockIdx.x == 0 && blockIdx.y == 0 && threadIdx.x == 0) {
+    gs->active = 0;
+    gs->active_next = 0;
+    gs->sweep = 0;
+    gs->err = 0;
+    gs->n_tiles = 0;
+  }
+}
+
+__global__ void k_group_params(GroupState* gs, double tol, int max_iter, int rule, int32_t* hist,
+                               int hist_n) {
+  gs->tol = tol;
+  gs->max_iter = max_iter;
+  gs->rule = rule;
+  gs->hist = hist;
+  gs->hist_n = hist_n;
+  gs->sweep = 0;
+  gs->err = 0;
+}
+
+// ---------------------------------------------------------------------------
+// Defect residual, one slot per lane, double-float over 3x3 bus blocks:
+//   r_j = i_j(v) - sum_b Y_LL[a][b] v_b - ys_j        (bus a holds rows 3a..3a+2)
+// The admittance sum (terms ~1e3 cancelling to ~1e-10 near the solution) runs
+// in double-float with the blocks loaded once per warp for 32 slots; the load
+// current (~1e-2, no cancellation) in FP32 from the hi part.  R[b][2j],
+// R[b][2j+1] = round(c_b Re r_j), round(c_b Im r_j) with c_b = 2^(12 -
+// floor(log2 amax_prev_b)) from the previous sweep's max |r| (the residual
+// shrinks from sweep to sweep; values beyond the FP16 range saturate, which
+// only shortens that step: the next residual is exact again).  Each warp
+// covers 4 buses (12 rows) per chunk and writes them through a shared-memory
+// transpose; rows n .. K_pad/2 - 1 are written as zeros.
+// ---------------------------------------------------------------------------
+template <bool BF>
+__global__ void __launch_bounds__(RES_WARPS * 32)
+k_residual_group(GroupState* __restrict__ gs, const ItemDesc* __restrict__ items) {
+  __shared__ uint32_t stage[RES_WARPS][CHUNK_ROWS][32];
+  __shared__ float sred[RES_WARPS][32];
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int k = find_item(items, gs->n_items, blockIdx.x, 0);
+  const ItemDesc& it = items[k];
+  const int local = blockIdx.x - it.res_begin;
+  const int split = it.res_split;
+  const int grp = local / split, ys = local % split;
+  const int Bp = it.Bp;
+  const int b = grp * 32 + lane;
+  const bool act = it.st[b] == SLOT_ACTIVE;
+  if (!__syncthreads_or(act)) return;   // all 32 slots of this group are idle
+  const float ap = it.amax[b];
+  int e = (ap > 0.f && ap <= 3.0e38f) ? 12 - ilogbf(ap) : 12;
+  e = max(-126, min(126, e));
+  const float c = ldexpf(1.f, e);
+  if (ys == 0 && warp == 0) it.rinv[b] = ldexpf(1.f, -e);
+  const float2* __restrict__ Vh = it.Vh;
+  const float2* __restrict__ Vl = it.Vl;
+  const float2* __restrict__ Sw = it.Swf;
+  const float2* __restrict__ Sd = it.Sdf;
+  const int32_t* __restrict__ bptr = it.bsr_ptr;
+  const int32_t* __restrict__ bcol = it.bsr_col;
+  const float4* __restrict__ bval = it.bsr_df;
+  const float4* __restrict__ ys4 = it.ys_df;
+  const int nb = it.nbus;
+  const int rows_pad = it.K_pad >> 1;
+  const int nchunks = (rows_pad + CHUNK_ROWS - 1) / CHUNK_ROWS;
+  float amax = 0.f;
+  for (int ch = ys * RES_WARPS + warp; ch < nchunks; ch += split * RES_WARPS) {
+    for (int q = 0; q < CHUNK_BUS; ++q) {
+      const int a = ch * CHUNK_BUS + q;
+      float2 r[3] = {make_float2(0.f, 0.f), make_float2(0.f, 0.f), make_float2(0.f, 0.f)};
+      if (a < nb && act) {
+        float2 vv[3], sw[3], sd[3], inj[3];
+#pragma unroll
+        for (int p = 0; p < 3; ++p) {
+          const int64_t g = (int64_t)(3 * a + p) * Bp + b;
+          vv[p] = Vh[g];
+          sw[p] = Sw[g];
+          sd[p] = Sd[g];
+        }
+        bus_injection_f(vv, sw, sd, 3, inj);
+        float ah[3][2], al[3][2];   // accumulators (re, im) per phase, hi / lo
+#pragma unroll
+        for (int p = 0; p < 3; ++p) {
+          const float4 y0 = ys4[3 * a + p];
+          ah[p][0] = y0.x; al[p][0] = y0.y; ah[p][1] = y0.z; al[p][1] = y0.w;
+        }
+        for (int t = bptr[a]; t < bptr[a + 1]; ++t) {
+          const int cb = bcol[t];
+          float2 xh[3], xl[3];
+#pragma unroll
+          for (int q2 = 0; q2 < 3; ++q2) {
+            const int64_t g = (int64_t)(3 * cb + q2) * Bp + b;
+            xh[q2] = Vh[g];
+            xl[q2] = Vl[g];
+          }
+          const float4* yb = bval + (int64_t)t * 9;
+#pragma unroll
+          for (int p = 0; p < 3; ++p) {
+#pragma unroll
+            for (int q2 = 0; q2 < 3; ++q2) {
+              const float4 y = yb[p * 3 + q2];
+              df_mac(ah[p][0], al[p][0], y.x, y.y, xh[q2].x, xl[q2].x);     // + yr vr
+              df_mac(ah[p][0], al[p][0], -y.z, -y.w, xh[q2].y, xl[q2].y);   // - yi vi
+              df_mac(ah[p][1], al[p][1], y.x, y.y, xh[q2].y, xl[q2].y);     // + yr vi
+              df_mac(ah[p][1], al[p][1], y.z, y.w, xh[q2].x, xl[q2].x);     // + yi vr
+            }
+          }
+        }
+#pragma unroll
+        for (int p = 0; p < 3; ++p) {
+          r[p] = make_float2(__fsub_rn(__fsub_rn(inj[p].x, ah[p][0]), al[p][0]),
+                             __fsub_rn(__fsub_rn(inj[p].y, ah[p][1]), al[p][1]));
+          const float m = fmaxf(fabsf(r[p].x), fabsf(r[p].y));
+          amax = (m == m) ? fmaxf(amax, m) : __int_as_float(0x7f800000);
+        }
+      }
+#pragma unroll
+      for (int p = 0; p < 3; ++p) {
+        float x = r[p].x * c, y = r[p].y * c;
+        uint32_t u;
+        if (BF) {
+          __nv_bfloat162 h = __floats2bfloat162_rn(x, y);
+          u = *reinterpret_cast<uint32_t*>(&h);
+        } else {
+          x = fminf(fmaxf(x, -65504.f), 65504.f);
+          y = fminf(fmaxf(y, -65504.f), 65504.f);
+          __half2 h = __floats2half2_rn(x, y);
+          u = *reinterpret_cast<uint32_t*>(&h);
+        }
+        stage[warp][3 * q + p][lane] = u;
+      }
+    }
+    __syncwarp();
+    if (act) {
+      // CHUNK_ROWS rows = CHUNK_ROWS / 4 16-byte stores into this slot's R row
+      uint4* dst = reinterpret_cast<uint4*>(reinterpret_cast<uint32_t*>(it.R) +
+                                            (int64_t)b * rows_pad + (int64_t)ch * CHUNK_ROWS);
+#pragma unroll
+      for (int v = 0; v < CHUNK_ROWS / 4; ++v) {
+        if (ch * CHUNK_ROWS + 4 * v < rows_pad)
+          dst[v] = make_uint4(stage[warp][4 * v][lane], stage[warp][4 * v + 1][lane],
+                              stage[warp][4 * v + 2][lane], stage[warp][4 * v + 3][lane]);
+      }
+    }
+    __syncwarp();
+  }
+  sred[warp][lane] = amax;
+  __syncthreads();
+  if (warp == 0 && act) {
+    float m = sred[0][lane];
+    for (int w = 1; w < RES_WARPS; ++w) m = fmaxf(m, sred[w][lane]);
+    atomicMax(reinterpret_cast<int*>(&it.amax[Bp + b]), __float_as_int(m));
+  }
+}
+
+// ---------------------------------------------------------------------------
+// tcgen05 contraction, persistent: one CTA per SM walks the tile list (tiles
+// of one 128-slot group are consecutive, N fastest, so CTAs running together
+// share the R tile in L2).  Each tile is a 128 x BN block of D = R Z_emb^T
+// over K_pad of its item in steps of 64 (128-byte swizzled rows staged by
+// TMA).  Two tensor-memory accumulators (2 x BN columns) let the epilogue of
+// one tile overlap the MMAs of the next.  Warp roles: 0 = TMA producer,
+// 1 = TMEM owner and MMA issuer, 2..5 = epilogue (warp w reads TMEM lanes
+// 32 (w % 4) .. + 31).  Barriers: full / empty per stage (TMA -> MMA -> TMA),
+// tfull / tempty per accumulator (MMA -> epilogue -> MMA).
+// ---------------------------------------------------------------------------
+template <int BN, int ZP, int STAGES, bool BF>
+__global__ void __launch_bounds__(TC_THREADS, 1)
+k_contract_group(GroupState* __restrict__ gs, const ItemDesc* __restrict__ items,
+                 const CUtensorMap* __restrict__ tmR, const CUtensorMap* __restrict__ tmZ0,
+                 const CUtensorMap* __restrict__ tmZ1) {
+  constexpr int A_BYTES = BM * BK * 2;
+  constexpr int B_BYTES = BN * BK * 2;
+  constexpr int STAGE_BYTES = A_BYTES + ZP * B_BYTES;
+  extern __shared__ uint8_t smem_raw[];
+  uint8_t* smem = (uint8_t*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
+  uint64_t* full = (uint64_t*)(smem + STAGES * STAGE_BYTES);
+  uint64_t* empty = full + STAGES;
+  uint64_t* tfull = empty + STAGES;
+  uint64_t* tempty = tfull + 2;
+  uint32_t* tmem_holder = (uint32_t*)(tempty + 2);
+
+  const int total = gs->n_tiles;
+  if ((int)blockIdx.x >= total) return;   // whole block, before any barrier
+  const uint64_t* __restrict__ tiles = gs->tiles;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < STAGES; ++s) {
+      mbar_init(&full[s], 1);
+      mbar_init(&empty[s], 1);
+    }
+    for (int u = 0; u < 2; ++u) {
+      mbar_init(&tfull[u], 1);
+      mbar_init(&tempty[u], 4);
+    }
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  if (warp == 1) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
+                     su32(tmem_holder)),
+                 "r"((uint32_t)(2 * BN)));
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+  }
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem = *tmem_holder;
+
+  if (warp == 0) {
+    if (lane == 0) {
+      uint32_t kc = 0;
+      bool ok = true;
+      for (int g = blockIdx.x; g < total && ok; g += gridDim.x) {
+        const uint64_t e = tiles[g];
+        const int k = (int)(e >> 32), mt = (int)((e >> 16) & 0xFFFF), nt = (int)(e & 0xFFFF);
+        const int num_kb = items[k].K_pad / BK;
+        const CUtensorMap* mR = tmR + k;
+        const CUtensorMap* mZ0 = tmZ0 + k;
+        const CUtensorMap* mZ1 = tmZ1 + k;
+        for (int kb = 0; kb < num_kb; ++kb, ++kc) {
+          const int s = kc % STAGES;
+          const uint32_t round = kc / STAGES;
+          if (!mbar_wait(&empty[s], (round & 1) ^ 1)) {
+            atomicCAS(&gs->err, 0, 101);
+            ok = false;
+            break;
+          }
+          uint8_t* st = smem + s * STAGE_BYTES;
+          mbar_expect_tx(&full[s], STAGE_BYTES);
+          tma_load_2d(st, mR, &full[s], kb * BK, mt * BM);
+          tma_load_2d(st + A_BYTES, mZ0, &full[s], kb * BK, nt * BN);
+          if (ZP == 2) tma_load_2d(st + A_BYTES + B_BYTES, mZ1, &full[s], kb * BK, nt * BN);
+        }
+      }
+    }
+  } else if (warp == 1) {
+    if (lane == 0) {
+      // kind::f16 instruction descriptor: D f32, A/B f16 or bf16, both K-major
+      const uint32_t idesc = (1u << 4) | ((BF ? 1u : 0u) << 7) | ((BF ? 1u : 0u) << 10) |
+                             ((uint32_t)(BN >> 3) << 17) | ((uint32_t)(BM >> 4) << 24);
+      uint32_t kc = 0;
+      bool ok = true;
+      int i = 0;
+      for (int g = blockIdx.x; g < total && ok; g += gridDim.x, ++i) {
+        const int k = (int)(tiles[g] >> 32);
+        const int num_kb = items[k].K_pad / BK;
+        const int buf = i & 1;
+        const uint32_t use = (uint32_t)(i >> 1);
+        if (!mbar_wait(&tempty[buf], (use & 1) ^ 1)) {
+          atomicCAS(&gs->err, 0, 104);
+          break;
+        }
+        tc_fence_after();
+        const uint32_t d = tmem + (uint32_t)(buf * BN);
+        for (int kb = 0; kb < num_kb; ++kb, ++kc) {
+          const int s = kc % STAGES;
+          const uint32_t round = kc / STAGES;
+          if (!mbar_wait(&full[s], round & 1)) {
+            atomicCAS(&gs->err, 0, 102);
+            ok = false;
+            break;
+          }
+          tc_fence_after();
+          const uint32_t a0 = su32(smem + s * STAGE_BYTES);
+#pragma unroll
+          for (int kk = 0; kk < BK / 16; ++kk) {
+#pragma unroll
+            for (int p = 0; p < ZP; ++p) {
+              const uint32_t b0 = a0 + A_BYTES + p * B_BYTES;
+              umma_f16(d, sw128_desc(a0 + kk * 32), sw128_desc(b0 + kk * 32), idesc,
+                       (kb | kk | p) != 0 ? 1u : 0u);
+            }
+          }
+          umma_commit(&empty[s]);
+        }
+        if (ok) umma_commit(&tfull[buf]);
+      }
+    }
+  } else {
+    const int q = warp & 3;
+    const int row = q * 32 + lane;
+    const bool summag = gs->rule == ZBUS_CONV_SUMMAG;
+    int i = 0;
+    for (int g = blockIdx.x; g < total; g += gridDim.x, ++i) {
+      const uint64_t e = tiles[g];
+      const int k = (int)(e >> 32), mt = (int)((e >> 16) & 0xFFFF), nt = (int)(e & 0xFFFF);
+      const ItemDesc& it = items[k];
+      const int buf = i & 1;
+      const uint32_t use = (uint32_t)(i >> 1);
+      const bool ok = mbar_wait(&tfull[buf], use & 1);
+      tc_fence_after();
+      if (!ok) {
+        if (lane == 0) atomicCAS(&gs->err, 0, 103);
+        break;
+      }
+      const int n = it.n, Bp = it.Bp, ntn = it.ntn;
+      const int b = mt * BM + row;
+      const bool valid = it.st[b] == SLOT_ACTIVE;
+      const float rs = valid ? it.rinv[b] : 0.f;
+      const float* __restrict__ zinv = it.zinv;
+      float2* Vh = it.Vh + b;
+      float2* Vl = it.Vl + b;
+      float dmax = 0.f, dsum = 0.f;
+#pragma unroll 1
+      for (int c = 0; c < BN / 32; ++c) {
+        float v[32];
+        tmem_ld32(tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)(buf * BN + c * 32), v);
+        if (c == BN / 32 - 1) {
+          // the accumulator is in registers now: hand the buffer back
+          tc_fence_before();
+          __syncwarp();
+          if (lane == 0) mbar_arrive(&tempty[buf]);
+        }
+        if (valid) {
+          const int i0 = (nt * BN + c * 32) >> 1;
+#pragma unroll
+          for (int t = 0; t < 16; ++t) {
+            const int oi = i0 + t;
+            if (oi < n) {
+              const float sc = rs * zinv[oi];
+              const float dr = v[2 * t] * sc, di = v[2 * t + 1] * sc;
+              const int64_t gi = (int64_t)oi * Bp;
+              const float2 h = Vh[gi], l = Vl[gi];
+              float sr, er, si, ei;
+              two_sum(h.x, dr, sr, er);
+              two_sum(h.y, di, si, ei);
+              float2 nh, nl;
+              fast_two_sum(sr, __fadd_rn(er, l.x), nh.x, nl.x);
+              fast_two_sum(si, __fadd_rn(ei, l.y), nh.y, nl.y);
+              Vh[gi] = nh;
+              Vl[gi] = nl;
+              float step = sqrtf(__fmaf_rn(dr, dr, di * di));
+              if (step != step) step = __int_as_float(0x7f800000);
+              dmax = fmaxf(dmax, step);
+              if (summag) {
+                // |v + d| - |v| = (2 Re(conj(v) d) + |d|^2) / (|v + d| + |v|)
+                const float o2 = __fmaf_rn(h.x, h.x, h.y * h.y);
+                const float n2 = __fmaf_rn(nh.x, nh.x, nh.y * nh.y);
+                dsum += (2.f * (h.x * dr + h.y * di) + dr * dr + di * di) /
+                        (sqrtf(n2) + sqrtf(o2));
+              }
+            }
+          }
+        }
+      }
+      if (valid) {
+        it.part[((int64_t)b * ntn + nt) * 2 + 0] = (double)dmax;
+        it.part[((int64_t)b * ntn + nt) * 2 + 1] = (double)dsum;
+      }
+    }
+  }
+  tc_fence_before();
+  __syncthreads();
+  if (warp == 1) {
+    tc_fence_after();
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem),
+                 "r"((uint32_t)(2 * BN)));
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Stop test, one thread per slot of every item: partials reduced in a fixed
+// order; a slot stops when its step meets tol (converged), is not finite or
+// reaches max_iter sweeps since its admission.
+// ---------------------------------------------------------------------------
+__global__ void __launch_bounds__(DEC_THREADS)
+k_decide_group(GroupState* __restrict__ gs, const ItemDesc* __restrict__ items) {
+  __shared__ int scount;
+  if (threadIdx.x == 0) scount = 0;
+  __syncthreads();
+  const int k = find_item(items, gs->n_items, blockIdx.x, 1);
+  const ItemDesc& it = items[k];
+  const int b = (blockIdx.x - it.dec_begin) * DEC_THREADS + threadIdx.x;
+  int keep = 0;
+  if (b < it.Bp && it.st[b] == SLOT_ACTIVE) {
+    const int sw = it.it[b] + 1;
+    it.it[b] = sw;
+    const int ntn = it.ntn;
+    const double* part = it.part + (int64_t)b * ntn * 2;
+    double dmax = 0.0, dsum = 0.0;
+    for (int t = 0; t < ntn; ++t) {
+      dmax = fmax(dmax, part[2 * t]);
+      dsum += part[2 * t + 1];
+    }
+    const double delta = gs->rule == ZBUS_CONV_SUMMAG ? fabs(dsum) : dmax;
+    if (!isfinite(delta)) {
+      it.conv[b] = 0;
+    } else if (delta <= gs->tol) {
+      it.conv[b] = 1;
+    } else if (sw < gs->max_iter) {
+      keep = 1;
+    }
+    if (keep) atomicOr(&it.mt_flag[b / 128], 1u);
+    else it.st[b] = SLOT_DONE;
+    it.amax[b] = it.amax[it.Bp + b];
+    it.amax[it.Bp + b] = 0.f;
+  }
+  const unsigned bal = __ballot_sync(0xffffffffu, keep);
+  if ((threadIdx.x & 31) == 0 && bal) atomicAdd(&scount, __popc(bal));
+  __syncthreads();
+  if (threadIdx.x == 0 && scount) atomicAdd(&gs->active_next, scount);
+}
+
+// ---------------------------------------------------------------------------
+// Sweep end (one block of 1024): the tile list of the next sweep (every
+// 128-slot tile flagged by the stop test, times its item's N-tiles, in a
+// stable order), the active count, the sweep counter and the graph's loop
+// condition.  initial = 1 builds the first list after the admissions.
+// ---------------------------------------------------------------------------
+__global__ void __launch_bounds__(1024)
+k_finish_group(GroupState* __restrict__ gs, const ItemDesc* __restrict__ items, int initial,
+               cudaGraphConditionalHandle h, int use_handle) {
+  __shared__ int swarp[32];
+  __shared__ int sbase, stotal;
+  const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
+  const int mt_total = gs->mt_total, n_items = gs->n_items;
+  uint64_t* tiles = gs->tiles;
+  if (tid == 0) sbase = 0;
+  __syncthreads();
+  for (int base = 0; base < mt_total; base += 1024) {
+    const int m = base + tid;
+    int cnt = 0, k = 0, lm = 0;
+    if (m < mt_total) {
+      k = find_item(items, n_items, m, 2);
+      lm = m - items[k].mt_begin;
+      if (items[k].mt_flag[lm]) cnt = items[k].ntn;
+      items[k].mt_flag[lm] = 0;
+    }
+    int incl = cnt;
+    for (int o = 1; o < 32; o <<= 1) {
+      const int y = __shfl_up_sync(0xffffffffu, incl, o);
+      if (lane >= o) incl += y;
+    }
+    if (lane == 31) swarp[wid] = incl;
+    __syncthreads();
+    if (wid == 0) {
+      const int x = swarp[lane];
+      int inc2 = x;
+      for (int o = 1; o < 32; o <<= 1) {
+        const int y = __shfl_up_sync(0xffffffffu, inc2, o);
+        if (lane >= o) inc2 += y;
+      }
+      swarp[lane] = inc2 - x;
+      if (lane == 31) stotal = inc2;
+    }
+    __syncthreads();
+    const int pos = sbase + swarp[wid] + incl - cnt;
+    for (int t = 0; t < cnt; ++t)
+      tiles[pos + t] = ((uint64_t)k << 32) | ((uint64_t)lm << 16) | (uint64_t)t;
+    __syncthreads();
+    if (tid == 0) sbase += stotal;
+    __syncthreads();
+  }
+  if (tid == 0) {
+    gs->n_tiles = sbase;
+    if (!initial && gs->hist && gs->sweep < gs->hist_n) gs->hist[gs->sweep] = gs->active;
+    const int c = gs->active_next;
+    gs->active = c;
+    gs->active_next = 0;
+    if (!initial) gs->sweep = gs->sweep + 1;
+    if (use_handle) cudaGraphSetConditional(h, c > 0 ? 1u : 0u);
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Collection: slots [s0, s0 + B) of item k merged into the FP64 output
+// [B][n], with their sweep counts and flags; the slots become free.
+// ---------------------------------------------------------------------------
+__global__ void k_slot_merge(const ItemDesc* __restrict__ items, int k, int s0, int B,
+                             double2* __restrict__ V, int32_t* __restrict__ iters,
+                             uint8_t* __restrict__ conv) {
+  __shared__ double2 t[32][33];
+  const ItemDesc it = items[k];
+  const int n = it.n, Bp = it.Bp;
+  const int j0 = blockIdx.x * 32, b0 = blockIdx.y * 32;
+  const int tx = threadIdx.x, ty = threadIdx.y;
+  for (int r = ty; r < 32; r += 8) {
+    const int j = j0 + r, b = b0 + tx;
+    double2 v = make_double2(0.0, 0.0);
+    if (j < n && b < B) {
+      const int64_t g = (int64_t)j * Bp + s0 + b;
+      const float2 h = it.Vh[g], l = it.Vl[g];
+      v = make_double2((double)h.x + (double)l.x, (double)h.y + (double)l.y);
+    }
+    t[tx][r] = v;
+  }
+  __syncthreads();
+  for (int r = ty; r < 32; r += 8) {
+    const int b = b0 + r, j = j0 + tx;
+    if (b < B && j < n) V[(int64_t)b * n + j] = t[r][tx];
+  }
+  if (blockIdx.x == 0 && ty == 0) {
+    const int b = b0 + tx;
+    if (b < B) {
+      iters[b] = it.it[s0 + b];
+      conv[b] = it.conv[s0 + b];
+      it.st[s0 + b] = SLOT_FREE;
+    }
+  }
+}
+
+// FP64 check of converged scenarios: max_j |v_j| |(Y_LL v + ys)_j - i_j(v)|
+// with the sparse admittance matrix; a flag above mtol is cleared.  One
+// block per scenario, v staged in shared memory (16 n bytes).
+__global__ void __launch_bounds__(256)
+k_check(const double2* __restrict__ V, const double2* __restrict__ Sw,
+        const double2* __restrict__ Sd, uint8_t* __restrict__ conv, int n,
+        const int32_t* __restrict__ ptr, const int32_t* __restrict__ col,
+        const double2* __restrict__ val, const double2* __restrict__ ys, double mtol,
+        double* mm_out) {
+  extern __shared__ double2 vsm[];
+  __shared__ double red[32];
+  const int b = blockIdx.x;
+  if (conv[b] == 0) {
+    if (threadIdx.x == 0 && mm_out) mm_out[b] = -1.0;
+    return;
+  }
+  const double2* vg = V + (int64_t)b * n;
+  for (int j = threadIdx.x; j < n; j += blockDim.x) vsm[j] = vg[j];
+  __syncthreads();
+  const double2* sw0 = Sw ? Sw + (int64_t)b * n : nullptr;
+  const double2* sd0 = Sd ? Sd + (int64_t)b * n : nullptr;
+  double worst = 0.0;   // max |v|^2 |r|^2
+  const int nb = (n + 2) / 3;
+  for (int k = threadIdx.x; k < nb; k += blockDim.x) {
+    const int j0 = 3 * k;
+    const int m = min(3, n - j0);
+    double2 vv[3], sw[3], sd[3], inj[3];
+    for (int p = 0; p < 3; ++p) {
+      vv[p] = p < m ? vsm[j0 + p] : make_double2(1.0, 0.0);
+      sw[p] = (sw0 && p < m) ? sw0[j0 + p] : make_double2(0.0, 0.0);
+      sd[p] = (sd0 && p < m) ? sd0[j0 + p] : make_double2(0.0, 0.0);
+    }
+    bus_injection(vv, sw0 ? sw : nullptr, sd0 ? sd : nullptr, m, inj);
+    for (int p = 0; p < m; ++p) {
+      const int j = j0 + p;
+      double2 acc = ys[j];
+      for (int t = ptr[j]; t < ptr[j + 1]; ++t) {
+        const double2 y = val[t], x = vsm[col[t]];
+        acc.x = fma(y.x, x.x, fma(-y.y, x.y, acc.x));
+        acc.y = fma(y.x, x.y, fma(y.y, x.x, acc.y));
+      }
+      const double rx = acc.x - inj[p].x, ry = acc.y - inj[p].y;
+      double e = (vv[p].x * vv[p].x + vv[p].y * vv[p].y) * (rx * rx + ry * ry);
+      if (e != e) e = INFINITY;
+      worst = fmax(worst, e);
+    }
+  }
+  for (int o = 16; o > 0; o >>= 1) worst = fmax(worst, __shfl_xor_sync(0xffffffffu, worst, o));
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = worst;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double x = 0.0;
+    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) x = fmax(x, red[w]);
+    const double mm = sqrt(x);
+    if (mm_out) mm_out[b] = mm;
+    if (!(mm <= mtol)) conv[b] = 0;
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Host side
+// ---------------------------------------------------------------------------
+template <int BN, int ZP, int STAGES, bool BF>
+constexpr size_t tc_smem() {
+  return 1024 + (size_t)STAGES * (BM * BK * 2 + ZP * BN * BK * 2) + 256;
+}
+
+template <int BN, int ZP, int STAGES, bool BF>
+cudaError_t tc_attr() {
+  return cudaFuncSetAttribute(k_contract_group<BN, ZP, STAGES, BF>,
+                              cudaFuncAttributeMaxDynamicSharedMemorySize,
+                              (int)tc_smem<BN, ZP, STAGES, BF>());
+}
+
+template <int BN, int ZP, int STAGES, bool BF>
+void tc_launch(Group* g, int grid, cudaStream_t st) {
+  k_contract_group<BN, ZP, STAGES, BF><<<grid, TC_THREADS, tc_smem<BN, ZP, STAGES, BF>(), st>>>(
+      g->d_state, g->d_items, g->d_tmR, g->d_tmZ0, g->d_tmZ1);
+}
+
+// (precision, BN, stages) variants compiled: FP16 x1 and BF16 x2.
+struct TcVariant {
+  int32_t precision;
+  int BN, stages;
+  cudaError_t (*attr)();
+  void (*launch)(Group*, int, cudaStream_t);
+};
+
+const TcVariant kVariants[] = {
+    {ZBUS_MIXED_FP16_SCALED, 128, 4, tc_attr<128, 1, 4, false>, tc_launch<128, 1, 4, false>},
+    {ZBUS_MIXED_FP16_SCALED, 128, 6, tc_attr<128, 1, 6, false>, tc_launch<128, 1, 6, false>},
+    {ZBUS_MIXED_FP16_SCALED, 256, 3, tc_attr<256, 1, 3, false>, tc_launch<256, 1, 3, false>},
+    {ZBUS_MIXED_FP16_SCALED, 256, 4, tc_attr<256, 1, 4, false>, tc_launch<256, 1, 4, false>},
+    {ZBUS_MIXED_BF16X2, 128, 3, tc_attr<128, 2, 3, true>, tc_launch<128, 2, 3, true>},
+    {ZBUS_MIXED_BF16X2, 128, 4, tc_attr<128, 2, 4, true>, tc_launch<128, 2, 4, true>},
+    {ZBUS_MIXED_BF16X2, 256, 2, tc_attr<256, 2, 2, true>, tc_launch<256, 2, 2, true>},
+};
+
+const TcVariant* find_variant(int32_t precision, int BN, int stages) {
+  for (const auto& v : kVariants)
+    if (v.precision == precision && v.BN == BN && v.stages == stages) return &v;
+  return nullptr;
+}
+
+const TcVariant* default_variant(int32_t precision, int max_n) {
+  const bool big = 2 * max_n > 1024;
+  if (precision == ZBUS_MIXED_BF16X2) return find_variant(precision, big ? 256 : 128, big ? 2 : 3);
+  return find_variant(precision, big ? 256 : 128, 4);
+}
+
+size_t a256(size_t x) { return (x + 255) & ~size_t(255); }
+
+}  // namespace
+
+bool tc_config_ok(int32_t precision, int BN, int stages) {
+  return find_variant(precision, BN, stages) != nullptr;
+}
+
+int tc_variants(int32_t precision, int* BN, int* stages, int max) {
+  int m = 0;
+  for (const auto& v : kVariants)
+    if (v.precision == precision && m < max) {
+      BN[m] = v.BN;
+      stages[m] = v.stages;
+      ++m;
+    }
+  return m;
+}
+
+void group_free(Group* g) {
+  if (!g) return;
+  if (g->exec) cudaGraphExecDestroy(g->exec);
+  if (g->graph) cudaGraphDestroy(g->graph);
+  if (g->cap_stream) cudaStreamDestroy(g->cap_stream);
+  for (auto e : g->ev) cudaEventDestroy(e);
+  cudaFree(g->d_hist);
+  cudaFree(g->dmem);
+  *g = Group();
+}
+
+zbus_status group_build(Group* g, const std::vector<zbus_network>& nets,
+                        const std::vector<int64_t>& Bs, int32_t precision, cudaStream_t st) {
+  group_free(g);
+  g->nets = nets;
+  g->Bs = Bs;
+  g->precision = precision;
+  g->n_items = (int)nets.size();
+  int max_n = 0;
+  int64_t total_B = 0;
+  for (size_t k = 0; k < nets.size(); ++k) {
+    ZB_CHECK(prepare_mixed(nets[k], precision, st));
+    ZB_CHECK(ensure_workspace(nets[k], Bs[k]));
+    max_n = std::max(max_n, nets[k]->n);
+    total_B += Bs[k];
+  }
+  int BN = 0, stages = 0;
+  g->tune_gen = tune_generation();
+  ZB_CHECK(tune_lookup(precision, max_n, total_B, &BN, &stages));
+  const TcVariant* var = find_variant(precision, BN, stages);
+  if (!var) var = default_variant(precision, max_n);
+  g->BN = var->BN;
+  g->stages = var->stages;
+  ZB_CUDA(var->attr());
+  int dev = 0;
+  ZB_CUDA(cudaGetDevice(&dev));
+  ZB_CUDA(cudaDeviceGetAttribute(&g->num_sms, cudaDevAttrMultiProcessorCount, dev));
+
+  g->h_items.resize(nets.size());
+  g->ws_gen.resize(nets.size());
+  int res = 0, dec = 0, mt = 0, tiles = 0;
+  for (size_t k = 0; k < nets.size(); ++k) {
+    zbus_network net = nets[k];
+    const MixedOperands& op = net->mixed[precision == ZBUS_MIXED_BF16X2 ? 1 : 0];
+    Workspace& ws = net->ws;
+    ItemDesc& d = g->h_items[k];
+    std::memset(&d, 0, sizeof(d));
+    d.bsr_ptr = net->bsr_ptr;
+    d.bsr_col = net->bsr_col;
+    d.bsr_df = net->bsr_df;
+    d.ys_df = net->ys_df;
+    d.zinv = op.zinv;
+    d.n = net->n;
+    d.nbus = net->nbus;
+    d.K_pad = op.K_pad;
+    d.N_pad = op.N_pad;
+    d.ntn = op.N_pad / g->BN;
+    d.Bp = (int32_t)ws.cap_Bp;
+    d.Vh = ws.Vh;
+    d.Vl = ws.Vl;
+    d.Swf = ws.Swf;
+    d.Sdf = ws.Sdf;
+    d.st = ws.st;
+    d.it = ws.slot_it;
+    d.conv = ws.slot_conv;
+    d.amax = ws.amax;
+    d.R = ws.R;
+    d.rinv = ws.rinv;
+    d.part = ws.part;
+    d.mt_flag = (uint32_t*)ws.mt;
+    const int rows_pad = op.K_pad / 2;
+    const int nchunks = (rows_pad + CHUNK_ROWS - 1) / CHUNK_ROWS;
+    d.res_split = (nchunks + RES_WARPS - 1) / RES_WARPS;
+    d.res_begin = res;
+    res += (d.Bp / 32) * d.res_split;
+    d.dec_begin = dec;
+    dec += (d.Bp + DEC_THREADS - 1) / DEC_THREADS;
+    d.mt_begin = mt;
+    mt += d.Bp / 128;
+    tiles += (d.Bp / 128) * d.ntn;
+    g->ws_gen[k] = ws.gen;
+  }
+  g->res_blocks = res;
+  g->dec_blocks = dec;
+  g->mt_total = mt;
+  g->max_tiles = tiles;
+
+  const size_t o_items = 0;
+  const size_t o_state = a256(o_items + nets.size() * sizeof(ItemDesc));
+  const size_t o_tiles = a256(o_state + sizeof(GroupState));
+  const size_t o_maps = a256(o_tiles + (size_t)tiles * sizeof(uint64_t));
+  const size_t total = o_maps + 3 * nets.size() * sizeof(CUtensorMap);
+  ZB_CUDA(cudaMalloc(&g->dmem, total));
+  char* p = (char*)g->dmem;
+  g->d_items = (ItemDesc*)(p + o_items);
+  g->d_state = (GroupState*)(p + o_state);
+  g->d_tiles = (uint64_t*)(p + o_tiles);
+  g->d_tmR = (CUtensorMap*)(p + o_maps);
+  g->d_tmZ0 = g->d_tmR + nets.size();
+  g->d_tmZ1 = g->d_tmZ0 + nets.size();
+
+  std::vector<CUtensorMap> maps(3 * nets.size());
+  const bool bf = precision == ZBUS_MIXED_BF16X2;
+  for (size_t k = 0; k < nets.size(); ++k) {
+    const MixedOperands& op = nets[k]->mixed[bf ? 1 : 0];
+    const ItemDesc& d = g->h_items[k];
+    ZB_CHECK(make_tmap_2d(&maps[k], d.R, bf, (uint64_t)d.K_pad, (uint64_t)d.Bp, BK, BM));
+    ZB_CHECK(make_tmap_2d(&maps[nets.size() + k], op.Z0, bf, (uint64_t)op.K_pad,
+                          (uint64_t)op.N_pad, BK, g->BN));
+    ZB_CHECK(make_tmap_2d(&maps[2 * nets.size() + k], bf ? op.Z1 : op.Z0, bf, (uint64_t)op.K_pad,
+                          (uint64_t)op.N_pad, BK, g->BN));
+  }
+  GroupState s;
+  std::memset(&s, 0, sizeof(s));
+  s.n_items = g->n_items;
+  s.mt_total = mt;
+  s.res_blocks = res;
+  s.dec_blocks = dec;
+  s.tiles = g->d_tiles;
+  ZB_CUDA(cudaMemcpyAsync(g->d_items, g->h_items.data(), nets.size() * sizeof(ItemDesc),
+                          cudaMemcpyHostToDevice, st));
+  ZB_CUDA(cudaMemcpyAsync(g->d_state, &s, sizeof(s), cudaMemcpyHostToDevice, st));
+  ZB_CUDA(cudaMemcpyAsync(g->d_tmR, maps.data(), maps.size() * sizeof(CUtensorMap),
+                          cudaMemcpyHostToDevice, st));
+  ZB_CUDA(cudaStreamSynchronize(st));
+  return ZBUS_OK;
+}
+
+zbus_status group_reset(Group* g, cudaStream_t st) {
+  k_group_reset<<<dim3(16, std::min(g->n_items, 64)), 256, 0, st>>>(g->d_state, g->d_items,
+                                                                  g->n_items);
+  ZB_CUDA(cudaGetLastError());
+  return ZBUS_OK;
+}
+
+zbus_status group_admit(Group* g, int k, int64_t s0, int64_t B, const double* V0,
+                        const double* S_wye, const double* S_delta, cudaStream_t st) {
+  if (B <= 0) return ZBUS_OK;
+  const ItemDesc& d = g->h_items[k];
+  k_slot_init<<<dim3((d.n + 31) / 32, (unsigned)((B + 31) / 32)), dim3(32, 8), 0, st>>>(
+      g->d_state, g->d_items, k, (int)s0, (int)B, (const double2*)V0, g->nets[k]->w,
+      (const double2*)S_wye, (const double2*)S_delta);
+  ZB_CUDA(cudaGetLastError());
+  return ZBUS_OK;
+}
+
+zbus_status group_start(Group* g, double tol, int32_t max_iter, int32_t rule, int32_t* hist,
+                        int32_t hist_n, cudaStream_t st) {
+  k_group_params<<<1, 1, 0, st>>>(g->d_state, tol, max_iter, rule, hist, hist_n);
+  k_finish_group<<<1, 1024, 0, st>>>(g->d_state, g->d_items, 1, 0, 0);
+  ZB_CUDA(cudaGetLastError());
+  return ZBUS_OK;
+}
+
+zbus_status group_sweep(Group* g, cudaGraphConditionalHandle h, bool use_handle, cudaStream_t st,
+                        cudaEvent_t* ev) {
+  const bool bf = g->precision == ZBUS_MIXED_BF16X2;
+  if (ev) ZB_CUDA(cudaEventRecord(ev[0], st));
+  if (bf)
+    k_residual_group<true><<<g->res_blocks, RES_WARPS * 32, 0, st>>>(g->d_state, g->d_items);
+  else
+    k_residual_group<false><<<g->res_blocks, RES_WARPS * 32, 0, st>>>(g->d_state, g->d_items);
+  if (ev) ZB_CUDA(cudaEventRecord(ev[1], st));
+  const TcVariant* var = find_variant(g->precision, g->BN, g->stages);
+  var->launch(g, std::min(g->num_sms, g->max_tiles), st);
+  if (ev) ZB_CUDA(cudaEventRecord(ev[2], st));
+  k_decide_group<<<g->dec_blocks, DEC_THREADS, 0, st>>>(g->d_state, g->d_items);
+  k_finish_group<<<1, 1024, 0, st>>>(g->d_state, g->d_items, 0, h, use_handle ? 1 : 0);
+  if (ev) ZB_CUDA(cudaEventRecord(ev[3], st));
+  ZB_CUDA(cudaGetLastError());
+  return ZBUS_OK;
+}
+
+zbus_status group_run(Group* g, cudaStream_t st) {
+  if (!g->exec) {
+    if (!g->cap_stream) ZB_CUDA(cudaStreamCreateWithFlags(&g->cap_stream, cudaStreamNonBlocking));
+    ZB_CUDA(cudaGraphCreate(&g->graph, 0));
+    cudaGraphConditionalHandle h;
+    ZB_CUDA(cudaGraphConditionalHandleCreate(&h, g->graph, 1, cudaGraphCondAssignDefault));
+    cudaGraphNodeParams cp = {cudaGraphNodeTypeConditional};
+    cp.conditional.handle = h;
+    cp.conditional.type = cudaGraphCondTypeWhile;
+    cp.conditional.size = 1;
+    cudaGraphNode_t node;
+    ZB_CUDA(cudaGraphAddNode(&node, g->graph, nullptr, nullptr, 0, &cp));
+    cudaGraph_t body = cp.conditional.phGraph_out[0];
+    ZB_CUDA(cudaStreamBeginCaptureToGraph(g->cap_stream, body, nullptr, nullptr, 0,
+                                          cudaStreamCaptureModeThreadLocal));
+    zbus_status s = group_sweep(g, h, true, g->cap_stream);
+    cudaGraph_t captured = nullptr;
+    cudaError_t ce = cudaStreamEndCapture(g->cap_stream, &captured);
+    if (s != ZBUS_OK) return s;
+    if (ce != cudaSuccess) return cuda_fail(ce, "cudaStreamEndCapture(group sweep)", __FILE__, __LINE__);
+    ce = cudaGraphInstantiate(&g->exec, g->graph, 0);
+    if (ce != cudaSuccess) return cuda_fail(ce, "cudaGraphInstantiate(group loop)", __FILE__, __LINE__);
+  }
+  ZB_CUDA(cudaGraphLaunch(g->exec, st));
+  return ZBUS_OK;
+}
+
+zbus_status group_collect(Group* g, int k, int64_t s0, int64_t B, double* V_out, int32_t* iters,
+                          uint8_t* converged, const double* S_wye, const double* S_delta,
+                          double mtol, double* mm_out, cudaStream_t st) {
+  if (B <= 0) return ZBUS_OK;
+  zbus_network net = g->nets[k];
+  k_slot_merge<<<dim3((net->n + 31) / 32, (unsigned)((B + 31) / 32)), dim3(32, 8), 0, st>>>(
+      g->d_items, k, (int)s0, (int)B, (double2*)V_out, iters, converged);
+  k_check<<<(unsigned)B, 256, (size_t)16 * net->n, st>>>(
+      (const double2*)V_out, (const double2*)S_wye, (const double2*)S_delta, converged, net->n,
+      net->csr_ptr, net->csr_col, net->csr_val, net->ys, mtol, mm_out);
+  ZB_CUDA(cudaGetLastError());
+  return ZBUS_OK;
+}
+
+zbus_status group_set_check_attr() {
+  ZB_CUDA(cudaFuncSetAttribute(k_check, cudaFuncAttributeMaxDynamicSharedMemorySize, 220 * 1024));
+  return ZBUS_OK;
+}
+
+}  // namespace zbus

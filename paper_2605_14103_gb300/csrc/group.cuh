@@ -1,0 +1,136 @@
+// Grouped mixed-precision sweep: several feeders ("items"), each with its own
+// scenario slots, advanced together by one set of kernels per sweep.  A
+// single-feeder solve is a group of one; the batched solve and the serving
+// loop use the same kernels.
+#pragma once
+
+#include <cuda.h>
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <vector>
+
+#include "zbus_internal.cuh"
+
+namespace zbus {
+
+// Slot states.
+constexpr uint8_t SLOT_ACTIVE = 0;
+constexpr uint8_t SLOT_DONE = 1;   // stopped, result not yet collected
+constexpr uint8_t SLOT_FREE = 2;
+
+// One feeder of a group (device-visible).
+struct ItemDesc {
+  // network operands
+  const int32_t* bsr_ptr;
+  const int32_t* bsr_col;
+  const float4* bsr_df;     // [nblk][9] double-float 3x3 blocks of Y_LL
+  const float4* ys_df;      // [n] double-float Y_Ls v_s
+  const float* zinv;        // [N_pad / 2] inverse row scales of Z
+  int32_t n, nbus, K_pad, N_pad, ntn;
+  int32_t Bp;               // slot capacity, multiple of 128
+  // slot state, scenario-minor [n][Bp]
+  float2* Vh;
+  float2* Vl;
+  float2* Swf;              // may be null (no wye loads)
+  float2* Sdf;              // may be null (no delta loads)
+  uint8_t* st;              // [Bp] SLOT_*
+  int32_t* it;              // [Bp] sweeps since admission
+  uint8_t* conv;            // [Bp] stop rule met
+  float* amax;              // [2][Bp] max |r| of the previous / current sweep
+  void* R;                  // [Bp][K_pad] fp16 / bf16 residual rows
+  float* rinv;              // [Bp] inverse residual scales
+  double* part;             // [Bp][ntn][2] per-tile step partials
+  uint32_t* mt_flag;        // [Bp / 128] tile holds an active slot after the stop test
+  // launch decomposition
+  int32_t res_begin;        // first residual block
+  int32_t res_split;        // residual blocks per 32 slots
+  int32_t dec_begin;        // first stop-test block (256 slots each)
+  int32_t mt_begin;         // global index of this item's first 128-slot tile
+};
+
+// Sweep-loop state of a group (device).
+struct GroupState {
+  int32_t n_items;
+  int32_t active;           // active slots at the start of the sweep
+  int32_t active_next;
+  int32_t sweep;
+  int32_t max_iter;
+  int32_t rule;
+  double tol;
+  int32_t err;
+  int32_t n_tiles;          // entries of tiles
+  int32_t mt_total;         // 128-slot tiles over all items
+  int32_t res_blocks;       // residual grid size
+  int32_t dec_blocks;       // stop-test grid size
+  int32_t* hist;            // profile mode: active slots of sweep k
+  int32_t hist_n;
+  uint64_t* tiles;          // (item << 32) | (mt << 16) | nt of every active tile
+};
+
+// Host object of a group: device descriptor arrays, tensor maps, loop graph.
+struct Group {
+  std::vector<zbus_network> nets;
+  std::vector<int64_t> Bs;
+  int32_t precision = -1;
+  int BN = 0;
+  int stages = 0;
+  int n_items = 0;
+  int mt_total = 0;
+  int max_tiles = 0;
+  int res_blocks = 0;
+  int dec_blocks = 0;
+  int num_sms = 148;
+  void* dmem = nullptr;        // one allocation: items | state | tiles | maps
+  ItemDesc* d_items = nullptr;
+  GroupState* d_state = nullptr;
+  uint64_t* d_tiles = nullptr;
+  CUtensorMap* d_tmR = nullptr;
+  CUtensorMap* d_tmZ0 = nullptr;
+  CUtensorMap* d_tmZ1 = nullptr;
+  std::vector<ItemDesc> h_items;
+  std::vector<uint64_t> ws_gen;  // workspace generation of each item when built
+  uint64_t tune_gen = 0;         // tile table generation when built
+  cudaStream_t cap_stream = nullptr;
+  cudaGraph_t graph = nullptr;
+  cudaGraphExec_t exec = nullptr;
+  // profile mode
+  std::vector<cudaEvent_t> ev;
+  int32_t* d_hist = nullptr;
+  int prof_cap = 0;
+  int prof_sweeps = 0;
+};
+
+zbus_status group_build(Group* g, const std::vector<zbus_network>& nets,
+                        const std::vector<int64_t>& Bs, int32_t precision, cudaStream_t st);
+void group_free(Group* g);
+// Run start for item k: slots [s0, s0 + B) from v^0 (V0 or w) and the loads
+// (FP64 [B][n]); admitted slots become active.
+zbus_status group_admit(Group* g, int k, int64_t s0, int64_t B, const double* V0,
+                        const double* S_wye, const double* S_delta, cudaStream_t st);
+// Mark every slot of every item free.
+zbus_status group_reset(Group* g, cudaStream_t st);
+// Loop parameters and the initial tile list (after the admissions).
+zbus_status group_start(Group* g, double tol, int32_t max_iter, int32_t rule, int32_t* hist,
+                        int32_t hist_n, cudaStream_t st);
+// One sweep (residual, contraction, stop test, tile list); h / use_handle set
+// the loop condition when captured in a graph.  ev: 4 events for profiling.
+zbus_status group_sweep(Group* g, cudaGraphConditionalHandle h, bool use_handle, cudaStream_t st,
+                        cudaEvent_t* ev = nullptr);
+// Device-resident loop: sweeps until no slot is active (CUDA graph WHILE).
+zbus_status group_run(Group* g, cudaStream_t st);
+// Results of item k, slots [s0, s0 + B): merged FP64 voltages, iteration
+// counts and flags into caller arrays, then the FP64 mismatch test (flags of
+// scenarios above mtol cleared; mm_out may be null).
+zbus_status group_collect(Group* g, int k, int64_t s0, int64_t B, double* V_out, int32_t* iters,
+                          uint8_t* converged, const double* S_wye, const double* S_delta,
+                          double mtol, double* mm_out, cudaStream_t st);
+// Tile configurations the contraction is compiled for (BN, stages).
+bool tc_config_ok(int32_t precision, int BN, int stages);
+int tc_variants(int32_t precision, int* BN, int* stages, int max);
+
+// tune.cu: tile choice of a workload, table generation (bumped on change).
+zbus_status tune_lookup(int32_t precision, int max_n, int64_t total_B, int* BN, int* stages);
+uint64_t tune_generation();
+
+}  // namespace zbus

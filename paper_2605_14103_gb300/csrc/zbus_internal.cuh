@@ -104,9 +104,9 @@ struct Workspace {
   float* amax = nullptr;     // mixed: [2][cap_Bp]
   int32_t* mt = nullptr;     // mixed: [2][cap_Bp / 128] tile list and flags
   int64_t cap_Bp = 0;        // cap_B rounded up to 128
-  CUtensorMap tmR;           // TMA map of R (box 64 x 128)
-  bool tmR_bf16 = false;
-  bool tmR_ready = false;
+  uint64_t gen = 0;          // bumped at every reallocation
+  int32_t* slot_it = nullptr;   // mixed: [cap_Bp] sweeps since admission
+  uint8_t* slot_conv = nullptr; // mixed: [cap_Bp] stop rule met
 };
 
 // Low-precision operands of Z for the tensor-core contraction.
@@ -116,12 +116,9 @@ struct MixedOperands {
   int zparts = 1;            // 1: FP16 row-scaled; 2: BF16 hi + lo
   int K_pad = 0;             // 2n rounded up to 64
   int N_pad = 0;             // 2n rounded up to 256
-  int BN = 128;              // N-tile of the contraction
-  int num_sms = 148;         // persistent grid size
   void* Z0 = nullptr;        // [N_pad][K_pad] (hi part)
   void* Z1 = nullptr;        // [N_pad][K_pad] (lo part, BF16 only)
   float* zinv = nullptr;     // [N_pad / 2] inverse row scales per complex output
-  CUtensorMap tmZ0, tmZ1;
 };
 
 // Host-driven profiling run: 4 events per sweep around the three kernels.
@@ -141,6 +138,10 @@ struct GraphEntry {
 };
 
 }  // namespace zbus
+
+namespace zbus {
+struct Group;
+}
 
 struct zbus_network_s {
   int device = 0;
@@ -172,6 +173,7 @@ struct zbus_network_s {
   float4* bsr_df = nullptr;     // [nblk][9] double-float copy (mixed sweeps)
   zbus::Workspace ws;
   zbus::MixedOperands mixed[2];   // [0] FP16 row-scaled, [1] BF16 hi + lo
+  struct zbus::Group* group1 = nullptr;   // single-network mixed solves
   std::vector<zbus::GraphEntry> graphs;
   cudaStream_t cap_stream = nullptr;  // private stream used only to capture graphs
   zbus::Profile prof;
@@ -198,20 +200,17 @@ void launch_mismatch(const double2* V, const double2* S_wye, const double2* S_de
                      const double2* ys, int n, int B, double* out, cudaStream_t st);
 
 
+// api.cu
+zbus_status ensure_workspace(zbus_network net, int64_t B);
+
+// group.cu
+zbus_status group_set_check_attr();
+
 // mixed.cu
 zbus_status make_tmap_2d(CUtensorMap* map, const void* base, bool bf16, uint64_t cols,
                          uint64_t rows, uint32_t box_cols, uint32_t box_rows);
 zbus_status prepare_mixed(zbus_network net, int32_t precision, cudaStream_t st);
 void free_mixed(zbus_network net);
-int tc_grid(const MixedOperands& op, int B);
-zbus_status launch_residual_mixed(zbus_network net, const MixedOperands& op, int B, void* R,
-                                  float* rinv, cudaStream_t st);
-zbus_status launch_contract_tc(zbus_network net, const MixedOperands& op, const CUtensorMap& tmR,
-                               const float* rinv, int grid, cudaStream_t st);
-zbus_status launch_final_check(zbus_network net, int B, double* mm_out, cudaStream_t st);
-void launch_init_df(SolveCtx* ctx, int n, int B, int B_pad, cudaStream_t st);
-void launch_merge_df(SolveCtx* ctx, int n, int B, int B_pad, cudaStream_t st);
-void launch_converge_mixed(SolveCtx* ctx, int B, cudaGraphConditionalHandle h, bool use_handle,
-                           cudaStream_t st);
+
 
 }  // namespace zbus

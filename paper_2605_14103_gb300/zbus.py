@@ -35,6 +35,12 @@ class zbus_solve_opts(C.Structure):
                 ("profile", C.c_int32), ("reserved", C.c_double * 4)]
 
 
+class zbus_batch_item(C.Structure):
+    _fields_ = [("net", C.c_void_p), ("B", C.c_int64), ("S_wye", C.c_void_p),
+                ("S_delta", C.c_void_p), ("V_init", C.c_void_p), ("V_out", C.c_void_p),
+                ("iters", C.c_void_p), ("converged", C.c_void_p)]
+
+
 _lib = None
 
 _P = C.c_void_p
@@ -52,6 +58,11 @@ _SIGS = {
     "zbus_last_profile": (C.c_int, [_P, C.c_int32, _P, _P, _P]),
     "zbus_solve_noalloc": (C.c_int, [_P, C.c_int64, _P, _P, _P, C.c_double, C.c_int32,
                                      C.c_int32, _P, _P, _P, _P]),
+    "zbus_solve_batched": (C.c_int, [C.POINTER(zbus_batch_item), C.c_int32, C.c_double,
+                                     C.c_int32, C.POINTER(zbus_solve_opts), _P]),
+    "zbus_autotune": (C.c_int, [C.POINTER(zbus_batch_item), C.c_int32,
+                                C.POINTER(zbus_solve_opts), C.c_double, C.c_int32, C.c_int32,
+                                _P, C.POINTER(C.c_int32), C.POINTER(C.c_int32)]),
     "zbus_status_string": (C.c_char_p, [C.c_int]),
     "zbus_last_error": (C.c_char_p, []),
 }
@@ -195,6 +206,62 @@ def zbus_last_profile(h, max_n):
                                    C.byref(sw)))
     m = min(max_n, sw.value)
     return ms[:m], act[:m]
+
+
+def _batch_array(items):
+    """items: list of (handle, S_wye, S_delta, V_init, V_out, iters, converged) tensors."""
+    import torch
+    arr = (zbus_batch_item * len(items))()
+    c128 = torch.complex128
+    for k, (h, sw, sd, v0, vo, it, cv) in enumerate(items):
+        n = zbus_network_size(h)
+        B = vo.shape[0]
+        arr[k].net = h
+        arr[k].B = B
+        arr[k].S_wye = _dptr(sw, "S_wye", c128, (B, n))
+        arr[k].S_delta = _dptr(sd, "S_delta", c128, (B, n))
+        arr[k].V_init = _dptr(v0, "V_init", c128, (B, n))
+        arr[k].V_out = _dptr(vo, "V_out", c128, (B, n))
+        arr[k].iters = _dptr(it, "iters", torch.int32, (B,))
+        arr[k].converged = _dptr(cv, "converged", torch.uint8, (B,))
+    return arr
+
+
+def zbus_solve_batched(items, tol, max_iter, opts, stream=None):
+    arr = _batch_array(items)
+    _check(lib().zbus_solve_batched(arr, len(items), float(tol), int(max_iter),
+                                    C.byref(opts) if opts is not None else None, _stream(stream)))
+
+
+def zbus_autotune(items, opts, tol, max_iter, reps=3, stream=None):
+    """Times every compiled contraction variant on these items; returns (BN, stages)."""
+    arr = _batch_array(items)
+    bn = C.c_int32(0)
+    stg = C.c_int32(0)
+    _check(lib().zbus_autotune(arr, len(items), C.byref(opts), float(tol), int(max_iter),
+                               int(reps), _stream(stream), C.byref(bn), C.byref(stg)))
+    return bn.value, stg.value
+
+
+def solve_batched(networks, loads, tol=1e-8, max_iter=50, precision="fp16_scaled",
+                  rule="maxabs", mismatch_tol=1e-6, stream=None):
+    """networks: [Network]; loads: [(S_wye, S_delta)] device tensors.  Returns [(V, iters, conv)]."""
+    import torch
+    o = zbus_solve_opts_default()
+    o.precision = PRECISION[precision]
+    o.conv_rule = RULE[rule]
+    o.mismatch_tol = mismatch_tol
+    items, outs = [], []
+    for net, (sw, sd) in zip(networks, loads):
+        ref = sw if sw is not None else sd
+        B = ref.shape[0]
+        out = (torch.empty((B, net.n), dtype=torch.complex128, device=ref.device),
+               torch.empty((B,), dtype=torch.int32, device=ref.device),
+               torch.empty((B,), dtype=torch.uint8, device=ref.device))
+        items.append((net.handle, sw, sd, None) + out)
+        outs.append(out)
+    zbus_solve_batched(items, tol, max_iter, o, stream)
+    return outs
 
 
 def zbus_status_string(s: int) -> str:
