@@ -27,6 +27,8 @@ import sys
 import tempfile
 import time
 
+import numpy as np
+
 ROOT = os.path.dirname(os.path.abspath(__file__))
 if ROOT not in sys.path:
     sys.path.insert(0, ROOT)
@@ -48,6 +50,7 @@ def parse():
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--forms", default="all", choices=["all", "one"])
     p.add_argument("--batch", type=int, default=0, help="override the scenario count")
+    p.add_argument("--requests", type=int, default=2000, help="serving: requests per run")
     return p.parse_args()
 
 
@@ -453,10 +456,171 @@ def run_ours(args):
         dist.destroy_process_group()
 
 
+# ---------------------------------------------------------------------------
+# heterogeneous batch and serving workloads
+# ---------------------------------------------------------------------------
+def _timed(fn, steps, flush):
+    import torch
+    evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+           for _ in range(steps)]
+    for k in range(steps):
+        flush.zero_()
+        evs[k][0].record()
+        fn()
+        evs[k][1].record()
+    torch.cuda.synchronize()
+    return [a.elapsed_time(b) for a, b in evs]
+
+
+def run_hetero(args):
+    """64 feeders of 50-800 buses, 32-2048 scenarios each, 40 % delta loads."""
+    import torch
+    import __graft_entry__
+    __graft_entry__.build()
+    from paper_2605_14103_gb300 import feeders as F
+    from paper_2605_14103_gb300 import zbus
+    peaks = load_peaks()
+    t0 = time.perf_counter()
+    fset = F.heterogeneous_set()
+    nets, loads, host = [], [], []
+    for f, B in fset:
+        Sw, Sd = F.make_scenarios(f, B, 0.8, 1.2)
+        nets.append(zbus.Network.from_feeder(f))
+        loads.append((torch.from_numpy(Sw).cuda(), torch.from_numpy(Sd).cuda()))
+        host.append((f, Sw, Sd))
+    setup_s = time.perf_counter() - t0
+    total_B = sum(B for _, B in fset)
+    flush = torch.empty(512 * 1024 * 1024, dtype=torch.uint8, device="cuda")
+    forms = {}
+
+    def count(outs):
+        good = 0
+        for (V, it, cv), net, (sw, sd) in zip(outs, nets, loads):
+            mm = net.power_mismatch(V, sw, sd)
+            good += int(((cv == 1) & (mm <= 1e-6)).sum().item())
+        return good
+
+    for prec in ("fp16_scaled", "bf16x2"):
+        for _ in range(args.warmup):
+            outs = zbus.solve_batched(nets, loads, precision=prec)
+        ms = _timed(lambda: zbus.solve_batched(nets, loads, precision=prec), args.steps, flush)
+        outs = zbus.solve_batched(nets, loads, precision=prec)
+        good = count(outs)
+        forms["batched_" + prec] = {"value": good / (statistics.median(ms) / 1e3),
+                                    "ms_per_step": statistics.median(ms), "converged": good}
+        if prec == "fp16_scaled":
+            head_outs = outs
+
+    def seq(prec):
+        return [net.solve(sw, sd, precision=prec) for net, (sw, sd) in zip(nets, loads)]
+    for prec, steps in (("fp16_scaled", max(2, args.steps // 2)), ("fp64", 1)):
+        seq(prec)
+        ms = _timed(lambda: seq(prec), steps, flush)
+        good = count(seq(prec))
+        forms["one_by_one_" + prec] = {"value": good / (statistics.median(ms) / 1e3),
+                                       "ms_per_step": statistics.median(ms), "converged": good}
+    head = forms["batched_fp16_scaled"]
+    plain = forms["one_by_one_fp64"]["value"]
+    for k in forms:
+        forms[k]["vs_plain_fp64"] = forms[k]["value"] / plain
+    # oracle parity on a sample of feeders
+    from oracle import zbus_oracle as O
+    worst, flags = 0.0, True
+    for idx in (0, 17, 40, 63):
+        f, Sw, Sd = host[idx]
+        ref = O.solve_coo(f.n_total, f.Y_row, f.Y_col, f.Y_val, f.slack_idx, f.v_slack,
+                          Sw[:64], Sd[:64])
+        V, it, cv = head_outs[idx]
+        flags &= bool(np.array_equal(cv[:64].cpu().numpy(), ref["converged"]))
+        worst = max(worst, float(np.abs(V[:64].cpu().numpy() - ref["V"]).max()))
+    out = {"metric": METRIC, "value": head["value"], "unit": UNIT, "n_gpus": 1,
+           "steps": args.steps, "warmup": args.warmup, "ms_per_step": head["ms_per_step"],
+           "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+           "dtype": "fp16_scaled+f64", "data": "synthetic",
+           "config": {"workload": "hetero64", "feeders": len(fset),
+                      "buses_range": [min(f.N for f, _ in fset), max(f.N for f, _ in fset)],
+                      "scenarios_total": total_B, "tol": 1e-8, "setup_s": setup_s,
+                      "l2": "flushed between steps (512 MiB write)"},
+           "forms": forms, "peaks": peaks["src"],
+           "parity": {"sampled_feeders": 4, "sampled_scenarios_each": 64,
+                      "max_dv_vs_oracle": worst, "flags_equal": flags},
+           "gpu_launches": None}
+    print(json.dumps(out), flush=True)
+
+
+def run_serve(args):
+    """Pool of 16 feeders (100-2000 buses); Poisson stream of 1-4096-scenario requests."""
+    import torch
+    import __graft_entry__
+    __graft_entry__.build()
+    from paper_2605_14103_gb300 import feeders as F
+    from paper_2605_14103_gb300 import zbus
+    rng = np.random.default_rng(505)
+    t0 = time.perf_counter()
+    pool = F.heterogeneous_set(n_feeders=16, seed=505, n_lo=100, n_hi=2000, b_lo=4096,
+                               b_hi=4096)
+    nets, sc = [], []
+    for f, _ in pool:
+        nets.append(zbus.Network.from_feeder(f))
+        Sw, Sd = F.make_scenarios(f, 4096, 0.8, 1.2)
+        sc.append((torch.from_numpy(Sw).cuda(), torch.from_numpy(Sd).cuda()))
+    setup_s = time.perf_counter() - t0
+    n_req = args.requests
+
+    def requests(arrivals):
+        out = []
+        for i, a in enumerate(arrivals):
+            k = int(rng.integers(0, len(pool)))
+            B = int(np.clip(np.rint(np.exp(rng.uniform(0.0, np.log(4096.0)))), 1, 4096))
+            o = int(rng.integers(0, 4096 - B + 1))
+            sw, sd = sc[k]
+            out.append({"feeder": k, "S_wye": sw[o:o + B], "S_delta": sd[o:o + B],
+                        "arrival": float(a)})
+        return out
+
+    def run(reqs):
+        t = time.perf_counter()
+        res = zbus.serve(nets, reqs, hbm_budget_bytes=120 << 30, max_slots=4096,
+                         keep_results=False)
+        wall = time.perf_counter() - t
+        lat = np.array([r["t_done"] - r["t_arrival"] for r in res])
+        scen = sum(r["B"] for r in res)
+        good = sum(r["n_converged"] for r in res)
+        span = max(r["t_done"] for r in res)
+        return {"requests": len(res), "scenarios": scen, "converged": good,
+                "throughput": good / span, "p50_ms": float(np.percentile(lat, 50) * 1e3),
+                "p99_ms": float(np.percentile(lat, 99) * 1e3), "wall_s": wall,
+                "all_ok": all(r["status"] == 0 for r in res)}
+
+    zbus.serve(nets, requests(np.zeros(32)), keep_results=False)         # warm-up
+    sat = run(requests(np.zeros(n_req)))
+    mean_B = sat["scenarios"] / sat["requests"]
+    runs = {"saturated": sat}
+    for load in (0.3, 0.7, 0.9):
+        lam = load * sat["throughput"] / mean_B
+        arr = np.cumsum(rng.exponential(1.0 / lam, size=n_req))
+        runs[f"load_{load}"] = run(requests(arr))
+    head = runs["load_0.7"]
+    out = {"metric": METRIC, "value": sat["throughput"], "unit": UNIT, "n_gpus": 1,
+           "steps": 1, "warmup": 1, "ms_per_step": sat["wall_s"] * 1e3,
+           "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+           "dtype": "fp16_scaled+f64", "data": "synthetic",
+           "config": {"workload": "serve16", "feeders": len(pool),
+                      "buses_range": [min(f.N for f, _ in pool), max(f.N for f, _ in pool)],
+                      "requests_per_run": n_req, "hbm_budget_gb": 120, "setup_s": setup_s},
+           "latency": {"p50_ms_at_0.7": head["p50_ms"], "p99_ms_at_0.7": head["p99_ms"]},
+           "runs": runs}
+    print(json.dumps(out), flush=True)
+
+
 def main():
     args = parse()
     if args.impl == "reference":
         run_reference(args)
+    elif args.workload == "hetero64":
+        run_hetero(args)
+    elif args.workload == "serve16":
+        run_serve(args)
     else:
         run_ours(args)
 

@@ -204,6 +204,83 @@ zbus_status zbus_autotune(const zbus_batch_item* items, int32_t n_items,
                           int32_t reps, void* cuda_stream, int32_t* best_BN,
                           int32_t* best_stages);
 
+/* ---------------------------------------------------------------------------
+ * Serving: a request loop over a pool of networks with continuous batching.
+ * ------------------------------------------------------------------------- */
+
+/* One request: B scenarios of one pool feeder. */
+typedef struct {
+  int32_t feeder;          /* index into the pool */
+  int64_t B;               /* scenarios, 1 .. the feeder's slot capacity */
+  const double* S_wye;     /* device [B][n] complex or NULL; valid until completion */
+  const double* S_delta;   /* device [B][n] complex or NULL */
+  double* V_out;           /* device [B][n] complex, or NULL: results stay in a
+                              library buffer passed to the sink (valid during
+                              the sink call only) */
+  int32_t* iters;          /* device [B] or NULL (with V_out NULL) */
+  uint8_t* converged;      /* device [B] or NULL (with V_out NULL) */
+  int32_t warm_start;      /* 1: start from the feeder's last converged voltage
+                              (kept on the device), else from w */
+  int32_t reserved0;
+  uint64_t tag;            /* caller's identifier */
+  double t_arrival;        /* arrival time, seconds on the serving clock */
+} zbus_request;
+
+/* Outcome of one request, passed to the sink. */
+typedef struct {
+  zbus_status status;      /* ZBUS_OK, or ZBUS_ERR_ARG for a request that can
+                              never fit (B above the slot capacity, bad feeder) */
+  int32_t n_converged;     /* scenarios flagged converged (after the FP64 test) */
+  int32_t max_iters;       /* largest iteration count of its scenarios */
+  int32_t reserved0;
+  double t_admit;          /* seconds on the serving clock */
+  double t_done;           /* results complete on the device */
+  const double* V;         /* device [B][n] results (V_out or the library buffer) */
+  const int32_t* iters;    /* device [B] */
+  const uint8_t* converged;/* device [B] */
+} zbus_request_result;
+
+/* Polled by the serving loop with the current serving-clock time (seconds
+ * since the loop started): return 1 and fill *req if a request is ready, 0 if
+ * none is ready now, -1 when no further request will come. */
+typedef int32_t (*zbus_request_source)(void* user, double now, zbus_request* req);
+/* Called once per request when its results are complete on the device. */
+typedef void (*zbus_completion_sink)(void* user, const zbus_request* req,
+                                     const zbus_request_result* res);
+
+typedef struct {
+  uint64_t hbm_budget_bytes;   /* device bytes for the pool's operands plus the
+                                  slot state of every feeder */
+  int32_t max_slots;           /* upper bound of scenario slots per feeder */
+  int32_t precision;           /* ZBUS_MIXED_FP16_SCALED or ZBUS_MIXED_BF16X2 */
+  int32_t conv_rule;
+  int32_t max_iter;
+  double tol;
+  double mismatch_tol;         /* <= 0 selects 1e-6 */
+  int32_t max_admit_per_sweep; /* <= 0: unlimited */
+  int32_t reserved0;
+} zbus_serve_config;
+
+/*
+ * zbus_serve -- run the request loop until the source signals the end and
+ * every admitted request has completed.  Each loop pass admits pending
+ * requests into free scenario slots of their feeder (first fit, in arrival
+ * order), runs one sweep of the grouped mixed-precision engine over every
+ * active slot of every feeder, and completes the requests whose scenarios
+ * have all stopped (FP64 mismatch test, results to the caller, sink call).
+ * Requests that arrive while others are on the GPU join at the next sweep
+ * (continuous batching); per-scenario arithmetic does not depend on the mix,
+ * so a result is the same alone and in the mix.  Slot capacity per feeder is
+ * the largest multiple of 128 (<= max_slots) whose state fits the budget
+ * left after the pool's operands; ZBUS_ERR_OOM if not even 128 fit.  The
+ * pool's operands stay resident; each feeder keeps its last converged
+ * voltage for warm starts.  Runs on the calling thread; the callbacks run on
+ * it too.
+ */
+zbus_status zbus_serve(const zbus_serve_config* cfg, zbus_network* pool, int32_t n_pool,
+                       zbus_request_source src, zbus_completion_sink sink, void* user,
+                       void* cuda_stream);
+
 /*
  * zbus_power_mismatch -- per-scenario FP64 power mismatch of given voltages,
  * max_j |v_j conj((Y_LL v + Y_Ls v_s)_j - i_j(v))|, computed with the sparse

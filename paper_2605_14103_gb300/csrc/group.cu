@@ -46,12 +46,13 @@ __device__ __forceinline__ int find_item(const ItemDesc* items, int n_items, int
 }
 
 // ---------------------------------------------------------------------------
-// Admission: slots [s0, s0 + B) of item k take v^0 (V0, else w) and the loads
-// (FP64, [B][n]), transposed to the scenario-minor state through 32 x 32
-// shared-memory tiles.  Admitted slots become active.
+// Admission: slots [s0, s0 + B) of item k take v^0 (V0 with row stride
+// v0_stride, 0 broadcasting one row; else w) and the loads (FP64, [B][n]),
+// transposed to the scenario-minor state through 32 x 32 shared-memory tiles.
+// Admitted slots become active.
 // ---------------------------------------------------------------------------
 __global__ void k_slot_init(GroupState* __restrict__ gs, const ItemDesc* __restrict__ items, int k,
-                            int s0, int B, const double2* __restrict__ V0,
+                            int s0, int B, const double2* __restrict__ V0, int v0_stride,
                             const double2* __restrict__ w, const double2* __restrict__ Sw,
                             const double2* __restrict__ Sd) {
   __shared__ double2 tv[32][33];
@@ -66,7 +67,7 @@ __global__ void k_slot_init(GroupState* __restrict__ gs, const ItemDesc* __restr
     double2 v = make_double2(0.0, 0.0), a = v, d = v;
     if (b < B && j < n) {
       const int64_t g = (int64_t)b * n + j;
-      v = V0 ? V0[g] : w[j];
+      v = V0 ? V0[(int64_t)b * v0_stride + j] : w[j];
       if (Sw) a = Sw[g];
       if (Sd) d = Sd[g];
     }
@@ -97,10 +98,7 @@ __global__ void k_slot_init(GroupState* __restrict__ gs, const ItemDesc* __restr
       it.conv[slot] = 0;
       it.amax[slot] = 1.0f;
       it.amax[Bp + slot] = 0.0f;
-      atomicOr(&it.mt_flag[slot / 128], 1u);
     }
-    const unsigned bal = __ballot_sync(0xffffffffu, adm);
-    if (tx == 0) atomicAdd(&gs->active_next, __popc(bal));
   }
 }
 
@@ -111,12 +109,10 @@ __global__ void k_group_reset(GroupState* __restrict__ gs, const ItemDesc* __res
     const ItemDesc it = items[k];
     for (int b = blockIdx.x * blockDim.x + threadIdx.x; b < it.Bp; b += gridDim.x * blockDim.x) {
       it.st[b] = SLOT_FREE;
-      if ((b & 127) == 0) it.mt_flag[b / 128] = 0;
     }
   }
   if (blockIdx.x == 0 && blockIdx.y == 0 && threadIdx.x == 0) {
     gs->active = 0;
-    gs->active_next = 0;
     gs->sweep = 0;
     gs->err = 0;
     gs->n_tiles = 0;
@@ -481,9 +477,6 @@ k_contract_group(GroupState* __restrict__ gs, const ItemDesc* __restrict__ items
 // ---------------------------------------------------------------------------
 __global__ void __launch_bounds__(DEC_THREADS)
 k_decide_group(GroupState* __restrict__ gs, const ItemDesc* __restrict__ items) {
-  __shared__ int scount;
-  if (threadIdx.x == 0) scount = 0;
-  __syncthreads();
   const int k = find_item(items, gs->n_items, blockIdx.x, 1);
   const ItemDesc& it = items[k];
   const int b = (blockIdx.x - it.dec_begin) * DEC_THREADS + threadIdx.x;
@@ -506,48 +499,54 @@ k_decide_group(GroupState* __restrict__ gs, const ItemDesc* __restrict__ items) 
     } else if (sw < gs->max_iter) {
       keep = 1;
     }
-    if (keep) atomicOr(&it.mt_flag[b / 128], 1u);
-    else it.st[b] = SLOT_DONE;
+    if (!keep) it.st[b] = SLOT_DONE;
     it.amax[b] = it.amax[it.Bp + b];
     it.amax[it.Bp + b] = 0.f;
   }
-  const unsigned bal = __ballot_sync(0xffffffffu, keep);
-  if ((threadIdx.x & 31) == 0 && bal) atomicAdd(&scount, __popc(bal));
-  __syncthreads();
-  if (threadIdx.x == 0 && scount) atomicAdd(&gs->active_next, scount);
 }
 
 // ---------------------------------------------------------------------------
 // Sweep end (one block of 1024): the tile list of the next sweep (every
-// 128-slot tile flagged by the stop test, times its item's N-tiles, in a
-// stable order), the active count, the sweep counter and the graph's loop
-// condition.  initial = 1 builds the first list after the admissions.
+// 128-slot tile holding an active slot, times its item's N-tiles, in a stable
+// order), the active count, the sweep counter and the graph's loop
+// condition.  initial = 1 only rebuilds the list and the count (after
+// admissions), without counting a sweep.
 // ---------------------------------------------------------------------------
 __global__ void __launch_bounds__(1024)
 k_finish_group(GroupState* __restrict__ gs, const ItemDesc* __restrict__ items, int initial,
                cudaGraphConditionalHandle h, int use_handle) {
-  __shared__ int swarp[32];
-  __shared__ int sbase, stotal;
+  __shared__ int swarp[32], sact[32];
+  __shared__ int sbase, stotal, sactive;
   const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
   const int mt_total = gs->mt_total, n_items = gs->n_items;
   uint64_t* tiles = gs->tiles;
-  if (tid == 0) sbase = 0;
+  if (tid == 0) {
+    sbase = 0;
+    sactive = 0;
+  }
   __syncthreads();
   for (int base = 0; base < mt_total; base += 1024) {
     const int m = base + tid;
-    int cnt = 0, k = 0, lm = 0;
+    int cnt = 0, k = 0, lm = 0, na = 0;
     if (m < mt_total) {
       k = find_item(items, n_items, m, 2);
       lm = m - items[k].mt_begin;
-      if (items[k].mt_flag[lm]) cnt = items[k].ntn;
-      items[k].mt_flag[lm] = 0;
+      const uint32_t* st4 = reinterpret_cast<const uint32_t*>(items[k].st + lm * 128);
+      for (int q = 0; q < 32; ++q) {
+        const uint32_t x = st4[q];   // four slot states, SLOT_ACTIVE == 0
+#pragma unroll
+        for (int y = 0; y < 4; ++y) na += ((x >> (8 * y)) & 0xFFu) == SLOT_ACTIVE;
+      }
+      if (na) cnt = items[k].ntn;
     }
-    int incl = cnt;
+    int incl = cnt, acc = na;
     for (int o = 1; o < 32; o <<= 1) {
       const int y = __shfl_up_sync(0xffffffffu, incl, o);
       if (lane >= o) incl += y;
+      acc += __shfl_xor_sync(0xffffffffu, acc, o);
     }
     if (lane == 31) swarp[wid] = incl;
+    if (lane == 0) sact[wid] = acc;
     __syncthreads();
     if (wid == 0) {
       const int x = swarp[lane];
@@ -557,7 +556,10 @@ k_finish_group(GroupState* __restrict__ gs, const ItemDesc* __restrict__ items, 
         if (lane >= o) inc2 += y;
       }
       swarp[lane] = inc2 - x;
+      int a2 = sact[lane];
+      for (int o = 16; o > 0; o >>= 1) a2 += __shfl_xor_sync(0xffffffffu, a2, o);
       if (lane == 31) stotal = inc2;
+      if (lane == 0) sactive += a2;
     }
     __syncthreads();
     const int pos = sbase + swarp[wid] + incl - cnt;
@@ -570,11 +572,9 @@ k_finish_group(GroupState* __restrict__ gs, const ItemDesc* __restrict__ items, 
   if (tid == 0) {
     gs->n_tiles = sbase;
     if (!initial && gs->hist && gs->sweep < gs->hist_n) gs->hist[gs->sweep] = gs->active;
-    const int c = gs->active_next;
-    gs->active = c;
-    gs->active_next = 0;
+    gs->active = sactive;
     if (!initial) gs->sweep = gs->sweep + 1;
-    if (use_handle) cudaGraphSetConditional(h, c > 0 ? 1u : 0u);
+    if (use_handle) cudaGraphSetConditional(h, sactive > 0 ? 1u : 0u);
   }
 }
 
@@ -813,8 +813,7 @@ zbus_status group_build(Group* g, const std::vector<zbus_network>& nets,
     d.R = ws.R;
     d.rinv = ws.rinv;
     d.part = ws.part;
-    d.mt_flag = (uint32_t*)ws.mt;
-    const int rows_pad = op.K_pad / 2;
+      const int rows_pad = op.K_pad / 2;
     const int nchunks = (rows_pad + CHUNK_ROWS - 1) / CHUNK_ROWS;
     d.res_split = (nchunks + RES_WARPS - 1) / RES_WARPS;
     d.res_begin = res;
@@ -880,12 +879,13 @@ zbus_status group_reset(Group* g, cudaStream_t st) {
 }
 
 zbus_status group_admit(Group* g, int k, int64_t s0, int64_t B, const double* V0,
-                        const double* S_wye, const double* S_delta, cudaStream_t st) {
+                        const double* S_wye, const double* S_delta, cudaStream_t st,
+                        bool v0_broadcast) {
   if (B <= 0) return ZBUS_OK;
   const ItemDesc& d = g->h_items[k];
   k_slot_init<<<dim3((d.n + 31) / 32, (unsigned)((B + 31) / 32)), dim3(32, 8), 0, st>>>(
-      g->d_state, g->d_items, k, (int)s0, (int)B, (const double2*)V0, g->nets[k]->w,
-      (const double2*)S_wye, (const double2*)S_delta);
+      g->d_state, g->d_items, k, (int)s0, (int)B, (const double2*)V0, v0_broadcast ? 0 : d.n,
+      g->nets[k]->w, (const double2*)S_wye, (const double2*)S_delta);
   ZB_CUDA(cudaGetLastError());
   return ZBUS_OK;
 }
@@ -893,6 +893,10 @@ zbus_status group_admit(Group* g, int k, int64_t s0, int64_t B, const double* V0
 zbus_status group_start(Group* g, double tol, int32_t max_iter, int32_t rule, int32_t* hist,
                         int32_t hist_n, cudaStream_t st) {
   k_group_params<<<1, 1, 0, st>>>(g->d_state, tol, max_iter, rule, hist, hist_n);
+  return group_rebuild(g, st);
+}
+
+zbus_status group_rebuild(Group* g, cudaStream_t st) {
   k_finish_group<<<1, 1024, 0, st>>>(g->d_state, g->d_items, 1, 0, 0);
   ZB_CUDA(cudaGetLastError());
   return ZBUS_OK;

@@ -41,7 +41,6 @@ struct ItemDesc {
   void* R;                  // [Bp][K_pad] fp16 / bf16 residual rows
   float* rinv;              // [Bp] inverse residual scales
   double* part;             // [Bp][ntn][2] per-tile step partials
-  uint32_t* mt_flag;        // [Bp / 128] tile holds an active slot after the stop test
   // launch decomposition
   int32_t res_begin;        // first residual block
   int32_t res_split;        // residual blocks per 32 slots
@@ -53,7 +52,6 @@ struct ItemDesc {
 struct GroupState {
   int32_t n_items;
   int32_t active;           // active slots at the start of the sweep
-  int32_t active_next;
   int32_t sweep;
   int32_t max_iter;
   int32_t rule;
@@ -107,7 +105,11 @@ void group_free(Group* g);
 // Run start for item k: slots [s0, s0 + B) from v^0 (V0 or w) and the loads
 // (FP64 [B][n]); admitted slots become active.
 zbus_status group_admit(Group* g, int k, int64_t s0, int64_t B, const double* V0,
-                        const double* S_wye, const double* S_delta, cudaStream_t st);
+                        const double* S_wye, const double* S_delta, cudaStream_t st,
+                        bool v0_broadcast = false);
+// Rebuild the tile list and the active count from the slot states (after
+// admissions between sweeps).
+zbus_status group_rebuild(Group* g, cudaStream_t st);
 // Mark every slot of every item free.
 zbus_status group_reset(Group* g, cudaStream_t st);
 // Loop parameters and the initial tile list (after the admissions).

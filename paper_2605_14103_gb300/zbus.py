@@ -41,6 +41,29 @@ class zbus_batch_item(C.Structure):
                 ("iters", C.c_void_p), ("converged", C.c_void_p)]
 
 
+class zbus_request(C.Structure):
+    _fields_ = [("feeder", C.c_int32), ("B", C.c_int64), ("S_wye", C.c_void_p),
+                ("S_delta", C.c_void_p), ("V_out", C.c_void_p), ("iters", C.c_void_p),
+                ("converged", C.c_void_p), ("warm_start", C.c_int32), ("reserved0", C.c_int32),
+                ("tag", C.c_uint64), ("t_arrival", C.c_double)]
+
+
+class zbus_request_result(C.Structure):
+    _fields_ = [("status", C.c_int), ("n_converged", C.c_int32), ("max_iters", C.c_int32),
+                ("reserved0", C.c_int32), ("t_admit", C.c_double), ("t_done", C.c_double),
+                ("V", C.c_void_p), ("iters", C.c_void_p), ("converged", C.c_void_p)]
+
+
+class zbus_serve_config(C.Structure):
+    _fields_ = [("hbm_budget_bytes", C.c_uint64), ("max_slots", C.c_int32),
+                ("precision", C.c_int32), ("conv_rule", C.c_int32), ("max_iter", C.c_int32),
+                ("tol", C.c_double), ("mismatch_tol", C.c_double),
+                ("max_admit_per_sweep", C.c_int32), ("reserved0", C.c_int32)]
+
+
+SOURCE_FN = C.CFUNCTYPE(C.c_int32, C.c_void_p, C.c_double, C.POINTER(zbus_request))
+SINK_FN = C.CFUNCTYPE(None, C.c_void_p, C.POINTER(zbus_request), C.POINTER(zbus_request_result))
+
 _lib = None
 
 _P = C.c_void_p
@@ -63,6 +86,8 @@ _SIGS = {
     "zbus_autotune": (C.c_int, [C.POINTER(zbus_batch_item), C.c_int32,
                                 C.POINTER(zbus_solve_opts), C.c_double, C.c_int32, C.c_int32,
                                 _P, C.POINTER(C.c_int32), C.POINTER(C.c_int32)]),
+    "zbus_serve": (C.c_int, [C.POINTER(zbus_serve_config), C.POINTER(C.c_void_p), C.c_int32,
+                             SOURCE_FN, SINK_FN, C.c_void_p, C.c_void_p]),
     "zbus_status_string": (C.c_char_p, [C.c_int]),
     "zbus_last_error": (C.c_char_p, []),
 }
@@ -262,6 +287,94 @@ def solve_batched(networks, loads, tol=1e-8, max_iter=50, precision="fp16_scaled
         outs.append(out)
     zbus_solve_batched(items, tol, max_iter, o, stream)
     return outs
+
+
+def zbus_serve(cfg, pool_handles, source, sink, stream=None):
+    """Raw call: source(now) -> zbus_request | None | -1; sink(req, res)."""
+    arr = (C.c_void_p * len(pool_handles))(*pool_handles)
+
+    @SOURCE_FN
+    def _src(user, now, out):
+        r = source(now)
+        if r is None:
+            return 0
+        if isinstance(r, int):
+            return r
+        out[0] = r
+        return 1
+
+    @SINK_FN
+    def _snk(user, req, res):
+        sink(req[0], res[0])
+
+    _check(lib().zbus_serve(C.byref(cfg), arr, len(pool_handles), _src, _snk, None,
+                            _stream(stream)))
+
+
+def serve(networks, requests, hbm_budget_bytes=120 << 30, max_slots=4096,
+          precision="fp16_scaled", tol=1e-8, max_iter=50, mismatch_tol=1e-6, rule="maxabs",
+          keep_results=True, max_admit_per_sweep=0, stream=None):
+    """Serve a list of requests over a pool of networks.
+
+    requests: dicts with keys feeder, S_wye, S_delta (device tensors [B, n]),
+    arrival (seconds after the start), optional warm_start.  Returns one dict
+    per request (in input order): status, t_arrival, t_admit, t_done,
+    n_converged, max_iters and, with keep_results, V / iters / converged.
+    """
+    import torch
+    order = sorted(range(len(requests)), key=lambda i: requests[i].get("arrival", 0.0))
+    out = [None] * len(requests)
+    keep = []
+    structs = []
+    for i in order:
+        q = requests[i]
+        ref = q["S_wye"] if q.get("S_wye") is not None else q["S_delta"]
+        B, n = ref.shape
+        r = zbus_request()
+        r.feeder = q["feeder"]
+        r.B = B
+        r.S_wye = q["S_wye"].data_ptr() if q.get("S_wye") is not None else None
+        r.S_delta = q["S_delta"].data_ptr() if q.get("S_delta") is not None else None
+        if keep_results:
+            V = torch.empty((B, n), dtype=torch.complex128, device=ref.device)
+            it = torch.empty((B,), dtype=torch.int32, device=ref.device)
+            cv = torch.empty((B,), dtype=torch.uint8, device=ref.device)
+            keep.append((i, V, it, cv))
+            r.V_out, r.iters, r.converged = V.data_ptr(), it.data_ptr(), cv.data_ptr()
+        r.warm_start = 1 if q.get("warm_start") else 0
+        r.tag = i
+        r.t_arrival = float(q.get("arrival", 0.0))
+        structs.append(r)
+    pos = [0]
+
+    def source(now):
+        if pos[0] >= len(structs):
+            return -1
+        r = structs[pos[0]]
+        if r.t_arrival <= now:
+            pos[0] += 1
+            return r
+        return None
+
+    def sink(req, res):
+        out[req.tag] = {"status": res.status, "t_arrival": req.t_arrival, "t_admit": res.t_admit,
+                        "t_done": res.t_done, "n_converged": res.n_converged,
+                        "max_iters": res.max_iters, "B": req.B}
+
+    cfg = zbus_serve_config()
+    cfg.hbm_budget_bytes = int(hbm_budget_bytes)
+    cfg.max_slots = int(max_slots)
+    cfg.precision = PRECISION[precision]
+    cfg.conv_rule = RULE[rule]
+    cfg.max_iter = int(max_iter)
+    cfg.tol = float(tol)
+    cfg.mismatch_tol = float(mismatch_tol)
+    cfg.max_admit_per_sweep = int(max_admit_per_sweep)
+    zbus_serve(cfg, [net.handle for net in networks], source, sink, stream)
+    for i, V, it, cv in keep:
+        if out[i] is not None:
+            out[i].update(V=V, iters=it, converged=cv)
+    return out
 
 
 def zbus_status_string(s: int) -> str:
