@@ -128,23 +128,13 @@ def barrier(ws):
 
 
 def allreduce_max(x, ws):
-    if ws == 1:
-        return x
-    import torch
-    import torch.distributed as dist
-    t = torch.tensor([x], dtype=torch.float64, device="cuda")
-    dist.all_reduce(t, op=dist.ReduceOp.MAX)
-    return float(t.item())
+    from paper_2605_14103_gb300 import dist as D
+    return D.reduce_max(x, device="cuda") if ws > 1 else x
 
 
 def allreduce_sum(x, ws):
-    if ws == 1:
-        return x
-    import torch
-    import torch.distributed as dist
-    t = torch.tensor([x], dtype=torch.float64, device="cuda")
-    dist.all_reduce(t, op=dist.ReduceOp.SUM)
-    return float(t.item())
+    from paper_2605_14103_gb300 import dist as D
+    return D.reduce_sum(x, device="cuda") if ws > 1 else x
 
 
 # ---------------------------------------------------------------------------
@@ -205,7 +195,8 @@ def run_reference(args):
         return
     from oracle import zbus_oracle as O
     from paper_2605_14103_gb300 import feeders as F
-    f, Sw, Sd, wl = F.make_workload(args.workload)
+    workload = args.workload if args.workload in F.WORKLOADS else "feeder128_b4096"
+    f, Sw, Sd, wl = F.make_workload(workload)
     Z, w = oracle_setup(f)
     bs = min(wl.B, 512)
     for s in range(args.warmup):
@@ -223,7 +214,7 @@ def run_reference(args):
            "n_gpus": ws, "steps": args.steps, "warmup": args.warmup,
            "ms_per_step": 1e3 * total / args.steps, "higher_is_better": True,
            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-           "config": {"workload": args.workload, "feeder_buses": wl.N, "unknowns": 3 * (wl.N - 1),
+           "config": {"workload": workload, "feeder_buses": wl.N, "unknowns": 3 * (wl.N - 1),
                       "scenarios_per_step": bs, "tol": wl.tol},
            "cpu_baseline": {"value": value, "unit": UNIT, "cores": cpu_cores(), "kind": "oracle",
                             "sample": f"{bs} scenarios of the {wl.B}-scenario batch per step"},
@@ -368,7 +359,8 @@ def run_ours(args):
     peaks = load_peaks()
     f, _, _, wl = F.make_workload(args.workload, B=1)
     Bw = args.batch if args.batch > 0 else wl.B
-    Sw_h, Sd_h = F.make_scenarios(f, Bw, wl.mult[0], wl.mult[1], seed=f.seed + 1 + 7919 * rank)
+    from paper_2605_14103_gb300 import dist as D
+    Sw_h, Sd_h = F.make_scenarios(f, Bw, wl.mult[0], wl.mult[1], seed=D.rank_seed(f.seed + 1, rank))
     B, n = Sw_h.shape
     Sw = torch.from_numpy(Sw_h).cuda()
     Sd = torch.from_numpy(Sd_h).cuda()
