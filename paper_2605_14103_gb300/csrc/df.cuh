@@ -34,6 +34,15 @@ __device__ __forceinline__ void df_mac(float& sh, float& sl, float ah, float al,
   sl = __fadd_rn(sl, __fadd_rn(t, e));
 }
 
+// (dh, dl) = (bh + bl) - (ah + al), unnormalised (|dl| small against |dh|).
+__device__ __forceinline__ void df_sub(float bh, float bl, float ah, float al, float& dh,
+                                       float& dl) {
+  float s, e;
+  two_sum(bh, -ah, s, e);
+  dh = s;
+  dl = __fadd_rn(e, __fsub_rn(bl, al));
+}
+
 // Split a double into hi + lo floats.
 __device__ __forceinline__ float2 df_split(double x) {
   const float h = __double2float_rn(x);

@@ -131,10 +131,12 @@ __global__ void k_group_params(GroupState* gs, double tol, int max_iter, int rul
 }
 
 // ---------------------------------------------------------------------------
-// Defect residual, one slot per lane, double-float over 3x3 bus blocks:
-//   r_j = i_j(v) - sum_b Y_LL[a][b] v_b - ys_j        (bus a holds rows 3a..3a+2)
-// The admittance sum (terms ~1e3 cancelling to ~1e-10 near the solution) runs
-// in double-float with the blocks loaded once per warp for 32 slots; the load
+// Defect residual, one slot per lane, double-float, branch form per bus a
+// (rows 3a..3a+2):
+//   r_a = i_a(v) - [sum_b Y_ab (v_b - v_a) + Y_as (v_s - v_a) + Sh_a v_a]
+// The admittance sum (currents up to ~10 pu cancelling to ~1e-10 near the
+// solution) runs in double-float with the blocks loaded once per warp for 32
+// slots; the load
 // current (~1e-2, no cancellation) in FP32 from the hi part.  R[b][2j],
 // R[b][2j+1] = round(c_b Re r_j), round(c_b Im r_j) with c_b = 2^(12 -
 // floor(log2 amax_prev_b)) from the previous sweep's max |r| (the residual
@@ -170,7 +172,6 @@ k_residual_group(GroupState* __restrict__ gs, const ItemDesc* __restrict__ items
   const int32_t* __restrict__ bptr = it.bsr_ptr;
   const int32_t* __restrict__ bcol = it.bsr_col;
   const float4* __restrict__ bval = it.bsr_df;
-  const float4* __restrict__ ys4 = it.ys_df;
   const int nb = it.nbus;
   const int rows_pad = it.K_pad >> 1;
   const int nchunks = (rows_pad + CHUNK_ROWS - 1) / CHUNK_ROWS;
@@ -180,29 +181,43 @@ k_residual_group(GroupState* __restrict__ gs, const ItemDesc* __restrict__ items
       const int a = ch * CHUNK_BUS + q;
       float2 r[3] = {make_float2(0.f, 0.f), make_float2(0.f, 0.f), make_float2(0.f, 0.f)};
       if (a < nb && act) {
-        float2 vv[3], sw[3], sd[3], inj[3];
+        float2 ah3[3], al3[3], sw[3], sd[3], inj[3];   // own state (hi, lo), loads
 #pragma unroll
         for (int p = 0; p < 3; ++p) {
           const int64_t g = (int64_t)(3 * a + p) * Bp + b;
-          vv[p] = Vh[g];
+          ah3[p] = Vh[g];
+          al3[p] = Vl[g];
           sw[p] = Sw[g];
           sd[p] = Sd[g];
         }
-        bus_injection_f(vv, sw, sd, 3, inj);
+        bus_injection_f(ah3, sw, sd, 3, inj);
         float ah[3][2], al[3][2];   // accumulators (re, im) per phase, hi / lo
 #pragma unroll
-        for (int p = 0; p < 3; ++p) {
-          const float4 y0 = ys4[3 * a + p];
-          ah[p][0] = y0.x; al[p][0] = y0.y; ah[p][1] = y0.z; al[p][1] = y0.w;
-        }
+        for (int p = 0; p < 3; ++p) ah[p][0] = al[p][0] = ah[p][1] = al[p][1] = 0.f;
         for (int t = bptr[a]; t < bptr[a + 1]; ++t) {
-          const int cb = bcol[t];
-          float2 xh[3], xl[3];
+          const int cb = bcol[t];   // the same for the whole warp
+          float dh[3][2], dl[3][2];   // vector multiplied by the block, double-float
+          if (cb >= 0) {
 #pragma unroll
-          for (int q2 = 0; q2 < 3; ++q2) {
-            const int64_t g = (int64_t)(3 * cb + q2) * Bp + b;
-            xh[q2] = Vh[g];
-            xl[q2] = Vl[g];
+            for (int q2 = 0; q2 < 3; ++q2) {
+              const int64_t g = (int64_t)(3 * cb + q2) * Bp + b;
+              const float2 xh = Vh[g], xl = Vl[g];
+              df_sub(xh.x, xl.x, ah3[q2].x, al3[q2].x, dh[q2][0], dl[q2][0]);
+              df_sub(xh.y, xl.y, ah3[q2].y, al3[q2].y, dh[q2][1], dl[q2][1]);
+            }
+          } else if (cb == -1) {
+#pragma unroll
+            for (int q2 = 0; q2 < 3; ++q2) {
+              const float4 s4 = it.vs_df[q2];
+              df_sub(s4.x, s4.y, ah3[q2].x, al3[q2].x, dh[q2][0], dl[q2][0]);
+              df_sub(s4.z, s4.w, ah3[q2].y, al3[q2].y, dh[q2][1], dl[q2][1]);
+            }
+          } else {
+#pragma unroll
+            for (int q2 = 0; q2 < 3; ++q2) {
+              dh[q2][0] = ah3[q2].x; dl[q2][0] = al3[q2].x;
+              dh[q2][1] = ah3[q2].y; dl[q2][1] = al3[q2].y;
+            }
           }
           const float4* yb = bval + (int64_t)t * 9;
 #pragma unroll
@@ -210,10 +225,10 @@ k_residual_group(GroupState* __restrict__ gs, const ItemDesc* __restrict__ items
 #pragma unroll
             for (int q2 = 0; q2 < 3; ++q2) {
               const float4 y = yb[p * 3 + q2];
-              df_mac(ah[p][0], al[p][0], y.x, y.y, xh[q2].x, xl[q2].x);     // + yr vr
-              df_mac(ah[p][0], al[p][0], -y.z, -y.w, xh[q2].y, xl[q2].y);   // - yi vi
-              df_mac(ah[p][1], al[p][1], y.x, y.y, xh[q2].y, xl[q2].y);     // + yr vi
-              df_mac(ah[p][1], al[p][1], y.z, y.w, xh[q2].x, xl[q2].x);     // + yi vr
+              df_mac(ah[p][0], al[p][0], y.x, y.y, dh[q2][0], dl[q2][0]);     // + yr dr
+              df_mac(ah[p][0], al[p][0], -y.z, -y.w, dh[q2][1], dl[q2][1]);   // - yi di
+              df_mac(ah[p][1], al[p][1], y.x, y.y, dh[q2][1], dl[q2][1]);     // + yr di
+              df_mac(ah[p][1], al[p][1], y.z, y.w, dh[q2][0], dl[q2][0]);     // + yi dr
             }
           }
         }
@@ -410,11 +425,25 @@ k_contract_group(GroupState* __restrict__ gs, const ItemDesc* __restrict__ items
       const bool valid = it.st[b] == SLOT_ACTIVE;
       const float rs = valid ? it.rinv[b] : 0.f;
       const float* __restrict__ zinv = it.zinv;
-      float2* Vh = it.Vh + b;
-      float2* Vl = it.Vl + b;
+      float2* __restrict__ Vh = it.Vh + b;
+      float2* __restrict__ Vl = it.Vl + b;
       float dmax = 0.f, dsum = 0.f;
 #pragma unroll 1
       for (int c = 0; c < BN / 32; ++c) {
+        const int i0 = (nt * BN + c * 32) >> 1;
+        // the chunk's 16 state entries are requested before any of them is
+        // used, so their memory latencies overlap
+        float2 h[16], l[16];
+        float zs[16];
+#pragma unroll
+        for (int t = 0; t < 16; ++t) {
+          const int oi = i0 + t;
+          const bool in = valid && oi < n;
+          const int64_t gi = (int64_t)(in ? oi : 0) * Bp;
+          h[t] = in ? Vh[gi] : make_float2(0.f, 0.f);
+          l[t] = in ? Vl[gi] : make_float2(0.f, 0.f);
+          zs[t] = in ? zinv[oi] : 0.f;
+        }
         float v[32];
         tmem_ld32(tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)(buf * BN + c * 32), v);
         if (c == BN / 32 - 1) {
@@ -424,21 +453,19 @@ k_contract_group(GroupState* __restrict__ gs, const ItemDesc* __restrict__ items
           if (lane == 0) mbar_arrive(&tempty[buf]);
         }
         if (valid) {
-          const int i0 = (nt * BN + c * 32) >> 1;
 #pragma unroll
           for (int t = 0; t < 16; ++t) {
             const int oi = i0 + t;
             if (oi < n) {
-              const float sc = rs * zinv[oi];
+              const float sc = rs * zs[t];
               const float dr = v[2 * t] * sc, di = v[2 * t + 1] * sc;
-              const int64_t gi = (int64_t)oi * Bp;
-              const float2 h = Vh[gi], l = Vl[gi];
               float sr, er, si, ei;
-              two_sum(h.x, dr, sr, er);
-              two_sum(h.y, di, si, ei);
+              two_sum(h[t].x, dr, sr, er);
+              two_sum(h[t].y, di, si, ei);
               float2 nh, nl;
-              fast_two_sum(sr, __fadd_rn(er, l.x), nh.x, nl.x);
-              fast_two_sum(si, __fadd_rn(ei, l.y), nh.y, nl.y);
+              fast_two_sum(sr, __fadd_rn(er, l[t].x), nh.x, nl.x);
+              fast_two_sum(si, __fadd_rn(ei, l[t].y), nh.y, nl.y);
+              const int64_t gi = (int64_t)oi * Bp;
               Vh[gi] = nh;
               Vl[gi] = nl;
               float step = sqrtf(__fmaf_rn(dr, dr, di * di));
@@ -446,9 +473,9 @@ k_contract_group(GroupState* __restrict__ gs, const ItemDesc* __restrict__ items
               dmax = fmaxf(dmax, step);
               if (summag) {
                 // |v + d| - |v| = (2 Re(conj(v) d) + |d|^2) / (|v + d| + |v|)
-                const float o2 = __fmaf_rn(h.x, h.x, h.y * h.y);
+                const float o2 = __fmaf_rn(h[t].x, h[t].x, h[t].y * h[t].y);
                 const float n2 = __fmaf_rn(nh.x, nh.x, nh.y * nh.y);
-                dsum += (2.f * (h.x * dr + h.y * di) + dr * dr + di * di) /
+                dsum += (2.f * (h[t].x * dr + h[t].y * di) + dr * dr + di * di) /
                         (sqrtf(n2) + sqrtf(o2));
               }
             }
@@ -615,17 +642,35 @@ __global__ void k_slot_merge(const ItemDesc* __restrict__ items, int k, int s0, 
   }
 }
 
-// FP64 check of converged scenarios: max_j |v_j| |(Y_LL v + ys)_j - i_j(v)|
-// with the sparse admittance matrix; a flag above mtol is cleared.  One
-// block per scenario, v staged in shared memory (16 n bytes).
-__global__ void __launch_bounds__(256)
+// 1 / d for the FP64 check: a single-precision reciprocal refined by two
+// Newton-Raphson steps r <- r (2 - d r) (quadratic convergence, 24 -> 48 ->
+// beyond 53 bits); plain division outside the single-precision range.
+__device__ __forceinline__ double recip64(double d) {
+  if (!(d > 1e-30 && d < 1e30)) return 1.0 / d;
+  double r = (double)__frcp_rn((float)d);
+  r = r * fma(-d, r, 2.0);
+  r = r * fma(-d, r, 2.0);
+  return r;
+}
+
+__device__ __forceinline__ double2 draw64(double2 S, double2 v) {
+  if (S.x == 0.0 && S.y == 0.0) return make_double2(0.0, 0.0);
+  const double inv = recip64(fma(v.x, v.x, v.y * v.y));
+  return make_double2(fma(S.x, v.x, S.y * v.y) * inv, fma(S.x, v.y, -S.y * v.x) * inv);
+}
+
+// FP64 check of converged scenarios: max_j |v_j| |(Y_LL v + Y_Ls v_s)_j - i_j(v)|
+// from the branch-form blocks (the same sum as the admittance rows); a flag
+// above mtol is cleared.  One block per scenario, v staged in shared memory
+// (16 n bytes), one thread per bus.
+__global__ void __launch_bounds__(128)
 k_check(const double2* __restrict__ V, const double2* __restrict__ Sw,
         const double2* __restrict__ Sd, uint8_t* __restrict__ conv, int n,
-        const int32_t* __restrict__ ptr, const int32_t* __restrict__ col,
-        const double2* __restrict__ val, const double2* __restrict__ ys, double mtol,
+        const int32_t* __restrict__ bptr, const int32_t* __restrict__ bcol,
+        const double2* __restrict__ bval, double2 vs0, double2 vs1, double2 vs2, double mtol,
         double* mm_out) {
   extern __shared__ double2 vsm[];
-  __shared__ double red[32];
+  __shared__ double red[4];
   const int b = blockIdx.x;
   if (conv[b] == 0) {
     if (threadIdx.x == 0 && mm_out) mm_out[b] = -1.0;
@@ -634,30 +679,49 @@ k_check(const double2* __restrict__ V, const double2* __restrict__ Sw,
   const double2* vg = V + (int64_t)b * n;
   for (int j = threadIdx.x; j < n; j += blockDim.x) vsm[j] = vg[j];
   __syncthreads();
-  const double2* sw0 = Sw ? Sw + (int64_t)b * n : nullptr;
-  const double2* sd0 = Sd ? Sd + (int64_t)b * n : nullptr;
+  const double2 vs[3] = {vs0, vs1, vs2};
   double worst = 0.0;   // max |v|^2 |r|^2
-  const int nb = (n + 2) / 3;
-  for (int k = threadIdx.x; k < nb; k += blockDim.x) {
-    const int j0 = 3 * k;
-    const int m = min(3, n - j0);
-    double2 vv[3], sw[3], sd[3], inj[3];
+  const int nb = n / 3;
+  for (int a = threadIdx.x; a < nb; a += blockDim.x) {
+    double2 va[3], drawn[3];
     for (int p = 0; p < 3; ++p) {
-      vv[p] = p < m ? vsm[j0 + p] : make_double2(1.0, 0.0);
-      sw[p] = (sw0 && p < m) ? sw0[j0 + p] : make_double2(0.0, 0.0);
-      sd[p] = (sd0 && p < m) ? sd0[j0 + p] : make_double2(0.0, 0.0);
+      va[p] = vsm[3 * a + p];
+      const double2 s = Sw ? Sw[(int64_t)b * n + 3 * a + p] : make_double2(0.0, 0.0);
+      drawn[p] = draw64(s, va[p]);
     }
-    bus_injection(vv, sw0 ? sw : nullptr, sd0 ? sd : nullptr, m, inj);
-    for (int p = 0; p < m; ++p) {
-      const int j = j0 + p;
-      double2 acc = ys[j];
-      for (int t = ptr[j]; t < ptr[j + 1]; ++t) {
-        const double2 y = val[t], x = vsm[col[t]];
-        acc.x = fma(y.x, x.x, fma(-y.y, x.y, acc.x));
-        acc.y = fma(y.x, x.y, fma(y.y, x.x, acc.y));
+    if (Sd) {
+      const double2* sd = Sd + (int64_t)b * n + 3 * a;
+      double2 ib[3];
+      for (int p = 0; p < 3; ++p) {
+        const int q = (p + 1) % 3;
+        ib[p] = draw64(sd[p], make_double2(va[p].x - va[q].x, va[p].y - va[q].y));
       }
-      const double rx = acc.x - inj[p].x, ry = acc.y - inj[p].y;
-      double e = (vv[p].x * vv[p].x + vv[p].y * vv[p].y) * (rx * rx + ry * ry);
+      for (int p = 0; p < 3; ++p) {
+        const int m = (p + 2) % 3;   // branch into phase p is (m -> p)
+        drawn[p].x += ib[p].x - ib[m].x;
+        drawn[p].y += ib[p].y - ib[m].y;
+      }
+    }
+    double2 acc[3] = {make_double2(0.0, 0.0), make_double2(0.0, 0.0), make_double2(0.0, 0.0)};
+    for (int t = bptr[a]; t < bptr[a + 1]; ++t) {
+      const int cb = bcol[t];
+      double2 d[3];
+      for (int q = 0; q < 3; ++q) {
+        const double2 x = cb >= 0 ? vsm[3 * cb + q] : (cb == -1 ? vs[q] : make_double2(0.0, 0.0));
+        d[q] = cb == -2 ? va[q] : make_double2(x.x - va[q].x, x.y - va[q].y);
+      }
+      const double2* y = bval + (int64_t)t * 9;
+      for (int p = 0; p < 3; ++p)
+        for (int q = 0; q < 3; ++q) {
+          const double2 yy = y[p * 3 + q];
+          acc[p].x = fma(yy.x, d[q].x, fma(-yy.y, d[q].y, acc[p].x));
+          acc[p].y = fma(yy.x, d[q].y, fma(yy.y, d[q].x, acc[p].y));
+        }
+    }
+    for (int p = 0; p < 3; ++p) {
+      // r = (Y v + Y_Ls v_s) - i = acc + drawn
+      const double rx = acc[p].x + drawn[p].x, ry = acc[p].y + drawn[p].y;
+      double e = (va[p].x * va[p].x + va[p].y * va[p].y) * (rx * rx + ry * ry);
       if (e != e) e = INFINITY;
       worst = fmax(worst, e);
     }
@@ -794,7 +858,11 @@ zbus_status group_build(Group* g, const std::vector<zbus_network>& nets,
     d.bsr_ptr = net->bsr_ptr;
     d.bsr_col = net->bsr_col;
     d.bsr_df = net->bsr_df;
-    d.ys_df = net->ys_df;
+    for (int q = 0; q < 3; ++q) {
+      const double2 v = net->v_slack[q];
+      const float rh = (float)v.x, ih = (float)v.y;
+      d.vs_df[q] = make_float4(rh, (float)(v.x - (double)rh), ih, (float)(v.y - (double)ih));
+    }
     d.zinv = op.zinv;
     d.n = net->n;
     d.nbus = net->nbus;
@@ -955,9 +1023,10 @@ zbus_status group_collect(Group* g, int k, int64_t s0, int64_t B, double* V_out,
   zbus_network net = g->nets[k];
   k_slot_merge<<<dim3((net->n + 31) / 32, (unsigned)((B + 31) / 32)), dim3(32, 8), 0, st>>>(
       g->d_items, k, (int)s0, (int)B, (double2*)V_out, iters, converged);
-  k_check<<<(unsigned)B, 256, (size_t)16 * net->n, st>>>(
+  k_check<<<(unsigned)B, 128, (size_t)16 * net->n, st>>>(
       (const double2*)V_out, (const double2*)S_wye, (const double2*)S_delta, converged, net->n,
-      net->csr_ptr, net->csr_col, net->csr_val, net->ys, mtol, mm_out);
+      net->bsr_ptr, net->bsr_col, net->bsr_val, net->v_slack[0], net->v_slack[1],
+      net->v_slack[2], mtol, mm_out);
   ZB_CUDA(cudaGetLastError());
   return ZBUS_OK;
 }

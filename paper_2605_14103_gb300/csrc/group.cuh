@@ -24,8 +24,8 @@ struct ItemDesc {
   // network operands
   const int32_t* bsr_ptr;
   const int32_t* bsr_col;
-  const float4* bsr_df;     // [nblk][9] double-float 3x3 blocks of Y_LL
-  const float4* ys_df;      // [n] double-float Y_Ls v_s
+  const float4* bsr_df;     // [nblk][9] double-float branch-form blocks
+  float4 vs_df[3];          // slack phase voltages, double-float (re hi, re lo, im hi, im lo)
   const float* zinv;        // [N_pad / 2] inverse row scales of Z
   int32_t n, nbus, K_pad, N_pad, ntn;
   int32_t Bp;               // slot capacity, multiple of 128

@@ -245,8 +245,14 @@ zbus_status build_network(zbus_network net, int32_t n_total, int64_t nnz, const 
   for (int i = 0; i < n; ++i) mr = std::max(mr, lp[i + 1] - lp[i]);
   net->max_row_nnz = mr;
 
-  // 3x3 bus-block form of Y_LL (block (a, b) holds rows 3a..3a+2, columns
-  // 3b..3b+2; absent entries are zero), for networks with three unknowns per bus
+  // Branch form of the admittance rows, per bus a (rows 3a..3a+2), used by
+  // the mixed sweeps and the FP64 mismatch test:
+  //   (Y_LL v + Y_Ls v_s)_a = sum_{b != a} Y_ab (v_b - v_a) + Y_as (v_s - v_a) + Sh_a v_a
+  // with Sh_a = Y_aa + sum_{b != a} Y_ab + Y_as the block row sum (the shunt;
+  // zero up to rounding for series-only lines, and then left out).  Entries:
+  // column >= 0 a neighbour bus, -1 the slack, -2 the shunt; 3x3 complex
+  // blocks, row-major.  Differences of neighbouring voltages are small, so
+  // the products stay well conditioned.
   if (net->bus_aligned) {
     const int nb = n / 3;
     std::vector<int32_t> bp(nb + 1, 0), bc;
@@ -254,18 +260,54 @@ zbus_status build_network(zbus_network net, int32_t n_total, int64_t nnz, const 
     for (int a = 0; a < nb; ++a) {
       std::vector<int32_t> cols;
       for (int r = 3 * a; r < 3 * a + 3; ++r)
-        for (int t = lp[r]; t < lp[r + 1]; ++t) cols.push_back(lc[t] / 3);
+        for (int t = lp[r]; t < lp[r + 1]; ++t)
+          if (lc[t] / 3 != a) cols.push_back(lc[t] / 3);
       std::sort(cols.begin(), cols.end());
       cols.erase(std::unique(cols.begin(), cols.end()), cols.end());
+      double2 diag[9], slk[9], sh[9];
+      for (int e = 0; e < 9; ++e) diag[e] = slk[e] = sh[e] = make_double2(0.0, 0.0);
+      bool has_slack = false;
       const size_t base = bc.size();
       for (int c : cols) bc.push_back(c);
       bv.resize(bc.size() * 9, make_double2(0.0, 0.0));
-      for (int r = 3 * a; r < 3 * a + 3; ++r)
+      for (int r = 3 * a; r < 3 * a + 3; ++r) {
         for (int t = lp[r]; t < lp[r + 1]; ++t) {
           const int cb = lc[t] / 3;
-          const size_t k = base + (std::lower_bound(cols.begin(), cols.end(), cb) - cols.begin());
-          bv[k * 9 + (size_t)(r - 3 * a) * 3 + (lc[t] - 3 * cb)] = lv[t];
+          const int e = (r - 3 * a) * 3 + (lc[t] - 3 * cb);
+          if (cb == a) {
+            diag[e] = lv[t];
+          } else {
+            const size_t k = base + (std::lower_bound(cols.begin(), cols.end(), cb) - cols.begin());
+            bv[k * 9 + e] = lv[t];
+          }
         }
+        for (int t = sp[r]; t < sp[r + 1]; ++t) {
+          slk[(r - 3 * a) * 3 + sc[t]] = sv[t];
+          has_slack = true;
+        }
+      }
+      // shunt = block row sum, summed in a fixed order
+      double ymax = 0.0, smax = 0.0;
+      for (int e = 0; e < 9; ++e) {
+        double2 acc = diag[e];
+        for (size_t k = base; k < bc.size(); ++k) {
+          acc.x += bv[k * 9 + e].x;
+          acc.y += bv[k * 9 + e].y;
+        }
+        acc.x += slk[e].x;
+        acc.y += slk[e].y;
+        sh[e] = acc;
+        ymax = std::max(ymax, std::hypot(diag[e].x, diag[e].y));
+        smax = std::max(smax, std::hypot(acc.x, acc.y));
+      }
+      if (has_slack) {
+        bc.push_back(-1);
+        bv.insert(bv.end(), slk, slk + 9);
+      }
+      if (smax > 1e-12 * ymax) {
+        bc.push_back(-2);
+        bv.insert(bv.end(), sh, sh + 9);
+      }
       bp[a + 1] = (int32_t)bc.size();
     }
     net->nbus = nb;

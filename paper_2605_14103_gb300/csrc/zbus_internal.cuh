@@ -164,10 +164,12 @@ struct zbus_network_s {
   int max_row_nnz = 0;
   float4* csr_df = nullptr;  // Y_LL values as double-float (re hi, re lo, im hi, im lo)
   float4* ys_df = nullptr;   // Y_Ls v_s as double-float
-  // Y_LL as 3x3 bus blocks (networks with n % 3 == 0): block rows per bus
+  // branch form of the admittance rows per bus (networks with n % 3 == 0):
+  // entries with column >= 0 (neighbour bus: Y_ab (v_b - v_a)), -1 (slack:
+  // Y_as (v_s - v_a)) or -2 (shunt: Sh_a v_a); 3x3 complex blocks
   int nbus = 0;
   int32_t* bsr_ptr = nullptr;   // [nbus + 1]
-  int32_t* bsr_col = nullptr;   // [nblk] bus column
+  int32_t* bsr_col = nullptr;   // [nblk]
   double2* bsr_val = nullptr;   // [nblk][3][3] row-major complex
   int64_t nblk = 0;
   float4* bsr_df = nullptr;     // [nblk][9] double-float copy (mixed sweeps)
