@@ -145,8 +145,8 @@ __global__ void k_group_params(GroupState* gs, double tol, int max_iter, int rul
 // covers 4 buses (12 rows) per chunk and writes them through a shared-memory
 // transpose; rows n .. K_pad/2 - 1 are written as zeros.
 // ---------------------------------------------------------------------------
-template <bool BF>
-__global__ void __launch_bounds__(RES_WARPS * 32)
+template <bool BF, int MINB>
+__global__ void __launch_bounds__(RES_WARPS * 32, MINB)
 k_residual_group(GroupState* __restrict__ gs, const ItemDesc* __restrict__ items) {
   __shared__ uint32_t stage[RES_WARPS][CHUNK_ROWS][32];
   __shared__ float sred[RES_WARPS][32];
@@ -642,9 +642,9 @@ __global__ void k_slot_merge(const ItemDesc* __restrict__ items, int k, int s0, 
   }
 }
 
-// 1 / d for the FP64 check: a single-precision reciprocal refined by two
-// Newton-Raphson steps r <- r (2 - d r) (quadratic convergence, 24 -> 48 ->
-// beyond 53 bits); plain division outside the single-precision range.
+// 1 / d: a single-precision reciprocal refined by two Newton-Raphson steps
+// r <- r (2 - d r) (quadratic convergence, 24 -> 48 -> beyond 53 bits);
+// plain division outside the single-precision range.
 __device__ __forceinline__ double recip64(double d) {
   if (!(d > 1e-30 && d < 1e30)) return 1.0 / d;
   double r = (double)__frcp_rn((float)d);
@@ -653,16 +653,20 @@ __device__ __forceinline__ double recip64(double d) {
   return r;
 }
 
+// conj(S / v), zero for an absent load.
 __device__ __forceinline__ double2 draw64(double2 S, double2 v) {
   if (S.x == 0.0 && S.y == 0.0) return make_double2(0.0, 0.0);
   const double inv = recip64(fma(v.x, v.x, v.y * v.y));
   return make_double2(fma(S.x, v.x, S.y * v.y) * inv, fma(S.x, v.y, -S.y * v.x) * inv);
 }
 
-// FP64 check of converged scenarios: max_j |v_j| |(Y_LL v + Y_Ls v_s)_j - i_j(v)|
-// from the branch-form blocks (the same sum as the admittance rows); a flag
-// above mtol is cleared.  One block per scenario, v staged in shared memory
-// (16 n bytes), one thread per bus.
+// FP64 check of converged scenarios, in power form: for every unknown j,
+//   dS_j = v_j conj((Y_LL v + Y_Ls v_s)_j) - v_j conj(i_j(v)),  |dS_j| = |v_j| |r_j|
+// with the admittance rows summed in FP64 from the branch-form blocks, the wye
+// term exactly S_j (v conj(conj(S / v)) = S, no division) and the delta term
+// v_j conj(drawn) from FP64 branch currents.  A converged flag with
+// max_j |dS_j| above mtol is cleared.  One block per scenario, v staged in
+// shared memory (16 n bytes), one thread per bus.
 __global__ void __launch_bounds__(128)
 k_check(const double2* __restrict__ V, const double2* __restrict__ Sw,
         const double2* __restrict__ Sd, uint8_t* __restrict__ conv, int n,
@@ -680,28 +684,11 @@ k_check(const double2* __restrict__ V, const double2* __restrict__ Sw,
   for (int j = threadIdx.x; j < n; j += blockDim.x) vsm[j] = vg[j];
   __syncthreads();
   const double2 vs[3] = {vs0, vs1, vs2};
-  double worst = 0.0;   // max |v|^2 |r|^2
+  double worst = 0.0;   // max |dS|^2
   const int nb = n / 3;
   for (int a = threadIdx.x; a < nb; a += blockDim.x) {
-    double2 va[3], drawn[3];
-    for (int p = 0; p < 3; ++p) {
-      va[p] = vsm[3 * a + p];
-      const double2 s = Sw ? Sw[(int64_t)b * n + 3 * a + p] : make_double2(0.0, 0.0);
-      drawn[p] = draw64(s, va[p]);
-    }
-    if (Sd) {
-      const double2* sd = Sd + (int64_t)b * n + 3 * a;
-      double2 ib[3];
-      for (int p = 0; p < 3; ++p) {
-        const int q = (p + 1) % 3;
-        ib[p] = draw64(sd[p], make_double2(va[p].x - va[q].x, va[p].y - va[q].y));
-      }
-      for (int p = 0; p < 3; ++p) {
-        const int m = (p + 2) % 3;   // branch into phase p is (m -> p)
-        drawn[p].x += ib[p].x - ib[m].x;
-        drawn[p].y += ib[p].y - ib[m].y;
-      }
-    }
+    double2 va[3];
+    for (int p = 0; p < 3; ++p) va[p] = vsm[3 * a + p];
     double2 acc[3] = {make_double2(0.0, 0.0), make_double2(0.0, 0.0), make_double2(0.0, 0.0)};
     for (int t = bptr[a]; t < bptr[a + 1]; ++t) {
       const int cb = bcol[t];
@@ -718,10 +705,33 @@ k_check(const double2* __restrict__ V, const double2* __restrict__ Sw,
           acc[p].y = fma(yy.x, d[q].y, fma(yy.y, d[q].x, acc[p].y));
         }
     }
+    // dS_p = v_p conj(acc_p) + S_wye_p + v_p conj(drawn_delta_p)
+    double2 dS[3];
     for (int p = 0; p < 3; ++p) {
-      // r = (Y v + Y_Ls v_s) - i = acc + drawn
-      const double rx = acc[p].x + drawn[p].x, ry = acc[p].y + drawn[p].y;
-      double e = (va[p].x * va[p].x + va[p].y * va[p].y) * (rx * rx + ry * ry);
+      dS[p] = make_double2(fma(va[p].x, acc[p].x, va[p].y * acc[p].y),
+                           fma(va[p].y, acc[p].x, -va[p].x * acc[p].y));
+      if (Sw) {
+        const double2 s = Sw[(int64_t)b * n + 3 * a + p];
+        dS[p].x += s.x;
+        dS[p].y += s.y;
+      }
+    }
+    if (Sd) {
+      const double2* sd = Sd + (int64_t)b * n + 3 * a;
+      double2 ib[3];
+      for (int p = 0; p < 3; ++p) {
+        const int q = (p + 1) % 3;
+        ib[p] = draw64(sd[p], make_double2(va[p].x - va[q].x, va[p].y - va[q].y));
+      }
+      for (int p = 0; p < 3; ++p) {
+        const int m = (p + 2) % 3;   // branch p leaves phase p, branch m returns into it
+        const double gx = ib[p].x - ib[m].x, gy = ib[p].y - ib[m].y;
+        dS[p].x += fma(va[p].x, gx, va[p].y * gy);
+        dS[p].y += fma(va[p].y, gx, -va[p].x * gy);
+      }
+    }
+    for (int p = 0; p < 3; ++p) {
+      double e = fma(dS[p].x, dS[p].x, dS[p].y * dS[p].y);
       if (e != e) e = INFINITY;
       worst = fmax(worst, e);
     }
@@ -841,6 +851,7 @@ zbus_status group_build(Group* g, const std::vector<zbus_network>& nets,
   if (!var) var = default_variant(precision, max_n);
   g->BN = var->BN;
   g->stages = var->stages;
+  g->max_n = max_n;
   ZB_CUDA(var->attr());
   int dev = 0;
   ZB_CUDA(cudaGetDevice(&dev));
@@ -974,10 +985,18 @@ zbus_status group_sweep(Group* g, cudaGraphConditionalHandle h, bool use_handle,
                         cudaEvent_t* ev) {
   const bool bf = g->precision == ZBUS_MIXED_BF16X2;
   if (ev) ZB_CUDA(cudaEventRecord(ev[0], st));
-  if (bf)
-    k_residual_group<true><<<g->res_blocks, RES_WARPS * 32, 0, st>>>(g->d_state, g->d_items);
-  else
-    k_residual_group<false><<<g->res_blocks, RES_WARPS * 32, 0, st>>>(g->d_state, g->d_items);
+  // register budget of the residual: 4 blocks per SM at small n (latency),
+  // 6 at large n (FP32 issue), measured on both workloads
+#define ZB_RES(BFV, M) \
+  k_residual_group<BFV, M><<<g->res_blocks, RES_WARPS * 32, 0, st>>>(g->d_state, g->d_items)
+  if (bf) {
+    if (g->max_n > 1024) ZB_RES(true, 6);
+    else ZB_RES(true, 4);
+  } else {
+    if (g->max_n > 1024) ZB_RES(false, 6);
+    else ZB_RES(false, 4);
+  }
+#undef ZB_RES
   if (ev) ZB_CUDA(cudaEventRecord(ev[1], st));
   const TcVariant* var = find_variant(g->precision, g->BN, g->stages);
   var->launch(g, std::min(g->num_sms, g->max_tiles), st);

@@ -79,6 +79,7 @@ struct Group {
   int res_blocks = 0;
   int dec_blocks = 0;
   int num_sms = 148;
+  int max_n = 0;               // largest feeder's unknowns
   void* dmem = nullptr;        // one allocation: items | state | tiles | maps
   ItemDesc* d_items = nullptr;
   GroupState* d_state = nullptr;

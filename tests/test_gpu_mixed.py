@@ -147,3 +147,29 @@ def test_modes_agree_with_each_other_and_fp64():
             for m in ["fp64", "fp16_scaled", "bf16x2"]}
     for m in ("fp16_scaled", "bf16x2"):
         assert np.abs(outs[m] - outs["fp64"]).max() <= 1e-6
+
+
+@pytest.mark.parametrize("mode", MODES)
+def test_final_mismatch_test_agrees_with_oracle(mode):
+    """The FP64 mismatch test of the mixed path decides like the oracle's mismatch.
+
+    Solve once, compute the oracle's power mismatch of the returned voltages,
+    then solve again with the threshold between the smallest and the largest
+    of those values: exactly the scenarios the oracle puts above it lose their
+    flag (the voltages are the same, the solve being deterministic).
+    """
+    f = F.make_feeder(90, 31, delta_frac=0.5)
+    Sw, Sd = F.make_scenarios(f, 64, 0.8, 1.2)
+    net = zbus.Network.from_feeder(f)
+    V, it, cv = net.solve(dev(Sw), dev(Sd), tol=1e-7, precision=mode)
+    assert cv.cpu().numpy().all()
+    ref = oracle(f, Sw[:1], Sd[:1])
+    mm = O.power_mismatch(ref["Y_LL"], ref["Y_Ls"], f.v_slack, V.cpu().numpy(), Sw, Sd)
+    thr = float(np.sqrt(mm.min() * mm.max()))
+    assert mm.min() < thr < mm.max()
+    V2, it2, cv2 = net.solve(dev(Sw), dev(Sd), tol=1e-7, precision=mode, mismatch_tol=thr)
+    assert torch.equal(V2, V)
+    want = (mm <= thr).astype(np.uint8)
+    # both sides sum in FP64 in different orders: leave out near-ties
+    clear = np.abs(mm / thr - 1.0) > 1e-3
+    np.testing.assert_array_equal(cv2.cpu().numpy()[clear], want[clear])
