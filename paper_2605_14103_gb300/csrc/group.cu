@@ -53,7 +53,7 @@ __device__ __forceinline__ int find_item(const ItemDesc* items, int n_items, int
 // ---------------------------------------------------------------------------
 __global__ void k_slot_init(GroupState* __restrict__ gs, const ItemDesc* __restrict__ items, int k,
                             int s0, int B, const double2* __restrict__ V0, int v0_stride,
-                            const double2* __restrict__ w, const double2* __restrict__ Sw,
+                            const float4* __restrict__ w_df, const double2* __restrict__ Sw,
                             const double2* __restrict__ Sd) {
   __shared__ double2 tv[32][33];
   __shared__ double2 tw[32][33];
@@ -67,7 +67,7 @@ __global__ void k_slot_init(GroupState* __restrict__ gs, const ItemDesc* __restr
     double2 v = make_double2(0.0, 0.0), a = v, d = v;
     if (b < B && j < n) {
       const int64_t g = (int64_t)b * n + j;
-      v = V0 ? V0[(int64_t)b * v0_stride + j] : w[j];
+      if (V0) v = V0[(int64_t)b * v0_stride + j];
       if (Sw) a = Sw[g];
       if (Sd) d = Sd[g];
     }
@@ -80,10 +80,17 @@ __global__ void k_slot_init(GroupState* __restrict__ gs, const ItemDesc* __restr
     const int j = j0 + r, b = b0 + tx;
     if (j < n && b < B) {
       const int64_t g = (int64_t)j * Bp + s0 + b;
-      const double2 v = tv[tx][r];
-      const float2 xr = df_split(v.x), xi = df_split(v.y);
-      it.Vh[g] = make_float2(xr.x, xi.x);
-      it.Vl[g] = make_float2(xr.y, xi.y);
+      if (V0) {
+        const double2 v = tv[tx][r];
+        const float2 xr = df_split(v.x), xi = df_split(v.y);
+        it.Vh[g] = make_float2(xr.x, xi.x);
+        it.Vl[g] = make_float2(xr.y, xi.y);
+      } else {
+        // no-load start: the double-float copy of w made at setup
+        const float4 wd = w_df[j];
+        it.Vh[g] = make_float2(wd.x, wd.z);
+        it.Vl[g] = make_float2(wd.y, wd.w);
+      }
       it.Swf[g] = make_float2(__double2float_rn(tw[tx][r].x), __double2float_rn(tw[tx][r].y));
       it.Sdf[g] = make_float2(__double2float_rn(td[tx][r].x), __double2float_rn(td[tx][r].y));
     }
@@ -611,7 +618,7 @@ k_finish_group(GroupState* __restrict__ gs, const ItemDesc* __restrict__ items, 
 // ---------------------------------------------------------------------------
 __global__ void k_slot_merge(const ItemDesc* __restrict__ items, int k, int s0, int B,
                              double2* __restrict__ V, int32_t* __restrict__ iters,
-                             uint8_t* __restrict__ conv) {
+                             uint8_t* __restrict__ conv, unsigned long long* __restrict__ mmax) {
   __shared__ double2 t[32][33];
   const ItemDesc it = items[k];
   const int n = it.n, Bp = it.Bp;
@@ -637,6 +644,7 @@ __global__ void k_slot_merge(const ItemDesc* __restrict__ items, int k, int s0, 
     if (b < B) {
       iters[b] = it.it[s0 + b];
       conv[b] = it.conv[s0 + b];
+      mmax[b] = 0ull;
       it.st[s0 + b] = SLOT_FREE;
     }
   }
@@ -664,88 +672,141 @@ __device__ __forceinline__ double2 draw64(double2 S, double2 v) {
 //   dS_j = v_j conj((Y_LL v + Y_Ls v_s)_j) - v_j conj(i_j(v)),  |dS_j| = |v_j| |r_j|
 // with the admittance rows summed in FP64 from the branch-form blocks, the wye
 // term exactly S_j (v conj(conj(S / v)) = S, no division) and the delta term
-// v_j conj(drawn) from FP64 branch currents.  A converged flag with
-// max_j |dS_j| above mtol is cleared.  One block per scenario, v staged in
-// shared memory (16 n bytes), one thread per bus.
-__global__ void __launch_bounds__(128)
+// v_j conj(drawn) from FP64 branch currents.
+//
+// Lanes are scenarios and every lane of a warp works on the same bus, so the
+// loop over a bus's blocks is uniform and the 3x3 blocks are broadcast loads;
+// the FP64 pipe (2 operations per clock per SM) only sees useful work.  Grid
+// (ceil(B / 32), ny), block (32, CHECK_WARPS): the warps of the grid's y
+// extent interleave over the buses.  Each block folds its max |dS|^2 per
+// scenario into mmax[b] (non-negative doubles order like their bit patterns;
+// NaN counts as +inf); mmax is zeroed by k_slot_merge.
+constexpr int CHECK_WARPS = 4;
+
+__global__ void __launch_bounds__(32 * CHECK_WARPS)
 k_check(const double2* __restrict__ V, const double2* __restrict__ Sw,
-        const double2* __restrict__ Sd, uint8_t* __restrict__ conv, int n,
+        const double2* __restrict__ Sd, const uint8_t* __restrict__ conv, int B, int n,
         const int32_t* __restrict__ bptr, const int32_t* __restrict__ bcol,
-        const double2* __restrict__ bval, double2 vs0, double2 vs1, double2 vs2, double mtol,
-        double* mm_out) {
-  extern __shared__ double2 vsm[];
-  __shared__ double red[4];
-  const int b = blockIdx.x;
-  if (conv[b] == 0) {
-    if (threadIdx.x == 0 && mm_out) mm_out[b] = -1.0;
-    return;
-  }
-  const double2* vg = V + (int64_t)b * n;
-  for (int j = threadIdx.x; j < n; j += blockDim.x) vsm[j] = vg[j];
-  __syncthreads();
-  const double2 vs[3] = {vs0, vs1, vs2};
+        const double2* __restrict__ bval, double2 vs0, double2 vs1, double2 vs2,
+        unsigned long long* __restrict__ mmax) {
+  __shared__ double red[CHECK_WARPS][32];
+  const int lane = threadIdx.x, ty = threadIdx.y;
+  const int b = blockIdx.x * 32 + lane;
+  const bool live = b < B && conv[b] != 0;
+  if (__ballot_sync(0xffffffffu, live) == 0u) return;   // same for every warp of the block
+  const int64_t row = (int64_t)(b < B ? b : B - 1) * n;
+  const double2* vg = V + row;
   double worst = 0.0;   // max |dS|^2
   const int nb = n / 3;
-  for (int a = threadIdx.x; a < nb; a += blockDim.x) {
+  for (int a = blockIdx.y * CHECK_WARPS + ty; a < nb; a += gridDim.y * CHECK_WARPS) {
     double2 va[3];
-    for (int p = 0; p < 3; ++p) va[p] = vsm[3 * a + p];
-    double2 acc[3] = {make_double2(0.0, 0.0), make_double2(0.0, 0.0), make_double2(0.0, 0.0)};
-    for (int t = bptr[a]; t < bptr[a + 1]; ++t) {
+#pragma unroll
+    for (int p = 0; p < 3; ++p) va[p] = vg[3 * a + p];
+    double ar[3] = {0.0, 0.0, 0.0}, ai[3] = {0.0, 0.0, 0.0};
+    const int t1 = bptr[a + 1];
+    for (int t = bptr[a]; t < t1; ++t) {
       const int cb = bcol[t];
-      double2 d[3];
-      for (int q = 0; q < 3; ++q) {
-        const double2 x = cb >= 0 ? vsm[3 * cb + q] : (cb == -1 ? vs[q] : make_double2(0.0, 0.0));
-        d[q] = cb == -2 ? va[q] : make_double2(x.x - va[q].x, x.y - va[q].y);
+      double dr[3], di[3];
+      if (cb >= 0) {
+#pragma unroll
+        for (int q = 0; q < 3; ++q) {
+          const double2 x = vg[3 * cb + q];
+          dr[q] = x.x - va[q].x;
+          di[q] = x.y - va[q].y;
+        }
+      } else if (cb == -1) {
+        const double2 vs[3] = {vs0, vs1, vs2};
+#pragma unroll
+        for (int q = 0; q < 3; ++q) {
+          dr[q] = vs[q].x - va[q].x;
+          di[q] = vs[q].y - va[q].y;
+        }
+      } else {
+#pragma unroll
+        for (int q = 0; q < 3; ++q) {
+          dr[q] = va[q].x;
+          di[q] = va[q].y;
+        }
       }
       const double2* y = bval + (int64_t)t * 9;
+#pragma unroll
       for (int p = 0; p < 3; ++p)
+#pragma unroll
         for (int q = 0; q < 3; ++q) {
           const double2 yy = y[p * 3 + q];
-          acc[p].x = fma(yy.x, d[q].x, fma(-yy.y, d[q].y, acc[p].x));
-          acc[p].y = fma(yy.x, d[q].y, fma(yy.y, d[q].x, acc[p].y));
+          ar[p] = fma(yy.x, dr[q], fma(-yy.y, di[q], ar[p]));
+          ai[p] = fma(yy.x, di[q], fma(yy.y, dr[q], ai[p]));
         }
     }
     // dS_p = v_p conj(acc_p) + S_wye_p + v_p conj(drawn_delta_p)
-    double2 dS[3];
+    double sr[3], si[3];
+#pragma unroll
     for (int p = 0; p < 3; ++p) {
-      dS[p] = make_double2(fma(va[p].x, acc[p].x, va[p].y * acc[p].y),
-                           fma(va[p].y, acc[p].x, -va[p].x * acc[p].y));
-      if (Sw) {
-        const double2 s = Sw[(int64_t)b * n + 3 * a + p];
-        dS[p].x += s.x;
-        dS[p].y += s.y;
+      sr[p] = fma(va[p].x, ar[p], va[p].y * ai[p]);
+      si[p] = fma(va[p].y, ar[p], -va[p].x * ai[p]);
+    }
+    if (Sw) {
+      const double2* sw = Sw + row + 3 * a;
+#pragma unroll
+      for (int p = 0; p < 3; ++p) {
+        const double2 x = sw[p];
+        sr[p] += x.x;
+        si[p] += x.y;
       }
     }
     if (Sd) {
-      const double2* sd = Sd + (int64_t)b * n + 3 * a;
-      double2 ib[3];
-      for (int p = 0; p < 3; ++p) {
-        const int q = (p + 1) % 3;
-        ib[p] = draw64(sd[p], make_double2(va[p].x - va[q].x, va[p].y - va[q].y));
-      }
-      for (int p = 0; p < 3; ++p) {
-        const int m = (p + 2) % 3;   // branch p leaves phase p, branch m returns into it
-        const double gx = ib[p].x - ib[m].x, gy = ib[p].y - ib[m].y;
-        dS[p].x += fma(va[p].x, gx, va[p].y * gy);
-        dS[p].y += fma(va[p].y, gx, -va[p].x * gy);
+      const double2* sd = Sd + row + 3 * a;
+      const double2 s0 = sd[0], s1 = sd[1], s2 = sd[2];
+      const bool any = (__double_as_longlong(s0.x) | __double_as_longlong(s0.y) |
+                        __double_as_longlong(s1.x) | __double_as_longlong(s1.y) |
+                        __double_as_longlong(s2.x) | __double_as_longlong(s2.y)) != 0;
+      if (any) {
+        double2 ib[3];
+        const double2 ss[3] = {s0, s1, s2};
+#pragma unroll
+        for (int p = 0; p < 3; ++p) {
+          const int q = (p + 1) % 3;
+          ib[p] = draw64(ss[p], make_double2(va[p].x - va[q].x, va[p].y - va[q].y));
+        }
+#pragma unroll
+        for (int p = 0; p < 3; ++p) {
+          const int m = (p + 2) % 3;   // branch p leaves phase p, branch m returns into it
+          const double gx = ib[p].x - ib[m].x, gy = ib[p].y - ib[m].y;
+          sr[p] += fma(va[p].x, gx, va[p].y * gy);
+          si[p] += fma(va[p].y, gx, -va[p].x * gy);
+        }
       }
     }
+#pragma unroll
     for (int p = 0; p < 3; ++p) {
-      double e = fma(dS[p].x, dS[p].x, dS[p].y * dS[p].y);
-      if (e != e) e = INFINITY;
-      worst = fmax(worst, e);
+      const double e = fma(sr[p], sr[p], si[p] * si[p]);
+      worst = (e != e) ? INFINITY : fmax(worst, e);
     }
   }
-  for (int o = 16; o > 0; o >>= 1) worst = fmax(worst, __shfl_xor_sync(0xffffffffu, worst, o));
-  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = worst;
+  red[ty][lane] = worst;
   __syncthreads();
-  if (threadIdx.x == 0) {
-    double x = 0.0;
-    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) x = fmax(x, red[w]);
-    const double mm = sqrt(x);
-    if (mm_out) mm_out[b] = mm;
-    if (!(mm <= mtol)) conv[b] = 0;
+  if (ty == 0 && live) {
+    double x = red[0][lane];
+#pragma unroll
+    for (int w = 1; w < CHECK_WARPS; ++w) x = fmax(x, red[w][lane]);
+    if (x > 0.0) atomicMax(&mmax[b], (unsigned long long)__double_as_longlong(x));
   }
+}
+
+// Verdict per scenario: mm = sqrt(max |dS|^2); a converged flag with mm above
+// mtol is cleared; mm_out[b] = mm, or -1 for a scenario that was not checked.
+// mm_out may alias mmax (each thread reads its entry before writing it).
+__global__ void k_check_finish(const unsigned long long* mmax, uint8_t* __restrict__ conv, int B,
+                               double mtol, double* mm_out) {
+  const int b = blockIdx.x * blockDim.x + threadIdx.x;
+  if (b >= B) return;
+  if (conv[b] == 0) {
+    if (mm_out) mm_out[b] = -1.0;
+    return;
+  }
+  const double mm = sqrt(__longlong_as_double((long long)mmax[b]));
+  if (mm_out) mm_out[b] = mm;
+  if (!(mm <= mtol)) conv[b] = 0;
 }
 
 // ---------------------------------------------------------------------------
@@ -964,7 +1025,7 @@ zbus_status group_admit(Group* g, int k, int64_t s0, int64_t B, const double* V0
   const ItemDesc& d = g->h_items[k];
   k_slot_init<<<dim3((d.n + 31) / 32, (unsigned)((B + 31) / 32)), dim3(32, 8), 0, st>>>(
       g->d_state, g->d_items, k, (int)s0, (int)B, (const double2*)V0, v0_broadcast ? 0 : d.n,
-      g->nets[k]->w, (const double2*)S_wye, (const double2*)S_delta);
+      g->nets[k]->w_df, (const double2*)S_wye, (const double2*)S_delta);
   ZB_CUDA(cudaGetLastError());
   return ZBUS_OK;
 }
@@ -1040,18 +1101,21 @@ zbus_status group_collect(Group* g, int k, int64_t s0, int64_t B, double* V_out,
                           double mtol, double* mm_out, cudaStream_t st) {
   if (B <= 0) return ZBUS_OK;
   zbus_network net = g->nets[k];
+  if (!net->ws.mm || B > net->ws.cap_B) return fail(ZBUS_ERR_ARG, "collect: batch above workspace");
+  unsigned long long* mmax = reinterpret_cast<unsigned long long*>(net->ws.mm);
   k_slot_merge<<<dim3((net->n + 31) / 32, (unsigned)((B + 31) / 32)), dim3(32, 8), 0, st>>>(
-      g->d_items, k, (int)s0, (int)B, (double2*)V_out, iters, converged);
-  k_check<<<(unsigned)B, 128, (size_t)16 * net->n, st>>>(
-      (const double2*)V_out, (const double2*)S_wye, (const double2*)S_delta, converged, net->n,
-      net->bsr_ptr, net->bsr_col, net->bsr_val, net->v_slack[0], net->v_slack[1],
-      net->v_slack[2], mtol, mm_out);
+      g->d_items, k, (int)s0, (int)B, (double2*)V_out, iters, converged, mmax);
+  const int gx = (int)((B + 31) / 32);
+  const int nb = net->n / 3;
+  const int ny = std::max(1, std::min((nb + CHECK_WARPS - 1) / CHECK_WARPS,
+                                      (8 * g->num_sms + gx - 1) / gx));
+  k_check<<<dim3((unsigned)gx, (unsigned)ny), dim3(32, CHECK_WARPS), 0, st>>>(
+      (const double2*)V_out, (const double2*)S_wye, (const double2*)S_delta, converged, (int)B,
+      net->n, net->bsr_ptr, net->bsr_col, net->bsr_val, net->v_slack[0], net->v_slack[1],
+      net->v_slack[2], mmax);
+  k_check_finish<<<(unsigned)((B + 255) / 256), 256, 0, st>>>(mmax, converged, (int)B, mtol,
+                                                               mm_out);
   ZB_CUDA(cudaGetLastError());
-  return ZBUS_OK;
-}
-
-zbus_status group_set_check_attr() {
-  ZB_CUDA(cudaFuncSetAttribute(k_check, cudaFuncAttributeMaxDynamicSharedMemorySize, 220 * 1024));
   return ZBUS_OK;
 }
 

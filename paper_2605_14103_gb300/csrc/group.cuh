@@ -32,8 +32,8 @@ struct ItemDesc {
   // slot state, scenario-minor [n][Bp]
   float2* Vh;
   float2* Vl;
-  float2* Swf;              // may be null (no wye loads)
-  float2* Sdf;              // may be null (no delta loads)
+  float2* Swf;              // FP32 wye loads (zeros where absent)
+  float2* Sdf;              // FP32 delta loads (zeros where absent)
   uint8_t* st;              // [Bp] SLOT_*
   int32_t* it;              // [Bp] sweeps since admission
   uint8_t* conv;            // [Bp] stop rule met

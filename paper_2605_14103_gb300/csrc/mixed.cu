@@ -123,8 +123,8 @@ zbus_status prepare_mixed(zbus_network net, int32_t precision, cudaStream_t st) 
   if (op.ready) return ZBUS_OK;
   if (!net->bus_aligned)
     return fail(ZBUS_ERR_UNSUPPORTED, "mixed modes need three unknowns per bus (n % 3 == 0)");
-  if ((size_t)16 * net->n > 220 * 1024)
-    return fail(ZBUS_ERR_UNSUPPORTED, "mixed modes support n <= 14080 unknowns");
+  if (net->n > 16383)
+    return fail(ZBUS_ERR_UNSUPPORTED, "mixed modes support n <= 16383 unknowns");
   if (!net->bsr_df) {
     const int64_t m = std::max<int64_t>(1, net->nblk * 9);
     ZB_CUDA(cudaMalloc((void**)&net->bsr_df, m * sizeof(float4)));
@@ -133,6 +133,8 @@ zbus_status prepare_mixed(zbus_network net, int32_t precision, cudaStream_t st) 
       k_split_c<<<(int)std::min<int64_t>(2048, (net->nblk * 9 + 255) / 256), 256, 0, st>>>(
           net->bsr_val, net->nblk * 9, net->bsr_df);
     k_split_c<<<(net->n + 255) / 256, 256, 0, st>>>(net->ys, net->n, net->ys_df);
+    ZB_CUDA(cudaMalloc((void**)&net->w_df, (size_t)net->n * sizeof(float4)));
+    k_split_c<<<(net->n + 255) / 256, 256, 0, st>>>(net->w, net->n, net->w_df);
     ZB_CUDA(cudaGetLastError());
   }
   const bool bf = precision == ZBUS_MIXED_BF16X2;
@@ -151,7 +153,6 @@ zbus_status prepare_mixed(zbus_network net, int32_t precision, cudaStream_t st) 
     k_pack_tc<false><<<op.N_pad / 2, 256, 0, st>>>(net->Z, net->n, op.K_pad, op.N_pad, op.Z0,
                                                    nullptr, op.zinv);
   ZB_CUDA(cudaGetLastError());
-  ZB_CHECK(group_set_check_attr());
   ZB_CUDA(cudaStreamSynchronize(st));
   op.ready = true;
   return ZBUS_OK;
@@ -160,8 +161,10 @@ zbus_status prepare_mixed(zbus_network net, int32_t precision, cudaStream_t st) 
 void free_mixed(zbus_network net) {
   cudaFree(net->bsr_df);
   cudaFree(net->ys_df);
+  cudaFree(net->w_df);
   net->bsr_df = nullptr;
   net->ys_df = nullptr;
+  net->w_df = nullptr;
   for (auto& op : net->mixed) {
     cudaFree(op.Z0);
     cudaFree(op.Z1);

@@ -164,6 +164,7 @@ struct zbus_network_s {
   int max_row_nnz = 0;
   float4* csr_df = nullptr;  // Y_LL values as double-float (re hi, re lo, im hi, im lo)
   float4* ys_df = nullptr;   // Y_Ls v_s as double-float
+  float4* w_df = nullptr;    // no-load voltage w as double-float (re hi, re lo, im hi, im lo)
   // branch form of the admittance rows per bus (networks with n % 3 == 0):
   // entries with column >= 0 (neighbour bus: Y_ab (v_b - v_a)), -1 (slack:
   // Y_as (v_s - v_a)) or -2 (shunt: Sh_a v_a); 3x3 complex blocks
@@ -206,7 +207,6 @@ void launch_mismatch(const double2* V, const double2* S_wye, const double2* S_de
 zbus_status ensure_workspace(zbus_network net, int64_t B);
 
 // group.cu
-zbus_status group_set_check_attr();
 
 // mixed.cu
 zbus_status make_tmap_2d(CUtensorMap* map, const void* base, bool bf16, uint64_t cols,
