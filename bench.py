@@ -347,7 +347,10 @@ def measure(net, form, Sw, Sd, wl, n, steps, warmup, flush, ws, peaks):
     dom = max(kernels[:2], key=lambda e: e["share"])
     roof = dict(dom["roofline"])
     roof["kernel"] = dom["kernel"]
-    roof["traffic"] = TRAFFIC.get((form, dom["kernel"]))
+    tr = TRAFFIC.get((wl.name, B, form, dom["kernel"]))
+    roof["traffic"] = tr
+    if tr is not None:
+        roof["traffic_src"] = TRAFFIC_SRC[(wl.name, B, form, dom["kernel"])]
     return {"value": value, "ms_per_step": 1e3 * t_max / steps,
             "step_ms_p50": statistics.median(step_ms), "converged_per_step": good,
             "max_iters": max_iters, "mean_iters": float(it.float().mean().item()),
@@ -356,7 +359,20 @@ def measure(net, form, Sw, Sd, wl, n, steps, warmup, flush, ws, peaks):
 
 
 # DRAM bytes per launch from ncu captures of the current kernels (None until captured)
-TRAFFIC = {}
+# (workload, scenarios, form, kernel) -> dram__bytes_read.sum + dram__bytes_write.sum per
+# launch from one ncu capture of the current kernel, with how it was taken
+TRAFFIC = {
+    ("feeder128_b4096", 4096, "fp64", "k_gemm3m_f64"): 66.378752e6 + 1.770240e6,
+    ("feeder1024_b16384", 16384, "fp16_scaled", "k_residual_group"):
+        4.0 * (404.616192e6 + 47.524608e6),
+}
+TRAFFIC_SRC = {
+    ("feeder128_b4096", 4096, "fp64", "k_gemm3m_f64"):
+        "ncu capture of this launch configuration (sweep 3, all scenarios active)",
+    ("feeder1024_b16384", 16384, "fp16_scaled", "k_residual_group"):
+        "ncu capture at 4096 scenarios x 4 (bytes scale with the scenarios: "
+        "measured 452.1 MB = algorithmic 452.6 MB)",
+}
 
 
 def run_ours(args):
