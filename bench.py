@@ -228,9 +228,15 @@ def run_reference(args):
 # ---------------------------------------------------------------------------
 KERNELS = {"fp64": ("k_currents_f64", "k_gemm3m_f64", "k_decide+k_compact"),
            "fp16_scaled": ("k_residual_group", "k_contract_group", "k_decide_group+k_finish_group"),
-           "bf16x2": ("k_residual_group", "k_contract_group", "k_decide_group+k_finish_group")}
+           "bf16x2": ("k_residual_group", "k_contract_group", "k_decide_group+k_finish_group"),
+           "tree": ("k_residual_group", "k_tree_group", "k_finish_group")}
+# arithmetic of each form: the sweep's, then the final test's
+DTYPE = {"fp64": "f64", "fp16_scaled": "fp16_scaled+f64", "bf16x2": "bf16x2+f64",
+         "tree": "f32+f64"}
 # launches outside the sweep loop, per solve
 OUTSIDE = {"fp64": ("k_init", 1),
+           "tree": ("k_group_reset+k_slot_init+k_group_params+k_slot_merge+k_check"
+                    "+k_check_finish", 6),
            "fp16_scaled": ("k_group_reset+k_slot_init+k_group_params+k_slot_merge+k_check"
                            "+k_check_finish", 6),
            "bf16x2": ("k_group_reset+k_slot_init+k_group_params+k_slot_merge+k_check"
@@ -260,10 +266,17 @@ def kernel_roofline(form, name, n, B_act_sweeps, ms, peaks, K_pad=None, N_pad=No
         hb = {"bound": "hbm", "achieved": byts, "peak": peaks["hbm_gbs"], "unit": "GB/s",
               "frac": byts / peaks["hbm_gbs"], "peak_src": "MEASURED_PEAKS hbm copy"}
         return tf if tf["frac"] >= hb["frac"] else hb
-    # residual / load-current kernels: bytes they must move per scenario-sweep:
-    # FP64: v (16 n) + two FP64 load arrays (32 n) + 3M operands written (24 n);
-    # mixed: double-float v (16 n) + two FP32 load arrays (16 n) + R row (4 n)
-    per = 72.0 * n if form == "fp64" else 36.0 * n
+    # residual / load-current / tree kernels: bytes they must move per
+    # scenario-sweep: FP64: v (16 n) + two FP64 load arrays (32 n) + 3M operands
+    # written (24 n); mixed residual: double-float v (16 n) + two FP32 load
+    # arrays (16 n) + R row (4 n), or the FP32 residual (8 n) for the tree;
+    # tree sweep: FP32 residual (8 n) + double-float v read and written (32 n)
+    if form == "fp64":
+        per = 72.0 * n
+    elif form == "tree":
+        per = 40.0 * n
+    else:
+        per = 36.0 * n
     byts = B_act_sweeps * per / t / 1e9
     return {"bound": "hbm", "achieved": byts, "peak": peaks["hbm_gbs"], "unit": "GB/s",
             "frac": byts / peaks["hbm_gbs"], "peak_src": "MEASURED_PEAKS hbm copy"}
@@ -354,7 +367,7 @@ def measure(net, form, Sw, Sd, wl, n, steps, warmup, flush, ws, peaks):
     return {"value": value, "ms_per_step": 1e3 * t_max / steps,
             "step_ms_p50": statistics.median(step_ms), "converged_per_step": good,
             "max_iters": max_iters, "mean_iters": float(it.float().mean().item()),
-            "gpu_launches": steps * (OUTSIDE[form][1] + 4 * max_iters),
+            "gpu_launches": steps * (OUTSIDE[form][1] + (3 if form == "tree" else 4) * max_iters),
             "kernels": kernels, "roofline": roof}, (V, it, cv)
 
 
@@ -397,7 +410,7 @@ def run_ours(args):
     net = zbus.Network.from_feeder(f)
     flush = torch.empty(512 * 1024 * 1024, dtype=torch.uint8, device="cuda")
 
-    forms = [args.precision] + ([m for m in ("fp64", "fp16_scaled", "bf16x2")
+    forms = [args.precision] + ([m for m in ("fp64", "fp16_scaled", "bf16x2", "tree")
                                  if m != args.precision] if args.forms == "all" else [])
     clocks = Clocks(torch.cuda.current_device()) if rank == 0 else None
     if clocks:
@@ -458,7 +471,7 @@ def run_ours(args):
         out = {"metric": METRIC, "value": head["value"], "unit": UNIT, "n_gpus": ws,
                "steps": args.steps, "warmup": args.warmup, "ms_per_step": head["ms_per_step"],
                "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
-               "dtype": "f64" if args.precision == "fp64" else args.precision + "+f64",
+               "dtype": DTYPE[args.precision],
                "data": "synthetic",
                "config": {"workload": args.workload, "feeder_buses": wl.N, "unknowns": n,
                           "scenarios_per_gpu": B, "tol": wl.tol, "max_iter": wl.max_iter,

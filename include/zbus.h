@@ -60,7 +60,11 @@ typedef enum {
 typedef enum {
   ZBUS_FP64 = 0,              /* plain map, FP64 on the CUDA cores */
   ZBUS_MIXED_BF16X2 = 1,      /* defect form, Z as BF16 hi+lo on tensor cores */
-  ZBUS_MIXED_FP16_SCALED = 2  /* defect form, Z as row-scaled FP16 hi+lo */
+  ZBUS_MIXED_FP16_SCALED = 2, /* defect form, Z as row-scaled FP16 hi+lo */
+  ZBUS_TREE_SWEEP = 3         /* defect form, Z applied as a backward / forward
+                                 sweep over a radial feeder (FP32, O(n) per
+                                 scenario instead of O(n^2)); radial networks
+                                 only, else ZBUS_ERR_UNSUPPORTED */
 } zbus_precision;
 
 typedef enum {
@@ -155,6 +159,14 @@ zbus_status zbus_network_reserve(zbus_network net, int64_t B, int32_t precision)
  *
  * Non-convergence is reported by the flags, not by the status.  V_out may
  * alias V_init.  B = 0 is a no-op.
+ *
+ * ZBUS_TREE_SWEEP (the sparse application of Z the paper leaves to future
+ * work, Sec. II-B): for a feeder whose buses form a tree hanging off the slack
+ * with reciprocal branches, Y_LL^{-1} r is a backward sweep (subtree sums of
+ * r) followed by a forward sweep (path sums of branch impedances times those
+ * sums); the defect residual stays exact (shunts included), so the fixed
+ * point is that of the other forms.  Returns ZBUS_ERR_UNSUPPORTED for a meshed
+ * or non-reciprocal network, or one above 3657 buses.
  */
 zbus_status zbus_solve(zbus_network net, int64_t B,
                        const double* S_wye, const double* S_delta,
@@ -252,7 +264,8 @@ typedef struct {
   uint64_t hbm_budget_bytes;   /* device bytes for the pool's operands plus the
                                   slot state of every feeder */
   int32_t max_slots;           /* upper bound of scenario slots per feeder */
-  int32_t precision;           /* ZBUS_MIXED_FP16_SCALED or ZBUS_MIXED_BF16X2 */
+  int32_t precision;           /* ZBUS_MIXED_FP16_SCALED, ZBUS_MIXED_BF16X2 or
+                                  ZBUS_TREE_SWEEP (every pool network radial) */
   int32_t conv_rule;
   int32_t max_iter;
   double tol;

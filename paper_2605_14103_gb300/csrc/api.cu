@@ -33,6 +33,11 @@ namespace {
 
 size_t align256(size_t x) { return (x + 255) & ~size_t(255); }
 
+bool known_precision(int32_t p) {
+  return p == ZBUS_FP64 || p == ZBUS_MIXED_BF16X2 || p == ZBUS_MIXED_FP16_SCALED ||
+         p == ZBUS_TREE_SWEEP;
+}
+
 void drop_graphs(zbus_network net) {
   for (auto& g : net->graphs) {
     if (g.exec) cudaGraphExecDestroy(g.exec);
@@ -66,8 +71,11 @@ WsLayout workspace_layout(const zbus_network net, int64_t B) {
   o += align256((size_t)B);
   L.part = o;
   o += align256(Bp * max_ntn(net) * 2 * sizeof(double));
+  // FP64 contraction operands; the tree sweep's FP32 residual [n][Bp] shares
+  // the region
   L.iop = o;
-  o += align256((size_t)3 * B * net->n_pad * sizeof(double));
+  o += align256(std::max((size_t)3 * B * net->n_pad * sizeof(double),
+                         Bp * net->n * sizeof(float2)));
   L.R = o;
   o += align256(Bp * k_pad_tc(net) * 2);
   L.rinv = o;
@@ -381,6 +389,10 @@ void zbus_network_destroy(zbus_network net) {
   cudaFree(net->bsr_ptr);
   cudaFree(net->bsr_col);
   cudaFree(net->bsr_val);
+  cudaFree(net->t_node);
+  cudaFree(net->t_lvl);
+  cudaFree(net->t_z);
+  cudaFree(net->t_zs);
   delete net;
 }
 
@@ -404,12 +416,11 @@ zbus_status zbus_network_reserve(zbus_network net, int64_t B, int32_t precision)
   g_last_error.clear();
   if (!net) return fail(ZBUS_ERR_ARG, "network is NULL");
   if (B < 0 || B > INT32_MAX / 4) return fail(ZBUS_ERR_ARG, "B out of range");
-  if (precision != ZBUS_FP64 && precision != ZBUS_MIXED_BF16X2 &&
-      precision != ZBUS_MIXED_FP16_SCALED)
-    return fail(ZBUS_ERR_ARG, "unknown precision");
+  if (!known_precision(precision)) return fail(ZBUS_ERR_ARG, "unknown precision");
   ZB_CHECK(check_device(net));
   ZB_CHECK(ensure_workspace(net, B));
-  if (precision != ZBUS_FP64) ZB_CHECK(prepare_mixed(net, precision, nullptr));
+  if (precision == ZBUS_TREE_SWEEP) ZB_CHECK(prepare_tree(net, nullptr));
+  else if (precision != ZBUS_FP64) ZB_CHECK(prepare_mixed(net, precision, nullptr));
   return ZBUS_OK;
 }
 
@@ -427,9 +438,7 @@ zbus_status zbus_solve(zbus_network net, int64_t B, const double* S_wye, const d
   if (opts) o = *opts;
   if (o.conv_rule != ZBUS_CONV_MAXABS && o.conv_rule != ZBUS_CONV_SUMMAG)
     return fail(ZBUS_ERR_ARG, "unknown convergence rule");
-  if (o.precision != ZBUS_FP64 && o.precision != ZBUS_MIXED_BF16X2 &&
-      o.precision != ZBUS_MIXED_FP16_SCALED)
-    return fail(ZBUS_ERR_ARG, "unknown precision");
+  if (!known_precision(o.precision)) return fail(ZBUS_ERR_ARG, "unknown precision");
   if (B == 0) return ZBUS_OK;
   if (!V_out || !iters || !converged) return fail(ZBUS_ERR_ARG, "an output pointer is NULL");
   if (S_delta && !net->bus_aligned)
@@ -502,9 +511,7 @@ zbus_status zbus_solve_batched(const zbus_batch_item* items, int32_t n_items, do
   if (opts) o = *opts;
   if (o.conv_rule != ZBUS_CONV_MAXABS && o.conv_rule != ZBUS_CONV_SUMMAG)
     return fail(ZBUS_ERR_ARG, "unknown convergence rule");
-  if (o.precision != ZBUS_FP64 && o.precision != ZBUS_MIXED_BF16X2 &&
-      o.precision != ZBUS_MIXED_FP16_SCALED)
-    return fail(ZBUS_ERR_ARG, "unknown precision");
+  if (!known_precision(o.precision)) return fail(ZBUS_ERR_ARG, "unknown precision");
   std::vector<zbus_network> nets;
   std::vector<int64_t> Bs;
   std::vector<const double*> Sw, Sd, V0;

@@ -31,14 +31,19 @@ constexpr int RES_WARPS = 4;
 constexpr int CHUNK_BUS = 4;
 constexpr int CHUNK_ROWS = 3 * CHUNK_BUS;
 constexpr int DEC_THREADS = 256;
-
+// output of the residual: scaled FP16 / BF16 rows of R (tensor-core
+// contraction) or FP32 values, scenario-minor (tree sweep)
+constexpr int RES_FP16 = 0, RES_BF16 = 1, RES_F32 = 2;
+constexpr int TREE_BATCH = 4;   // buses whose state a tree-sweep warp loads at once
 // Item owning global index x, for a non-decreasing begin field.
 __device__ __forceinline__ int find_item(const ItemDesc* items, int n_items, int x, int which) {
   int lo = 0, hi = n_items - 1;
   while (lo < hi) {
     const int mid = (lo + hi + 1) >> 1;
-    const int v = which == 0 ? items[mid].res_begin
-                             : (which == 1 ? items[mid].dec_begin : items[mid].mt_begin);
+    const int v = which == 0   ? items[mid].res_begin
+                  : which == 1 ? items[mid].dec_begin
+                  : which == 2 ? items[mid].mt_begin
+                               : items[mid].tree_begin;
     if (v <= x) lo = mid;
     else hi = mid - 1;
   }
@@ -152,9 +157,10 @@ __global__ void k_group_params(GroupState* gs, double tol, int max_iter, int rul
 // covers 4 buses (12 rows) per chunk and writes them through a shared-memory
 // transpose; rows n .. K_pad/2 - 1 are written as zeros.
 // ---------------------------------------------------------------------------
-template <bool BF, int MINB>
+template <int OUT, int MINB>
 __global__ void __launch_bounds__(RES_WARPS * 32, MINB)
 k_residual_group(GroupState* __restrict__ gs, const ItemDesc* __restrict__ items) {
+  constexpr bool BF = OUT == RES_BF16;
   __shared__ uint32_t stage[RES_WARPS][CHUNK_ROWS][32];
   __shared__ float sred[RES_WARPS][32];
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -167,11 +173,14 @@ k_residual_group(GroupState* __restrict__ gs, const ItemDesc* __restrict__ items
   const int b = grp * 32 + lane;
   const bool act = it.st[b] == SLOT_ACTIVE;
   if (!__syncthreads_or(act)) return;   // all 32 slots of this group are idle
-  const float ap = it.amax[b];
-  int e = (ap > 0.f && ap <= 3.0e38f) ? 12 - ilogbf(ap) : 12;
-  e = max(-126, min(126, e));
-  const float c = ldexpf(1.f, e);
-  if (ys == 0 && warp == 0) it.rinv[b] = ldexpf(1.f, -e);
+  float c = 1.f;
+  if (OUT != RES_F32) {
+    const float ap = it.amax[b];
+    int e = (ap > 0.f && ap <= 3.0e38f) ? 12 - ilogbf(ap) : 12;
+    e = max(-126, min(126, e));
+    c = ldexpf(1.f, e);
+    if (ys == 0 && warp == 0) it.rinv[b] = ldexpf(1.f, -e);
+  }
   const float2* __restrict__ Vh = it.Vh;
   const float2* __restrict__ Vl = it.Vl;
   const float2* __restrict__ Sw = it.Swf;
@@ -180,7 +189,7 @@ k_residual_group(GroupState* __restrict__ gs, const ItemDesc* __restrict__ items
   const int32_t* __restrict__ bcol = it.bsr_col;
   const float4* __restrict__ bval = it.bsr_df;
   const int nb = it.nbus;
-  const int rows_pad = it.K_pad >> 1;
+  const int rows_pad = OUT == RES_F32 ? it.n : it.K_pad >> 1;
   const int nchunks = (rows_pad + CHUNK_ROWS - 1) / CHUNK_ROWS;
   float amax = 0.f;
   for (int ch = ys * RES_WARPS + warp; ch < nchunks; ch += split * RES_WARPS) {
@@ -247,22 +256,30 @@ k_residual_group(GroupState* __restrict__ gs, const ItemDesc* __restrict__ items
           amax = (m == m) ? fmaxf(amax, m) : __int_as_float(0x7f800000);
         }
       }
+      if constexpr (OUT == RES_F32) {
+        if (a < nb && act) {
 #pragma unroll
-      for (int p = 0; p < 3; ++p) {
-        float x = r[p].x * c, y = r[p].y * c;
-        uint32_t u;
-        if (BF) {
-          __nv_bfloat162 h = __floats2bfloat162_rn(x, y);
-          u = *reinterpret_cast<uint32_t*>(&h);
-        } else {
-          x = fminf(fmaxf(x, -65504.f), 65504.f);
-          y = fminf(fmaxf(y, -65504.f), 65504.f);
-          __half2 h = __floats2half2_rn(x, y);
-          u = *reinterpret_cast<uint32_t*>(&h);
+          for (int p = 0; p < 3; ++p) it.Rt[(int64_t)(3 * a + p) * Bp + b] = r[p];
         }
-        stage[warp][3 * q + p][lane] = u;
+      } else {
+#pragma unroll
+        for (int p = 0; p < 3; ++p) {
+          float x = r[p].x * c, y = r[p].y * c;
+          uint32_t u;
+          if (BF) {
+            __nv_bfloat162 h = __floats2bfloat162_rn(x, y);
+            u = *reinterpret_cast<uint32_t*>(&h);
+          } else {
+            x = fminf(fmaxf(x, -65504.f), 65504.f);
+            y = fminf(fmaxf(y, -65504.f), 65504.f);
+            __half2 h = __floats2half2_rn(x, y);
+            u = *reinterpret_cast<uint32_t*>(&h);
+          }
+          stage[warp][3 * q + p][lane] = u;
+        }
       }
     }
+    if constexpr (OUT == RES_F32) continue;
     __syncwarp();
     if (act) {
       // CHUNK_ROWS rows = CHUNK_ROWS / 4 16-byte stores into this slot's R row
@@ -277,6 +294,7 @@ k_residual_group(GroupState* __restrict__ gs, const ItemDesc* __restrict__ items
     }
     __syncwarp();
   }
+  if constexpr (OUT == RES_F32) return;   // the tree sweep needs no residual scale
   sred[warp][lane] = amax;
   __syncthreads();
   if (warp == 0 && act) {
@@ -536,6 +554,210 @@ k_decide_group(GroupState* __restrict__ gs, const ItemDesc* __restrict__ items) 
     if (!keep) it.st[b] = SLOT_DONE;
     it.amax[b] = it.amax[it.Bp + b];
     it.amax[it.Bp + b] = 0.f;
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Tree sweep (radial feeders): the step X = T r of a defect sweep, with T the
+// inverse of the series admittance of the tree, applied without forming it:
+//   backward, deepest level first: S_c = r_c + the sum of the children's S
+//     (the current into the subtree of c);
+//   forward, from the slack: X_c = X_parent + z_c S_c (z_c the impedance of
+//     c's parent branch, X = 0 at the slack);
+// in place in the FP32 residual rows (scenario-minor, one slot per lane, so
+// every access is a coalesced row segment).  A block's warps split each
+// level's buses, TREE_BATCH at a time with all their loads issued before any
+// store, and a barrier separates the levels; the position tables (bus,
+// parent, children; FP16 z blocks scaled per bus, which set only the
+// convergence rate of the defect form, not its fixed point) sit in shared
+// memory.  Then v += X in double-float, the step partials per slot reduced
+// over the warps, and the stop test of each slot (the rule of
+// k_decide_group), so the sweep needs neither a contraction nor a separate
+// stop-test launch.
+// ---------------------------------------------------------------------------
+template <int TREE_WARPS, int MINB>
+__global__ void __launch_bounds__(32 * TREE_WARPS, MINB)
+k_tree_group(GroupState* __restrict__ gs, const ItemDesc* __restrict__ items) {
+  extern __shared__ __align__(16) uint8_t tsm[];
+  __shared__ float sdmax[TREE_WARPS][32];
+  __shared__ float sdsum[TREE_WARPS][32];
+  const int k = find_item(items, gs->n_items, blockIdx.x, 3);
+  const ItemDesc& it = items[k];
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int b = (blockIdx.x - it.tree_begin) * 32 + lane;
+  const bool act = it.st[b] == SLOT_ACTIVE;
+  if (!__syncthreads_or(act)) return;   // the block's 32 slots are idle
+  const int Bp = it.Bp, D = it.tlevels, nb = it.nbus;
+  int4* node = reinterpret_cast<int4*>(tsm);                 // bus, parent, children
+  __half2* zt = reinterpret_cast<__half2*>(node + nb);       // [nb][9]
+  float* zst = reinterpret_cast<float*>(zt + 9 * nb);        // [nb]
+  for (int i = threadIdx.x; i < nb; i += blockDim.x) {
+    node[i] = it.t_node[i];
+    zst[i] = it.t_zs[i];
+  }
+  for (int i = threadIdx.x; i < 9 * nb; i += blockDim.x) {
+    const float2 z = it.t_z[i];
+    zt[i] = __floats2half2_rn(z.x, z.y);
+  }
+  __syncthreads();
+  const int32_t* __restrict__ lvl = it.t_lvl;
+  float2* R = it.Rt + b;   // row j of this slot at R[j * Bp]
+  const int64_t r3 = 3 * (int64_t)Bp;
+  const int first = warp;   // the warp's first bus of a level
+  constexpr int STRIDE = TREE_WARPS;
+  for (int L = D - 2; L >= 0; --L) {
+    const int l0 = lvl[L], l1 = lvl[L + 1];
+    for (int i0 = l0 + first; i0 < l1; i0 += STRIDE * TREE_BATCH) {
+      float2 acc[TREE_BATCH][3];
+#pragma unroll
+      for (int u = 0; u < TREE_BATCH; ++u) {
+        const int i = i0 + u * STRIDE;
+        if (i < l1 && act) {
+          const int4 nd = node[i];
+          if (nd.z != nd.w) {
+            const float2* own = R + nd.x * r3;
+#pragma unroll
+            for (int p = 0; p < 3; ++p) acc[u][p] = own[p * Bp];
+            for (int c = nd.z; c < nd.w; ++c) {
+              const float2* ch = R + node[c].x * r3;
+#pragma unroll
+              for (int p = 0; p < 3; ++p) {
+                const float2 x = ch[p * Bp];
+                acc[u][p].x += x.x;
+                acc[u][p].y += x.y;
+              }
+            }
+          }
+        }
+      }
+#pragma unroll
+      for (int u = 0; u < TREE_BATCH; ++u) {
+        const int i = i0 + u * STRIDE;
+        if (i < l1 && act) {
+          const int4 nd = node[i];
+          if (nd.z != nd.w) {
+            float2* own = R + nd.x * r3;
+#pragma unroll
+            for (int p = 0; p < 3; ++p) own[p * Bp] = acc[u][p];
+          }
+        }
+      }
+    }
+    __syncthreads();
+  }
+  for (int L = 0; L < D; ++L) {
+    const int l0 = lvl[L], l1 = lvl[L + 1];
+    for (int i0 = l0 + first; i0 < l1; i0 += STRIDE * TREE_BATCH) {
+      float2 sv[TREE_BATCH][3], xp[TREE_BATCH][3];
+#pragma unroll
+      for (int u = 0; u < TREE_BATCH; ++u) {
+        const int i = i0 + u * STRIDE;
+#pragma unroll
+        for (int p = 0; p < 3; ++p) sv[u][p] = xp[u][p] = make_float2(0.f, 0.f);
+        if (i < l1 && act) {
+          const int4 nd = node[i];
+          const float2* own = R + nd.x * r3;
+#pragma unroll
+          for (int p = 0; p < 3; ++p) sv[u][p] = own[p * Bp];
+          if (nd.y >= 0) {
+            const float2* pa = R + node[nd.y].x * r3;
+#pragma unroll
+            for (int p = 0; p < 3; ++p) xp[u][p] = pa[p * Bp];
+          }
+        }
+      }
+#pragma unroll
+      for (int u = 0; u < TREE_BATCH; ++u) {
+        const int i = i0 + u * STRIDE;
+        if (i < l1 && act) {
+          float2* own = R + node[i].x * r3;
+          const float sc = zst[i];
+          const __half2* z = zt + 9 * i;
+#pragma unroll
+          for (int p = 0; p < 3; ++p) {
+            float ar = 0.f, ai = 0.f;
+#pragma unroll
+            for (int q2 = 0; q2 < 3; ++q2) {
+              const float2 zz = __half22float2(z[3 * p + q2]);
+              ar = __fmaf_rn(zz.x, sv[u][q2].x, __fmaf_rn(-zz.y, sv[u][q2].y, ar));
+              ai = __fmaf_rn(zz.x, sv[u][q2].y, __fmaf_rn(zz.y, sv[u][q2].x, ai));
+            }
+            own[p * Bp] = make_float2(__fmaf_rn(ar, sc, xp[u][p].x), __fmaf_rn(ai, sc, xp[u][p].y));
+          }
+        }
+      }
+    }
+    __syncthreads();
+  }
+  // v += X (double-float) and the step partials, TREE_BATCH buses per warp
+  // requested before any of them is written back
+  const bool summag = gs->rule == ZBUS_CONV_SUMMAG;
+  float dmax = 0.f, dsum = 0.f;
+  if (act) {
+    for (int a0 = first; a0 < nb; a0 += STRIDE * TREE_BATCH) {
+      float2 xb[TREE_BATCH][3], hb[TREE_BATCH][3], lb[TREE_BATCH][3];
+#pragma unroll
+      for (int u = 0; u < TREE_BATCH; ++u) {
+        const int a = a0 + u * STRIDE;
+#pragma unroll
+        for (int p = 0; p < 3; ++p) {
+          const int64_t g = (int64_t)(3 * (a < nb ? a : 0) + p) * Bp + b;
+          xb[u][p] = it.Rt[g];
+          hb[u][p] = it.Vh[g];
+          lb[u][p] = it.Vl[g];
+        }
+      }
+#pragma unroll
+      for (int u = 0; u < TREE_BATCH; ++u) {
+        const int a = a0 + u * STRIDE;
+        if (a >= nb) break;
+#pragma unroll
+        for (int p = 0; p < 3; ++p) {
+          const float2 d = xb[u][p], h = hb[u][p], l = lb[u][p];
+          float sr, er, si, ei;
+          two_sum(h.x, d.x, sr, er);
+          two_sum(h.y, d.y, si, ei);
+          float2 nh, nl;
+          fast_two_sum(sr, __fadd_rn(er, l.x), nh.x, nl.x);
+          fast_two_sum(si, __fadd_rn(ei, l.y), nh.y, nl.y);
+          const int64_t g = (int64_t)(3 * a + p) * Bp + b;
+          it.Vh[g] = nh;
+          it.Vl[g] = nl;
+          float step = sqrtf(__fmaf_rn(d.x, d.x, d.y * d.y));
+          if (step != step) step = __int_as_float(0x7f800000);
+          dmax = fmaxf(dmax, step);
+          if (summag) {
+            const float o2 = __fmaf_rn(h.x, h.x, h.y * h.y);
+            const float n2 = __fmaf_rn(nh.x, nh.x, nh.y * nh.y);
+            dsum += (2.f * (h.x * d.x + h.y * d.y) + d.x * d.x + d.y * d.y) /
+                    (sqrtf(n2) + sqrtf(o2));
+          }
+        }
+      }
+    }
+  }
+  // per slot, over the warps in order
+  sdmax[warp][lane] = dmax;
+  sdsum[warp][lane] = dsum;
+  __syncthreads();
+  if (warp == 0 && act) {
+    float m = 0.f, u = 0.f;
+    for (int w = 0; w < TREE_WARPS; ++w) {
+      m = fmaxf(m, sdmax[w][lane]);
+      u += sdsum[w][lane];
+    }
+    const int sw = it.it[b] + 1;
+    it.it[b] = sw;
+    const double delta = summag ? fabs((double)u) : (double)m;
+    int keep = 0;
+    if (!isfinite(delta)) {
+      it.conv[b] = 0;
+    } else if (delta <= gs->tol) {
+      it.conv[b] = 1;
+    } else if (sw < gs->max_iter) {
+      keep = 1;
+    }
+    if (!keep) it.st[b] = SLOT_DONE;
   }
 }
 
@@ -897,30 +1119,39 @@ zbus_status group_build(Group* g, const std::vector<zbus_network>& nets,
   g->Bs = Bs;
   g->precision = precision;
   g->n_items = (int)nets.size();
+  const bool tree = precision == ZBUS_TREE_SWEEP;
   int max_n = 0;
   int64_t total_B = 0;
   for (size_t k = 0; k < nets.size(); ++k) {
-    ZB_CHECK(prepare_mixed(nets[k], precision, st));
+    ZB_CHECK(tree ? prepare_tree(nets[k], st) : prepare_mixed(nets[k], precision, st));
     ZB_CHECK(ensure_workspace(nets[k], Bs[k]));
     max_n = std::max(max_n, nets[k]->n);
     total_B += Bs[k];
   }
-  int BN = 0, stages = 0;
   g->tune_gen = tune_generation();
-  ZB_CHECK(tune_lookup(precision, max_n, total_B, &BN, &stages));
-  const TcVariant* var = find_variant(precision, BN, stages);
-  if (!var) var = default_variant(precision, max_n);
-  g->BN = var->BN;
-  g->stages = var->stages;
   g->max_n = max_n;
-  ZB_CUDA(var->attr());
+  if (!tree) {
+    int BN = 0, stages = 0;
+    ZB_CHECK(tune_lookup(precision, max_n, total_B, &BN, &stages));
+    const TcVariant* var = find_variant(precision, BN, stages);
+    if (!var) var = default_variant(precision, max_n);
+    g->BN = var->BN;
+    g->stages = var->stages;
+    ZB_CUDA(var->attr());
+  }
   int dev = 0;
   ZB_CUDA(cudaGetDevice(&dev));
   ZB_CUDA(cudaDeviceGetAttribute(&g->num_sms, cudaDevAttrMultiProcessorCount, dev));
 
   g->h_items.resize(nets.size());
   g->ws_gen.resize(nets.size());
-  int res = 0, dec = 0, mt = 0, tiles = 0;
+  int res = 0, dec = 0, mt = 0, tiles = 0, tb = 0;
+  g->tree_smem = 0;
+  // tree-sweep blocks of 32 slots: 16 warps per block while the blocks are
+  // fewer than the SMs can hold, else 8 warps and two blocks per SM
+  int64_t tree_slots = 0;
+  for (size_t k = 0; k < nets.size(); ++k) tree_slots += nets[k]->ws.cap_Bp;
+  g->tree_wide = tree_slots / 32 <= 2 * g->num_sms;
   for (size_t k = 0; k < nets.size(); ++k) {
     zbus_network net = nets[k];
     const MixedOperands& op = net->mixed[precision == ZBUS_MIXED_BF16X2 ? 1 : 0];
@@ -935,13 +1166,28 @@ zbus_status group_build(Group* g, const std::vector<zbus_network>& nets,
       const float rh = (float)v.x, ih = (float)v.y;
       d.vs_df[q] = make_float4(rh, (float)(v.x - (double)rh), ih, (float)(v.y - (double)ih));
     }
-    d.zinv = op.zinv;
     d.n = net->n;
     d.nbus = net->nbus;
-    d.K_pad = op.K_pad;
-    d.N_pad = op.N_pad;
-    d.ntn = op.N_pad / g->BN;
     d.Bp = (int32_t)ws.cap_Bp;
+    if (tree) {
+      d.K_pad = round_up(2 * net->n, 64);
+      d.N_pad = 0;
+      d.ntn = 1;
+      d.t_node = net->t_node;
+      d.t_z = net->t_z;
+      d.t_zs = net->t_zs;
+      d.Rt = reinterpret_cast<float2*>(ws.Iop);
+      d.t_lvl = net->t_lvl;
+      d.tlevels = net->depth;
+      d.tree_begin = tb;
+      tb += d.Bp / 32;
+      g->tree_smem = std::max(g->tree_smem, tree_smem_bytes(net->nbus));
+    } else {
+      d.zinv = op.zinv;
+      d.K_pad = op.K_pad;
+      d.N_pad = op.N_pad;
+      d.ntn = op.N_pad / g->BN;
+    }
     d.Vh = ws.Vh;
     d.Vl = ws.Vl;
     d.Swf = ws.Swf;
@@ -953,7 +1199,7 @@ zbus_status group_build(Group* g, const std::vector<zbus_network>& nets,
     d.R = ws.R;
     d.rinv = ws.rinv;
     d.part = ws.part;
-      const int rows_pad = op.K_pad / 2;
+    const int rows_pad = tree ? d.n : d.K_pad / 2;
     const int nchunks = (rows_pad + CHUNK_ROWS - 1) / CHUNK_ROWS;
     d.res_split = (nchunks + RES_WARPS - 1) / RES_WARPS;
     d.res_begin = res;
@@ -967,6 +1213,14 @@ zbus_status group_build(Group* g, const std::vector<zbus_network>& nets,
   }
   g->res_blocks = res;
   g->dec_blocks = dec;
+  g->tree_groups = tb;
+  if (tree) {
+    const int smem = (int)g->tree_smem;
+    ZB_CUDA(cudaFuncSetAttribute(k_tree_group<16, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 smem));
+    ZB_CUDA(cudaFuncSetAttribute(k_tree_group<8, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 smem));
+  }
   g->mt_total = mt;
   g->max_tiles = tiles;
 
@@ -986,7 +1240,7 @@ zbus_status group_build(Group* g, const std::vector<zbus_network>& nets,
 
   std::vector<CUtensorMap> maps(3 * nets.size());
   const bool bf = precision == ZBUS_MIXED_BF16X2;
-  for (size_t k = 0; k < nets.size(); ++k) {
+  for (size_t k = 0; k < nets.size() && !tree; ++k) {
     const MixedOperands& op = nets[k]->mixed[bf ? 1 : 0];
     const ItemDesc& d = g->h_items[k];
     ZB_CHECK(make_tmap_2d(&maps[k], d.R, bf, (uint64_t)d.K_pad, (uint64_t)d.Bp, BK, BM));
@@ -1001,6 +1255,7 @@ zbus_status group_build(Group* g, const std::vector<zbus_network>& nets,
   s.mt_total = mt;
   s.res_blocks = res;
   s.dec_blocks = dec;
+  s.tree_groups = tb;
   s.tiles = g->d_tiles;
   ZB_CUDA(cudaMemcpyAsync(g->d_items, g->h_items.data(), nets.size() * sizeof(ItemDesc),
                           cudaMemcpyHostToDevice, st));
@@ -1045,24 +1300,37 @@ zbus_status group_rebuild(Group* g, cudaStream_t st) {
 zbus_status group_sweep(Group* g, cudaGraphConditionalHandle h, bool use_handle, cudaStream_t st,
                         cudaEvent_t* ev) {
   const bool bf = g->precision == ZBUS_MIXED_BF16X2;
+  const bool tree = g->precision == ZBUS_TREE_SWEEP;
   if (ev) ZB_CUDA(cudaEventRecord(ev[0], st));
   // register budget of the residual: 4 blocks per SM at small n (latency),
   // 6 at large n (FP32 issue), measured on both workloads
-#define ZB_RES(BFV, M) \
-  k_residual_group<BFV, M><<<g->res_blocks, RES_WARPS * 32, 0, st>>>(g->d_state, g->d_items)
-  if (bf) {
-    if (g->max_n > 1024) ZB_RES(true, 6);
-    else ZB_RES(true, 4);
+#define ZB_RES(OUT, M) \
+  k_residual_group<OUT, M><<<g->res_blocks, RES_WARPS * 32, 0, st>>>(g->d_state, g->d_items)
+  const int out = tree ? RES_F32 : (bf ? RES_BF16 : RES_FP16);
+  if (g->max_n > 1024) {
+    if (out == RES_F32) ZB_RES(RES_F32, 6);
+    else if (out == RES_BF16) ZB_RES(RES_BF16, 6);
+    else ZB_RES(RES_FP16, 6);
   } else {
-    if (g->max_n > 1024) ZB_RES(false, 6);
-    else ZB_RES(false, 4);
+    if (out == RES_F32) ZB_RES(RES_F32, 4);
+    else if (out == RES_BF16) ZB_RES(RES_BF16, 4);
+    else ZB_RES(RES_FP16, 4);
   }
 #undef ZB_RES
   if (ev) ZB_CUDA(cudaEventRecord(ev[1], st));
-  const TcVariant* var = find_variant(g->precision, g->BN, g->stages);
-  var->launch(g, std::min(g->num_sms, g->max_tiles), st);
-  if (ev) ZB_CUDA(cudaEventRecord(ev[2], st));
-  k_decide_group<<<g->dec_blocks, DEC_THREADS, 0, st>>>(g->d_state, g->d_items);
+  if (tree) {
+    // step, update and stop test in one launch
+    if (g->tree_wide)
+      k_tree_group<16, 1><<<g->tree_groups, 512, g->tree_smem, st>>>(g->d_state, g->d_items);
+    else
+      k_tree_group<8, 2><<<g->tree_groups, 256, g->tree_smem, st>>>(g->d_state, g->d_items);
+    if (ev) ZB_CUDA(cudaEventRecord(ev[2], st));
+  } else {
+    const TcVariant* var = find_variant(g->precision, g->BN, g->stages);
+    var->launch(g, std::min(g->num_sms, g->max_tiles), st);
+    if (ev) ZB_CUDA(cudaEventRecord(ev[2], st));
+    k_decide_group<<<g->dec_blocks, DEC_THREADS, 0, st>>>(g->d_state, g->d_items);
+  }
   k_finish_group<<<1, 1024, 0, st>>>(g->d_state, g->d_items, 0, h, use_handle ? 1 : 0);
   if (ev) ZB_CUDA(cudaEventRecord(ev[3], st));
   ZB_CUDA(cudaGetLastError());

@@ -41,6 +41,14 @@ struct ItemDesc {
   void* R;                  // [Bp][K_pad] fp16 / bf16 residual rows
   float* rinv;              // [Bp] inverse residual scales
   double* part;             // [Bp][ntn][2] per-tile step partials
+  // tree sweep (ZBUS_TREE_SWEEP): radial structure and FP32 residual
+  const int4* t_node;       // [nbus] per breadth-first position: bus, parent, children range
+  const int32_t* t_lvl;     // [tlevels + 1] level ranges of positions
+  const float2* t_z;        // [nbus][9] scaled parent-branch impedances
+  const float* t_zs;        // [nbus] their scales
+  float2* Rt;               // [n][Bp] FP32 residual, scenario-minor
+  int32_t tlevels;          // depth of the tree + 1
+  int32_t tree_begin;       // first tree block of this item
   // launch decomposition
   int32_t res_begin;        // first residual block
   int32_t res_split;        // residual blocks per 32 slots
@@ -61,6 +69,7 @@ struct GroupState {
   int32_t mt_total;         // 128-slot tiles over all items
   int32_t res_blocks;       // residual grid size
   int32_t dec_blocks;       // stop-test grid size
+  int32_t tree_groups;      // tree-sweep blocks over all items
   int32_t* hist;            // profile mode: active slots of sweep k
   int32_t hist_n;
   uint64_t* tiles;          // (item << 32) | (mt << 16) | nt of every active tile
@@ -78,6 +87,9 @@ struct Group {
   int max_tiles = 0;
   int res_blocks = 0;
   int dec_blocks = 0;
+  int tree_groups = 0;          // blocks of the tree sweep
+  bool tree_wide = true;        // 16 warps per tree-sweep block (else 8)
+  size_t tree_smem = 0;         // their dynamic shared memory (tables)
   int num_sms = 148;
   int max_n = 0;               // largest feeder's unknowns
   void* dmem = nullptr;        // one allocation: items | state | tiles | maps
@@ -128,6 +140,9 @@ zbus_status group_run(Group* g, cudaStream_t st);
 zbus_status group_collect(Group* g, int k, int64_t s0, int64_t B, double* V_out, int32_t* iters,
                           uint8_t* converged, const double* S_wye, const double* S_delta,
                           double mtol, double* mm_out, cudaStream_t st);
+// Shared memory of a tree-sweep block for a feeder of nbus buses: per bus
+// its node record (16 B), FP16 z block (36 B) and scale (4 B).
+inline size_t tree_smem_bytes(int nbus) { return (size_t)56 * nbus; }
 // Tile configurations the contraction is compiled for (BN, stages).
 bool tc_config_ok(int32_t precision, int BN, int stages);
 int tc_variants(int32_t precision, int* BN, int* stages, int max);

@@ -12,6 +12,7 @@
 #include <cstring>
 
 #include "df.cuh"
+#include "group.cuh"
 #include "mixed.cuh"
 
 namespace zbus {
@@ -118,13 +119,11 @@ zbus_status make_tmap_2d(CUtensorMap* map, const void* base, bool bf16, uint64_t
   return ZBUS_OK;
 }
 
-zbus_status prepare_mixed(zbus_network net, int32_t precision, cudaStream_t st) {
-  MixedOperands& op = net->mixed[precision == ZBUS_MIXED_BF16X2 ? 1 : 0];
-  if (op.ready) return ZBUS_OK;
-  if (!net->bus_aligned)
-    return fail(ZBUS_ERR_UNSUPPORTED, "mixed modes need three unknowns per bus (n % 3 == 0)");
-  if (net->n > 16383)
-    return fail(ZBUS_ERR_UNSUPPORTED, "mixed modes support n <= 16383 unknowns");
+namespace {
+
+// Double-float copies of the branch-form blocks, Y_Ls v_s and w, shared by
+// the defect forms.
+zbus_status prepare_df(zbus_network net, cudaStream_t st) {
   if (!net->bsr_df) {
     const int64_t m = std::max<int64_t>(1, net->nblk * 9);
     ZB_CUDA(cudaMalloc((void**)&net->bsr_df, m * sizeof(float4)));
@@ -137,6 +136,33 @@ zbus_status prepare_mixed(zbus_network net, int32_t precision, cudaStream_t st) 
     k_split_c<<<(net->n + 255) / 256, 256, 0, st>>>(net->w, net->n, net->w_df);
     ZB_CUDA(cudaGetLastError());
   }
+  return ZBUS_OK;
+}
+
+}  // namespace
+
+zbus_status prepare_tree(zbus_network net, cudaStream_t st) {
+  if (!net->bus_aligned)
+    return fail(ZBUS_ERR_UNSUPPORTED, "the tree sweep needs three unknowns per bus (n % 3 == 0)");
+  if (!net->radial)
+    return fail(ZBUS_ERR_UNSUPPORTED,
+                "the tree sweep needs a radial feeder (buses form a tree hanging off the slack, "
+                "reciprocal invertible branch blocks)");
+  if (tree_smem_bytes(net->nbus) > (size_t)200 * 1024)
+    return fail(ZBUS_ERR_UNSUPPORTED, "the tree sweep supports up to 3657 buses");
+  ZB_CHECK(prepare_df(net, st));
+  ZB_CUDA(cudaStreamSynchronize(st));
+  return ZBUS_OK;
+}
+
+zbus_status prepare_mixed(zbus_network net, int32_t precision, cudaStream_t st) {
+  MixedOperands& op = net->mixed[precision == ZBUS_MIXED_BF16X2 ? 1 : 0];
+  if (op.ready) return ZBUS_OK;
+  if (!net->bus_aligned)
+    return fail(ZBUS_ERR_UNSUPPORTED, "mixed modes need three unknowns per bus (n % 3 == 0)");
+  if (net->n > 16383)
+    return fail(ZBUS_ERR_UNSUPPORTED, "mixed modes support n <= 16383 unknowns");
+  ZB_CHECK(prepare_df(net, st));
   const bool bf = precision == ZBUS_MIXED_BF16X2;
   op.bf16 = bf;
   op.zparts = bf ? 2 : 1;

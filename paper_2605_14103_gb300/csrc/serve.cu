@@ -23,6 +23,7 @@ size_t operand_bytes(zbus_network net) {
   b += (size_t)net->nnz_ll * 20 + (size_t)net->nblk * (144 + 144);  // CSR, blocks (FP64, df)
   for (const auto& op : net->mixed)
     if (op.ready) b += (size_t)op.N_pad * op.K_pad * 2 * op.zparts;
+  if (net->radial) b += (size_t)net->nbus * (16 + 4 + 72 + 4) + 4 * (size_t)(net->depth + 1);
   return b;
 }
 
@@ -63,7 +64,8 @@ extern "C" zbus_status zbus_serve(const zbus_serve_config* cfg, zbus_network* po
                                   zbus_completion_sink sink, void* user, void* cuda_stream) {
   set_error("");
   if (!cfg || !pool || n_pool <= 0 || !src || !sink) return fail(ZBUS_ERR_ARG, "bad arguments");
-  if (cfg->precision != ZBUS_MIXED_FP16_SCALED && cfg->precision != ZBUS_MIXED_BF16X2)
+  if (cfg->precision != ZBUS_MIXED_FP16_SCALED && cfg->precision != ZBUS_MIXED_BF16X2 &&
+      cfg->precision != ZBUS_TREE_SWEEP)
     return fail(ZBUS_ERR_ARG, "serving runs the mixed precisions");
   if (cfg->max_iter < 1 || !(cfg->tol >= 0.0)) return fail(ZBUS_ERR_ARG, "bad tol / max_iter");
   if (cfg->conv_rule != ZBUS_CONV_MAXABS && cfg->conv_rule != ZBUS_CONV_SUMMAG)
@@ -80,7 +82,8 @@ extern "C" zbus_status zbus_serve(const zbus_serve_config* cfg, zbus_network* po
   // operands first, then the slot capacity the budget leaves
   size_t fixed = 0;
   for (auto net : nets) {
-    ZB_CHECK(prepare_mixed(net, cfg->precision, st));
+    ZB_CHECK(cfg->precision == ZBUS_TREE_SWEEP ? prepare_tree(net, st)
+                                                : prepare_mixed(net, cfg->precision, st));
     fixed += operand_bytes(net);
   }
   if (fixed >= cfg->hbm_budget_bytes)

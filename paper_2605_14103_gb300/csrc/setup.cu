@@ -6,6 +6,7 @@
 //   FP64 contraction operands Zr, Zi, Zr + Zi (zero-padded, row-major).
 #include <algorithm>
 #include <cmath>
+#include <complex>
 #include <numeric>
 
 #include "zbus_internal.cuh"
@@ -176,6 +177,133 @@ zbus_status upload(T** dst, const std::vector<T>& src, cudaStream_t st) {
   return ZBUS_OK;
 }
 
+// Inverse of a 3x3 complex matrix (row-major) by Gauss-Jordan elimination
+// with partial pivoting; false when a pivot vanishes.
+bool inv3(const double2* a, double2* out) {
+  std::complex<double> m[3][6];
+  for (int i = 0; i < 3; ++i)
+    for (int j = 0; j < 3; ++j) {
+      m[i][j] = {a[3 * i + j].x, a[3 * i + j].y};
+      m[i][3 + j] = i == j ? 1.0 : 0.0;
+    }
+  double scale = 0.0;
+  for (int e = 0; e < 9; ++e) scale = std::max(scale, std::hypot(a[e].x, a[e].y));
+  for (int k = 0; k < 3; ++k) {
+    int piv = k;
+    for (int i = k + 1; i < 3; ++i)
+      if (std::abs(m[i][k]) > std::abs(m[piv][k])) piv = i;
+    if (!(std::abs(m[piv][k]) > 1e-13 * scale)) return false;
+    if (piv != k)
+      for (int j = 0; j < 6; ++j) std::swap(m[k][j], m[piv][j]);
+    const std::complex<double> d = 1.0 / m[k][k];
+    for (int j = 0; j < 6; ++j) m[k][j] *= d;
+    for (int i = 0; i < 3; ++i) {
+      if (i == k) continue;
+      const std::complex<double> f = m[i][k];
+      for (int j = 0; j < 6; ++j) m[i][j] -= f * m[k][j];
+    }
+  }
+  for (int i = 0; i < 3; ++i)
+    for (int j = 0; j < 3; ++j) out[3 * i + j] = make_double2(m[i][3 + j].real(), m[i][3 + j].imag());
+  return true;
+}
+
+// Radial structure of the branch form, when the buses form a tree hanging off
+// the slack with reciprocal branches (Y_cp = Y_pc): breadth-first positions
+// (so every level and every bus's children are contiguous ranges), each
+// position's bus, parent and children, the level ranges, and z_c =
+// (-Y_c,parent)^{-1}, the series impedance of each bus's parent branch
+// (-Y_c,slack for buses on the slack).  For such a network without shunts,
+// Y_LL^{-1} r is, at every bus, the sum over its path to the slack of z times
+// the subtree sums of r.  Leaves net->radial false otherwise.
+zbus_status build_tree(zbus_network net, const std::vector<int32_t>& bp,
+                       const std::vector<int32_t>& bc, const std::vector<double2>& bv,
+                       cudaStream_t st) {
+  const int nb = net->nbus;
+  auto block_of = [&](int a, int col) -> int {
+    for (int t = bp[a]; t < bp[a + 1]; ++t)
+      if (bc[t] == col) return t;
+    return -1;
+  };
+  // parents by a breadth-first search from the slack-connected buses; a bus
+  // reached twice means a loop
+  std::vector<int32_t> par(nb, -2), roots, queue;
+  for (int a = 0; a < nb; ++a)
+    if (block_of(a, -1) >= 0) {
+      par[a] = -1;
+      roots.push_back(a);
+    }
+  queue = roots;
+  for (size_t h = 0; h < queue.size(); ++h) {
+    const int a = queue[h];
+    for (int t = bp[a]; t < bp[a + 1]; ++t) {
+      const int c = bc[t];
+      if (c < 0 || c == par[a]) continue;
+      if (par[c] != -2) return ZBUS_OK;
+      par[c] = a;
+      queue.push_back(c);
+    }
+  }
+  if ((int)queue.size() != nb) return ZBUS_OK;
+  // levels in breadth-first order (the queue), children of each bus as a
+  // contiguous range of that order
+  std::vector<int32_t> depth(nb, 0), qpos(nb);
+  for (int i = 0; i < nb; ++i) {
+    const int c = queue[i];
+    qpos[c] = i;
+    if (par[c] >= 0) depth[c] = depth[par[c]] + 1;
+  }
+  const int levels = 1 + *std::max_element(depth.begin(), depth.end());
+  std::vector<int32_t> lvl(levels + 1, 0);
+  for (int i = 0; i < nb; ++i) lvl[depth[queue[i]] + 1] = i + 1;
+  for (int L = 1; L <= levels; ++L) lvl[L] = std::max(lvl[L], lvl[L - 1]);
+  std::vector<int4> node(nb);        // per breadth-first position
+  std::vector<float2> z((size_t)nb * 9);
+  std::vector<float> zs(nb);
+  int next = (int)roots.size();
+  for (int i = 0; i < nb; ++i) {
+    const int c = queue[i], p = par[c];
+    int cnt = 0;
+    for (int t = bp[c]; t < bp[c + 1]; ++t)
+      if (bc[t] >= 0 && bc[t] != p) ++cnt;
+    node[i] = make_int4(c, p >= 0 ? qpos[p] : -1, next, next + cnt);
+    for (int q = next; q < next + cnt; ++q)
+      if (par[queue[q]] != c) return ZBUS_OK;   // children not contiguous: not expected
+    next += cnt;
+    const int t = block_of(c, p >= 0 ? p : -1);
+    if (p >= 0) {
+      const int u = block_of(p, c);
+      if (t < 0 || u < 0) return ZBUS_OK;
+      double ymax = 0.0, dmax = 0.0;
+      for (int e = 0; e < 9; ++e) {
+        const double2 x = bv[(size_t)t * 9 + e], y = bv[(size_t)u * 9 + e];
+        ymax = std::max(ymax, std::hypot(x.x, x.y));
+        dmax = std::max(dmax, std::hypot(x.x - y.x, x.y - y.y));
+      }
+      if (dmax > 1e-12 * ymax) return ZBUS_OK;   // not reciprocal
+    }
+    double2 y[9], zi[9];
+    for (int e = 0; e < 9; ++e)
+      y[e] = make_double2(-bv[(size_t)t * 9 + e].x, -bv[(size_t)t * 9 + e].y);
+    if (!inv3(y, zi)) return ZBUS_OK;
+    double m = 0.0;
+    for (int e = 0; e < 9; ++e) m = std::max(m, std::max(std::fabs(zi[e].x), std::fabs(zi[e].y)));
+    if (!(m > 0.0) || !std::isfinite(m)) return ZBUS_OK;
+    const int ex = std::ilogb(m);
+    zs[i] = std::ldexp(1.0f, ex);
+    for (int e = 0; e < 9; ++e)
+      z[(size_t)i * 9 + e] =
+          make_float2((float)std::ldexp(zi[e].x, -ex), (float)std::ldexp(zi[e].y, -ex));
+  }
+  ZB_CHECK(upload(&net->t_lvl, lvl, st));
+  ZB_CHECK(upload(&net->t_node, node, st));
+  ZB_CHECK(upload(&net->t_z, z, st));
+  ZB_CHECK(upload(&net->t_zs, zs, st));
+  net->depth = levels;
+  net->radial = true;
+  return ZBUS_OK;
+}
+
 }  // namespace
 
 zbus_status build_network(zbus_network net, int32_t n_total, int64_t nnz, const int32_t* row,
@@ -315,6 +443,7 @@ zbus_status build_network(zbus_network net, int32_t n_total, int64_t nnz, const 
     ZB_CHECK(upload(&net->bsr_ptr, bp, st));
     ZB_CHECK(upload(&net->bsr_col, bc, st));
     ZB_CHECK(upload(&net->bsr_val, bv, st));
+    ZB_CHECK(build_tree(net, bp, bc, bv, st));
   }
 
   const size_t zb = (size_t)n * n * sizeof(double2);

@@ -130,6 +130,8 @@ extern "C" zbus_status zbus_autotune(const zbus_batch_item* items, int32_t n_ite
   if (n_items <= 0 || !items) return fail(ZBUS_ERR_ARG, "no items");
   if (!opts || opts->precision == ZBUS_FP64)
     return fail(ZBUS_ERR_ARG, "the autotuner needs a mixed precision in opts");
+  if (opts->precision == ZBUS_TREE_SWEEP)
+    return fail(ZBUS_ERR_UNSUPPORTED, "the tree sweep has no tensor-core tiles to tune");
   if (reps < 1) reps = 3;
   int max_n = 0;
   int64_t total_B = 0;

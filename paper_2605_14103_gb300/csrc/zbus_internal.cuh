@@ -174,6 +174,17 @@ struct zbus_network_s {
   double2* bsr_val = nullptr;   // [nblk][3][3] row-major complex
   int64_t nblk = 0;
   float4* bsr_df = nullptr;     // [nblk][9] double-float copy (mixed sweeps)
+  // radial structure (buses form a tree hanging off the slack, reciprocal
+  // branches), for the tree-sweep application of Z: breadth-first positions,
+  // levels, children ranges, and the inverse series block of each bus's
+  // parent branch
+  bool radial = false;
+  int depth = 0;                // levels of the tree
+  int4* t_node = nullptr;       // [nbus] per position: bus, parent position (-1: slack),
+                                //        first child position, end of the children
+  int32_t* t_lvl = nullptr;     // [depth + 1] first position of each level
+  float2* t_z = nullptr;        // [nbus][9] z = y^{-1} of the parent branch, scaled by 2^-e
+  float* t_zs = nullptr;        // [nbus] 2^e
   zbus::Workspace ws;
   zbus::MixedOperands mixed[2];   // [0] FP16 row-scaled, [1] BF16 hi + lo
   struct zbus::Group* group1 = nullptr;   // single-network mixed solves
@@ -212,6 +223,8 @@ zbus_status ensure_workspace(zbus_network net, int64_t B);
 zbus_status make_tmap_2d(CUtensorMap* map, const void* base, bool bf16, uint64_t cols,
                          uint64_t rows, uint32_t box_cols, uint32_t box_rows);
 zbus_status prepare_mixed(zbus_network net, int32_t precision, cudaStream_t st);
+// double-float operands of the tree sweep (radial networks only)
+zbus_status prepare_tree(zbus_network net, cudaStream_t st);
 void free_mixed(zbus_network net);
 
 

@@ -19,7 +19,7 @@ ZBUS_OK = 0
 STATUS = {0: "ZBUS_OK", 1: "ZBUS_ERR_ARG", 2: "ZBUS_ERR_SINGULAR", 3: "ZBUS_ERR_OOM",
           4: "ZBUS_ERR_CUDA", 5: "ZBUS_ERR_TIMEOUT", 6: "ZBUS_ERR_DEVICE",
           7: "ZBUS_ERR_UNSUPPORTED"}
-PRECISION = {"fp64": 0, "bf16x2": 1, "fp16_scaled": 2}
+PRECISION = {"fp64": 0, "bf16x2": 1, "fp16_scaled": 2, "tree": 3}
 RULE = {"maxabs": 0, "summag": 1}
 
 

@@ -45,7 +45,7 @@ def make_set(specs, seed0=40):
 SPECS = [(50, 33), (130, 1), (300, 260), (17, 7), (700, 129), (90, 128)]
 
 
-@pytest.mark.parametrize("mode", ["fp16_scaled", "bf16x2"])
+@pytest.mark.parametrize("mode", ["fp16_scaled", "bf16x2", "tree"])
 def test_batched_equals_single_and_oracle(mode):
     fs = make_set(SPECS)
     nets = [zbus.Network.from_feeder(f) for f, _, _ in fs]

@@ -1,11 +1,13 @@
-"""GPU parity of the mixed-precision (tcgen05) defect form against the FP64 oracle.
+"""GPU parity of the defect forms against the FP64 oracle: the mixed-precision
+tcgen05 contraction (FP16 row-scaled, BF16 hi+lo) and the tree sweep.
 
 Bar (per scenario): identical converged flags, max |V_gpu - V_oracle| <= 1e-6 pu
 on converged scenarios, FP64 power mismatch <= 1e-6 pu, iteration counts
 within one of the oracle's.  A single sweep from a warm start isolates the
 residual, the tensor-core contraction and the epilogue: its step must match
 the FP64 step Z r(v) to the precision of the operands (FP16 row-scaled:
-relative 2^-10 of the step size; BF16 hi+lo with BF16 residual: 2^-7).
+relative 2^-10 of the step size; BF16 hi+lo with BF16 residual: 2^-7; tree
+sweep with FP16 branch impedances: 2^-9).
 """
 import numpy as np
 import pytest
@@ -18,8 +20,9 @@ from paper_2605_14103_gb300 import zbus                  # noqa: E402
 
 pytestmark = pytest.mark.gpu
 
-MODES = ["fp16_scaled", "bf16x2"]
-STEP_RTOL = {"fp16_scaled": 2.0 ** -10, "bf16x2": 2.0 ** -7}
+MODES = ["fp16_scaled", "bf16x2", "tree"]
+# the tree sweep applies Z exactly up to its FP16 branch impedances
+STEP_RTOL = {"fp16_scaled": 2.0 ** -10, "bf16x2": 2.0 ** -7, "tree": 2.0 ** -9}
 
 
 @pytest.fixture(scope="module", autouse=True)
@@ -144,8 +147,8 @@ def test_modes_agree_with_each_other_and_fp64():
     f, Sw, Sd, w = F.make_workload("feeder128_b4096", B=256)
     net = zbus.Network.from_feeder(f)
     outs = {m: net.solve(dev(Sw), dev(Sd), precision=m)[0].cpu().numpy()
-            for m in ["fp64", "fp16_scaled", "bf16x2"]}
-    for m in ("fp16_scaled", "bf16x2"):
+            for m in ["fp64", "fp16_scaled", "bf16x2", "tree"]}
+    for m in ("fp16_scaled", "bf16x2", "tree"):
         assert np.abs(outs[m] - outs["fp64"]).max() <= 1e-6
 
 

@@ -49,7 +49,7 @@ def make_requests(feeders, sizes, seed=0):
     return reqs, host
 
 
-@pytest.mark.parametrize("mode", ["fp16_scaled", "bf16x2"])
+@pytest.mark.parametrize("mode", ["fp16_scaled", "bf16x2", "tree"])
 def test_same_alone_and_in_the_mix(pool, mode):
     feeders, nets = pool
     reqs, host = make_requests(feeders, [1, 5, 33, 130, 200, 7, 64, 129], seed=3)
