@@ -157,6 +157,14 @@ zbus_status zbus_network_reserve(zbus_network net, int64_t B, int32_t precision)
  *                   after it synchronises.  Scratch grows on demand (a
  *                   synchronous allocation) unless reserved beforehand.
  *
+ * The array arguments are all device memory or all host memory (pinned or
+ * pageable; a mix returns ZBUS_ERR_ARG).  With host memory the batch is
+ * solved in chunks staged through the device: the host-to-device copy of one
+ * chunk and the device-to-host copy of the previous one run on copy streams
+ * while the sweeps of another chunk run on cuda_stream (pinned memory lets
+ * them overlap), and cuda_stream waits for the last copy.  Results are the
+ * same bit for bit as with device buffers.
+ *
  * Non-convergence is reported by the flags, not by the status.  V_out may
  * alias V_init.  B = 0 is a no-op.
  *

@@ -374,6 +374,17 @@ void zbus_network_destroy(zbus_network net) {
   }
   if (net->cap_stream) cudaStreamDestroy(net->cap_stream);
   for (auto e : net->prof.ev) cudaEventDestroy(e);
+  {
+    HostStage& h = net->stage;
+    if (h.h2d) cudaStreamSynchronize(h.h2d);
+    if (h.d2h) cudaStreamSynchronize(h.d2h);
+    for (int s = 0; s < 2; ++s) cudaFree(h.buf[s]);
+    if (h.h2d) cudaStreamDestroy(h.h2d);
+    if (h.d2h) cudaStreamDestroy(h.d2h);
+    cudaEvent_t evs[] = {h.start, h.end, h.in[0], h.in[1], h.done[0], h.done[1], h.out[0], h.out[1]};
+    for (auto e : evs)
+      if (e) cudaEventDestroy(e);
+  }
   cudaFree(net->prof.d_hist);
   cudaFree(net->ws.base);
   free_mixed(net);
@@ -424,27 +435,16 @@ zbus_status zbus_network_reserve(zbus_network net, int64_t B, int32_t precision)
   return ZBUS_OK;
 }
 
-zbus_status zbus_solve(zbus_network net, int64_t B, const double* S_wye, const double* S_delta,
-                       const double* V_init, double tol, int32_t max_iter,
-                       const zbus_solve_opts* opts, double* V_out, int32_t* iters,
-                       uint8_t* converged, void* cuda_stream) {
-  g_last_error.clear();
-  if (!net) return fail(ZBUS_ERR_ARG, "network is NULL");
-  if (B < 0 || B > INT32_MAX / 4) return fail(ZBUS_ERR_ARG, "B out of range");
-  if (!(tol >= 0.0) || !std::isfinite(tol)) return fail(ZBUS_ERR_ARG, "tol must be finite, >= 0");
-  if (max_iter < 1) return fail(ZBUS_ERR_ARG, "max_iter must be >= 1");
-  zbus_solve_opts o;
-  zbus_solve_opts_default(&o);
-  if (opts) o = *opts;
-  if (o.conv_rule != ZBUS_CONV_MAXABS && o.conv_rule != ZBUS_CONV_SUMMAG)
-    return fail(ZBUS_ERR_ARG, "unknown convergence rule");
-  if (!known_precision(o.precision)) return fail(ZBUS_ERR_ARG, "unknown precision");
-  if (B == 0) return ZBUS_OK;
-  if (!V_out || !iters || !converged) return fail(ZBUS_ERR_ARG, "an output pointer is NULL");
-  if (S_delta && !net->bus_aligned)
-    return fail(ZBUS_ERR_ARG, "delta loads need three unknowns per bus (n % 3 == 0)");
-  ZB_CHECK(check_device(net));
-  cudaStream_t st = (cudaStream_t)cuda_stream;
+}  // extern "C"
+
+namespace zbus {
+namespace {
+
+// The solve on device buffers (the arguments checked by zbus_solve).
+zbus_status solve_device(zbus_network net, int64_t B, const double* S_wye, const double* S_delta,
+                         const double* V_init, double tol, int32_t max_iter,
+                         const zbus_solve_opts& o, double* V_out, int32_t* iters,
+                         uint8_t* converged, cudaStream_t st) {
   ZB_CHECK(ensure_workspace(net, B));
   if (o.precision != ZBUS_FP64) {
     // mixed precision: a group of one feeder
@@ -497,6 +497,146 @@ zbus_status zbus_solve(zbus_network net, int64_t B, const double* S_wye, const d
   }
   ZB_CUDA(cudaGetLastError());
   return ZBUS_OK;
+}
+
+
+// Where a caller buffer lives: 1 device (or managed) memory, 0 host memory
+// (pinned or pageable), -1 null.
+int buffer_kind(const void* p) {
+  if (!p) return -1;
+  cudaPointerAttributes a;
+  if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+    cudaGetLastError();
+    return 0;
+  }
+  return (a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged) ? 1 : 0;
+}
+
+// Staging of host-buffer solves: two sets of device buffers (loads, warm
+// start, outputs) of `cap` scenarios, copy streams and events.
+zbus_status ensure_stage(zbus_network net, int64_t cap) {
+  HostStage& h = net->stage;
+  if (!h.h2d) {
+    ZB_CUDA(cudaStreamCreateWithFlags(&h.h2d, cudaStreamNonBlocking));
+    ZB_CUDA(cudaStreamCreateWithFlags(&h.d2h, cudaStreamNonBlocking));
+    cudaEvent_t* evs[] = {&h.start, &h.end, &h.in[0], &h.in[1], &h.done[0], &h.done[1],
+                          &h.out[0], &h.out[1]};
+    for (auto e : evs) ZB_CUDA(cudaEventCreateWithFlags(e, cudaEventDisableTiming));
+  }
+  if (h.cap >= cap) return ZBUS_OK;
+  ZB_CUDA(cudaDeviceSynchronize());
+  for (int s = 0; s < 2; ++s) {
+    cudaFree(h.buf[s]);
+    h.buf[s] = nullptr;
+  }
+  h.cap = 0;
+  const size_t vec = (size_t)cap * net->n * 2;   // doubles of one [cap][n] complex array
+  for (int s = 0; s < 2; ++s)
+    ZB_CUDA(cudaMalloc((void**)&h.buf[s], 4 * vec * sizeof(double) + (size_t)cap * 8));
+  h.cap = cap;
+  return ZBUS_OK;
+}
+
+// The solve on host buffers: chunks of the batch staged through two sets of
+// device buffers, so that the copies of one chunk (host to device on one
+// stream, device to host on another) overlap the sweeps of the next on the
+// caller's stream.  The caller's stream waits for the last copy.
+zbus_status solve_host(zbus_network net, int64_t B, const double* S_wye, const double* S_delta,
+                       const double* V_init, double tol, int32_t max_iter,
+                       const zbus_solve_opts& o, double* V_out, int32_t* iters,
+                       uint8_t* converged, cudaStream_t st) {
+  // four chunks for the defect forms (whose sweeps take about as long as the
+  // copies); one for the plain method, whose FP64 sweeps take some fifty
+  // times longer than its copies and run less efficiently on smaller batches
+  const int64_t C = (B <= 2048 || o.precision == ZBUS_FP64) ? B
+                                                            : std::max<int64_t>(1024, (B + 3) / 4);
+  ZB_CHECK(ensure_stage(net, C));
+  ZB_CHECK(ensure_workspace(net, C));
+  HostStage& h = net->stage;
+  const size_t n2 = (size_t)net->n * 2;           // doubles per scenario
+  const size_t vec = (size_t)h.cap * n2;
+  ZB_CUDA(cudaEventRecord(h.start, st));
+  ZB_CUDA(cudaStreamWaitEvent(h.h2d, h.start, 0));
+  ZB_CUDA(cudaStreamWaitEvent(h.d2h, h.start, 0));
+  for (int64_t b0 = 0, k = 0; b0 < B; b0 += C, ++k) {
+    const int64_t Bk = std::min(C, B - b0);
+    const int s = (int)(k & 1);
+    double* sw = h.buf[s];
+    double* sd = sw + vec;
+    double* v0 = sd + vec;
+    double* vo = v0 + vec;
+    int32_t* it = reinterpret_cast<int32_t*>(vo + vec);
+    uint8_t* cv = reinterpret_cast<uint8_t*>(it + h.cap);
+    if (k >= 2) {   // the set's previous chunk: inputs consumed, outputs copied out
+      ZB_CUDA(cudaStreamWaitEvent(h.h2d, h.done[s], 0));
+      ZB_CUDA(cudaStreamWaitEvent(h.h2d, h.out[s], 0));
+    }
+    const size_t bytes = (size_t)Bk * n2 * sizeof(double);
+    if (S_wye)
+      ZB_CUDA(cudaMemcpyAsync(sw, S_wye + b0 * n2, bytes, cudaMemcpyHostToDevice, h.h2d));
+    if (S_delta)
+      ZB_CUDA(cudaMemcpyAsync(sd, S_delta + b0 * n2, bytes, cudaMemcpyHostToDevice, h.h2d));
+    if (V_init)
+      ZB_CUDA(cudaMemcpyAsync(v0, V_init + b0 * n2, bytes, cudaMemcpyHostToDevice, h.h2d));
+    ZB_CUDA(cudaEventRecord(h.in[s], h.h2d));
+    ZB_CUDA(cudaStreamWaitEvent(st, h.in[s], 0));
+    ZB_CHECK(solve_device(net, Bk, S_wye ? sw : nullptr, S_delta ? sd : nullptr,
+                          V_init ? v0 : nullptr, tol, max_iter, o, vo, it, cv, st));
+    ZB_CUDA(cudaEventRecord(h.done[s], st));
+    ZB_CUDA(cudaStreamWaitEvent(h.d2h, h.done[s], 0));
+    ZB_CUDA(cudaMemcpyAsync(V_out + b0 * n2, vo, bytes, cudaMemcpyDeviceToHost, h.d2h));
+    ZB_CUDA(cudaMemcpyAsync(iters + b0, it, (size_t)Bk * sizeof(int32_t), cudaMemcpyDeviceToHost,
+                            h.d2h));
+    ZB_CUDA(cudaMemcpyAsync(converged + b0, cv, (size_t)Bk, cudaMemcpyDeviceToHost, h.d2h));
+    ZB_CUDA(cudaEventRecord(h.out[s], h.d2h));
+  }
+  ZB_CUDA(cudaEventRecord(h.end, h.d2h));
+  ZB_CUDA(cudaStreamWaitEvent(st, h.end, 0));
+  return ZBUS_OK;
+}
+
+}  // namespace
+}  // namespace zbus
+
+extern "C" {
+
+zbus_status zbus_solve(zbus_network net, int64_t B, const double* S_wye, const double* S_delta,
+                       const double* V_init, double tol, int32_t max_iter,
+                       const zbus_solve_opts* opts, double* V_out, int32_t* iters,
+                       uint8_t* converged, void* cuda_stream) {
+  g_last_error.clear();
+  if (!net) return fail(ZBUS_ERR_ARG, "network is NULL");
+  if (B < 0 || B > INT32_MAX / 4) return fail(ZBUS_ERR_ARG, "B out of range");
+  if (!(tol >= 0.0) || !std::isfinite(tol)) return fail(ZBUS_ERR_ARG, "tol must be finite, >= 0");
+  if (max_iter < 1) return fail(ZBUS_ERR_ARG, "max_iter must be >= 1");
+  zbus_solve_opts o;
+  zbus_solve_opts_default(&o);
+  if (opts) o = *opts;
+  if (o.conv_rule != ZBUS_CONV_MAXABS && o.conv_rule != ZBUS_CONV_SUMMAG)
+    return fail(ZBUS_ERR_ARG, "unknown convergence rule");
+  if (!known_precision(o.precision)) return fail(ZBUS_ERR_ARG, "unknown precision");
+  if (B == 0) return ZBUS_OK;
+  if (!V_out || !iters || !converged) return fail(ZBUS_ERR_ARG, "an output pointer is NULL");
+  if (S_delta && !net->bus_aligned)
+    return fail(ZBUS_ERR_ARG, "delta loads need three unknowns per bus (n % 3 == 0)");
+  ZB_CHECK(check_device(net));
+  cudaStream_t st = (cudaStream_t)cuda_stream;
+  // every buffer on the device, or every buffer in host memory
+  const int kinds[] = {buffer_kind(S_wye), buffer_kind(S_delta), buffer_kind(V_init),
+                       buffer_kind(V_out), buffer_kind(iters), buffer_kind(converged)};
+  int host = 0, dev = 0;
+  for (int x : kinds) {
+    host += x == 0;
+    dev += x == 1;
+  }
+  if (host && dev) return fail(ZBUS_ERR_ARG, "buffers must all be on the device or all in host memory");
+  if (host) {
+    if (o.profile == 1) return fail(ZBUS_ERR_ARG, "profiling needs device buffers");
+    return solve_host(net, B, S_wye, S_delta, V_init, tol, max_iter, o, V_out, iters, converged,
+                      st);
+  }
+  return solve_device(net, B, S_wye, S_delta, V_init, tol, max_iter, o, V_out, iters, converged,
+                      st);
 }
 
 zbus_status zbus_solve_batched(const zbus_batch_item* items, int32_t n_items, double tol,

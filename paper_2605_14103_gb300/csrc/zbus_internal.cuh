@@ -129,6 +129,19 @@ struct Profile {
   int32_t sweeps = 0;
 };
 
+// Device staging of solves on host buffers: two sets of [cap] scenarios
+// (wye loads, delta loads, warm start, V, then iters and flags), a copy stream
+// each way, and events ordering copies and sweeps.
+struct HostStage {
+  int64_t cap = 0;
+  double* buf[2] = {nullptr, nullptr};
+  cudaStream_t h2d = nullptr, d2h = nullptr;
+  cudaEvent_t start = nullptr, end = nullptr;
+  cudaEvent_t in[2] = {nullptr, nullptr};     // a set's inputs are on the device
+  cudaEvent_t done[2] = {nullptr, nullptr};   // a set's chunk is solved
+  cudaEvent_t out[2] = {nullptr, nullptr};    // a set's outputs are back in host memory
+};
+
 struct GraphEntry {
   int64_t B = 0;
   int32_t precision = -1;
@@ -191,6 +204,7 @@ struct zbus_network_s {
   std::vector<zbus::GraphEntry> graphs;
   cudaStream_t cap_stream = nullptr;  // private stream used only to capture graphs
   zbus::Profile prof;
+  zbus::HostStage stage;
 };
 
 namespace zbus {

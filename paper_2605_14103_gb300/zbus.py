@@ -121,11 +121,12 @@ def _stream(stream) -> int | None:
     return s.cuda_stream or None
 
 
-def _dptr(t, name, dtype=None, shape=None):
-    """Device pointer of a contiguous CUDA tensor (None passes through)."""
+def _dptr(t, name, dtype=None, shape=None, host_ok=False):
+    """Pointer of a contiguous tensor (None passes through): CUDA memory, or
+    host memory where the call accepts it (host_ok)."""
     if t is None:
         return None
-    if not t.is_cuda:
+    if not t.is_cuda and not host_ok:
         raise ValueError(f"{name} must be a CUDA tensor")
     if not t.is_contiguous():
         raise ValueError(f"{name} must be contiguous")
@@ -189,12 +190,15 @@ def zbus_solve(h, S_wye, S_delta, V_init, tol, max_iter, opts, V_out, iters, con
     n = zbus_network_size(h)
     B = V_out.shape[0]
     c128 = torch.complex128
+    # all buffers on the device, or all in host memory (then the library stages
+    # them through the device, overlapping the copies with the sweeps)
     _check(lib().zbus_solve(
-        h, int(B), _dptr(S_wye, "S_wye", c128, (B, n)), _dptr(S_delta, "S_delta", c128, (B, n)),
-        _dptr(V_init, "V_init", c128, (B, n)), float(tol), int(max_iter),
+        h, int(B), _dptr(S_wye, "S_wye", c128, (B, n), True),
+        _dptr(S_delta, "S_delta", c128, (B, n), True),
+        _dptr(V_init, "V_init", c128, (B, n), True), float(tol), int(max_iter),
         C.byref(opts) if opts is not None else None,
-        _dptr(V_out, "V_out", c128, (B, n)), _dptr(iters, "iters", torch.int32, (B,)),
-        _dptr(converged, "converged", torch.uint8, (B,)), _stream(stream)))
+        _dptr(V_out, "V_out", c128, (B, n), True), _dptr(iters, "iters", torch.int32, (B,), True),
+        _dptr(converged, "converged", torch.uint8, (B,), True), _stream(stream)))
 
 
 def zbus_solve_noalloc(h, S_wye, S_delta, V_init, tol, max_iter, rule, V_out, iters, converged,
@@ -424,7 +428,9 @@ class Network:
     def solve(self, S_wye, S_delta=None, V_init=None, tol=1e-8, max_iter=50,
               precision="fp64", rule="maxabs", mismatch_tol=1e-6, max_correction=8,
               profile=False, out=None, stream=None):
-        """Returns (V [B,n] complex128, iters int32[B], converged uint8[B]) on the device."""
+        """Returns (V [B,n] complex128, iters int32[B], converged uint8[B]) where the
+        loads live: on the device, or in host memory (results valid once the
+        stream has synchronised)."""
         import torch
         B = (S_wye if S_wye is not None else S_delta).shape[0]
         dev = (S_wye if S_wye is not None else S_delta).device
