@@ -535,14 +535,21 @@ def run_hetero(args):
             good += int(((cv == 1) & (mm <= 1e-6)).sum().item())
         return good
 
-    for prec in ("fp16_scaled", "bf16x2"):
+    for prec in ("fp16_scaled", "bf16x2", "tree"):
         for _ in range(args.warmup):
             outs = zbus.solve_batched(nets, loads, precision=prec)
         ms = _timed(lambda: zbus.solve_batched(nets, loads, precision=prec), args.steps, flush)
         outs = zbus.solve_batched(nets, loads, precision=prec)
         good = count(outs)
+        sweeps = max(int(it.max().item()) for _, it, _ in outs)
         forms["batched_" + prec] = {"value": good / (statistics.median(ms) / 1e3),
-                                    "ms_per_step": statistics.median(ms), "converged": good}
+                                    "ms_per_step": statistics.median(ms), "converged": good,
+                                    "sweeps": sweeps,
+                                    # reset, parameters and tile list, per feeder the
+                                    # admission and the three collection kernels, per sweep
+                                    # the sweep's kernels
+                                    "gpu_launches": 3 + 4 * len(nets) +
+                                    (3 if prec == "tree" else 4) * sweeps}
         if prec == "fp16_scaled":
             head_outs = outs
 
@@ -579,7 +586,7 @@ def run_hetero(args):
            "forms": forms, "peaks": peaks["src"],
            "parity": {"sampled_feeders": 4, "sampled_scenarios_each": 64,
                       "max_dv_vs_oracle": worst, "flags_equal": flags},
-           "gpu_launches": None}
+           "gpu_launches": head["gpu_launches"]}
     print(json.dumps(out), flush=True)
 
 
@@ -613,10 +620,12 @@ def run_serve(args):
                         "arrival": float(a)})
         return out
 
+    prec = args.precision if args.precision != "fp64" else "fp16_scaled"
+
     def run(reqs):
         t = time.perf_counter()
         res = zbus.serve(nets, reqs, hbm_budget_bytes=120 << 30, max_slots=4096,
-                         keep_results=False)
+                         keep_results=False, precision=prec)
         wall = time.perf_counter() - t
         lat = np.array([r["t_done"] - r["t_arrival"] for r in res])
         scen = sum(r["B"] for r in res)
@@ -627,7 +636,7 @@ def run_serve(args):
                 "p99_ms": float(np.percentile(lat, 99) * 1e3), "wall_s": wall,
                 "all_ok": all(r["status"] == 0 for r in res)}
 
-    zbus.serve(nets, requests(np.zeros(32)), keep_results=False)         # warm-up
+    zbus.serve(nets, requests(np.zeros(32)), keep_results=False, precision=prec)   # warm-up
     sat = run(requests(np.zeros(n_req)))
     mean_B = sat["scenarios"] / sat["requests"]
     runs = {"saturated": sat}
@@ -639,8 +648,8 @@ def run_serve(args):
     out = {"metric": METRIC, "value": sat["throughput"], "unit": UNIT, "n_gpus": 1,
            "steps": 1, "warmup": 1, "ms_per_step": sat["wall_s"] * 1e3,
            "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
-           "dtype": "fp16_scaled+f64", "data": "synthetic",
-           "config": {"workload": "serve16", "feeders": len(pool),
+           "dtype": DTYPE[prec], "data": "synthetic",
+           "config": {"workload": "serve16", "feeders": len(pool), "precision": prec,
                       "buses_range": [min(f.N for f, _ in pool), max(f.N for f, _ in pool)],
                       "requests_per_run": n_req, "hbm_budget_gb": 120, "setup_s": setup_s},
            "latency": {"p50_ms_at_0.7": head["p50_ms"], "p99_ms_at_0.7": head["p99_ms"]},
