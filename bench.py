@@ -229,7 +229,7 @@ def run_reference(args):
 KERNELS = {"fp64": ("k_currents_f64", "k_gemm3m_f64", "k_decide+k_compact"),
            "fp16_scaled": ("k_residual_group", "k_contract_group", "k_decide_group+k_finish_group"),
            "bf16x2": ("k_residual_group", "k_contract_group", "k_decide_group+k_finish_group"),
-           "tree": ("k_residual_group", "k_tree_group", "k_finish_group")}
+           "tree": ("k_residual_group", "k_tree_group", "(sweep end inside k_tree_group)")}
 # arithmetic of each form: the sweep's, then the final test's
 DTYPE = {"fp64": "f64", "fp16_scaled": "fp16_scaled+f64", "bf16x2": "bf16x2+f64",
          "tree": "f32+f64"}
@@ -367,7 +367,7 @@ def measure(net, form, Sw, Sd, wl, n, steps, warmup, flush, ws, peaks):
     return {"value": value, "ms_per_step": 1e3 * t_max / steps,
             "step_ms_p50": statistics.median(step_ms), "converged_per_step": good,
             "max_iters": max_iters, "mean_iters": float(it.float().mean().item()),
-            "gpu_launches": steps * (OUTSIDE[form][1] + (3 if form == "tree" else 4) * max_iters),
+            "gpu_launches": steps * (OUTSIDE[form][1] + (2 if form == "tree" else 4) * max_iters),
             "kernels": kernels, "roofline": roof}, (V, it, cv)
 
 
@@ -549,7 +549,7 @@ def run_hetero(args):
                                     # admission and the three collection kernels, per sweep
                                     # the sweep's kernels
                                     "gpu_launches": 3 + 4 * len(nets) +
-                                    (3 if prec == "tree" else 4) * sweeps}
+                                    (2 if prec == "tree" else 4) * sweeps}
         if prec == "fp16_scaled":
             head_outs = outs
 

@@ -35,6 +35,12 @@ constexpr int DEC_THREADS = 256;
 // contraction) or FP32 values, scenario-minor (tree sweep)
 constexpr int RES_FP16 = 0, RES_BF16 = 1, RES_F32 = 2;
 constexpr int TREE_BATCH = 4;   // buses whose state a tree-sweep warp loads at once
+constexpr size_t TREE_ONCHIP_MAX = 200 * 1024;   // shared memory of an on-chip tree block
+
+// Shared memory of the position tables of a tree-sweep block, padded to 16 B.
+__host__ __device__ inline size_t tree_table_bytes(int nbus) {
+  return ((size_t)56 * nbus + 15) & ~(size_t)15;
+}
 // Item owning global index x, for a non-decreasing begin field.
 __device__ __forceinline__ int find_item(const ItemDesc* items, int n_items, int x, int which) {
   int lo = 0, hi = n_items - 1;
@@ -128,6 +134,8 @@ __global__ void k_group_reset(GroupState* __restrict__ gs, const ItemDesc* __res
     gs->sweep = 0;
     gs->err = 0;
     gs->n_tiles = 0;
+    gs->tree_done = 0;
+    gs->tree_active = 0;
   }
 }
 
@@ -575,9 +583,29 @@ k_decide_group(GroupState* __restrict__ gs, const ItemDesc* __restrict__ items) 
 // k_decide_group), so the sweep needs neither a contraction nor a separate
 // stop-test launch.
 // ---------------------------------------------------------------------------
-template <int TREE_WARPS, int MINB>
+// End of a tree-sweep block: add its slots still active to the sweep's sum;
+// the block that arrives last closes the sweep (the work of k_finish_group
+// without a tile list): profile record, active count, sweep counter, the
+// graph's loop condition, and the counters reset for the next sweep.
+__device__ void tree_block_done(GroupState* gs, int still_active, cudaGraphConditionalHandle h,
+                                int use_handle) {
+  if (still_active) atomicAdd(&gs->tree_active, still_active);
+  __threadfence();
+  if (atomicAdd(&gs->tree_done, 1) != (int)gridDim.x - 1) return;
+  __threadfence();
+  const int total = atomicAdd(&gs->tree_active, 0);
+  if (gs->hist && gs->sweep < gs->hist_n) gs->hist[gs->sweep] = gs->active;
+  gs->active = total;
+  gs->sweep = gs->sweep + 1;
+  gs->tree_active = 0;
+  gs->tree_done = 0;
+  if (use_handle) cudaGraphSetConditional(h, total > 0 ? 1u : 0u);
+}
+
+template <int TREE_WARPS, int MINB, bool ONCHIP>
 __global__ void __launch_bounds__(32 * TREE_WARPS, MINB)
-k_tree_group(GroupState* __restrict__ gs, const ItemDesc* __restrict__ items) {
+k_tree_group(GroupState* __restrict__ gs, const ItemDesc* __restrict__ items,
+             cudaGraphConditionalHandle h, int use_handle) {
   extern __shared__ __align__(16) uint8_t tsm[];
   __shared__ float sdmax[TREE_WARPS][32];
   __shared__ float sdsum[TREE_WARPS][32];
@@ -586,7 +614,10 @@ k_tree_group(GroupState* __restrict__ gs, const ItemDesc* __restrict__ items) {
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int b = (blockIdx.x - it.tree_begin) * 32 + lane;
   const bool act = it.st[b] == SLOT_ACTIVE;
-  if (!__syncthreads_or(act)) return;   // the block's 32 slots are idle
+  if (!__syncthreads_or(act)) {   // the block's 32 slots are idle
+    if (threadIdx.x == 0) tree_block_done(gs, 0, h, use_handle);
+    return;
+  }
   const int Bp = it.Bp, D = it.tlevels, nb = it.nbus;
   int4* node = reinterpret_cast<int4*>(tsm);                 // bus, parent, children
   __half2* zt = reinterpret_cast<__half2*>(node + nb);       // [nb][9]
@@ -601,8 +632,35 @@ k_tree_group(GroupState* __restrict__ gs, const ItemDesc* __restrict__ items) {
   }
   __syncthreads();
   const int32_t* __restrict__ lvl = it.t_lvl;
-  float2* R = it.Rt + b;   // row j of this slot at R[j * Bp]
-  const int64_t r3 = 3 * (int64_t)Bp;
+  // row j of this slot at R[j * rs]: the residual rows in place in global
+  // memory, or (ONCHIP, small feeders) a shared-memory copy of the block's
+  // 32 slots, so that the level sweeps never leave the SM
+  float2* R;
+  int64_t rs;
+  if (ONCHIP) {
+    float2* rsm = reinterpret_cast<float2*>(tsm + tree_table_bytes(nb));
+    const int n = 3 * nb;
+    for (int j0 = warp; j0 < n; j0 += TREE_WARPS * TREE_BATCH) {
+      float2 v[TREE_BATCH];
+#pragma unroll
+      for (int u = 0; u < TREE_BATCH; ++u) {
+        const int j = j0 + u * TREE_WARPS;
+        v[u] = (act && j < n) ? it.Rt[(int64_t)j * Bp + b] : make_float2(0.f, 0.f);
+      }
+#pragma unroll
+      for (int u = 0; u < TREE_BATCH; ++u) {
+        const int j = j0 + u * TREE_WARPS;
+        if (j < n) rsm[j * 32 + lane] = v[u];
+      }
+    }
+    __syncthreads();
+    R = rsm + lane;
+    rs = 32;
+  } else {
+    R = it.Rt + b;
+    rs = Bp;
+  }
+  const int64_t r3 = 3 * rs;
   const int first = warp;   // the warp's first bus of a level
   constexpr int STRIDE = TREE_WARPS;
   for (int L = D - 2; L >= 0; --L) {
@@ -617,12 +675,12 @@ k_tree_group(GroupState* __restrict__ gs, const ItemDesc* __restrict__ items) {
           if (nd.z != nd.w) {
             const float2* own = R + nd.x * r3;
 #pragma unroll
-            for (int p = 0; p < 3; ++p) acc[u][p] = own[p * Bp];
+            for (int p = 0; p < 3; ++p) acc[u][p] = own[p * rs];
             for (int c = nd.z; c < nd.w; ++c) {
               const float2* ch = R + node[c].x * r3;
 #pragma unroll
               for (int p = 0; p < 3; ++p) {
-                const float2 x = ch[p * Bp];
+                const float2 x = ch[p * rs];
                 acc[u][p].x += x.x;
                 acc[u][p].y += x.y;
               }
@@ -638,7 +696,7 @@ k_tree_group(GroupState* __restrict__ gs, const ItemDesc* __restrict__ items) {
           if (nd.z != nd.w) {
             float2* own = R + nd.x * r3;
 #pragma unroll
-            for (int p = 0; p < 3; ++p) own[p * Bp] = acc[u][p];
+            for (int p = 0; p < 3; ++p) own[p * rs] = acc[u][p];
           }
         }
       }
@@ -658,11 +716,11 @@ k_tree_group(GroupState* __restrict__ gs, const ItemDesc* __restrict__ items) {
           const int4 nd = node[i];
           const float2* own = R + nd.x * r3;
 #pragma unroll
-          for (int p = 0; p < 3; ++p) sv[u][p] = own[p * Bp];
+          for (int p = 0; p < 3; ++p) sv[u][p] = own[p * rs];
           if (nd.y >= 0) {
             const float2* pa = R + node[nd.y].x * r3;
 #pragma unroll
-            for (int p = 0; p < 3; ++p) xp[u][p] = pa[p * Bp];
+            for (int p = 0; p < 3; ++p) xp[u][p] = pa[p * rs];
           }
         }
       }
@@ -682,7 +740,7 @@ k_tree_group(GroupState* __restrict__ gs, const ItemDesc* __restrict__ items) {
               ar = __fmaf_rn(zz.x, sv[u][q2].x, __fmaf_rn(-zz.y, sv[u][q2].y, ar));
               ai = __fmaf_rn(zz.x, sv[u][q2].y, __fmaf_rn(zz.y, sv[u][q2].x, ai));
             }
-            own[p * Bp] = make_float2(__fmaf_rn(ar, sc, xp[u][p].x), __fmaf_rn(ai, sc, xp[u][p].y));
+            own[p * rs] = make_float2(__fmaf_rn(ar, sc, xp[u][p].x), __fmaf_rn(ai, sc, xp[u][p].y));
           }
         }
       }
@@ -701,8 +759,9 @@ k_tree_group(GroupState* __restrict__ gs, const ItemDesc* __restrict__ items) {
         const int a = a0 + u * STRIDE;
 #pragma unroll
         for (int p = 0; p < 3; ++p) {
-          const int64_t g = (int64_t)(3 * (a < nb ? a : 0) + p) * Bp + b;
-          xb[u][p] = it.Rt[g];
+          const int j = 3 * (a < nb ? a : 0) + p;
+          const int64_t g = (int64_t)j * Bp + b;
+          xb[u][p] = R[j * rs];
           hb[u][p] = it.Vh[g];
           lb[u][p] = it.Vl[g];
         }
@@ -740,24 +799,28 @@ k_tree_group(GroupState* __restrict__ gs, const ItemDesc* __restrict__ items) {
   sdmax[warp][lane] = dmax;
   sdsum[warp][lane] = dsum;
   __syncthreads();
-  if (warp == 0 && act) {
-    float m = 0.f, u = 0.f;
-    for (int w = 0; w < TREE_WARPS; ++w) {
-      m = fmaxf(m, sdmax[w][lane]);
-      u += sdsum[w][lane];
-    }
-    const int sw = it.it[b] + 1;
-    it.it[b] = sw;
-    const double delta = summag ? fabs((double)u) : (double)m;
+  if (warp == 0) {
     int keep = 0;
-    if (!isfinite(delta)) {
-      it.conv[b] = 0;
-    } else if (delta <= gs->tol) {
-      it.conv[b] = 1;
-    } else if (sw < gs->max_iter) {
-      keep = 1;
+    if (act) {
+      float m = 0.f, u = 0.f;
+      for (int w = 0; w < TREE_WARPS; ++w) {
+        m = fmaxf(m, sdmax[w][lane]);
+        u += sdsum[w][lane];
+      }
+      const int sw = it.it[b] + 1;
+      it.it[b] = sw;
+      const double delta = summag ? fabs((double)u) : (double)m;
+      if (!isfinite(delta)) {
+        it.conv[b] = 0;
+      } else if (delta <= gs->tol) {
+        it.conv[b] = 1;
+      } else if (sw < gs->max_iter) {
+        keep = 1;
+      }
+      if (!keep) it.st[b] = SLOT_DONE;
     }
-    if (!keep) it.st[b] = SLOT_DONE;
+    const int still = __popc(__ballot_sync(0xffffffffu, keep));
+    if (lane == 0) tree_block_done(gs, still, h, use_handle);
   }
 }
 
@@ -1181,7 +1244,7 @@ zbus_status group_build(Group* g, const std::vector<zbus_network>& nets,
       d.tlevels = net->depth;
       d.tree_begin = tb;
       tb += d.Bp / 32;
-      g->tree_smem = std::max(g->tree_smem, tree_smem_bytes(net->nbus));
+      g->tree_smem = std::max(g->tree_smem, tree_table_bytes(net->nbus));
     } else {
       d.zinv = op.zinv;
       d.K_pad = op.K_pad;
@@ -1215,11 +1278,19 @@ zbus_status group_build(Group* g, const std::vector<zbus_network>& nets,
   g->dec_blocks = dec;
   g->tree_groups = tb;
   if (tree) {
+    // the residual rows of a block's 32 slots on chip where they fit
+    int max_nb = 0;
+    for (size_t k = 0; k < nets.size(); ++k) max_nb = std::max(max_nb, nets[k]->nbus);
+    const size_t onchip = tree_table_bytes(max_nb) + (size_t)3 * max_nb * 32 * sizeof(float2);
+    g->tree_onchip = onchip <= TREE_ONCHIP_MAX;
+    if (g->tree_onchip) g->tree_smem = onchip;
     const int smem = (int)g->tree_smem;
-    ZB_CUDA(cudaFuncSetAttribute(k_tree_group<16, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                 smem));
-    ZB_CUDA(cudaFuncSetAttribute(k_tree_group<8, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                 smem));
+    ZB_CUDA(cudaFuncSetAttribute(k_tree_group<16, 1, true>,
+                                 cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
+    ZB_CUDA(cudaFuncSetAttribute(k_tree_group<16, 1, false>,
+                                 cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
+    ZB_CUDA(cudaFuncSetAttribute(k_tree_group<8, 2, false>,
+                                 cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
   }
   g->mt_total = mt;
   g->max_tiles = tiles;
@@ -1319,19 +1390,25 @@ zbus_status group_sweep(Group* g, cudaGraphConditionalHandle h, bool use_handle,
 #undef ZB_RES
   if (ev) ZB_CUDA(cudaEventRecord(ev[1], st));
   if (tree) {
-    // step, update and stop test in one launch
-    if (g->tree_wide)
-      k_tree_group<16, 1><<<g->tree_groups, 512, g->tree_smem, st>>>(g->d_state, g->d_items);
+    // step, update, stop test and the end of the sweep in one launch
+    const int uh = use_handle ? 1 : 0;
+    if (g->tree_onchip)
+      k_tree_group<16, 1, true><<<g->tree_groups, 512, g->tree_smem, st>>>(g->d_state,
+                                                                             g->d_items, h, uh);
+    else if (g->tree_wide)
+      k_tree_group<16, 1, false><<<g->tree_groups, 512, g->tree_smem, st>>>(g->d_state,
+                                                                              g->d_items, h, uh);
     else
-      k_tree_group<8, 2><<<g->tree_groups, 256, g->tree_smem, st>>>(g->d_state, g->d_items);
+      k_tree_group<8, 2, false><<<g->tree_groups, 256, g->tree_smem, st>>>(g->d_state,
+                                                                             g->d_items, h, uh);
     if (ev) ZB_CUDA(cudaEventRecord(ev[2], st));
   } else {
     const TcVariant* var = find_variant(g->precision, g->BN, g->stages);
     var->launch(g, std::min(g->num_sms, g->max_tiles), st);
     if (ev) ZB_CUDA(cudaEventRecord(ev[2], st));
     k_decide_group<<<g->dec_blocks, DEC_THREADS, 0, st>>>(g->d_state, g->d_items);
+    k_finish_group<<<1, 1024, 0, st>>>(g->d_state, g->d_items, 0, h, use_handle ? 1 : 0);
   }
-  k_finish_group<<<1, 1024, 0, st>>>(g->d_state, g->d_items, 0, h, use_handle ? 1 : 0);
   if (ev) ZB_CUDA(cudaEventRecord(ev[3], st));
   ZB_CUDA(cudaGetLastError());
   return ZBUS_OK;

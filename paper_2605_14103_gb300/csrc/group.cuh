@@ -70,6 +70,8 @@ struct GroupState {
   int32_t res_blocks;       // residual grid size
   int32_t dec_blocks;       // stop-test grid size
   int32_t tree_groups;      // tree-sweep blocks over all items
+  int32_t tree_done;        // tree-sweep blocks finished in this sweep
+  int32_t tree_active;      // slots still active after this sweep (tree blocks' sum)
   int32_t* hist;            // profile mode: active slots of sweep k
   int32_t hist_n;
   uint64_t* tiles;          // (item << 32) | (mt << 16) | nt of every active tile
@@ -89,6 +91,7 @@ struct Group {
   int dec_blocks = 0;
   int tree_groups = 0;          // blocks of the tree sweep
   bool tree_wide = true;        // 16 warps per tree-sweep block (else 8)
+  bool tree_onchip = false;     // the block's residual rows in shared memory
   size_t tree_smem = 0;         // their dynamic shared memory (tables)
   int num_sms = 148;
   int max_n = 0;               // largest feeder's unknowns
