@@ -359,6 +359,18 @@ zbus_status zbus_solve_noalloc(zbus_network net, int64_t B,
                                double* V_out, int32_t* iters, uint8_t* converged,
                                void* cuda_stream);
 
+/*
+ * zbus_last_device_status -- the errors the device detected during the last
+ * solve on net (the error word its kernels set instead of hanging or
+ * faulting).  Synchronises cuda_stream first, so the solve must have been
+ * enqueued on it.  ZBUS_OK if the solve ran clean (or was FP64, which has no
+ * device-side waits); ZBUS_ERR_TIMEOUT if a bounded wait of the tensor-core
+ * pipeline gave up (its results are then not to be used); ZBUS_ERR_DEVICE
+ * for any other error word.  The next solve clears the word.  Project-
+ * written; the paper has no counterpart.
+ */
+zbus_status zbus_last_device_status(zbus_network net, void* cuda_stream);
+
 /* Human-readable name of a status code (static storage). */
 const char* zbus_status_string(zbus_status s);
 

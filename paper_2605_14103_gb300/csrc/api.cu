@@ -231,6 +231,8 @@ void drop_groups_of(zbus_network net) {
   for (size_t i = 0; i < g_batch_groups.size();) {
     Group* g = g_batch_groups[i];
     if (std::find(g->nets.begin(), g->nets.end(), net) != g->nets.end()) {
+      for (auto other : g->nets)
+        if (other->last_group == g) other->last_group = nullptr;
       group_free(g);
       delete g;
       g_batch_groups.erase(g_batch_groups.begin() + i);
@@ -256,6 +258,7 @@ zbus_status run_group(Group* g, const std::vector<zbus_network>& nets, const std
                       const std::vector<int32_t*>& iters, const std::vector<uint8_t*>& conv,
                       double tol, int32_t max_iter, const zbus_solve_opts& o, cudaStream_t st) {
   const double mtol = o.mismatch_tol > 0 ? o.mismatch_tol : 1e-6;
+  for (auto net : nets) net->last_group = g;
   ZB_CHECK(group_reset(g, st));
   for (size_t k = 0; k < nets.size(); ++k)
     ZB_CHECK(group_admit(g, (int)k, 0, Bs[k], V0[k], Sw[k], Sd[k], st));
@@ -301,6 +304,18 @@ void zbus_solve_opts_default(zbus_solve_opts* o) {
   o->conv_rule = ZBUS_CONV_MAXABS;
   o->mismatch_tol = 1e-6;
   o->max_correction = 8;
+}
+
+zbus_status zbus_last_device_status(zbus_network net, void* cuda_stream) {
+  g_last_error.clear();
+  if (!net) return fail(ZBUS_ERR_ARG, "network is NULL");
+  ZB_CHECK(check_device(net));
+  cudaStream_t st = (cudaStream_t)cuda_stream;
+  if (!net->last_group) {
+    ZB_CUDA(cudaStreamSynchronize(st));
+    return ZBUS_OK;
+  }
+  return group_device_status(net->last_group, st);
 }
 
 const char* zbus_status_string(zbus_status s) {
@@ -455,6 +470,7 @@ zbus_status solve_device(zbus_network net, int64_t B, const double* S_wye, const
                      {converged}, tol, max_iter, o, st);
   }
 
+  net->last_group = nullptr;   // the plain method has no device-side waits
   SolveCtx h;
   std::memset(&h, 0, sizeof(h));
   h.S_wye = (const double2*)S_wye;

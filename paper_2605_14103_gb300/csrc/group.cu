@@ -1441,6 +1441,20 @@ zbus_status group_run(Group* g, cudaStream_t st) {
   return ZBUS_OK;
 }
 
+const int32_t* group_error_word(const Group* g) { return &g->d_state->err; }
+
+zbus_status group_device_status(Group* g, cudaStream_t st) {
+  if (!g || !g->d_state) return ZBUS_OK;
+  int32_t err = 0;
+  ZB_CUDA(cudaMemcpyAsync(&err, group_error_word(g), sizeof(err), cudaMemcpyDeviceToHost, st));
+  ZB_CUDA(cudaStreamSynchronize(st));
+  if (err == 0) return ZBUS_OK;
+  if (err >= 101 && err <= 104)
+    return fail(ZBUS_ERR_TIMEOUT, "a bounded wait of the tensor-core pipeline gave up (code " +
+                                      std::to_string(err) + ")");
+  return fail(ZBUS_ERR_DEVICE, "device error word " + std::to_string(err));
+}
+
 zbus_status group_collect(Group* g, int k, int64_t s0, int64_t B, double* V_out, int32_t* iters,
                           uint8_t* converged, const double* S_wye, const double* S_delta,
                           double mtol, double* mm_out, cudaStream_t st) {

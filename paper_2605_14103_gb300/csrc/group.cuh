@@ -146,6 +146,11 @@ zbus_status group_collect(Group* g, int k, int64_t s0, int64_t B, double* V_out,
 // Shared memory of a tree-sweep block for a feeder of nbus buses: per bus
 // its node record (16 B), FP16 z block (36 B) and scale (4 B).
 inline size_t tree_smem_bytes(int nbus) { return (size_t)56 * nbus; }
+// Device error word of the group's last run (0: none; 101-104: a bounded
+// wait of the tensor-core pipeline gave up), read after synchronising st.
+zbus_status group_device_status(Group* g, cudaStream_t st);
+// Where the error word lives on the device.
+const int32_t* group_error_word(const Group* g);
 // Tile configurations the contraction is compiled for (BN, stages).
 bool tc_config_ok(int32_t precision, int BN, int stages);
 int tc_variants(int32_t precision, int* BN, int* stages, int max);

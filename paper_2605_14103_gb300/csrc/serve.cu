@@ -111,8 +111,10 @@ extern "C" zbus_status zbus_serve(const zbus_serve_config* cfg, zbus_network* po
     group_free(&g);
     return s;
   }
+  int32_t* h_err = nullptr;
   auto cleanup = [&]() {
     cudaStreamSynchronize(st);
+    cudaFreeHost(h_err);
     for (auto& f : fd) {
       cudaFree(f.warm);
       cudaFree(f.res_V);
@@ -150,6 +152,8 @@ extern "C" zbus_status zbus_serve(const zbus_serve_config* cfg, zbus_network* po
     SV_CUDA(cudaMalloc((void**)&f.res_cv, (size_t)f.cap));
     SV_CUDA(cudaMallocHost((void**)&f.h_st, (size_t)f.cap));
   }
+  SV_CUDA(cudaMallocHost((void**)&h_err, sizeof(int32_t)));
+  *h_err = 0;
   SV_CHECK(group_reset(&g, st));
   SV_CHECK(group_start(&g, cfg->tol, cfg->max_iter, cfg->conv_rule, nullptr, 0, st));
   SV_CUDA(cudaStreamSynchronize(st));
@@ -214,7 +218,10 @@ extern "C" zbus_status zbus_serve(const zbus_serve_config* cfg, zbus_network* po
       if (!fd[k].live.empty())
         SV_CUDA(cudaMemcpyAsync(fd[k].h_st, g.h_items[k].st, (size_t)fd[k].cap,
                                 cudaMemcpyDeviceToHost, st));
+    SV_CUDA(cudaMemcpyAsync(h_err, group_error_word(&g), sizeof(int32_t), cudaMemcpyDeviceToHost,
+                            st));
     SV_CUDA(cudaStreamSynchronize(st));
+    if (*h_err != 0) SV_CHECK(group_device_status(&g, st));   // a device wait gave up
     // completions
     struct Done {
       size_t k;

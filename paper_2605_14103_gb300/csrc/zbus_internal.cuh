@@ -201,6 +201,7 @@ struct zbus_network_s {
   zbus::Workspace ws;
   zbus::MixedOperands mixed[2];   // [0] FP16 row-scaled, [1] BF16 hi + lo
   struct zbus::Group* group1 = nullptr;   // single-network mixed solves
+  struct zbus::Group* last_group = nullptr;   // group of the last mixed solve (error word)
   std::vector<zbus::GraphEntry> graphs;
   cudaStream_t cap_stream = nullptr;  // private stream used only to capture graphs
   zbus::Profile prof;

@@ -88,6 +88,7 @@ _SIGS = {
                                 _P, C.POINTER(C.c_int32), C.POINTER(C.c_int32)]),
     "zbus_serve": (C.c_int, [C.POINTER(zbus_serve_config), C.POINTER(C.c_void_p), C.c_int32,
                              SOURCE_FN, SINK_FN, C.c_void_p, C.c_void_p]),
+    "zbus_last_device_status": (C.c_int, [_P, _P]),
     "zbus_status_string": (C.c_char_p, [C.c_int]),
     "zbus_last_error": (C.c_char_p, []),
 }
@@ -199,6 +200,11 @@ def zbus_solve(h, S_wye, S_delta, V_init, tol, max_iter, opts, V_out, iters, con
         C.byref(opts) if opts is not None else None,
         _dptr(V_out, "V_out", c128, (B, n), True), _dptr(iters, "iters", torch.int32, (B,), True),
         _dptr(converged, "converged", torch.uint8, (B,), True), _stream(stream)))
+
+
+def zbus_last_device_status(h, stream=None) -> int:
+    """ZBUS_OK (0), or the status of an error the device detected in the last solve."""
+    return int(lib().zbus_last_device_status(h, _stream(stream)))
 
 
 def zbus_solve_noalloc(h, S_wye, S_delta, V_init, tol, max_iter, rule, V_out, iters, converged,
@@ -447,6 +453,10 @@ class Network:
         V, it, cv = out
         zbus_solve(self.handle, S_wye, S_delta, V_init, tol, max_iter, o, V, it, cv, stream)
         return V, it, cv
+
+    def device_status(self, stream=None):
+        """Status of the device-side checks of the last solve (after a sync)."""
+        return zbus_last_device_status(self.handle, stream)
 
     def last_profile(self, max_n=1024):
         return zbus_last_profile(self.handle, max_n)

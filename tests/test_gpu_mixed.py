@@ -176,3 +176,13 @@ def test_final_mismatch_test_agrees_with_oracle(mode):
     # both sides sum in FP64 in different orders: leave out near-ties
     clear = np.abs(mm / thr - 1.0) > 1e-3
     np.testing.assert_array_equal(cv2.cpu().numpy()[clear], want[clear])
+
+
+def test_device_status_is_clean_after_solves():
+    """No bounded device wait gives up in ordinary solves of every form."""
+    f, Sw, Sd, w = F.make_workload("feeder128_b4096", B=200)
+    net = zbus.Network.from_feeder(f)
+    for mode in ("fp64", "fp16_scaled", "bf16x2", "tree"):
+        V, it, cv = net.solve(dev(Sw), dev(Sd), precision=mode)
+        assert net.device_status() == 0, mode
+        assert cv.cpu().numpy().all()
