@@ -78,8 +78,11 @@ typedef struct {
   double mismatch_tol;     /* mixed modes: a converged scenario must also have
                               max_j |v_j conj(r_j)| <= mismatch_tol (FP64);
                               <= 0 selects 1e-6 */
-  int32_t max_correction;  /* mixed modes: extra sweeps granted to scenarios
-                              that fail the mismatch test; < 0 selects 8 */
+  int32_t max_correction;  /* reserved, accepted and unused: the defect forms
+                              converge to the fixed point of the exact
+                              (double-float) residual, so no separate
+                              correction sweeps run; a scenario that fails
+                              the FP64 mismatch test keeps its flag cleared */
   int32_t profile;         /* 1: run the sweeps from the host with CUDA events
                               around every kernel on cuda_stream, for
                               zbus_last_profile; 0: device-resident loop */
