@@ -86,11 +86,17 @@ def _safe_conj_div(S: np.ndarray, V: np.ndarray) -> np.ndarray:
     return out
 
 
-def load_currents(V: np.ndarray, S_wye: np.ndarray, S_del: np.ndarray) -> np.ndarray:
+def load_currents(V: np.ndarray, S_wye: np.ndarray, S_del: np.ndarray,
+                  bus_phase: np.ndarray | None = None) -> np.ndarray:
     """Current injection i(V) of constant-power loads, [B, n] complex.
 
-    V, S_wye, S_del: [B, n] with n = 3 * (load buses); consumption convention.
+    V, S_wye, S_del: [B, n]; consumption convention.  Without bus_phase the
+    unknowns come in three-phase triples (n = 3 * load buses).  With it,
+    bus_phase[j] = 3 * bus + phase names each unknown (partial-phase feeders),
+    and see load_currents_phased.
     """
+    if bus_phase is not None:
+        return load_currents_phased(V, S_wye, S_del, bus_phase)
     B, n = V.shape
     Vb = V.reshape(B, n // 3, 3)
     i_wye = -_safe_conj_div(S_wye.reshape(B, n // 3, 3), Vb)
@@ -104,16 +110,44 @@ def load_currents(V: np.ndarray, S_wye: np.ndarray, S_del: np.ndarray) -> np.nda
     return (i_wye - drawn).reshape(B, n)
 
 
+def load_currents_phased(V: np.ndarray, S_wye: np.ndarray, S_del: np.ndarray,
+                         bus_phase: np.ndarray) -> np.ndarray:
+    """i(V) on a feeder whose buses carry any subset of the phases.
+
+    The same definitions per existing phase and branch: a wye load draws
+    conj(S_j / v_j) out of its phase; the delta entry at phase x of a bus is
+    the branch x -> y (y the next phase of a, b, c) and draws
+    I = conj(S / (v_x - v_y)) out of phase x and returns it into phase y.  A
+    delta entry whose branch lacks phase y is not a load (it must be zero).
+    """
+    bus_phase = np.asarray(bus_phase)
+    B, n = V.shape
+    where = {int(g): j for j, g in enumerate(bus_phase)}
+    drawn = _safe_conj_div(S_wye, V)
+    for j in range(n):
+        if not np.any(S_del[:, j] != 0):
+            continue
+        k, x = divmod(int(bus_phase[j]), 3)
+        m = where.get(3 * k + (x + 1) % 3)
+        if m is None:
+            raise ValueError(f"delta load at unknown {j}: branch has no second phase")
+        I = _safe_conj_div(S_del[:, j], V[:, j] - V[:, m])
+        drawn[:, j] += I
+        drawn[:, m] -= I
+    return -drawn
+
+
 # ---------------------------------------------------------------------------
 # The fixed point (Sec. II-B, eq. of the Z-bus map; stop rule and iteration cap).
 # ---------------------------------------------------------------------------
 
 def fixed_point(Z: np.ndarray, w: np.ndarray, S_wye: np.ndarray, S_del: np.ndarray,
-                tol: float, max_iter: int, rule: str = "maxabs", V0: np.ndarray | None = None):
+                tol: float, max_iter: int, rule: str = "maxabs", V0: np.ndarray | None = None,
+                bus_phase: np.ndarray | None = None):
     """Batched Z-bus fixed point.  Returns (V [B,n], iters int32[B], converged uint8[B]).
 
     Every scenario iterates independently; a scenario that has stopped is left
-    untouched while the others continue.
+    untouched while the others continue.  bus_phase: see load_currents.
     """
     S_wye = np.asarray(S_wye, dtype=np.complex128)
     S_del = np.asarray(S_del, dtype=np.complex128)
@@ -129,7 +163,7 @@ def fixed_point(Z: np.ndarray, w: np.ndarray, S_wye: np.ndarray, S_del: np.ndarr
         if active.size == 0:
             break
         Va = V[active]
-        I = load_currents(Va, S_wye[active], S_del[active])
+        I = load_currents(Va, S_wye[active], S_del[active], bus_phase)
         Vn = I @ Z.T + w                      # v^{k} = Z i(v^{k-1}) + w
         if rule == "maxabs":
             delta = np.abs(Vn - Va).max(axis=1)
@@ -147,18 +181,24 @@ def fixed_point(Z: np.ndarray, w: np.ndarray, S_wye: np.ndarray, S_del: np.ndarr
 
 
 def power_mismatch(Y_LL: np.ndarray, Y_Ls: np.ndarray, v_slack: np.ndarray,
-                   V: np.ndarray, S_wye: np.ndarray, S_del: np.ndarray) -> np.ndarray:
+                   V: np.ndarray, S_wye: np.ndarray, S_del: np.ndarray,
+                   bus_phase: np.ndarray | None = None) -> np.ndarray:
     """Per-scenario max_j |v_j conj((Y_LL v + Y_Ls v_s)_j - i_j(v))|, with Y, never Z."""
     net = V @ Y_LL.T + (Y_Ls @ v_slack)[None, :]
-    r = net - load_currents(V, S_wye, S_del)
+    r = net - load_currents(V, S_wye, S_del, bus_phase)
     return np.abs(V * np.conj(r)).max(axis=1)
 
 
 def solve_coo(n_total, row, col, val, slack_idx, v_slack, S_wye, S_del,
-              tol=1e-8, max_iter=50, rule="maxabs", V0=None):
-    """Convenience: network setup from COO, then the batched fixed point."""
+              tol=1e-8, max_iter=50, rule="maxabs", V0=None, bus_phase=None):
+    """Convenience: network setup from COO, then the batched fixed point.
+
+    bus_phase: None for three-phase triples, else [n_total] (3 * bus + phase
+    of every global index, slack included) for partial-phase feeders.
+    """
     Y = dense_from_coo(n_total, row, col, val)
-    Y_LL, Y_Ls, _ = partition(Y, slack_idx)
+    Y_LL, Y_Ls, load_idx = partition(Y, slack_idx)
     Z, w = reduced_impedance(Y_LL, Y_Ls, np.asarray(v_slack))
-    V, it, cv = fixed_point(Z, w, S_wye, S_del, tol, max_iter, rule=rule, V0=V0)
-    return dict(V=V, iters=it, converged=cv, Z=Z, w=w, Y_LL=Y_LL, Y_Ls=Y_Ls)
+    bp = None if bus_phase is None else np.asarray(bus_phase)[load_idx]
+    V, it, cv = fixed_point(Z, w, S_wye, S_del, tol, max_iter, rule=rule, V0=V0, bus_phase=bp)
+    return dict(V=V, iters=it, converged=cv, Z=Z, w=w, Y_LL=Y_LL, Y_Ls=Y_Ls, bus_phase=bp)

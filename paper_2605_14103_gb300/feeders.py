@@ -194,6 +194,124 @@ def make_scenarios(feeder: Feeder, B: int, mult_lo: float, mult_hi: float,
 
 
 # ---------------------------------------------------------------------------
+# Partial-phase feeders: single- and two-phase laterals.
+# ---------------------------------------------------------------------------
+
+@dataclasses.dataclass
+class PhasedFeeder:
+    """A radial feeder whose buses carry 1, 2 or 3 of the phases a, b, c.
+
+    Unknowns are numbered compactly: bus-major, present phases in ascending
+    order, the slack's three phases first (global indices 0, 1, 2).
+    bus_phase[g] = 3 k + p for global index g at bus k, phase p.  Loads are
+    given per present phase ([B, n] arrays, compact order); delta loads sit on
+    three-phase buses only, at the slot of the branch's first phase
+    (ab, bc, ca).
+    """
+    N: int
+    parent: np.ndarray        # int64[N]
+    phases: np.ndarray        # bool[N, 3]
+    z_line: np.ndarray        # complex128[N, 3, 3]; the present-phase sub-block is used
+    Y_row: np.ndarray         # int32[nnz], compact global indices
+    Y_col: np.ndarray
+    Y_val: np.ndarray
+    slack_idx: np.ndarray     # int32[3] = [0, 1, 2]
+    v_slack: np.ndarray       # complex128[3]
+    bus_phase: np.ndarray     # int32[n_total]
+    base_S: np.ndarray        # complex128[N-1, 3], zero on absent phases
+    is_delta: np.ndarray      # bool[N-1], three-phase buses only
+    kappa: float
+    seed: int
+
+    @property
+    def n_total(self) -> int:
+        return int(self.bus_phase.size)
+
+    @property
+    def n(self) -> int:
+        return self.n_total - 3
+
+
+def make_partial_feeder(N: int, seed: int, lateral_frac: float = 0.3,
+                        delta_frac: float = 0.0, mult_hi: float = 1.2) -> PhasedFeeder:
+    """The feeder of make_feeder(N, seed) with laterals of fewer phases.
+
+    Tree, lengths, loads and the three-phase line impedances are those of
+    make_feeder.  Then, from default_rng(seed + 7), each bus in index order
+    (parents first) keeps its parent's phases, except that with probability
+    lateral_frac a bus whose parent has two or three phases and whose subtree
+    is small (at most max(2, N / 16) buses: laterals sit at the periphery)
+    starts a lateral: a random proper subset (one or two) of the parent's
+    phases.  A line carries its downstream bus's phases with the matching
+    sub-block of the 3x3 impedance; loads sit on present phases; delta loads
+    stay on three-phase buses.
+    """
+    base = make_feeder(N, seed, delta_frac=delta_frac, mult_hi=mult_hi)
+    rng = np.random.default_rng(seed + 7)
+    size = np.ones(N, dtype=np.int64)
+    for k in range(N - 1, 0, -1):
+        size[base.parent[k]] += size[k]
+    small = max(2, N // 16)
+    phases = np.zeros((N, 3), dtype=bool)
+    phases[0] = True
+    for k in range(1, N):
+        pp = np.nonzero(phases[base.parent[k]])[0]
+        u = rng.random()
+        if pp.size >= 2 and size[k] <= small and u < lateral_frac:
+            m = int(rng.integers(1, pp.size))            # 1 .. |pp| - 1 phases
+            keep = np.sort(rng.choice(pp, size=m, replace=False))
+            phases[k, keep] = True
+        else:
+            phases[k, pp] = True
+    gidx = -np.ones((N, 3), dtype=np.int64)
+    bus_phase = []
+    for k in range(N):
+        for p in range(3):
+            if phases[k, p]:
+                gidx[k, p] = len(bus_phase)
+                bus_phase.append(3 * k + p)
+    rows, cols, vals = [], [], []
+    for k in range(1, N):
+        a = int(base.parent[k])
+        ph = np.nonzero(phases[k])[0]
+        y = np.linalg.inv(base.z_line[k][np.ix_(ph, ph)])
+        for (u, v, sgn) in ((a, a, 1.0), (k, k, 1.0), (a, k, -1.0), (k, a, -1.0)):
+            for i, p in enumerate(ph):
+                for j, q in enumerate(ph):
+                    rows.append(gidx[u, p])
+                    cols.append(gidx[v, q])
+                    vals.append(sgn * y[i, j])
+    three = phases[1:].all(axis=1)
+    return PhasedFeeder(N=N, parent=base.parent, phases=phases, z_line=base.z_line,
+                        Y_row=np.asarray(rows, dtype=np.int32),
+                        Y_col=np.asarray(cols, dtype=np.int32),
+                        Y_val=np.asarray(vals, dtype=np.complex128),
+                        slack_idx=np.array([0, 1, 2], dtype=np.int32),
+                        v_slack=V_SLACK.copy(), bus_phase=np.asarray(bus_phase, dtype=np.int32),
+                        base_S=np.where(phases[1:], base.base_S, 0.0),
+                        is_delta=base.is_delta & three, kappa=base.kappa, seed=seed)
+
+
+def make_partial_scenarios(feeder: PhasedFeeder, B: int, mult_lo: float, mult_hi: float,
+                           seed: int | None = None):
+    """(S_wye, S_delta), complex128[B, n] in the feeder's compact order.
+
+    One multiplier per (scenario, load bus) from default_rng(seed) (default
+    feeder.seed + 1), as in make_scenarios.
+    """
+    if seed is None:
+        seed = feeder.seed + 1
+    rng = np.random.default_rng(seed)
+    mult = rng.uniform(mult_lo, mult_hi, size=(B, feeder.N - 1))
+    S = mult[:, :, None] * feeder.base_S[None, :, :]          # [B, N-1, 3]
+    dmask = feeder.is_delta[None, :, None]
+    Sw = np.where(dmask, 0.0, S)
+    Sd = np.where(dmask, S, 0.0)
+    sel = feeder.phases[1:]                                    # [N-1, 3]
+    return (np.ascontiguousarray(Sw[:, sel]), np.ascontiguousarray(Sd[:, sel]))
+
+
+# ---------------------------------------------------------------------------
 # Named workloads.  Each is one feeder (or a set of feeders) plus its scenario
 # batch and solver settings.
 # ---------------------------------------------------------------------------

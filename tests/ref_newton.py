@@ -36,12 +36,44 @@ def drawn_current(v, s_wye, s_del):
     return d
 
 
-def newton_solve(Y_LL, Y_Ls, v_s, s_wye, s_del, v_start, tol=1e-13, max_iter=50):
+def drawn_current_phased(v, s_wye, s_del, bus_phase):
+    """The same load model on a feeder whose buses carry any subset of phases.
+
+    bus_phase[j] = 3 * bus + phase of unknown j.  Each bus gathers its present
+    phases into a 3-slot vector (absent slots zero) and applies the branch
+    incidence to the branches whose two phases are present.
+    """
+    d = np.zeros(v.size, dtype=np.complex128)
+    buses = {}
+    for j, g in enumerate(bus_phase):
+        buses.setdefault(int(g) // 3, {})[int(g) % 3] = j
+    for k, slots in buses.items():
+        for p, j in slots.items():
+            if s_wye[j] != 0:
+                d[j] += np.conj(s_wye[j]) / np.conj(v[j])
+        for br in range(3):
+            x, y = BRANCH_FROM[br], BRANCH_TO[br]
+            if x not in slots or s_del[slots[x]] == 0:
+                continue
+            assert y in slots, "delta branch without its second phase"
+            ib = np.conj(s_del[slots[x]]) / np.conj(v[slots[x]] - v[slots[y]])
+            for p in (x, y):
+                d[slots[p]] += INCIDENCE[p, br] * ib
+    return d
+
+
+def newton_solve(Y_LL, Y_Ls, v_s, s_wye, s_del, v_start, tol=1e-13, max_iter=50,
+                 bus_phase=None):
     n = Y_LL.shape[0]
+
+    def drawn(v):
+        if bus_phase is None:
+            return drawn_current(v, s_wye, s_del)
+        return drawn_current_phased(v, s_wye, s_del, bus_phase)
 
     def F(x):
         v = x[:n] + 1j * x[n:]
-        g = Y_LL @ v + Y_Ls @ v_s + drawn_current(v, s_wye, s_del)
+        g = Y_LL @ v + Y_Ls @ v_s + drawn(v)
         return np.concatenate([g.real, g.imag])
 
     x = np.concatenate([v_start.real, v_start.imag]).astype(float)
