@@ -120,6 +120,32 @@ zbus_status zbus_network_create(int32_t n_total, int64_t nnz,
                                 const double* v_slack_reim,
                                 void* cuda_stream, zbus_network* out);
 
+/*
+ * zbus_network_create_phased -- zbus_network_create for a feeder whose buses
+ * carry any subset of the phases (single- and two-phase laterals).
+ *
+ *   bus_phase  host int32[n_total]: 3 * bus + phase (phase 0, 1, 2 = a, b, c)
+ *              of every global index; the slack is bus 0 and bus_phase of
+ *              slack_idx[p] must be p; every value at most once.
+ *
+ * The other arguments are those of zbus_network_create.  The device solves
+ * the network padded to three phase slots per bus, an absent phase an
+ * isolated node with a unit self-admittance (its voltage stays 0): the fixed
+ * point of Sec. II-B on the present phases.  Every array of zbus_solve and
+ * zbus_power_mismatch is then [B][n] over the present non-slack phases in
+ * ascending global index (n = zbus_network_size); zbus_network_get_z gives Z
+ * and w on those unknowns.  A delta entry sits at the branch's first phase
+ * (ab, bc, ca) and is a load only where the branch's second phase is present
+ * (other entries are ignored).  zbus_solve_batched, zbus_serve,
+ * zbus_autotune and zbus_solve_noalloc return ZBUS_ERR_UNSUPPORTED for such
+ * a network.  Returns ZBUS_ERR_ARG for a map that breaks these rules.
+ */
+zbus_status zbus_network_create_phased(int32_t n_total, int64_t nnz,
+                                       const int32_t* row, const int32_t* col,
+                                       const double* val_reim, const int32_t* slack_idx,
+                                       const double* v_slack_reim, const int32_t* bus_phase,
+                                       void* cuda_stream, zbus_network* out);
+
 /* Release a network and every device buffer it owns.  NULL is ignored.  The
  * caller must make sure no work of this handle is still running. */
 void zbus_network_destroy(zbus_network net);
@@ -177,7 +203,7 @@ zbus_status zbus_network_reserve(zbus_network net, int64_t B, int32_t precision)
  * r) followed by a forward sweep (path sums of branch impedances times those
  * sums); the defect residual stays exact (shunts included), so the fixed
  * point is that of the other forms.  Returns ZBUS_ERR_UNSUPPORTED for a meshed
- * or non-reciprocal network, or one above 3657 buses.
+ * or non-reciprocal network, or one above 3592 buses.
  */
 zbus_status zbus_solve(zbus_network net, int64_t B,
                        const double* S_wye, const double* S_delta,

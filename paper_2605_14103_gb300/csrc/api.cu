@@ -379,6 +379,44 @@ zbus_status zbus_network_create(int32_t n_total, int64_t nnz, const int32_t* row
   return ZBUS_OK;
 }
 
+zbus_status zbus_network_create_phased(int32_t n_total, int64_t nnz, const int32_t* row,
+                                       const int32_t* col, const double* val_reim,
+                                       const int32_t* slack_idx, const double* v_slack_reim,
+                                       const int32_t* bus_phase, void* cuda_stream,
+                                       zbus_network* out) {
+  g_last_error.clear();
+  if (!out) return fail(ZBUS_ERR_ARG, "out is NULL");
+  *out = nullptr;
+  if (n_total < 4) return fail(ZBUS_ERR_ARG, "n_total must be >= 4 (three slack phases + 1)");
+  if (nnz < 1) return fail(ZBUS_ERR_ARG, "nnz must be >= 1");
+  if (!row || !col || !val_reim || !slack_idx || !v_slack_reim)
+    return fail(ZBUS_ERR_ARG, "a required host array is NULL");
+  for (int p = 0; p < 3; ++p)
+    if (slack_idx[p] < 0 || slack_idx[p] >= n_total)
+      return fail(ZBUS_ERR_ARG, "slack index out of range");
+  for (int64_t t = 0; t < nnz; ++t)
+    if (row[t] < 0 || row[t] >= n_total || col[t] < 0 || col[t] >= n_total)
+      return fail(ZBUS_ERR_ARG, "COO index out of range at entry " + std::to_string(t));
+  int32_t n_bus = 0;
+  ZB_CHECK(phased_validate(n_total, slack_idx, bus_phase, &n_bus));
+  std::vector<int32_t> r2, c2;
+  std::vector<double> v2;
+  phased_pad_coo(n_total, nnz, row, col, val_reim, bus_phase, n_bus, r2, c2, v2);
+  const int32_t slack3[3] = {0, 1, 2};
+  zbus_network net = nullptr;
+  ZB_CHECK(zbus_network_create(3 * n_bus, (int64_t)r2.size(), r2.data(), c2.data(), v2.data(),
+                               slack3, v_slack_reim, cuda_stream, &net));
+  zbus_status s = phased_attach(net, n_total, slack_idx, bus_phase, (cudaStream_t)cuda_stream);
+  if (s != ZBUS_OK) {
+    std::string msg = g_last_error;
+    zbus_network_destroy(net);
+    g_last_error = msg;
+    return s;
+  }
+  *out = net;
+  return ZBUS_OK;
+}
+
 void zbus_network_destroy(zbus_network net) {
   if (!net) return;
   drop_graphs(net);
@@ -403,6 +441,7 @@ void zbus_network_destroy(zbus_network net) {
   cudaFree(net->prof.d_hist);
   cudaFree(net->ws.base);
   free_mixed(net);
+  phased_free(net);
   cudaFree(net->Z);
   cudaFree(net->w);
   cudaFree(net->ys);
@@ -417,18 +456,26 @@ void zbus_network_destroy(zbus_network net) {
   cudaFree(net->bsr_val);
   cudaFree(net->t_node);
   cudaFree(net->t_lvl);
+  cudaFree(net->t_mask);
   cudaFree(net->t_z);
   cudaFree(net->t_zs);
   delete net;
 }
 
-int32_t zbus_network_size(zbus_network net) { return net ? net->n : -1; }
+int32_t zbus_network_size(zbus_network net) {
+  return net ? (net->phased ? net->n_user : net->n) : -1;
+}
 
 zbus_status zbus_network_get_z(zbus_network net, double* Z_out, double* w_out, void* cuda_stream) {
   g_last_error.clear();
   if (!net) return fail(ZBUS_ERR_ARG, "network is NULL");
   ZB_CHECK(check_device(net));
   cudaStream_t st = (cudaStream_t)cuda_stream;
+  if (net->phased) {   // the caller's unknowns only
+    if (Z_out) ZB_CHECK(phased_z(net, Z_out, st));
+    if (w_out) ZB_CHECK(phased_out(net, 1, (const double*)net->w, w_out, st));
+    return ZBUS_OK;
+  }
   if (Z_out)
     ZB_CUDA(cudaMemcpyAsync(Z_out, net->Z, (size_t)net->n * net->n * sizeof(double2),
                             cudaMemcpyDeviceToDevice, st));
@@ -516,6 +563,26 @@ zbus_status solve_device(zbus_network net, int64_t B, const double* S_wye, const
 }
 
 
+// The solve on device buffers in the caller's layout: for a partial-phase
+// network the arrays move into the padded layout and the voltages back.
+zbus_status solve_device_user(zbus_network net, int64_t B, const double* S_wye,
+                              const double* S_delta, const double* V_init, double tol,
+                              int32_t max_iter, const zbus_solve_opts& o, double* V_out,
+                              int32_t* iters, uint8_t* converged, cudaStream_t st) {
+  if (!net->phased)
+    return solve_device(net, B, S_wye, S_delta, V_init, tol, max_iter, o, V_out, iters,
+                        converged, st);
+  double* buf[4];
+  ZB_CHECK(phased_stage(net, B, buf));
+  if (S_wye) ZB_CHECK(phased_in(net, B, S_wye, buf[0], false, st));
+  if (S_delta) ZB_CHECK(phased_in(net, B, S_delta, buf[1], true, st));
+  if (V_init) ZB_CHECK(phased_in(net, B, V_init, buf[2], false, st));
+  ZB_CHECK(solve_device(net, B, S_wye ? buf[0] : nullptr, S_delta ? buf[1] : nullptr,
+                        V_init ? buf[2] : nullptr, tol, max_iter, o, buf[3], iters, converged,
+                        st));
+  return phased_out(net, B, buf[3], V_out, st);
+}
+
 // Where a caller buffer lives: 1 device (or managed) memory, 0 host memory
 // (pinned or pageable), -1 null.
 int buffer_kind(const void* p) {
@@ -569,7 +636,7 @@ zbus_status solve_host(zbus_network net, int64_t B, const double* S_wye, const d
   ZB_CHECK(ensure_stage(net, C));
   ZB_CHECK(ensure_workspace(net, C));
   HostStage& h = net->stage;
-  const size_t n2 = (size_t)net->n * 2;           // doubles per scenario
+  const size_t n2 = (size_t)(net->phased ? net->n_user : net->n) * 2;   // doubles per scenario
   const size_t vec = (size_t)h.cap * n2;
   ZB_CUDA(cudaEventRecord(h.start, st));
   ZB_CUDA(cudaStreamWaitEvent(h.h2d, h.start, 0));
@@ -596,8 +663,8 @@ zbus_status solve_host(zbus_network net, int64_t B, const double* S_wye, const d
       ZB_CUDA(cudaMemcpyAsync(v0, V_init + b0 * n2, bytes, cudaMemcpyHostToDevice, h.h2d));
     ZB_CUDA(cudaEventRecord(h.in[s], h.h2d));
     ZB_CUDA(cudaStreamWaitEvent(st, h.in[s], 0));
-    ZB_CHECK(solve_device(net, Bk, S_wye ? sw : nullptr, S_delta ? sd : nullptr,
-                          V_init ? v0 : nullptr, tol, max_iter, o, vo, it, cv, st));
+    ZB_CHECK(solve_device_user(net, Bk, S_wye ? sw : nullptr, S_delta ? sd : nullptr,
+                               V_init ? v0 : nullptr, tol, max_iter, o, vo, it, cv, st));
     ZB_CUDA(cudaEventRecord(h.done[s], st));
     ZB_CUDA(cudaStreamWaitEvent(h.d2h, h.done[s], 0));
     ZB_CUDA(cudaMemcpyAsync(V_out + b0 * n2, vo, bytes, cudaMemcpyDeviceToHost, h.d2h));
@@ -651,8 +718,8 @@ zbus_status zbus_solve(zbus_network net, int64_t B, const double* S_wye, const d
     return solve_host(net, B, S_wye, S_delta, V_init, tol, max_iter, o, V_out, iters, converged,
                       st);
   }
-  return solve_device(net, B, S_wye, S_delta, V_init, tol, max_iter, o, V_out, iters, converged,
-                      st);
+  return solve_device_user(net, B, S_wye, S_delta, V_init, tol, max_iter, o, V_out, iters,
+                           converged, st);
 }
 
 zbus_status zbus_solve_batched(const zbus_batch_item* items, int32_t n_items, double tol,
@@ -685,6 +752,9 @@ zbus_status zbus_solve_batched(const zbus_batch_item* items, int32_t n_items, do
       return fail(ZBUS_ERR_ARG, "item " + std::to_string(k) + ": an output pointer is NULL");
     if (x.S_delta && !x.net->bus_aligned)
       return fail(ZBUS_ERR_ARG, "delta loads need three unknowns per bus (n % 3 == 0)");
+    if (x.net->phased)
+      return fail(ZBUS_ERR_UNSUPPORTED, "batched solves take three-phase networks; solve a "
+                                        "partial-phase network with zbus_solve");
     ZB_CHECK(check_device(x.net));
     if (x.B == 0) continue;
     nets.push_back(x.net);
@@ -752,9 +822,19 @@ zbus_status zbus_power_mismatch(zbus_network net, int64_t B, const double* V,
   if (S_delta && !net->bus_aligned)
     return fail(ZBUS_ERR_ARG, "delta loads need three unknowns per bus (n % 3 == 0)");
   ZB_CHECK(check_device(net));
+  cudaStream_t st = (cudaStream_t)cuda_stream;
+  if (net->phased) {   // into the padded layout first
+    double* buf[4];
+    ZB_CHECK(phased_stage(net, B, buf));
+    ZB_CHECK(phased_in(net, B, V, buf[3], false, st));
+    if (S_wye) ZB_CHECK(phased_in(net, B, S_wye, buf[0], false, st));
+    if (S_delta) ZB_CHECK(phased_in(net, B, S_delta, buf[1], true, st));
+    V = buf[3];
+    S_wye = S_wye ? buf[0] : nullptr;
+    S_delta = S_delta ? buf[1] : nullptr;
+  }
   launch_mismatch((const double2*)V, (const double2*)S_wye, (const double2*)S_delta,
-                  net->csr_ptr, net->csr_col, net->csr_val, net->ys, net->n, (int)B, out,
-                  (cudaStream_t)cuda_stream);
+                  net->csr_ptr, net->csr_col, net->csr_val, net->ys, net->n, (int)B, out, st);
   ZB_CUDA(cudaGetLastError());
   return ZBUS_OK;
 }

@@ -37,10 +37,7 @@ constexpr int RES_FP16 = 0, RES_BF16 = 1, RES_F32 = 2;
 constexpr int TREE_BATCH = 4;   // buses whose state a tree-sweep warp loads at once
 constexpr size_t TREE_ONCHIP_MAX = 200 * 1024;   // shared memory of an on-chip tree block
 
-// Shared memory of the position tables of a tree-sweep block, padded to 16 B.
-__host__ __device__ inline size_t tree_table_bytes(int nbus) {
-  return ((size_t)56 * nbus + 15) & ~(size_t)15;
-}
+
 // Item owning global index x, for a non-decreasing begin field.
 __device__ __forceinline__ int find_item(const ItemDesc* items, int n_items, int x, int which) {
   int lo = 0, hi = n_items - 1;
@@ -622,9 +619,11 @@ k_tree_group(GroupState* __restrict__ gs, const ItemDesc* __restrict__ items,
   int4* node = reinterpret_cast<int4*>(tsm);                 // bus, parent, children
   __half2* zt = reinterpret_cast<__half2*>(node + nb);       // [nb][9]
   float* zst = reinterpret_cast<float*>(zt + 9 * nb);        // [nb]
+  uint8_t* pmask = reinterpret_cast<uint8_t*>(zst + nb);     // [nb] phases of the parent line
   for (int i = threadIdx.x; i < nb; i += blockDim.x) {
     node[i] = it.t_node[i];
     zst[i] = it.t_zs[i];
+    pmask[i] = it.t_mask[i];
   }
   for (int i = threadIdx.x; i < 9 * nb; i += blockDim.x) {
     const float2 z = it.t_z[i];
@@ -678,11 +677,14 @@ k_tree_group(GroupState* __restrict__ gs, const ItemDesc* __restrict__ items,
             for (int p = 0; p < 3; ++p) acc[u][p] = own[p * rs];
             for (int c = nd.z; c < nd.w; ++c) {
               const float2* ch = R + node[c].x * r3;
+              const int cm = pmask[c];   // a phase the child's line lacks stays below
 #pragma unroll
               for (int p = 0; p < 3; ++p) {
                 const float2 x = ch[p * rs];
-                acc[u][p].x += x.x;
-                acc[u][p].y += x.y;
+                if ((cm >> p) & 1) {
+                  acc[u][p].x += x.x;
+                  acc[u][p].y += x.y;
+                }
               }
             }
           }
@@ -719,8 +721,10 @@ k_tree_group(GroupState* __restrict__ gs, const ItemDesc* __restrict__ items,
           for (int p = 0; p < 3; ++p) sv[u][p] = own[p * rs];
           if (nd.y >= 0) {
             const float2* pa = R + node[nd.y].x * r3;
+            const int cm = pmask[i];   // the parent's drop reaches the phases the line carries
 #pragma unroll
-            for (int p = 0; p < 3; ++p) xp[u][p] = pa[p * rs];
+            for (int p = 0; p < 3; ++p)
+              if ((cm >> p) & 1) xp[u][p] = pa[p * rs];
           }
         }
       }
@@ -1241,6 +1245,7 @@ zbus_status group_build(Group* g, const std::vector<zbus_network>& nets,
       d.t_zs = net->t_zs;
       d.Rt = reinterpret_cast<float2*>(ws.Iop);
       d.t_lvl = net->t_lvl;
+      d.t_mask = net->t_mask;
       d.tlevels = net->depth;
       d.tree_begin = tb;
       tb += d.Bp / 32;

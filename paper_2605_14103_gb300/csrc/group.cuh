@@ -44,6 +44,7 @@ struct ItemDesc {
   // tree sweep (ZBUS_TREE_SWEEP): radial structure and FP32 residual
   const int4* t_node;       // [nbus] per breadth-first position: bus, parent, children range
   const int32_t* t_lvl;     // [tlevels + 1] level ranges of positions
+  const uint8_t* t_mask;    // [nbus] phases of each position's parent line
   const float2* t_z;        // [nbus][9] scaled parent-branch impedances
   const float* t_zs;        // [nbus] their scales
   float2* Rt;               // [n][Bp] FP32 residual, scenario-minor
@@ -143,9 +144,12 @@ zbus_status group_run(Group* g, cudaStream_t st);
 zbus_status group_collect(Group* g, int k, int64_t s0, int64_t B, double* V_out, int32_t* iters,
                           uint8_t* converged, const double* S_wye, const double* S_delta,
                           double mtol, double* mm_out, cudaStream_t st);
-// Shared memory of a tree-sweep block for a feeder of nbus buses: per bus
-// its node record (16 B), FP16 z block (36 B) and scale (4 B).
-inline size_t tree_smem_bytes(int nbus) { return (size_t)56 * nbus; }
+// Shared memory of the position tables of a tree-sweep block for a feeder of
+// nbus buses: per bus its node record (16 B), FP16 z block (36 B), scale
+// (4 B) and parent-line phase mask (1 B), padded to 16 B.
+__host__ __device__ inline size_t tree_table_bytes(int nbus) {
+  return ((size_t)57 * nbus + 15) & ~(size_t)15;
+}
 // Device error word of the group's last run (0: none; 101-104: a bounded
 // wait of the tensor-core pipeline gave up), read after synchronising st.
 zbus_status group_device_status(Group* g, cudaStream_t st);

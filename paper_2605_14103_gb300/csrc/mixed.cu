@@ -148,8 +148,8 @@ zbus_status prepare_tree(zbus_network net, cudaStream_t st) {
     return fail(ZBUS_ERR_UNSUPPORTED,
                 "the tree sweep needs a radial feeder (buses form a tree hanging off the slack, "
                 "reciprocal invertible branch blocks)");
-  if (tree_smem_bytes(net->nbus) > (size_t)200 * 1024)
-    return fail(ZBUS_ERR_UNSUPPORTED, "the tree sweep supports up to 3657 buses");
+  if (tree_table_bytes(net->nbus) > (size_t)200 * 1024)
+    return fail(ZBUS_ERR_UNSUPPORTED, "the tree sweep supports up to 3592 buses");
   ZB_CHECK(prepare_df(net, st));
   ZB_CUDA(cudaStreamSynchronize(st));
   return ZBUS_OK;

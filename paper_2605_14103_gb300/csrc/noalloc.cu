@@ -65,6 +65,8 @@ extern "C" zbus_status zbus_solve_noalloc(zbus_network net, int64_t B, const dou
   if (max_iter < 1) return fail(ZBUS_ERR_ARG, "max_iter must be >= 1");
   if (conv_rule != ZBUS_CONV_MAXABS && conv_rule != ZBUS_CONV_SUMMAG)
     return fail(ZBUS_ERR_ARG, "unknown convergence rule");
+  if (net->phased)
+    return fail(ZBUS_ERR_UNSUPPORTED, "the allocation-free solve takes three-phase networks");
   if (B == 0) return ZBUS_OK;
   if (!V_out || !iters || !converged) return fail(ZBUS_ERR_ARG, "an output pointer is NULL");
   if (S_delta && !net->bus_aligned)

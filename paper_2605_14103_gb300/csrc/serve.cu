@@ -73,6 +73,8 @@ extern "C" zbus_status zbus_serve(const zbus_serve_config* cfg, zbus_network* po
   std::vector<zbus_network> nets(pool, pool + n_pool);
   for (int k = 0; k < n_pool; ++k) {
     if (!nets[k]) return fail(ZBUS_ERR_ARG, "pool network is NULL");
+    if (nets[k]->phased)
+      return fail(ZBUS_ERR_UNSUPPORTED, "the serving pool takes three-phase networks");
     for (int j = 0; j < k; ++j)
       if (nets[j] == nets[k]) return fail(ZBUS_ERR_ARG, "a network may appear once in the pool");
   }

@@ -177,34 +177,48 @@ zbus_status upload(T** dst, const std::vector<T>& src, cudaStream_t st) {
   return ZBUS_OK;
 }
 
-// Inverse of a 3x3 complex matrix (row-major) by Gauss-Jordan elimination
-// with partial pivoting; false when a pivot vanishes.
+// Inverse of a 3x3 complex matrix (row-major) on the phases its entries
+// touch (a line of fewer phases has zero rows and columns for the others,
+// which stay zero in the result), by Gauss-Jordan elimination with partial
+// pivoting; false when a pivot vanishes or no phase is touched.
 bool inv3(const double2* a, double2* out) {
-  std::complex<double> m[3][6];
-  for (int i = 0; i < 3; ++i)
-    for (int j = 0; j < 3; ++j) {
-      m[i][j] = {a[3 * i + j].x, a[3 * i + j].y};
-      m[i][3 + j] = i == j ? 1.0 : 0.0;
+  int ph[3], m = 0;
+  for (int p = 0; p < 3; ++p) {
+    bool any = false;
+    for (int q = 0; q < 3; ++q)
+      any = any || a[3 * p + q].x != 0.0 || a[3 * p + q].y != 0.0 || a[3 * q + p].x != 0.0 ||
+            a[3 * q + p].y != 0.0;
+    if (any) ph[m++] = p;
+  }
+  if (m == 0) return false;
+  std::complex<double> g[3][6];
+  for (int i = 0; i < m; ++i)
+    for (int j = 0; j < m; ++j) {
+      const double2 x = a[3 * ph[i] + ph[j]];
+      g[i][j] = {x.x, x.y};
+      g[i][m + j] = i == j ? 1.0 : 0.0;
     }
   double scale = 0.0;
   for (int e = 0; e < 9; ++e) scale = std::max(scale, std::hypot(a[e].x, a[e].y));
-  for (int k = 0; k < 3; ++k) {
+  for (int k = 0; k < m; ++k) {
     int piv = k;
-    for (int i = k + 1; i < 3; ++i)
-      if (std::abs(m[i][k]) > std::abs(m[piv][k])) piv = i;
-    if (!(std::abs(m[piv][k]) > 1e-13 * scale)) return false;
+    for (int i = k + 1; i < m; ++i)
+      if (std::abs(g[i][k]) > std::abs(g[piv][k])) piv = i;
+    if (!(std::abs(g[piv][k]) > 1e-13 * scale)) return false;
     if (piv != k)
-      for (int j = 0; j < 6; ++j) std::swap(m[k][j], m[piv][j]);
-    const std::complex<double> d = 1.0 / m[k][k];
-    for (int j = 0; j < 6; ++j) m[k][j] *= d;
-    for (int i = 0; i < 3; ++i) {
+      for (int j = 0; j < 2 * m; ++j) std::swap(g[k][j], g[piv][j]);
+    const std::complex<double> d = 1.0 / g[k][k];
+    for (int j = 0; j < 2 * m; ++j) g[k][j] *= d;
+    for (int i = 0; i < m; ++i) {
       if (i == k) continue;
-      const std::complex<double> f = m[i][k];
-      for (int j = 0; j < 6; ++j) m[i][j] -= f * m[k][j];
+      const std::complex<double> f = g[i][k];
+      for (int j = 0; j < 2 * m; ++j) g[i][j] -= f * g[k][j];
     }
   }
-  for (int i = 0; i < 3; ++i)
-    for (int j = 0; j < 3; ++j) out[3 * i + j] = make_double2(m[i][3 + j].real(), m[i][3 + j].imag());
+  for (int e = 0; e < 9; ++e) out[e] = make_double2(0.0, 0.0);
+  for (int i = 0; i < m; ++i)
+    for (int j = 0; j < m; ++j)
+      out[3 * ph[i] + ph[j]] = make_double2(g[i][m + j].real(), g[i][m + j].imag());
   return true;
 }
 
@@ -260,6 +274,7 @@ zbus_status build_tree(zbus_network net, const std::vector<int32_t>& bp,
   std::vector<int4> node(nb);        // per breadth-first position
   std::vector<float2> z((size_t)nb * 9);
   std::vector<float> zs(nb);
+  std::vector<uint8_t> mask(nb);     // phases the parent line carries
   int next = (int)roots.size();
   for (int i = 0; i < nb; ++i) {
     const int c = queue[i], p = par[c];
@@ -286,6 +301,11 @@ zbus_status build_tree(zbus_network net, const std::vector<int32_t>& bp,
     for (int e = 0; e < 9; ++e)
       y[e] = make_double2(-bv[(size_t)t * 9 + e].x, -bv[(size_t)t * 9 + e].y);
     if (!inv3(y, zi)) return ZBUS_OK;
+    uint8_t mk = 0;
+    for (int p = 0; p < 3; ++p)
+      for (int q = 0; q < 3; ++q)
+        if (y[3 * p + q].x != 0.0 || y[3 * p + q].y != 0.0) mk |= (uint8_t)((1 << p) | (1 << q));
+    mask[i] = mk;
     double m = 0.0;
     for (int e = 0; e < 9; ++e) m = std::max(m, std::max(std::fabs(zi[e].x), std::fabs(zi[e].y)));
     if (!(m > 0.0) || !std::isfinite(m)) return ZBUS_OK;
@@ -296,6 +316,7 @@ zbus_status build_tree(zbus_network net, const std::vector<int32_t>& bp,
           make_float2((float)std::ldexp(zi[e].x, -ex), (float)std::ldexp(zi[e].y, -ex));
   }
   ZB_CHECK(upload(&net->t_lvl, lvl, st));
+  ZB_CHECK(upload(&net->t_mask, mask, st));
   ZB_CHECK(upload(&net->t_node, node, st));
   ZB_CHECK(upload(&net->t_z, z, st));
   ZB_CHECK(upload(&net->t_zs, zs, st));

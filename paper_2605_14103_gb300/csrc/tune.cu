@@ -137,6 +137,8 @@ extern "C" zbus_status zbus_autotune(const zbus_batch_item* items, int32_t n_ite
   int64_t total_B = 0;
   for (int32_t k = 0; k < n_items; ++k) {
     if (!items[k].net) return fail(ZBUS_ERR_ARG, "network is NULL");
+    if (items[k].net->phased)
+      return fail(ZBUS_ERR_UNSUPPORTED, "the autotuner takes three-phase networks");
     max_n = std::max(max_n, items[k].net->n);
     total_B += items[k].B;
   }

@@ -196,6 +196,7 @@ struct zbus_network_s {
   int4* t_node = nullptr;       // [nbus] per position: bus, parent position (-1: slack),
                                 //        first child position, end of the children
   int32_t* t_lvl = nullptr;     // [depth + 1] first position of each level
+  uint8_t* t_mask = nullptr;    // [nbus] phases (bits 0..2) of each position's parent line
   float2* t_z = nullptr;        // [nbus][9] z = y^{-1} of the parent branch, scaled by 2^-e
   float* t_zs = nullptr;        // [nbus] 2^e
   zbus::Workspace ws;
@@ -206,6 +207,14 @@ struct zbus_network_s {
   cudaStream_t cap_stream = nullptr;  // private stream used only to capture graphs
   zbus::Profile prof;
   zbus::HostStage stage;
+  // partial-phase networks: the caller's unknowns (present phases, ascending
+  // global index) inside the padded three-phase network solved on the device
+  bool phased = false;
+  int n_user = 0;                 // the caller's unknowns
+  int32_t* ph_map = nullptr;      // [n_user] padded unknown of each caller unknown
+  uint8_t* ph_dvalid = nullptr;   // [n_user] 1 where its delta branch has both phases
+  double* ph_buf = nullptr;       // four padded [ph_cap][n] complex staging arrays
+  int64_t ph_cap = 0;
 };
 
 namespace zbus {
@@ -231,6 +240,23 @@ void launch_mismatch(const double2* V, const double2* S_wye, const double2* S_de
 
 // api.cu
 zbus_status ensure_workspace(zbus_network net, int64_t B);
+
+// phased.cu
+zbus_status phased_validate(int32_t n_total, const int32_t* slack_idx, const int32_t* bus_phase,
+                            int32_t* n_bus);
+void phased_pad_coo(int32_t n_total, int64_t nnz, const int32_t* row, const int32_t* col,
+                    const double* val, const int32_t* bus_phase, int32_t n_bus,
+                    std::vector<int32_t>& r2, std::vector<int32_t>& c2, std::vector<double>& v2);
+zbus_status phased_attach(zbus_network net, int32_t n_total, const int32_t* slack_idx,
+                          const int32_t* bus_phase, cudaStream_t st);
+// staging: bufs[0..3] = padded [B][n] arrays (wye, delta, warm start, voltages)
+zbus_status phased_stage(zbus_network net, int64_t B, double** bufs);
+zbus_status phased_in(zbus_network net, int64_t B, const double* src, double* dst, bool delta,
+                      cudaStream_t st);
+zbus_status phased_out(zbus_network net, int64_t B, const double* src, double* dst,
+                       cudaStream_t st);
+zbus_status phased_z(zbus_network net, double* Z_out, cudaStream_t st);
+void phased_free(zbus_network net);
 
 // group.cu
 

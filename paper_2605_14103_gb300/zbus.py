@@ -71,6 +71,8 @@ _SIGS = {
     "zbus_solve_opts_default": (None, [C.POINTER(zbus_solve_opts)]),
     "zbus_network_create": (C.c_int, [C.c_int32, C.c_int64, _P, _P, _P, _P, _P, _P,
                                       C.POINTER(_P)]),
+    "zbus_network_create_phased": (C.c_int, [C.c_int32, C.c_int64, _P, _P, _P, _P, _P, _P, _P,
+                                             C.POINTER(_P)]),
     "zbus_network_destroy": (None, [_P]),
     "zbus_network_size": (C.c_int32, [_P]),
     "zbus_network_get_z": (C.c_int, [_P, _P, _P, _P]),
@@ -148,8 +150,11 @@ def zbus_solve_opts_default() -> zbus_solve_opts:
     return o
 
 
-def zbus_network_create(n_total, row, col, val, slack_idx, v_slack, stream=None) -> int:
-    """Host COO (numpy) -> network handle (an integer)."""
+def zbus_network_create(n_total, row, col, val, slack_idx, v_slack, stream=None,
+                        bus_phase=None) -> int:
+    """Host COO (numpy) -> network handle (an integer).  With bus_phase
+    (int32[n_total], 3 * bus + phase of every global index) the network may
+    have partial-phase buses (zbus_network_create_phased)."""
     row = np.ascontiguousarray(row, dtype=np.int32)
     col = np.ascontiguousarray(col, dtype=np.int32)
     val = np.ascontiguousarray(val, dtype=np.complex128)
@@ -158,9 +163,18 @@ def zbus_network_create(n_total, row, col, val, slack_idx, v_slack, stream=None)
     if not (row.shape == col.shape == val.shape) or sl.shape != (3,) or vs.shape != (3,):
         raise ValueError("row/col/val must have equal length; slack_idx and v_slack 3 entries")
     h = _P()
-    _check(lib().zbus_network_create(int(n_total), int(row.size), row.ctypes.data,
-                                     col.ctypes.data, val.ctypes.data, sl.ctypes.data,
-                                     vs.ctypes.data, _stream(stream), C.byref(h)))
+    if bus_phase is None:
+        _check(lib().zbus_network_create(int(n_total), int(row.size), row.ctypes.data,
+                                         col.ctypes.data, val.ctypes.data, sl.ctypes.data,
+                                         vs.ctypes.data, _stream(stream), C.byref(h)))
+    else:
+        bp = np.ascontiguousarray(bus_phase, dtype=np.int32)
+        if bp.shape != (int(n_total),):
+            raise ValueError("bus_phase must have n_total entries")
+        _check(lib().zbus_network_create_phased(int(n_total), int(row.size), row.ctypes.data,
+                                                col.ctypes.data, val.ctypes.data,
+                                                sl.ctypes.data, vs.ctypes.data, bp.ctypes.data,
+                                                _stream(stream), C.byref(h)))
     return h.value
 
 
@@ -402,13 +416,15 @@ def zbus_last_error() -> str:
 class Network:
     """One feeder's Z-bus data on the current CUDA device."""
 
-    def __init__(self, n_total, row, col, val, slack_idx, v_slack, stream=None):
-        self.handle = zbus_network_create(n_total, row, col, val, slack_idx, v_slack, stream)
+    def __init__(self, n_total, row, col, val, slack_idx, v_slack, stream=None, bus_phase=None):
+        self.handle = zbus_network_create(n_total, row, col, val, slack_idx, v_slack, stream,
+                                          bus_phase)
         self.n = zbus_network_size(self.handle)
 
     @classmethod
     def from_feeder(cls, f, stream=None):
-        return cls(f.n_total, f.Y_row, f.Y_col, f.Y_val, f.slack_idx, f.v_slack, stream)
+        return cls(f.n_total, f.Y_row, f.Y_col, f.Y_val, f.slack_idx, f.v_slack, stream,
+                   getattr(f, "bus_phase", None))
 
     def close(self):
         if self.handle:

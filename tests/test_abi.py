@@ -8,6 +8,7 @@ import numpy as np
 import pytest
 
 from paper_2605_14103_gb300 import build as B
+from paper_2605_14103_gb300 import feeders as F
 from paper_2605_14103_gb300 import zbus
 
 ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
@@ -89,3 +90,38 @@ def test_solve_rejects_null_network(lib):
     assert "NULL" in zbus.zbus_last_error()
     assert lib.zbus_network_size(None) == -1
     lib.zbus_network_destroy(None)   # ignored
+
+
+def test_create_phased_rejects_bad_maps(lib):
+    f = F.make_partial_feeder(12, 5, lateral_frac=1.0)
+    row = np.ascontiguousarray(f.Y_row, np.int32)
+    col = np.ascontiguousarray(f.Y_col, np.int32)
+    val = np.ascontiguousarray(f.Y_val, np.complex128)
+    sl = np.array([0, 1, 2], np.int32)
+    vs = np.ascontiguousarray(f.v_slack)
+    out = C.c_void_p()
+
+    def call(bp):
+        bp = np.ascontiguousarray(bp, np.int32)
+        return lib.zbus_network_create_phased(f.n_total, row.size, row.ctypes.data,
+                                              col.ctypes.data, val.ctypes.data, sl.ctypes.data,
+                                              vs.ctypes.data, bp.ctypes.data, None,
+                                              C.byref(out))
+
+    bp = f.bus_phase.copy()
+    dup = bp.copy()
+    dup[5] = dup[4]                         # two indices on one bus-phase
+    assert call(dup) == 1
+    swapped = bp.copy()
+    swapped[[0, 1]] = swapped[[1, 0]]       # slack phases out of order
+    assert call(swapped) == 1
+    onslack = bp.copy()
+    onslack[4] = 0                          # a load phase on the slack bus (duplicate too)
+    assert call(onslack) == 1
+    neg = bp.copy()
+    neg[7] = -3
+    assert call(neg) == 1
+    assert lib.zbus_network_create_phased(f.n_total, row.size, row.ctypes.data, col.ctypes.data,
+                                          val.ctypes.data, sl.ctypes.data, vs.ctypes.data,
+                                          None, None, C.byref(out)) == 1
+    assert not out.value
