@@ -31,7 +31,10 @@ Parity status: every function below is pinned by tests that do not retype it
 (closed-form two-bus solution, balanced delta equal to balanced wye, per-branch
 delta power balance, lowest-common-ancestor form of Z on radial feeders,
 no-load voltage, brute-force Newton-Raphson on tiny feeders, and the power
-mismatch invariant).
+mismatch invariant).  The load-gradient adjoint (solve_adjoint) is pinned by
+central finite differences of the forward solve (directional and entry by
+entry), by the derivative of the two-bus closed form, and on partial-phase
+feeders.
 """
 from __future__ import annotations
 
@@ -202,3 +205,102 @@ def solve_coo(n_total, row, col, val, slack_idx, v_slack, S_wye, S_del,
     bp = None if bus_phase is None else np.asarray(bus_phase)[load_idx]
     V, it, cv = fixed_point(Z, w, S_wye, S_del, tol, max_iter, rule=rule, V0=V0, bus_phase=bp)
     return dict(V=V, iters=it, converged=cv, Z=Z, w=w, Y_LL=Y_LL, Y_Ls=Y_Ls, bus_phase=bp)
+
+
+# ---------------------------------------------------------------------------
+# Gradient of the converged fixed point with respect to the loads.  The paper
+# motivates the solver as a component of GPU learning pipelines (Sec. I and
+# the conclusion); here the solution v*(S) of v = Z i(v, S) + w is
+# differentiated through the fixed-point condition (implicit function
+# theorem), not through the iterations.
+#
+# Convention (the one of complex autograd): for a real loss L of a complex
+# array x, grad_x = dL/dRe(x) + j dL/dIm(x), so that dL = Re(sum conj(grad) dx).
+# ---------------------------------------------------------------------------
+
+def _unknown_map(n: int, bus_phase) -> tuple[np.ndarray, dict]:
+    """(bus_phase of every unknown, {bus_phase value: unknown index})."""
+    if bus_phase is None:
+        if n % 3:
+            raise ValueError("three-phase unknowns need n % 3 == 0 (give bus_phase otherwise)")
+        bp = np.arange(n) + 3        # bus k >= 1, phase p -> 3 k + p
+    else:
+        bp = np.asarray(bus_phase)
+    return bp, {int(g): j for j, g in enumerate(bp)}
+
+
+def load_current_jacobians(v: np.ndarray, s_wye: np.ndarray, s_del: np.ndarray,
+                           bus_phase=None):
+    """Derivatives of the load currents of one scenario.
+
+    The current i(v, S) of constant-power loads depends on conj(v) and conj(S)
+    only, so its differential is di = A conj(dv) + Dw conj(dS_wye) +
+    Dd conj(dS_del).  Returns the complex [n, n] matrices (A, Dw, Dd).
+
+      wye slot j:      i_j = -conj(S_j) / conj(v_j)
+                       A[j, j] = conj(S_j / v_j^2),  Dw[j, j] = -1 / conj(v_j)
+      delta slot x     I = conj(S / u), u = v_x - v_y, drawn from x, returned
+      (branch x -> y): into y (y the next phase of a, b, c on the same bus);
+                       dI = -conj(S / u^2) conj(du) + conj(dS) / conj(u)
+                       A gains c on (x, x), (y, y) and -c on (x, y), (y, x),
+                       c = conj(S / u^2);  Dd[x, x] = -1 / conj(u),
+                       Dd[y, x] = +1 / conj(u)
+    A delta slot whose branch has no second phase is not a load (its column
+    of Dd stays zero).
+    """
+    n = v.size
+    bp, where = _unknown_map(n, bus_phase)
+    A = np.zeros((n, n), dtype=np.complex128)
+    Dw = np.zeros((n, n), dtype=np.complex128)
+    Dd = np.zeros((n, n), dtype=np.complex128)
+    for j in range(n):
+        Dw[j, j] = -1.0 / np.conj(v[j])
+        if s_wye[j] != 0:
+            A[j, j] += np.conj(s_wye[j] / v[j] ** 2)
+        k, x = divmod(int(bp[j]), 3)
+        m = where.get(3 * k + (x + 1) % 3)
+        if m is None:
+            continue
+        u = v[j] - v[m]
+        Dd[j, j] = -1.0 / np.conj(u)
+        Dd[m, j] = 1.0 / np.conj(u)
+        if s_del[j] != 0:
+            c = np.conj(s_del[j] / u ** 2)
+            A[j, j] += c
+            A[m, m] += c
+            A[j, m] -= c
+            A[m, j] -= c
+    return A, Dw, Dd
+
+
+def _real_conj_map(M: np.ndarray) -> np.ndarray:
+    """Real [2n, 2n] matrix of z -> M conj(z) acting on [Re z; Im z]."""
+    return np.block([[M.real, M.imag], [M.imag, -M.real]])
+
+
+def solve_adjoint(Z: np.ndarray, V: np.ndarray, S_wye: np.ndarray, S_del: np.ndarray,
+                  G: np.ndarray, bus_phase=None):
+    """Gradients (H_wye, H_del) of a real loss with respect to S_wye and S_del.
+
+    V [B, n] is a fixed point v = Z i(v, S) + w of each scenario and G [B, n]
+    the loss gradient with respect to V.  Differentiating the fixed-point
+    condition gives dv = Z A conj(dv) + Z (Dw conj(dS_wye) + Dd conj(dS_del))
+    (load_current_jacobians); written as a real map on [Re; Im],
+    dx = J_v dx + J_w ds_wye + J_d ds_del, so dx/ds = (I - J_v)^{-1} J_s and
+    grad_s = J_s^T (I - J_v)^{-T} g.  Dense real solve per scenario.
+    """
+    V = np.asarray(V, dtype=np.complex128)
+    B, n = V.shape
+    Hw = np.zeros((B, n), dtype=np.complex128)
+    Hd = np.zeros((B, n), dtype=np.complex128)
+    eye = np.eye(2 * n)
+    for b in range(B):
+        A, Dw, Dd = load_current_jacobians(V[b], S_wye[b], S_del[b], bus_phase)
+        Jv = _real_conj_map(Z @ A)
+        g = np.concatenate([G[b].real, G[b].imag])
+        lam = np.linalg.solve((eye - Jv).T, g)
+        hw = _real_conj_map(Z @ Dw).T @ lam
+        hd = _real_conj_map(Z @ Dd).T @ lam
+        Hw[b] = hw[:n] + 1j * hw[n:]
+        Hd[b] = hd[:n] + 1j * hd[n:]
+    return Hw, Hd
