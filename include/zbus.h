@@ -389,6 +389,58 @@ zbus_status zbus_solve_noalloc(zbus_network net, int64_t B,
                                void* cuda_stream);
 
 /*
+ * zbus_solve_adjoint -- gradient of a real loss L(v*) with respect to the
+ * loads, v* a converged solution of the Sec. II-B fixed point v = Z i(v, S) + w
+ * (the paper presents the solver as a component of GPU learning pipelines,
+ * Sec. I and the conclusion; this makes the solve differentiable).  The
+ * gradient is taken through the fixed-point condition (implicit function
+ * theorem), not through the iterations:
+ *     lambda = G + A^T mu,   mu = Z^T conj(lambda)   (iterated from mu = 0),
+ *     dL/dS = D^T mu,
+ * with di = A conj(dv) + D conj(dS) the linearised load current at v* (wye
+ * slot j: A_jj = conj(S_j / v_j^2), D_jj = -1 / conj(v_j); delta branch
+ * x -> y, u = v_x - v_y: conj(S / u^2) in A on (x,x), (y,y) and its negative on
+ * (x,y), (y,x); -1 / conj(u), +1 / conj(u) at rows x, y of D).  FP64 throughout
+ * (the 3M contraction of the plain method with Z^T); the sweeps run in a
+ * device-side loop like the solve.
+ *
+ * Complex gradients follow the convention of complex autograd:
+ * grad = dL/dRe + j dL/dIm, so dL = Re(sum conj(grad) dS).
+ *
+ *   S_wye, S_delta  device [B][n] complex loads of the solve (either NULL)
+ *   V               device [B][n] complex converged voltages (e.g. V_out of
+ *                   zbus_solve)
+ *   G               device [B][n] complex dL/dV
+ *   tol             stop when max_j |mu^k_j - mu^{k-1}_j| <= tol after G_b
+ *                   is scaled to max_j |G_bj| = 1 (a tolerance relative to
+ *                   each scenario's loss gradient); >= 0
+ *   max_iter        iteration cap, >= 1
+ *   dS_wye          device [B][n] complex dL/dS_wye, or NULL; defined for
+ *                   every slot (the sensitivity to adding a load there)
+ *   dS_delta        device [B][n] complex dL/dS_delta, or NULL; slot x is the
+ *                   branch x -> next phase; zero where the branch lacks its
+ *                   second phase (partial-phase networks)
+ *   iters           device int32[B] adjoint sweeps performed
+ *   converged       device uint8[B] 1 where the stop rule was met; a
+ *                   scenario whose V is not a stable fixed point does not
+ *                   converge and its gradient is not to be used
+ *   cuda_stream     all work is enqueued on this stream
+ *
+ * Device buffers only (ZBUS_ERR_ARG otherwise).  The first call on a network
+ * forms Z^T (three n_pad x n_pad FP64 arrays kept with the handle); scratch
+ * grows on demand (synchronous).  Shares the handle's solve scratch, so it
+ * must not overlap a solve of the same handle on another stream.  Works on
+ * partial-phase networks.  B = 0 is a no-op.
+ */
+zbus_status zbus_solve_adjoint(zbus_network net, int64_t B,
+                               const double* S_wye, const double* S_delta,
+                               const double* V, const double* G,
+                               double tol, int32_t max_iter,
+                               double* dS_wye, double* dS_delta,
+                               int32_t* iters, uint8_t* converged,
+                               void* cuda_stream);
+
+/*
  * zbus_last_device_status -- the errors the device detected during the last
  * solve on net (the error word its kernels set instead of hanging or
  * faulting).  Synchronises cuda_stream first, so the solve must have been

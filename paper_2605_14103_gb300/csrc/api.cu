@@ -146,12 +146,12 @@ zbus_status ensure_workspace(zbus_network net, int64_t B) {
   return ZBUS_OK;
 }
 
-namespace {
-
 bool use_graphs() {
   const char* e = std::getenv("ZBUS_NO_GRAPH");
   return !(e && e[0] == '1');
 }
+
+namespace {
 
 // One sweep of the plain FP64 method on stream st (optionally bracketed by
 // events for the profile mode).
@@ -167,16 +167,21 @@ zbus_status enqueue_sweep_f64(zbus_network net, int64_t B, int grid, cudaGraphCo
   return ZBUS_OK;
 }
 
-zbus_status get_loop_graph(zbus_network net, int64_t B, GraphEntry** out) {
+}  // namespace
+
+// A graph whose WHILE node repeats one sweep (enqueued by `sweep`) until the
+// sweep's last kernel clears the condition; cached per (B, key).
+zbus_status get_while_graph(zbus_network net, int64_t B, int32_t key, int grid, SweepFn sweep,
+                            GraphEntry** out) {
   for (auto& g : net->graphs)
-    if (g.B == B) {
+    if (g.B == B && g.precision == key) {
       *out = &g;
       return ZBUS_OK;
     }
   GraphEntry e;
   e.B = B;
-  e.precision = ZBUS_FP64;
-  e.grid_gemm = gemm_f64_grid((int)B, net->n_pad);
+  e.precision = key;
+  e.grid_gemm = grid;
   if (!net->cap_stream) ZB_CUDA(cudaStreamCreateWithFlags(&net->cap_stream, cudaStreamNonBlocking));
   ZB_CUDA(cudaGraphCreate(&e.graph, 0));
   cudaGraphConditionalHandle h;
@@ -190,7 +195,7 @@ zbus_status get_loop_graph(zbus_network net, int64_t B, GraphEntry** out) {
   cudaGraph_t body = cp.conditional.phGraph_out[0];
   ZB_CUDA(cudaStreamBeginCaptureToGraph(net->cap_stream, body, nullptr, nullptr, 0,
                                         cudaStreamCaptureModeThreadLocal));
-  zbus_status s = enqueue_sweep_f64(net, B, e.grid_gemm, h, true, net->cap_stream);
+  zbus_status s = sweep(net, B, grid, h, true, net->cap_stream, nullptr);
   cudaGraph_t captured = nullptr;
   cudaError_t ce = cudaStreamEndCapture(net->cap_stream, &captured);
   if (s != ZBUS_OK || ce != cudaSuccess) {
@@ -207,6 +212,8 @@ zbus_status get_loop_graph(zbus_network net, int64_t B, GraphEntry** out) {
   *out = &net->graphs.back();
   return ZBUS_OK;
 }
+
+namespace {
 
 // Profile buffers (events, per-sweep active counts) for up to max_iter sweeps.
 zbus_status ensure_profile(zbus_network net, int32_t max_iter) {
@@ -442,6 +449,7 @@ void zbus_network_destroy(zbus_network net) {
   cudaFree(net->ws.base);
   free_mixed(net);
   phased_free(net);
+  free_adjoint(net);
   cudaFree(net->Z);
   cudaFree(net->w);
   cudaFree(net->ys);
@@ -552,7 +560,7 @@ zbus_status solve_device(zbus_network net, int64_t B, const double* S_wye, const
     ZB_CUDA(cudaGetLastError());
     if (use_graphs()) {
       GraphEntry* g = nullptr;
-      ZB_CHECK(get_loop_graph(net, B, &g));
+      ZB_CHECK(get_while_graph(net, B, ZBUS_FP64, grid, enqueue_sweep_f64, &g));
       ZB_CUDA(cudaGraphLaunch(g->exec, st));
     } else {
       for (int k = 0; k < max_iter; ++k) ZB_CHECK(enqueue_sweep_f64(net, B, grid, 0, false, st));

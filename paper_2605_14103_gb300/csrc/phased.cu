@@ -31,15 +31,16 @@ __global__ void k_ph_scatter(const double2* __restrict__ src, double2* __restric
   }
 }
 
-// dst[b][j] = src[b][map[j]].
+// dst[b][j] = src[b][map[j]]; with keep, zero where keep[j] is 0.
 __global__ void k_ph_gather(const double2* __restrict__ src, double2* __restrict__ dst, int B,
-                            int n_user, int n, const int32_t* __restrict__ map) {
+                            int n_user, int n, const int32_t* __restrict__ map,
+                            const uint8_t* __restrict__ keep) {
   const int64_t total = (int64_t)B * n_user;
   for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < total;
        t += (int64_t)gridDim.x * blockDim.x) {
     const int64_t b = t / n_user;
     const int j = (int)(t - b * n_user);
-    dst[t] = src[b * n + map[j]];
+    dst[t] = (keep && !keep[j]) ? make_double2(0.0, 0.0) : src[b * n + map[j]];
   }
 }
 
@@ -169,7 +170,18 @@ zbus_status phased_out(zbus_network net, int64_t B, const double* src, double* d
   if (B == 0 || net->n_user == 0) return ZBUS_OK;
   const int64_t total = B * (int64_t)net->n_user;
   k_ph_gather<<<grid_for(total), 256, 0, st>>>((const double2*)src, (double2*)dst, (int)B,
-                                                net->n_user, net->n, net->ph_map);
+                                                net->n_user, net->n, net->ph_map, nullptr);
+  ZB_CUDA(cudaGetLastError());
+  return ZBUS_OK;
+}
+
+zbus_status phased_out_delta(zbus_network net, int64_t B, const double* src, double* dst,
+                             cudaStream_t st) {
+  if (B == 0 || net->n_user == 0) return ZBUS_OK;
+  const int64_t total = B * (int64_t)net->n_user;
+  k_ph_gather<<<grid_for(total), 256, 0, st>>>((const double2*)src, (double2*)dst, (int)B,
+                                                net->n_user, net->n, net->ph_map,
+                                                net->ph_dvalid);
   ZB_CUDA(cudaGetLastError());
   return ZBUS_OK;
 }

@@ -82,6 +82,11 @@ struct SolveCtx {
   int32_t* mt_list;       // mixed: [B_pad / 128] tiles holding an active scenario
   uint32_t* mt_flag;      // mixed: [B_pad / 128] set by the stop test
   int32_t mt_count;       // mixed: entries of mt_list
+  // load gradient (adjoint sweeps): V holds the adjoint iterate mu, these the
+  // converged voltages, the loss gradient and its per-scenario scale
+  const double2* Vf;      // [B][n]
+  const double2* G;       // [B][n]
+  const double* gscale;   // [B]
 };
 
 struct Workspace {
@@ -215,6 +220,16 @@ struct zbus_network_s {
   uint8_t* ph_dvalid = nullptr;   // [n_user] 1 where its delta branch has both phases
   double* ph_buf = nullptr;       // four padded [ph_cap][n] complex staging arrays
   int64_t ph_cap = 0;
+  // load gradient (zbus_solve_adjoint): Z^T in the 3M layout, a zero no-load
+  // term for the contraction epilogue, the adjoint iterate and the
+  // per-scenario gradient scales
+  double* ZrT = nullptr;
+  double* ZiT = nullptr;
+  double* ZsT = nullptr;
+  double2* adj_zero = nullptr;    // [n_pad]
+  double2* adj_mu = nullptr;      // [adj_cap][n]
+  double* adj_scale = nullptr;    // [adj_cap]
+  int64_t adj_cap = 0;
 };
 
 namespace zbus {
@@ -240,6 +255,19 @@ void launch_mismatch(const double2* V, const double2* S_wye, const double2* S_de
 
 // api.cu
 zbus_status ensure_workspace(zbus_network net, int64_t B);
+bool use_graphs();   // false when ZBUS_NO_GRAPH=1 (sweeps launched from the host)
+// One sweep enqueued on a stream: the last kernel sets the WHILE condition
+// through h when use_handle; ev (or nullptr) brackets the kernels.
+typedef zbus_status (*SweepFn)(zbus_network net, int64_t B, int grid,
+                               cudaGraphConditionalHandle h, bool use_handle, cudaStream_t st,
+                               cudaEvent_t* ev);
+// Graph keys besides the precisions of the solve.
+constexpr int32_t GRAPH_KEY_ADJOINT = -2;
+zbus_status get_while_graph(zbus_network net, int64_t B, int32_t key, int grid, SweepFn sweep,
+                            GraphEntry** out);
+
+// adjoint.cu
+void free_adjoint(zbus_network net);
 
 // phased.cu
 zbus_status phased_validate(int32_t n_total, const int32_t* slack_idx, const int32_t* bus_phase,
@@ -255,6 +283,10 @@ zbus_status phased_in(zbus_network net, int64_t B, const double* src, double* ds
                       cudaStream_t st);
 zbus_status phased_out(zbus_network net, int64_t B, const double* src, double* dst,
                        cudaStream_t st);
+// phased_out for delta-slot arrays: entries whose branch lacks its second
+// phase come out zero
+zbus_status phased_out_delta(zbus_network net, int64_t B, const double* src, double* dst,
+                             cudaStream_t st);
 zbus_status phased_z(zbus_network net, double* Z_out, cudaStream_t st);
 void phased_free(zbus_network net);
 

@@ -1,0 +1,205 @@
+"""GPU parity of the load gradient (zbus_solve_adjoint) against the oracle.
+
+Both sides receive the oracle's converged voltages and the same seeded loss
+gradient G; the oracle solves the adjoint system directly (dense real solve),
+the library iterates it in FP64 to a relative tolerance of 1e-13.  Bar: per
+scenario max |H_gpu - H_oracle| <= 1e-9 max |H_oracle| (the iteration's
+truncation is ~1e-13 of the gradient's size and FP64 rounding far below), the
+adjoint converged on every scenario.  Also: the autograd wrapper against
+central differences of the GPU forward solve, batch independence (bitwise),
+host-driven and graph loops equal, zero G, a scenario with non-finite
+voltages, partial-phase feeders and the bench's 128-bus workload at full
+batch (sampled).
+"""
+import os
+
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+
+from oracle import zbus_oracle as O                      # noqa: E402
+from paper_2605_14103_gb300 import feeders as F          # noqa: E402
+from paper_2605_14103_gb300 import zbus                  # noqa: E402
+
+pytestmark = pytest.mark.gpu
+REL = 1e-9
+
+
+@pytest.fixture(scope="module", autouse=True)
+def built():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2605_14103_gb300 import build as B
+    B.build()
+    zbus.lib()
+
+
+def dev(x):
+    return torch.from_numpy(np.ascontiguousarray(x)).cuda()
+
+
+def forward_oracle(f, Sw, Sd, bus_phase=None):
+    r = O.solve_coo(f.n_total, f.Y_row, f.Y_col, f.Y_val, f.slack_idx, f.v_slack, Sw, Sd,
+                    tol=1e-14, max_iter=300, bus_phase=bus_phase)
+    assert r["converged"].all()
+    return r
+
+
+def loss_grad(shape, seed):
+    rng = np.random.default_rng(seed)
+    return rng.normal(size=shape) + 1j * rng.normal(size=shape)
+
+
+def assert_close(H, Href):
+    for b in range(Href.shape[0]):
+        scale = max(np.abs(Href[b]).max(), 1e-300)
+        err = np.abs(H[b] - Href[b]).max()
+        assert err <= REL * scale, (b, err, scale)
+
+
+@pytest.mark.parametrize("N,B,delta,seed", [(13, 5, 0.0, 101), (40, 33, 0.4, 7),
+                                            (128, 17, 0.3, 202), (200, 3, 0.3, 9)])
+def test_parity_against_the_oracle(N, B, delta, seed):
+    f = F.make_feeder(N, seed, delta_frac=delta, mult_hi=1.5)
+    Sw, Sd = F.make_scenarios(f, B, 0.5, 1.5)
+    r = forward_oracle(f, Sw, Sd)
+    G = loss_grad(Sw.shape, seed)
+    Hw, Hd = O.solve_adjoint(r["Z"], r["V"], Sw, Sd, G)
+    net = zbus.Network.from_feeder(f)
+    dw, dd, it, cv = net.solve_adjoint(dev(r["V"]), dev(G), dev(Sw), dev(Sd), tol=1e-13)
+    assert cv.cpu().numpy().all()
+    assert it.cpu().numpy().max() < 200
+    assert_close(dw.cpu().numpy(), Hw)
+    assert_close(dd.cpu().numpy(), Hd)
+    net.close()
+
+
+def test_wye_only_and_one_output():
+    f = F.make_feeder(60, 31, delta_frac=0.0)
+    Sw, Sd = F.make_scenarios(f, 9, 0.8, 1.2)
+    r = forward_oracle(f, Sw, Sd)
+    G = loss_grad(Sw.shape, 3)
+    Hw, Hd = O.solve_adjoint(r["Z"], r["V"], Sw, 0 * Sw, G)
+    net = zbus.Network.from_feeder(f)
+    dw, dd, it, cv = net.solve_adjoint(dev(r["V"]), dev(G), dev(Sw), None, tol=1e-13,
+                                       delta=False)
+    assert dd is None and cv.cpu().numpy().all()
+    assert_close(dw.cpu().numpy(), Hw)
+    _, dd2, _, _ = net.solve_adjoint(dev(r["V"]), dev(G), dev(Sw), None, tol=1e-13, wye=False)
+    assert_close(dd2.cpu().numpy(), Hd)
+
+
+def test_autograd_against_finite_differences_of_the_gpu_solve():
+    f = F.make_feeder(20, 44, delta_frac=0.5)
+    Sw, Sd = F.make_scenarios(f, 4, 0.8, 1.2)
+    net = zbus.Network.from_feeder(f)
+    G = dev(loss_grad(Sw.shape, 5))
+    sw = dev(Sw).requires_grad_(True)
+    sd = dev(Sd).requires_grad_(True)
+    V, it, cv = zbus.solve_differentiable(net, sw, sd, tol=1e-13, max_iter=300)
+    assert cv.all()
+    L = (torch.conj(G) * V).real.sum()
+    L.backward()
+    ait, acv = net.last_adjoint
+    assert acv.all()
+
+    def Lof(a, b):
+        V, _, c = net.solve(a, b, tol=1e-13, max_iter=300)
+        assert c.all()
+        return float((torch.conj(G) * V).real.sum())
+
+    rng = np.random.default_rng(9)
+    h = 1e-4
+    for grad, wye in ((sw.grad, True), (sd.grad, False)):
+        d = dev((rng.normal(size=Sw.shape) + 1j * rng.normal(size=Sw.shape)) * 0.05)
+        base_w, base_d = dev(Sw), dev(Sd)
+        if wye:
+            fd = (Lof(base_w + h * d, base_d) - Lof(base_w - h * d, base_d)) / (2 * h)
+        else:
+            fd = (Lof(base_w, base_d + h * d) - Lof(base_w, base_d - h * d)) / (2 * h)
+        ad = float((torch.conj(grad) * d).real.sum())
+        assert abs(ad - fd) <= 1e-5 * max(1.0, abs(fd)), (wye, ad, fd)
+
+
+def test_batch_independence_and_loop_forms(monkeypatch):
+    f, Sw, Sd, w = F.make_workload("feeder128_b4096", B=100)
+    r = forward_oracle(f, Sw, Sd)
+    G = loss_grad(Sw.shape, 11)
+    net = zbus.Network.from_feeder(f)
+    dw, dd, it, cv = net.solve_adjoint(dev(r["V"]), dev(G), dev(Sw), dev(Sd))
+    perm = np.random.default_rng(0).permutation(100)[:37]
+    dw2, dd2, it2, cv2 = net.solve_adjoint(dev(r["V"][perm]), dev(G[perm]), dev(Sw[perm]),
+                                           dev(Sd[perm]))
+    idx = torch.from_numpy(perm).cuda()
+    assert torch.equal(dw2, dw[idx]) and torch.equal(dd2, dd[idx])     # bitwise
+    assert torch.equal(it2, it[idx])
+    monkeypatch.setenv("ZBUS_NO_GRAPH", "1")
+    dw3, dd3, it3, cv3 = net.solve_adjoint(dev(r["V"]), dev(G), dev(Sw), dev(Sd))
+    assert torch.equal(dw3, dw) and torch.equal(dd3, dd) and torch.equal(it3, it)
+
+
+def test_zero_gradient_and_non_finite_voltages():
+    f = F.make_feeder(30, 12, delta_frac=0.3)
+    Sw, Sd = F.make_scenarios(f, 6, 0.8, 1.2)
+    r = forward_oracle(f, Sw, Sd)
+    net = zbus.Network.from_feeder(f)
+    G = loss_grad(Sw.shape, 4)
+    G[2] = 0
+    V = r["V"].copy()
+    V[4, 7] = np.nan
+    dw, dd, it, cv = net.solve_adjoint(dev(V), dev(G), dev(Sw), dev(Sd), tol=1e-13)
+    cv, it = cv.cpu().numpy(), it.cpu().numpy()
+    assert cv[2] == 1 and it[2] == 1
+    assert not np.any(dw.cpu().numpy()[2]) and not np.any(dd.cpu().numpy()[2])
+    assert cv[4] == 0
+    ok = [0, 1, 3, 5]
+    Hw, Hd = O.solve_adjoint(r["Z"], r["V"][ok], Sw[ok], Sd[ok], G[ok])
+    assert cv[ok].all()
+    assert_close(dw.cpu().numpy()[ok], Hw)
+    assert_close(dd.cpu().numpy()[ok], Hd)
+
+
+@pytest.mark.parametrize("N,B,seed", [(12, 4, 3), (90, 20, 77)])
+def test_partial_phase_feeders(N, B, seed):
+    f = F.make_partial_feeder(N, seed, lateral_frac=0.8, delta_frac=0.5, mult_hi=1.5)
+    Sw, Sd = F.make_partial_scenarios(f, B, 0.5, 1.5)
+    r = forward_oracle(f, Sw, Sd, f.bus_phase)
+    G = loss_grad(Sw.shape, seed)
+    Hw, Hd = O.solve_adjoint(r["Z"], r["V"], Sw, Sd, G, bus_phase=r["bus_phase"])
+    net = zbus.Network.from_feeder(f)
+    dw, dd, it, cv = net.solve_adjoint(dev(r["V"]), dev(G), dev(Sw), dev(Sd), tol=1e-13)
+    assert cv.cpu().numpy().all()
+    assert_close(dw.cpu().numpy(), Hw)
+    assert_close(dd.cpu().numpy(), Hd)
+
+
+def test_bench_workload_full_batch_sampled():
+    """The 128-bus workload at its full 4096 scenarios, in the launch
+    configuration the benchmark times; the oracle checks a sample."""
+    f, Sw, Sd, w = F.make_workload("feeder128_b4096")
+    r = forward_oracle(f, Sw, Sd)
+    G = loss_grad(Sw.shape, 2024)
+    net = zbus.Network.from_feeder(f)
+    dw, dd, it, cv = net.solve_adjoint(dev(r["V"]), dev(G), dev(Sw), dev(Sd), tol=1e-12)
+    assert cv.cpu().numpy().all()
+    pick = np.random.default_rng(1).choice(Sw.shape[0], 6, replace=False)
+    Hw, Hd = O.solve_adjoint(r["Z"], r["V"][pick], Sw[pick], Sd[pick], G[pick])
+    assert_close(dw.cpu().numpy()[pick], Hw)
+    assert_close(dd.cpu().numpy()[pick], Hd)
+
+
+def test_argument_errors():
+    f = F.make_feeder(10, 1)
+    Sw, Sd = F.make_scenarios(f, 2, 0.8, 1.2)
+    net = zbus.Network.from_feeder(f)
+    V = dev(Sw)
+    with pytest.raises(zbus.ZbusError):
+        zbus.zbus_solve_adjoint(net.handle, None, None, V, V, -1.0, 10, None, None,
+                                torch.empty(2, dtype=torch.int32, device="cuda"),
+                                torch.empty(2, dtype=torch.uint8, device="cuda"))
+    with pytest.raises(zbus.ZbusError):
+        zbus.zbus_solve_adjoint(net.handle, None, None, V, V, 1e-10, 0, None, None,
+                                torch.empty(2, dtype=torch.int32, device="cuda"),
+                                torch.empty(2, dtype=torch.uint8, device="cuda"))
+    assert os.environ.get("ZBUS_NO_GRAPH") != "1"
