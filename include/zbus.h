@@ -452,6 +452,91 @@ zbus_status zbus_solve_adjoint(zbus_network net, int64_t B,
  */
 zbus_status zbus_last_device_status(zbus_network net, void* cuda_stream);
 
+/* ------------------------------------------------------------------------
+ * Transmission grids: batched Newton-Raphson power flow (Sec. II-A).
+ *
+ * State x_b = [theta_Theta; |V|_Q] (angles of the PV and PQ buses,
+ * magnitudes of the PQ buses), mismatch F_b = [P_calc - P on Theta;
+ * Q_calc - Q on Q], S_calc = V o conj(Y V) (eqs. 1-2); Newton steps
+ * J dx = -F (eq. 3) solved by restarted GMRES with Jacobian-vector products
+ * and the block lower-triangular fast-decoupled preconditioner of eqs. 7-9
+ * (B' = -Im(Y)[Theta,Theta], B'' = -Im(Y)[Q,Q] with eps I added,
+ * G_Q,Theta = -Re(Y)[Q,Theta]), FP64.  B' + eps I and B'' + eps I are
+ * applied through sparse LU factors formed at network creation.
+ * ------------------------------------------------------------------------ */
+typedef struct zbus_nr_network_s* zbus_nr_network;
+
+typedef struct {
+  int32_t gmres_restart;      /* Krylov vectors per GMRES cycle, 1 .. 60 (default 30) */
+  int32_t gmres_max_restarts; /* GMRES cycles per Newton step, >= 1 (default 4) */
+  double gmres_tol;           /* stop a Newton step's GMRES when the preconditioned
+                                 residual is below gmres_tol times its start, (0, 1)
+                                 (default 1e-6) */
+  double reserved[4];
+} zbus_nr_opts;
+
+/* Fill *opts with the defaults above. */
+void zbus_nr_opts_default(zbus_nr_opts* opts);
+
+/*
+ * zbus_nr_network_create -- a transmission grid on the current device.
+ *
+ *   N          number of buses (>= 2)
+ *   nnz        COO entries of the N x N bus admittance matrix (>= 1)
+ *   row, col   host int32[nnz]; val_reim host double[2 nnz] (complex, pu;
+ *              duplicates summed)
+ *   bus_type   host int32[N]: 0 = PQ, 1 = PV, 2 = slack (exactly one; its
+ *              angle is the reference 0)
+ *   v_set      host double[N]: |V| set-point of PV buses and the slack
+ *              (ignored at PQ buses)
+ *   eps        diagonal regularisation of B' and B'' (>= 0, e.g. 1e-8)
+ *   cuda_stream  stream for the set-up copies; the call returns after them
+ *
+ * Orders B' + eps I and B'' + eps I by minimum degree and factors them
+ * (LU without pivoting).  ZBUS_ERR_SINGULAR if a pivot vanishes,
+ * ZBUS_ERR_ARG for invalid input.
+ */
+zbus_status zbus_nr_network_create(int32_t N, int64_t nnz, const int32_t* row,
+                                   const int32_t* col, const double* val_reim,
+                                   const int32_t* bus_type, const double* v_set,
+                                   double eps, void* cuda_stream, zbus_nr_network* out);
+
+/* Release a grid; NULL is ignored.  No solve of it may still be running. */
+void zbus_nr_network_destroy(zbus_nr_network net);
+
+/* Sizes of a grid: angle unknowns, magnitude unknowns, entries of the two
+ * preconditioner factors, and the sum of their triangular-solve levels.
+ * Any output may be NULL. */
+zbus_status zbus_nr_network_info(zbus_nr_network net, int32_t* n_theta, int32_t* n_q,
+                                 int64_t* factor_nnz, int32_t* factor_levels);
+
+/*
+ * zbus_nr_solve -- Newton-Raphson over B scenarios from the flat start
+ * (theta = 0, |V| = 1 at PQ buses, the set-point elsewhere).
+ *
+ *   P, Q         device double[B][N]: net injections (generation - load, pu);
+ *                P of the slack and Q of PV buses and the slack are ignored
+ *   tol          converged when max |F_b| <= tol (pu)
+ *   max_iter     Newton steps at most (>= 0)
+ *   opts         NULL for zbus_nr_opts_default
+ *   V_out        device complex [B][N]: the last iterate
+ *   iters        device int32[B]: Newton steps taken
+ *   converged    device uint8[B]: 1 if max |F_b| <= tol was reached; a
+ *                non-finite mismatch stops the scenario unconverged
+ *   gmres_iters  device int32[B] or NULL: GMRES iterations (Jacobian-vector
+ *                products inside the Krylov cycles) of all Newton steps
+ *   cuda_stream  all work is enqueued on this stream
+ *
+ * Each scenario is solved by one CTA from start to stop (no host round trip
+ * per step).  Scratch (about (66 dim + 9 N) doubles per resident CTA, dim =
+ * n_theta + n_q) grows on demand with a synchronous allocation.  Device
+ * buffers only.  B = 0 is a no-op.
+ */
+zbus_status zbus_nr_solve(zbus_nr_network net, int64_t B, const double* P, const double* Q,
+                          double tol, int32_t max_iter, const zbus_nr_opts* opts,
+                          double* V_out, int32_t* iters, uint8_t* converged,
+                          int32_t* gmres_iters, void* cuda_stream);
+
 /* Human-readable name of a status code (static storage). */
 const char* zbus_status_string(zbus_status s);
 

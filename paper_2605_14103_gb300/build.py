@@ -13,7 +13,7 @@ BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libzbus.so")
 
 SOURCES = ["api.cu", "setup.cu", "kernels_f64.cu", "mixed.cu", "group.cu", "tune.cu", "serve.cu",
-           "noalloc.cu", "phased.cu", "adjoint.cu"]
+           "noalloc.cu", "phased.cu", "adjoint.cu", "nr.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-Xcompiler", "-O2",
          "-I" + INCLUDE, "-I" + CSRC]

@@ -61,6 +61,11 @@ class zbus_serve_config(C.Structure):
                 ("max_admit_per_sweep", C.c_int32), ("reserved0", C.c_int32)]
 
 
+class zbus_nr_opts(C.Structure):
+    _fields_ = [("gmres_restart", C.c_int32), ("gmres_max_restarts", C.c_int32),
+                ("gmres_tol", C.c_double), ("reserved", C.c_double * 4)]
+
+
 SOURCE_FN = C.CFUNCTYPE(C.c_int32, C.c_void_p, C.c_double, C.POINTER(zbus_request))
 SINK_FN = C.CFUNCTYPE(None, C.c_void_p, C.POINTER(zbus_request), C.POINTER(zbus_request_result))
 
@@ -93,6 +98,14 @@ _SIGS = {
     "zbus_last_device_status": (C.c_int, [_P, _P]),
     "zbus_solve_adjoint": (C.c_int, [_P, C.c_int64, _P, _P, _P, _P, C.c_double, C.c_int32, _P,
                                      _P, _P, _P, _P]),
+    "zbus_nr_opts_default": (None, [C.POINTER(zbus_nr_opts)]),
+    "zbus_nr_network_create": (C.c_int, [C.c_int32, C.c_int64, _P, _P, _P, _P, _P, C.c_double,
+                                         _P, C.POINTER(_P)]),
+    "zbus_nr_network_destroy": (None, [_P]),
+    "zbus_nr_network_info": (C.c_int, [_P, C.POINTER(C.c_int32), C.POINTER(C.c_int32),
+                                       C.POINTER(C.c_int64), C.POINTER(C.c_int32)]),
+    "zbus_nr_solve": (C.c_int, [_P, C.c_int64, _P, _P, C.c_double, C.c_int32,
+                                C.POINTER(zbus_nr_opts), _P, _P, _P, _P, _P]),
     "zbus_status_string": (C.c_char_p, [C.c_int]),
     "zbus_last_error": (C.c_char_p, []),
 }
@@ -559,3 +572,97 @@ def solve_differentiable(net, S_wye, S_delta=None, tol=1e-10, max_iter=50, preci
         _SOLVE_FN = _solve_function()
     return _SOLVE_FN.apply(S_wye, S_delta, net,
                            (tol, max_iter, precision, adj_tol, adj_max_iter))
+
+
+# ---------------------------------------------------------------------------
+# Transmission grids: batched Newton-Raphson (Sec. II-A).
+# ---------------------------------------------------------------------------
+
+def zbus_nr_opts_default() -> zbus_nr_opts:
+    o = zbus_nr_opts()
+    lib().zbus_nr_opts_default(C.byref(o))
+    return o
+
+
+def zbus_nr_network_create(N, row, col, val, bus_type, v_set, eps=1e-8, stream=None) -> int:
+    row = np.ascontiguousarray(row, dtype=np.int32)
+    col = np.ascontiguousarray(col, dtype=np.int32)
+    val = np.ascontiguousarray(val, dtype=np.complex128)
+    bt = np.ascontiguousarray(bus_type, dtype=np.int32)
+    vs = np.ascontiguousarray(v_set, dtype=np.float64)
+    if not (row.shape == col.shape == val.shape) or bt.shape != (N,) or vs.shape != (N,):
+        raise ValueError("row/col/val must have equal length; bus_type and v_set N entries")
+    h = _P()
+    _check(lib().zbus_nr_network_create(int(N), int(row.size), row.ctypes.data, col.ctypes.data,
+                                        val.ctypes.data, bt.ctypes.data, vs.ctypes.data,
+                                        float(eps), _stream(stream), C.byref(h)))
+    return h.value
+
+
+def zbus_nr_network_destroy(h):
+    if h:
+        lib().zbus_nr_network_destroy(h)
+
+
+def zbus_nr_network_info(h):
+    """(n_theta, n_q, factor_nnz, factor_levels)."""
+    a, b, c, d = C.c_int32(0), C.c_int32(0), C.c_int64(0), C.c_int32(0)
+    _check(lib().zbus_nr_network_info(h, C.byref(a), C.byref(b), C.byref(c), C.byref(d)))
+    return a.value, b.value, c.value, d.value
+
+
+def zbus_nr_solve(h, N, P, Q, tol, max_iter, opts, V_out, iters, converged, gmres_iters=None,
+                  stream=None):
+    import torch
+    B = V_out.shape[0]
+    f64 = torch.float64
+    _check(lib().zbus_nr_solve(
+        h, int(B), _dptr(P, "P", f64, (B, N)), _dptr(Q, "Q", f64, (B, N)), float(tol),
+        int(max_iter), C.byref(opts) if opts is not None else None,
+        _dptr(V_out, "V_out", torch.complex128, (B, N)),
+        _dptr(iters, "iters", torch.int32, (B,)), _dptr(converged, "converged", torch.uint8, (B,)),
+        _dptr(gmres_iters, "gmres_iters", torch.int32, (B,)), _stream(stream)))
+
+
+class NrNetwork:
+    """One transmission grid for the batched Newton-Raphson solve."""
+
+    def __init__(self, N, row, col, val, bus_type, v_set, eps=1e-8, stream=None):
+        self.N = int(N)
+        self.handle = zbus_nr_network_create(N, row, col, val, bus_type, v_set, eps, stream)
+
+    @classmethod
+    def from_grid(cls, g, eps=1e-8, stream=None):
+        return cls(g.N, g.Y_row, g.Y_col, g.Y_val, g.bus_type, g.v_set, eps, stream)
+
+    def close(self):
+        if self.handle:
+            zbus_nr_network_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def info(self):
+        return zbus_nr_network_info(self.handle)
+
+    def solve(self, P, Q, tol=1e-10, max_iter=20, gmres_restart=30, gmres_max_restarts=4,
+              gmres_tol=1e-6, out=None, stream=None):
+        """Returns (V [B,N] complex128, iters, converged, gmres_iters) on P's device."""
+        import torch
+        B = P.shape[0]
+        if out is None:
+            out = (torch.empty((B, self.N), dtype=torch.complex128, device=P.device),
+                   torch.empty((B,), dtype=torch.int32, device=P.device),
+                   torch.empty((B,), dtype=torch.uint8, device=P.device),
+                   torch.empty((B,), dtype=torch.int32, device=P.device))
+        o = zbus_nr_opts_default()
+        o.gmres_restart = gmres_restart
+        o.gmres_max_restarts = gmres_max_restarts
+        o.gmres_tol = gmres_tol
+        V, it, cv, gm = out
+        zbus_nr_solve(self.handle, self.N, P, Q, tol, max_iter, o, V, it, cv, gm, stream)
+        return V, it, cv, gm
