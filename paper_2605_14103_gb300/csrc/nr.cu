@@ -38,7 +38,8 @@
 namespace zbus {
 namespace nr {
 
-constexpr int NR_THREADS = 256;
+constexpr int NR_THREADS = 128;
+constexpr int NR_MIN_CTAS = 8;   // CTAs per SM the register budget is sized for
 constexpr int NR_WARPS = NR_THREADS / 32;
 constexpr int NR_MAX_RESTART_LEN = 60;
 
@@ -46,14 +47,18 @@ constexpr int NR_MAX_RESTART_LEN = 60;
 struct Factor {
   int n = 0;
   int32_t* perm = nullptr;    // [n] factor index -> position in the block
-  int32_t* l_ptr = nullptr;   // strictly lower part, factor indices, CSR
+  // Rows of both triangles are stored in the order of their solve's levels:
+  // slot k of the forward solve is row fl_row[k], its strictly lower entries
+  // l_col / l_val[l_ptr[k] .. l_ptr[k+1]); slot k of the backward solve is
+  // row bl_row[k] with strictly upper entries u_* and 1 / U_kk in dinv[k].
+  int32_t* l_ptr = nullptr;
   int32_t* l_col = nullptr;
   double* l_val = nullptr;
-  int32_t* u_ptr = nullptr;   // strictly upper part
+  int32_t* u_ptr = nullptr;
   int32_t* u_col = nullptr;
   double* u_val = nullptr;
-  double* dinv = nullptr;     // [n] 1 / U_kk
-  int32_t* fl_ptr = nullptr;  // forward levels: rows fl_row[fl_ptr[l] .. fl_ptr[l+1])
+  double* dinv = nullptr;
+  int32_t* fl_ptr = nullptr;  // forward levels: slots fl_ptr[l] .. fl_ptr[l+1]
   int32_t* fl_row = nullptr;
   int32_t* bl_ptr = nullptr;  // backward levels
   int32_t* bl_row = nullptr;
@@ -92,7 +97,8 @@ struct zbus_nr_network_s {
   std::vector<void*> allocs;      // every device buffer of the network
   double* scratch = nullptr;
   int64_t scratch_ctas = 0;
-  int ctas_per_sm = 1;
+  int64_t scratch_stride = 0;
+  size_t smem_set = 0;
   int sms = 1;
 };
 
@@ -148,8 +154,9 @@ __device__ void factor_solve(const Factor& f, const double* in, double* y, doubl
   for (int l = 0; l < f.n_fl; ++l) {
     for (int k = f.fl_ptr[l] + t; k < f.fl_ptr[l + 1]; k += NR_THREADS) {
       const int i = f.fl_row[k];
+      const int e0 = f.l_ptr[k], e1 = f.l_ptr[k + 1];
       double s = y[i];
-      for (int e = f.l_ptr[i]; e < f.l_ptr[i + 1]; ++e) s -= f.l_val[e] * y[f.l_col[e]];
+      for (int e = e0; e < e1; ++e) s -= f.l_val[e] * y[f.l_col[e]];
       y[i] = s;
     }
     __syncthreads();
@@ -157,9 +164,11 @@ __device__ void factor_solve(const Factor& f, const double* in, double* y, doubl
   for (int l = 0; l < f.n_bl; ++l) {
     for (int k = f.bl_ptr[l] + t; k < f.bl_ptr[l + 1]; k += NR_THREADS) {
       const int i = f.bl_row[k];
+      const int e0 = f.u_ptr[k], e1 = f.u_ptr[k + 1];
+      const double di = f.dinv[k];
       double s = y[i];
-      for (int e = f.u_ptr[i]; e < f.u_ptr[i + 1]; ++e) s -= f.u_val[e] * y[f.u_col[e]];
-      y[i] = s * f.dinv[i];
+      for (int e = e0; e < e1; ++e) s -= f.u_val[e] * y[f.u_col[e]];
+      y[i] = s * di;
     }
     __syncthreads();
   }
@@ -234,7 +243,7 @@ struct SolveArgs {
   int32_t* gmres;
 };
 
-__global__ void __launch_bounds__(NR_THREADS) k_nr_solve(NrDev d, SolveArgs a) {
+__global__ void __launch_bounds__(NR_THREADS, NR_MIN_CTAS) k_nr_solve(NrDev d, SolveArgs a) {
   extern __shared__ double sm[];
   const int m = d.m;
   double* H = sm;                          // [(m + 1) * m], column j at H[j * (m + 1)]
@@ -243,6 +252,7 @@ __global__ void __launch_bounds__(NR_THREADS) k_nr_solve(NrDev d, SolveArgs a) {
   double* gv = sn + m;                     // [m + 1]
   double* hh = gv + m + 1;                 // [m + 1] this step's Gram-Schmidt coefficients
   double* red = hh + m + 1;                // [(m + 1) * NR_WARPS]
+  double* y = red + (m + 1) * NR_WARPS;    // [N] factor work space (the levels' reads)
   __shared__ int s_flag;
   __shared__ int s_jd;
 
@@ -257,8 +267,7 @@ __global__ void __launch_bounds__(NR_THREADS) k_nr_solve(NrDev d, SolveArgs a) {
   double* va = vm + N;
   double* dVr = va + N;
   double* dVi = dVr + N;
-  double* y = dVi + N;                     // factor work, N
-  double* F = y + N;                       // dim
+  double* F = dVi + N;                     // dim
   double* bv = F + dim;
   double* x = bv + dim;
   double* wv = x + dim;
@@ -536,50 +545,56 @@ bool factorise(int n, const std::vector<std::map<int, double>>& A, HostFactor& h
       }
     }
   }
-  hf.l_ptr.assign(n + 1, 0);
-  hf.u_ptr.assign(n + 1, 0);
-  for (int i = 0; i < n; ++i) {
-    std::sort(Lrows[i].begin(), Lrows[i].end());
-    for (auto& kv : Lrows[i]) {
-      hf.l_col.push_back(kv.first);
-      hf.l_val.push_back(kv.second);
-    }
-    hf.l_ptr[i + 1] = (int32_t)hf.l_col.size();
-    for (auto& kv : Urows[i]) {
-      hf.u_col.push_back(kv.first);
-      hf.u_val.push_back(kv.second);
-    }
-    hf.u_ptr[i + 1] = (int32_t)hf.u_col.size();
-  }
-  // level lists: forward (row i after its lower columns), backward (after its upper columns)
+  for (int i = 0; i < n; ++i) std::sort(Lrows[i].begin(), Lrows[i].end());
+  // level lists: forward (row i after its lower columns), backward (after
+  // its upper columns); rows stored slot by slot in level order
   std::vector<int> lev(n, 0);
   int nl = 0;
   for (int i = 0; i < n; ++i) {
     int v = 0;
-    for (int e = hf.l_ptr[i]; e < hf.l_ptr[i + 1]; ++e) v = std::max(v, lev[hf.l_col[e]] + 1);
+    for (auto& kv : Lrows[i]) v = std::max(v, lev[kv.first] + 1);
     lev[i] = v;
     nl = std::max(nl, v + 1);
   }
   std::vector<std::vector<int>> byl(nl);
   for (int i = 0; i < n; ++i) byl[lev[i]].push_back(i);
   hf.fl_ptr.push_back(0);
+  hf.l_ptr.push_back(0);
   for (auto& v : byl) {
-    for (int i : v) hf.fl_row.push_back(i);
+    for (int i : v) {
+      hf.fl_row.push_back(i);
+      for (auto& kv : Lrows[i]) {
+        hf.l_col.push_back(kv.first);
+        hf.l_val.push_back(kv.second);
+      }
+      hf.l_ptr.push_back((int32_t)hf.l_col.size());
+    }
     hf.fl_ptr.push_back((int32_t)hf.fl_row.size());
   }
   std::fill(lev.begin(), lev.end(), 0);
   nl = 0;
   for (int i = n - 1; i >= 0; --i) {
     int v = 0;
-    for (int e = hf.u_ptr[i]; e < hf.u_ptr[i + 1]; ++e) v = std::max(v, lev[hf.u_col[e]] + 1);
+    for (auto& kv : Urows[i]) v = std::max(v, lev[kv.first] + 1);
     lev[i] = v;
     nl = std::max(nl, v + 1);
   }
   std::vector<std::vector<int>> byb(nl);
   for (int i = 0; i < n; ++i) byb[lev[i]].push_back(i);
+  std::vector<double> dinv_row = hf.dinv;
+  hf.dinv.clear();
   hf.bl_ptr.push_back(0);
+  hf.u_ptr.push_back(0);
   for (auto& v : byb) {
-    for (int i : v) hf.bl_row.push_back(i);
+    for (int i : v) {
+      hf.bl_row.push_back(i);
+      hf.dinv.push_back(dinv_row[i]);
+      for (auto& kv : Urows[i]) {
+        hf.u_col.push_back(kv.first);
+        hf.u_val.push_back(kv.second);
+      }
+      hf.u_ptr.push_back((int32_t)hf.u_col.size());
+    }
     hf.bl_ptr.push_back((int32_t)hf.bl_row.size());
   }
   return true;
@@ -615,13 +630,14 @@ zbus_status upload_factor(zbus_nr_network net, const HostFactor& hf, Factor& f, 
   return ZBUS_OK;
 }
 
-size_t smem_bytes(int m) {
-  return sizeof(double) * ((size_t)(m + 1) * m + 2 * m + 2 * (m + 1) + (size_t)(m + 1) * NR_WARPS);
+size_t smem_bytes(int m, int N) {
+  return sizeof(double) *
+         ((size_t)(m + 1) * m + 2 * m + 2 * (m + 1) + (size_t)(m + 1) * NR_WARPS + N);
 }
 
 int64_t scratch_doubles(const zbus_nr_network net, int m) {
   const int64_t dim = net->nt + net->nq;
-  const int64_t s = 9 * (int64_t)net->N + 5 * dim + (int64_t)(m + 1) * dim;
+  const int64_t s = 8 * (int64_t)net->N + 5 * dim + (int64_t)(m + 1) * dim;
   return (s + 31) / 32 * 32;
 }
 
@@ -819,23 +835,26 @@ zbus_status zbus_nr_solve(zbus_nr_network net, int64_t B, const double* P, const
   if (dev != net->device) return fail(ZBUS_ERR_ARG, "current CUDA device differs from the network's");
   cudaStream_t st = (cudaStream_t)cuda_stream;
   const int m = o.gmres_restart;
-  const size_t smem = smem_bytes(m);
-  if (net->ctas_per_sm <= 1) {
+  const size_t smem = smem_bytes(m, net->N);
+  if (smem > 227 * 1024)
+    return fail(ZBUS_ERR_ARG, "grid too large for the per-CTA shared work space");
+  if (net->smem_set < smem) {
     ZB_CUDA(cudaFuncSetAttribute(k_nr_solve, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                 (int)smem_bytes(NR_MAX_RESTART_LEN)));
-    int per = 0;
-    ZB_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_nr_solve, NR_THREADS, smem));
-    net->ctas_per_sm = std::max(1, per);
+                                 (int)smem));
+    net->smem_set = smem;
   }
-  const int64_t ctas = std::min<int64_t>(B, (int64_t)net->sms * net->ctas_per_sm);
-  const int64_t stride = scratch_doubles(net, NR_MAX_RESTART_LEN);
-  if (net->scratch_ctas < ctas) {
+  int per = 0;
+  ZB_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_nr_solve, NR_THREADS, smem));
+  const int64_t ctas = std::min<int64_t>(B, (int64_t)net->sms * std::max(1, per));
+  const int64_t stride = scratch_doubles(net, m);
+  if (net->scratch_ctas < ctas || net->scratch_stride < stride) {
     ZB_CUDA(cudaStreamSynchronize(st));
     cudaFree(net->scratch);
     net->scratch = nullptr;
     net->scratch_ctas = 0;
     ZB_CUDA(cudaMalloc((void**)&net->scratch, (size_t)ctas * stride * sizeof(double)));
     net->scratch_ctas = ctas;
+    net->scratch_stride = stride;
   }
   NrDev d = net->dev;
   d.m = m;
