@@ -193,6 +193,8 @@ def run_reference(args):
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
         return
+    if args.workload.startswith("grid"):
+        return run_reference_nr(args, ws)
     from oracle import zbus_oracle as O
     from paper_2605_14103_gb300 import feeders as F
     workload = args.workload if args.workload in F.WORKLOADS else "feeder128_b4096"
@@ -218,6 +220,37 @@ def run_reference(args):
                       "scenarios_per_step": bs, "tol": wl.tol},
            "cpu_baseline": {"value": value, "unit": UNIT, "cores": cpu_cores(), "kind": "oracle",
                             "sample": f"{bs} scenarios of the {wl.B}-scenario batch per step"},
+           "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0,
+                   "d2h_bytes_per_step": 0}}
+    print(json.dumps(out), flush=True)
+
+
+def run_reference_nr(args, ws):
+    """The Newton-Raphson oracle on the host cores, a few scenarios per step."""
+    from oracle import nr_oracle as O
+    from paper_2605_14103_gb300 import grids as Gr
+    g, P, Q, wl = Gr.make_grid_workload(args.workload)
+    Y = O.dense_Y(g.N, g.Y_row, g.Y_col, g.Y_val)
+    per = max(1, min(wl.B, int(2000 // g.N)))   # scenarios per step (bounded CPU time)
+    for s in range(args.warmup):
+        O.newton(Y, g.bus_type, g.v_set, P[s % wl.B], Q[s % wl.B], wl.tol, wl.max_iter)
+    times, solved = [], 0
+    for s in range(args.steps):
+        t0 = time.perf_counter()
+        for k in range(per):
+            b = (s * per + k) % wl.B
+            solved += O.newton(Y, g.bus_type, g.v_set, P[b], Q[b], wl.tol, wl.max_iter)[2]
+        times.append(time.perf_counter() - t0)
+    value = solved / sum(times)
+    out = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT,
+           "n_gpus": ws, "steps": args.steps, "warmup": args.warmup,
+           "ms_per_step": 1e3 * sum(times) / args.steps, "higher_is_better": True,
+           "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+           "config": {"workload": args.workload, "buses": g.N, "scenarios_per_step": per,
+                      "tol": wl.tol},
+           "cpu_baseline": {"value": value, "unit": UNIT, "cores": cpu_cores(), "kind": "oracle",
+                            "sample": f"{per} scenarios of the {wl.B}-scenario batch per step "
+                                      "(dense Newton-Raphson)"},
            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0,
                    "d2h_bytes_per_step": 0}}
     print(json.dumps(out), flush=True)
@@ -710,10 +743,164 @@ def run_serve(args):
     print(json.dumps(out), flush=True)
 
 
+# ---------------------------------------------------------------------------
+# transmission grids: batched Newton-Raphson (Sec. II-A)
+# ---------------------------------------------------------------------------
+NR_MISMATCH_OK = 1e-9
+
+
+def nr_cpu_mismatch(g, V, P, Q):
+    """max |F_b| of every scenario from the GPU voltages, sparse Y on the CPU
+    (outside the timed region)."""
+    import scipy.sparse as sp
+    Y = sp.csr_matrix((g.Y_val, (g.Y_row, g.Y_col)), shape=(g.N, g.N))
+    S = V * np.conj((Y @ V.T).T)
+    th = np.nonzero(g.bus_type != 2)[0]
+    q = np.nonzero(g.bus_type == 0)[0]
+    F = np.concatenate([S.real[:, th] - P[:, th], S.imag[:, q] - Q[:, q]], axis=1)
+    return np.abs(F).max(axis=1)
+
+
+def nr_flops(g, info, iters, gmres):
+    """Algorithmic FP64 flops of the solves (estimate from the step counts):
+    mismatch per Newton step 8 nnz(Y) + 12 N; per GMRES iteration the
+    Jacobian-vector product (8 nnz(Y) + 14 N), the preconditioner (2 nnz of
+    the factors + 2 nnz(G) + 2 dim), Gram-Schmidt twice over j vectors
+    (8 j dim, j = 1 .. the iterations of that Newton step) and a norm."""
+    nnzY = int(g.Y_val.size)
+    nt, nq, fnnz, _ = info
+    dim = nt + nq
+    nnzG = nnzY   # bound: G is a sub-block of Re(Y)
+    per_gm = 8 * nnzY + 14 * g.N + 2 * fnnz + 2 * nnzG + 2 * dim + 4 * dim
+    tot = 0.0
+    for k, gm in zip(iters, gmres):
+        k = max(int(k), 1)
+        j = gm / k
+        tot += (k + 1) * (8 * nnzY + 12 * g.N) + gm * per_gm + k * 8 * dim * j * (j + 1) / 2
+    return tot
+
+
+def run_nr(args):
+    import torch
+    import __graft_entry__
+    __graft_entry__.build()
+    from paper_2605_14103_gb300 import grids as Gr
+    from paper_2605_14103_gb300 import zbus
+    ws, rank, local = dist_setup()
+    torch.cuda.set_device(local)
+    g, _, _, wl = Gr.make_grid_workload(args.workload, B=1)
+    B = args.batch if args.batch > 0 else wl.B
+    from paper_2605_14103_gb300 import dist as D
+    P_h, Q_h = Gr.make_injections(g, B, seed=D.rank_seed(g.seed + 1, rank))
+    P, Q = torch.from_numpy(P_h).cuda(), torch.from_numpy(Q_h).cuda()
+    net = zbus.NrNetwork.from_grid(g)
+    info = net.info()
+    flush = torch.empty(512 * 1024 * 1024, dtype=torch.uint8, device="cuda")
+    out = (torch.empty((B, g.N), dtype=torch.complex128, device="cuda"),
+           torch.empty((B,), dtype=torch.int32, device="cuda"),
+           torch.empty((B,), dtype=torch.uint8, device="cuda"),
+           torch.empty((B,), dtype=torch.int32, device="cuda"))
+
+    def solve():
+        net.solve(P, Q, tol=wl.tol, max_iter=wl.max_iter, out=out)
+
+    for _ in range(max(3, args.warmup)):
+        solve()
+    torch.cuda.synchronize()
+    clocks = Clocks(torch.cuda.current_device()) if rank == 0 else None
+    if clocks:
+        clocks.start()
+    barrier(ws)
+    ms = _timed(solve, args.steps, flush)
+    barrier(ws)
+    clk = clocks.stop() if clocks else None
+    V, it, cv, gm = (x.cpu().numpy() for x in out)
+    mm = nr_cpu_mismatch(g, V, P_h, Q_h)
+    good = int(((cv == 1) & (mm <= NR_MISMATCH_OK)).sum())
+    t_max = allreduce_max(sum(ms) / 1e3, ws)
+    value = allreduce_sum(good, ws) * args.steps / t_max
+    t_step = statistics.median(ms) / 1e3
+    flops = nr_flops(g, info, it, gm)
+    ach = flops / t_step / 1e12
+    roof = {"bound": "alu", "achieved": ach, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
+            "frac": ach / FP64_PEAK_TFLOPS, "kernel": "k_nr_solve", "traffic": None,
+            "peak_src": "nominal FP64 1.25 TFLOP/s (DFMA probe: 1.197 measured)",
+            "note": "one CTA per scenario; bound by the latency of the level-by-level "
+                    "triangular solves and block barriers, not by a pipe"}
+
+    # end to end through the binding: pinned host injections in, voltages,
+    # counts and flags out, inside the timed region
+    P_p, Q_p = torch.from_numpy(P_h).pin_memory(), torch.from_numpy(Q_h).pin_memory()
+    V_p = torch.empty((B, g.N), dtype=torch.complex128).pin_memory()
+    it_p = torch.empty((B,), dtype=torch.int32).pin_memory()
+    cv_p = torch.empty((B,), dtype=torch.uint8).pin_memory()
+
+    def e2e():
+        P.copy_(P_p, non_blocking=True)
+        Q.copy_(Q_p, non_blocking=True)
+        solve()
+        V_p.copy_(out[0], non_blocking=True)
+        it_p.copy_(out[1], non_blocking=True)
+        cv_p.copy_(out[2], non_blocking=True)
+
+    for _ in range(2):
+        e2e()
+    torch.cuda.synchronize()
+    ms2 = _timed(e2e, args.steps, flush)
+    e2e_val = allreduce_sum(int(cv_p.numpy().sum()), ws) * args.steps / \
+        allreduce_max(sum(ms2) / 1e3, ws)
+
+    cpu, parity = None, None
+    if rank == 0 and ws == 1 and not args.no_cpu_baseline:
+        from oracle import nr_oracle as O
+        Y = O.dense_Y(g.N, g.Y_row, g.Y_col, g.Y_val)
+        t0, k, solved = time.perf_counter(), 0, 0
+        dv, flags_eq, it_ok = 0.0, True, True
+        while (time.perf_counter() - t0 < args.cpu_seconds or k == 0) and k < B:
+            Vo, ito, cvo = O.newton(Y, g.bus_type, g.v_set, P_h[k], Q_h[k], wl.tol, wl.max_iter)
+            solved += int(cvo)
+            flags_eq &= bool(cvo == cv[k])
+            if cvo:
+                dv = max(dv, float(np.abs(V[k] - Vo).max()))
+                it_ok &= abs(int(ito) - int(it[k])) <= 1
+            k += 1
+        t_cpu = time.perf_counter() - t0
+        cpu = {"value": solved / t_cpu, "unit": UNIT, "cores": cpu_cores(), "kind": "oracle",
+               "sample": f"first {k} scenarios of the {B}-scenario batch, one after another "
+                         f"(dense Newton-Raphson, numpy BLAS threads; {t_cpu:.1f} s)"}
+        parity = {"sampled": k, "max_dv_vs_oracle": dv, "flags_equal": flags_eq,
+                  "newton_steps_within_one": it_ok}
+    if rank == 0:
+        line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws,
+                "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * t_max / args.steps,
+                "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+                "data": "synthetic",
+                "config": {"workload": args.workload, "method": "batched Newton-Raphson, "
+                           "preconditioned GMRES (Sec. II-A)", "buses": g.N,
+                           "branches": g.n_branch, "scenarios_per_gpu": B, "tol": wl.tol,
+                           "max_iter": wl.max_iter, "gmres": "restart 30, tol 1e-6",
+                           "l2": "flushed between steps (512 MiB write)",
+                           "parallelism": f"replicas x{ws}"},
+                "converged_per_step": good, "newton_steps_mean": float(it.mean()),
+                "gmres_iters_mean": float(gm.mean()), "max_mismatch": float(mm.max()),
+                "factor": {"n_theta": info[0], "n_q": info[1], "nnz": info[2],
+                           "levels": info[3]},
+                "gpu_launches": args.steps, "roofline": roof,
+                "latency": {"p50_ms": statistics.median(ms),
+                            "p99_ms": float(np.percentile(ms, 99)),
+                            "per": f"solve of {B} scenarios"},
+                "e2e": {"value": e2e_val, "unit": UNIT, "h2d_bytes_per_step": 2 * B * g.N * 8,
+                        "d2h_bytes_per_step": B * g.N * 16 + B * 5},
+                "clocks": clk, "cpu_baseline": cpu, "parity": parity}
+        print(json.dumps(line), flush=True)
+
+
 def main():
     args = parse()
     if args.impl == "reference":
         run_reference(args)
+    elif args.workload.startswith("grid"):
+        run_nr(args)
     elif args.workload == "hetero64":
         run_hetero(args)
     elif args.workload == "serve16":

@@ -528,9 +528,11 @@ zbus_status zbus_nr_network_info(zbus_nr_network net, int32_t* n_theta, int32_t*
  *   cuda_stream  all work is enqueued on this stream
  *
  * Each scenario is solved by one CTA from start to stop (no host round trip
- * per step).  Scratch (about (66 dim + 9 N) doubles per resident CTA, dim =
- * n_theta + n_q) grows on demand with a synchronous allocation.  Device
- * buffers only.  B = 0 is a no-op.
+ * per step).  Scratch ((gmres_restart + 6) dim + 9 N doubles per resident
+ * CTA, dim = n_theta + n_q; up to eight CTAs per SM) grows on demand with a
+ * synchronous allocation.  Device buffers only.  B = 0 is a no-op.  Returns
+ * ZBUS_ERR_ARG for a grid whose per-CTA shared work space (N + a few
+ * (gmres_restart + 1)^2 doubles) exceeds 227 KB (N above about 27000).
  */
 zbus_status zbus_nr_solve(zbus_nr_network net, int64_t B, const double* P, const double* Q,
                           double tol, int32_t max_iter, const zbus_nr_opts* opts,

@@ -176,33 +176,33 @@ __device__ void factor_solve(const Factor& f, const double* in, double* y, doubl
   __syncthreads();
 }
 
-// z = M^-1 r (eqs. 8-9).  tmp: dim doubles, y: max(nt, nq) doubles.
-__device__ void precondition(const NrDev& d, const double* vm, const double* r, double* z,
+// z = M^-1 r (eqs. 8-9).  ivm = 1 / |V|; tmp: dim doubles, y: max(nt, nq) doubles.
+__device__ void precondition(const NrDev& d, const double* ivm, const double* r, double* z,
                              double* tmp, double* y) {
   const int t = threadIdx.x;
-  for (int p = t; p < d.nt; p += NR_THREADS) tmp[p] = r[p] / vm[d.t_bus[p]];
+  for (int p = t; p < d.nt; p += NR_THREADS) tmp[p] = r[p] * ivm[d.t_bus[p]];
   __syncthreads();
   factor_solve(d.Bp, tmp, y, z);
   if (d.nq > 0) {
     for (int p = t; p < d.nq; p += NR_THREADS) {
       double s = r[d.nt + p];
       for (int e = d.g_ptr[p]; e < d.g_ptr[p + 1]; ++e) s -= d.g_val[e] * z[d.g_col[e]];
-      tmp[d.nt + p] = s / vm[d.q_bus[p]];
+      tmp[d.nt + p] = s * ivm[d.q_bus[p]];
     }
     __syncthreads();
     factor_solve(d.Bpp, tmp + d.nt, y, z + d.nt);
   }
 }
 
-// out = J u, the Jacobian of F at V (I = Y V) applied to u (dim).
+// out = J u, the Jacobian of F at V (I = Y V) applied to u (dim); ivm = 1 / |V|.
 __device__ void jvp(const NrDev& d, const double* Vr, const double* Vi, const double* Ir,
-                    const double* Ii, const double* vm, const double* u, double* dVr,
+                    const double* Ii, const double* ivm, const double* u, double* dVr,
                     double* dVi, double* out) {
   const int t = threadIdx.x;
   for (int i = t; i < d.N; i += NR_THREADS) {
     const int pt = d.pos_t[i], pq = d.pos_q[i];
     const double dth = pt >= 0 ? u[pt] : 0.0;
-    const double a = pq >= 0 ? u[d.nt + pq] / vm[i] : 0.0;
+    const double a = pq >= 0 ? u[d.nt + pq] * ivm[i] : 0.0;
     dVr[i] = Vr[i] * a - Vi[i] * dth;
     dVi[i] = Vi[i] * a + Vr[i] * dth;
   }
@@ -267,7 +267,8 @@ __global__ void __launch_bounds__(NR_THREADS, NR_MIN_CTAS) k_nr_solve(NrDev d, S
   double* va = vm + N;
   double* dVr = va + N;
   double* dVi = dVr + N;
-  double* F = dVi + N;                     // dim
+  double* ivm = dVi + N;                   // N, 1 / |V| of the current iterate
+  double* F = ivm + N;                     // dim
   double* bv = F + dim;
   double* x = bv + dim;
   double* wv = x + dim;
@@ -290,6 +291,7 @@ __global__ void __launch_bounds__(NR_THREADS, NR_MIN_CTAS) k_nr_solve(NrDev d, S
         sincos(va[i], &s, &c);
         Vr[i] = vm[i] * c;
         Vi[i] = vm[i] * s;
+        ivm[i] = 1.0 / vm[i];
       }
       __syncthreads();
       double fmax = 0.0;
@@ -331,7 +333,7 @@ __global__ void __launch_bounds__(NR_THREADS, NR_MIN_CTAS) k_nr_solve(NrDev d, S
         x[e] = 0.0;
       }
       __syncthreads();
-      precondition(d, vm, wv, bv, tmp, y);
+      precondition(d, ivm, wv, bv, tmp, y);
       double nb = 0.0;
       for (int e = t; e < dim; e += NR_THREADS) nb += bv[e] * bv[e];
       const double beta0 = sqrt(block_sum(nb, red));
@@ -339,8 +341,8 @@ __global__ void __launch_bounds__(NR_THREADS, NR_MIN_CTAS) k_nr_solve(NrDev d, S
       for (int rs = 0; rs < a.max_restart && !done; ++rs) {
         // r = b - A x (x = 0 on the first pass)
         if (rs > 0) {
-          jvp(d, Vr, Vi, Ir, Ii, vm, x, dVr, dVi, tmp);
-          precondition(d, vm, tmp, wv, F, y);   // F is free now: work space
+          jvp(d, Vr, Vi, Ir, Ii, ivm, x, dVr, dVi, tmp);
+          precondition(d, ivm, tmp, wv, F, y);   // F is free now: work space
           for (int e = t; e < dim; e += NR_THREADS) Vk[e] = bv[e] - wv[e];
         } else {
           for (int e = t; e < dim; e += NR_THREADS) Vk[e] = bv[e];
@@ -349,7 +351,8 @@ __global__ void __launch_bounds__(NR_THREADS, NR_MIN_CTAS) k_nr_solve(NrDev d, S
         for (int e = t; e < dim; e += NR_THREADS) nr += Vk[e] * Vk[e];
         const double beta = sqrt(block_sum(nr, red));
         if (!(beta > a.eta * beta0)) break;
-        for (int e = t; e < dim; e += NR_THREADS) Vk[e] /= beta;
+        const double ib = 1.0 / beta;
+        for (int e = t; e < dim; e += NR_THREADS) Vk[e] *= ib;
         if (t == 0) {
           gv[0] = beta;
           s_jd = 0;
@@ -358,8 +361,8 @@ __global__ void __launch_bounds__(NR_THREADS, NR_MIN_CTAS) k_nr_solve(NrDev d, S
         __syncthreads();
         for (int j = 0; j < m; ++j) {
           double* vj = Vk + (int64_t)j * dim;
-          jvp(d, Vr, Vi, Ir, Ii, vm, vj, dVr, dVi, tmp);
-          precondition(d, vm, tmp, wv, F, y);   // F doubles as work space
+          jvp(d, Vr, Vi, Ir, Ii, ivm, vj, dVr, dVi, tmp);
+          precondition(d, ivm, tmp, wv, F, y);   // F doubles as work space
           // classical Gram-Schmidt, twice
           for (int i = t; i <= j; i += NR_THREADS) H[j * (m + 1) + i] = 0.0;
           __syncthreads();
@@ -637,7 +640,7 @@ size_t smem_bytes(int m, int N) {
 
 int64_t scratch_doubles(const zbus_nr_network net, int m) {
   const int64_t dim = net->nt + net->nq;
-  const int64_t s = 8 * (int64_t)net->N + 5 * dim + (int64_t)(m + 1) * dim;
+  const int64_t s = 9 * (int64_t)net->N + 5 * dim + (int64_t)(m + 1) * dim;
   return (s + 31) / 32 * 32;
 }
 
