@@ -801,19 +801,34 @@ def run_nr(args):
            torch.empty((B,), dtype=torch.uint8, device="cuda"),
            torch.empty((B,), dtype=torch.int32, device="cuda"))
 
-    def solve():
-        net.solve(P, Q, tol=wl.tol, max_iter=wl.max_iter, out=out)
+    prec = args.precision if args.precision in ("fp64", "mixed") else "fp64"
 
-    for _ in range(max(3, args.warmup)):
-        solve()
-    torch.cuda.synchronize()
+    def solve(p=None):
+        net.solve(P, Q, tol=wl.tol, max_iter=wl.max_iter, precision=p or prec, out=out)
+
     clocks = Clocks(torch.cuda.current_device()) if rank == 0 else None
     if clocks:
         clocks.start()
-    barrier(ws)
-    ms = _timed(solve, args.steps, flush)
-    barrier(ws)
+    # the other arithmetic form of the Newton direction, for comparison
+    forms = {}
+    for p in [x for x in ("fp64", "mixed") if x != prec] + [prec]:
+        for _ in range(max(3, args.warmup)):
+            solve(p)
+        torch.cuda.synchronize()
+        barrier(ws)
+        msp = _timed(lambda: solve(p), args.steps if p == prec else max(3, args.steps // 2), flush)
+        barrier(ws)
+        Vp, itp, cvp, gmp = (x.cpu().numpy() for x in out)
+        mmp = nr_cpu_mismatch(g, Vp, P_h, Q_h)
+        goodp = int(((cvp == 1) & (mmp <= NR_MISMATCH_OK)).sum())
+        forms[p] = {"value": goodp / (statistics.median(msp) / 1e3),
+                    "ms_per_step": statistics.median(msp), "converged_per_step": goodp,
+                    "newton_steps_mean": float(itp.mean()), "gmres_iters_mean": float(gmp.mean()),
+                    "max_mismatch": float(mmp.max())}
+        ms = msp
     clk = clocks.stop() if clocks else None
+    for p in forms:
+        forms[p]["vs_fp64"] = forms[p]["value"] / forms["fp64"]["value"]
     V, it, cv, gm = (x.cpu().numpy() for x in out)
     mm = nr_cpu_mismatch(g, V, P_h, Q_h)
     good = int(((cv == 1) & (mm <= NR_MISMATCH_OK)).sum())
@@ -823,7 +838,7 @@ def run_nr(args):
     flops = nr_flops(g, info, it, gm)
     ach = flops / t_step / 1e12
     roof = {"bound": "alu", "achieved": ach, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
-            "frac": ach / FP64_PEAK_TFLOPS, "kernel": "k_nr_solve", "traffic": None,
+            "frac": ach / FP64_PEAK_TFLOPS, "kernel": f"k_nr_solve<{prec}>", "traffic": None,
             "peak_src": "nominal FP64 1.25 TFLOP/s (DFMA probe: 1.197 measured)",
             "note": "one CTA per scenario; bound by the latency of the level-by-level "
                     "triangular solves and block barriers, not by a pipe"}
@@ -834,6 +849,8 @@ def run_nr(args):
     V_p = torch.empty((B, g.N), dtype=torch.complex128).pin_memory()
     it_p = torch.empty((B,), dtype=torch.int32).pin_memory()
     cv_p = torch.empty((B,), dtype=torch.uint8).pin_memory()
+
+    dtype_line = "f64" if prec == "fp64" else "f32+f64"
 
     def e2e():
         P.copy_(P_p, non_blocking=True)
@@ -873,14 +890,15 @@ def run_nr(args):
     if rank == 0:
         line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws,
                 "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * t_max / args.steps,
-                "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
-                "data": "synthetic",
+                "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+                "dtype": dtype_line, "data": "synthetic",
                 "config": {"workload": args.workload, "method": "batched Newton-Raphson, "
                            "preconditioned GMRES (Sec. II-A)", "buses": g.N,
                            "branches": g.n_branch, "scenarios_per_gpu": B, "tol": wl.tol,
-                           "max_iter": wl.max_iter, "gmres": "restart 30, tol 1e-6",
+                           "max_iter": wl.max_iter, "gmres": "restart 30, tol 1e-6", "precision": prec,
                            "l2": "flushed between steps (512 MiB write)",
                            "parallelism": f"replicas x{ws}"},
+                "precision": prec, "forms": forms,
                 "converged_per_step": good, "newton_steps_mean": float(it.mean()),
                 "gmres_iters_mean": float(gm.mean()), "max_mismatch": float(mm.max()),
                 "factor": {"n_theta": info[0], "n_q": info[1], "nnz": info[2],

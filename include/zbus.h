@@ -466,13 +466,22 @@ zbus_status zbus_last_device_status(zbus_network net, void* cuda_stream);
  * ------------------------------------------------------------------------ */
 typedef struct zbus_nr_network_s* zbus_nr_network;
 
+/* Arithmetic of the Newton direction.  ZBUS_NR_FP64: everything in FP64
+ * (the paper's solver).  ZBUS_NR_MIXED: GMRES, the Jacobian-vector products
+ * and the preconditioner in FP32 (dot products summed in FP64), while the
+ * mismatch, the state update and the stop test stay FP64: the direction is
+ * an inexact Newton step, the converged solution that of F = 0 in FP64. */
+typedef enum { ZBUS_NR_FP64 = 0, ZBUS_NR_MIXED = 1 } zbus_nr_precision;
+
 typedef struct {
   int32_t gmres_restart;      /* Krylov vectors per GMRES cycle, 1 .. 60 (default 30) */
   int32_t gmres_max_restarts; /* GMRES cycles per Newton step, >= 1 (default 4) */
   double gmres_tol;           /* stop a Newton step's GMRES when the preconditioned
                                  residual is below gmres_tol times its start, (0, 1)
                                  (default 1e-6) */
-  double reserved[4];
+  int32_t precision;          /* zbus_nr_precision (default ZBUS_NR_FP64) */
+  int32_t reserved0;
+  double reserved[3];
 } zbus_nr_opts;
 
 /* Fill *opts with the defaults above. */

@@ -58,6 +58,9 @@ struct Factor {
   int32_t* u_col = nullptr;
   double* u_val = nullptr;
   double* dinv = nullptr;
+  float* l_val_f = nullptr;   // FP32 copies of the values (mixed form)
+  float* u_val_f = nullptr;
+  float* dinv_f = nullptr;
   int32_t* fl_ptr = nullptr;  // forward levels: slots fl_ptr[l] .. fl_ptr[l+1]
   int32_t* fl_row = nullptr;
   int32_t* bl_ptr = nullptr;  // backward levels
@@ -81,6 +84,8 @@ struct NrDev {
   const int32_t* g_ptr;   // G_Q,Theta CSR: rows = Q positions, cols = Theta positions
   const int32_t* g_col;
   const double* g_val;
+  const float2* y_val_f;  // FP32 copies (mixed form)
+  const float* g_val_f;
   Factor Bp, Bpp;
   double* scratch;
   int64_t stride;         // doubles of scratch per CTA
@@ -98,7 +103,7 @@ struct zbus_nr_network_s {
   double* scratch = nullptr;
   int64_t scratch_ctas = 0;
   int64_t scratch_stride = 0;
-  size_t smem_set = 0;
+  size_t smem_set[2] = {0, 0};
   int sms = 1;
 };
 
@@ -145,18 +150,45 @@ __device__ double block_max(double v, double* red) {
   return s;
 }
 
+// Values in the Krylov precision T: FP64 (the paper's solver) or FP32 (the
+// mixed form, whose Newton direction is found in FP32 while the mismatch,
+// the state and the stop test stay FP64).
+template <class T> struct Cx;
+template <> struct Cx<double> { using type = double2; };
+template <> struct Cx<float> { using type = float2; };
+
+template <class T> __device__ __forceinline__ const T* lval(const Factor& f);
+template <> __device__ __forceinline__ const double* lval<double>(const Factor& f) { return f.l_val; }
+template <> __device__ __forceinline__ const float* lval<float>(const Factor& f) { return f.l_val_f; }
+template <class T> __device__ __forceinline__ const T* uval(const Factor& f);
+template <> __device__ __forceinline__ const double* uval<double>(const Factor& f) { return f.u_val; }
+template <> __device__ __forceinline__ const float* uval<float>(const Factor& f) { return f.u_val_f; }
+template <class T> __device__ __forceinline__ const T* dval(const Factor& f);
+template <> __device__ __forceinline__ const double* dval<double>(const Factor& f) { return f.dinv; }
+template <> __device__ __forceinline__ const float* dval<float>(const Factor& f) { return f.dinv_f; }
+template <class T> __device__ __forceinline__ const T* gval(const NrDev& d);
+template <> __device__ __forceinline__ const double* gval<double>(const NrDev& d) { return d.g_val; }
+template <> __device__ __forceinline__ const float* gval<float>(const NrDev& d) { return d.g_val_f; }
+template <class T> __device__ __forceinline__ const typename Cx<T>::type* yval(const NrDev& d);
+template <> __device__ __forceinline__ const double2* yval<double>(const NrDev& d) { return d.y_val; }
+template <> __device__ __forceinline__ const float2* yval<float>(const NrDev& d) { return d.y_val_f; }
+
 // Solve (P A P^T) with its LU factors: out[perm[i]] = (U^-1 L^-1 (in o perm))_i.
 // in / out indexed by block position; y is factor-order work space.
-__device__ void factor_solve(const Factor& f, const double* in, double* y, double* out) {
+template <class T>
+__device__ void factor_solve(const Factor& f, const T* in, T* y, T* out) {
   const int t = threadIdx.x;
+  const T* lv = lval<T>(f);
+  const T* uv = uval<T>(f);
+  const T* dv = dval<T>(f);
   for (int i = t; i < f.n; i += NR_THREADS) y[i] = in[f.perm[i]];
   __syncthreads();
   for (int l = 0; l < f.n_fl; ++l) {
     for (int k = f.fl_ptr[l] + t; k < f.fl_ptr[l + 1]; k += NR_THREADS) {
       const int i = f.fl_row[k];
       const int e0 = f.l_ptr[k], e1 = f.l_ptr[k + 1];
-      double s = y[i];
-      for (int e = e0; e < e1; ++e) s -= f.l_val[e] * y[f.l_col[e]];
+      T s = y[i];
+      for (int e = e0; e < e1; ++e) s -= lv[e] * y[f.l_col[e]];
       y[i] = s;
     }
     __syncthreads();
@@ -165,9 +197,9 @@ __device__ void factor_solve(const Factor& f, const double* in, double* y, doubl
     for (int k = f.bl_ptr[l] + t; k < f.bl_ptr[l + 1]; k += NR_THREADS) {
       const int i = f.bl_row[k];
       const int e0 = f.u_ptr[k], e1 = f.u_ptr[k + 1];
-      const double di = f.dinv[k];
-      double s = y[i];
-      for (int e = e0; e < e1; ++e) s -= f.u_val[e] * y[f.u_col[e]];
+      const T di = dv[k];
+      T s = y[i];
+      for (int e = e0; e < e1; ++e) s -= uv[e] * y[f.u_col[e]];
       y[i] = s * di;
     }
     __syncthreads();
@@ -176,33 +208,35 @@ __device__ void factor_solve(const Factor& f, const double* in, double* y, doubl
   __syncthreads();
 }
 
-// z = M^-1 r (eqs. 8-9).  ivm = 1 / |V|; tmp: dim doubles, y: max(nt, nq) doubles.
-__device__ void precondition(const NrDev& d, const double* ivm, const double* r, double* z,
-                             double* tmp, double* y) {
+// z = M^-1 r (eqs. 8-9).  ivm = 1 / |V|; tmp: dim values, y: max(nt, nq) values.
+template <class T>
+__device__ void precondition(const NrDev& d, const T* ivm, const T* r, T* z, T* tmp, T* y) {
   const int t = threadIdx.x;
   for (int p = t; p < d.nt; p += NR_THREADS) tmp[p] = r[p] * ivm[d.t_bus[p]];
   __syncthreads();
-  factor_solve(d.Bp, tmp, y, z);
+  factor_solve<T>(d.Bp, tmp, y, z);
   if (d.nq > 0) {
+    const T* gv = gval<T>(d);
     for (int p = t; p < d.nq; p += NR_THREADS) {
-      double s = r[d.nt + p];
-      for (int e = d.g_ptr[p]; e < d.g_ptr[p + 1]; ++e) s -= d.g_val[e] * z[d.g_col[e]];
+      T s = r[d.nt + p];
+      for (int e = d.g_ptr[p]; e < d.g_ptr[p + 1]; ++e) s -= gv[e] * z[d.g_col[e]];
       tmp[d.nt + p] = s * ivm[d.q_bus[p]];
     }
     __syncthreads();
-    factor_solve(d.Bpp, tmp + d.nt, y, z + d.nt);
+    factor_solve<T>(d.Bpp, tmp + d.nt, y, z + d.nt);
   }
 }
 
 // out = J u, the Jacobian of F at V (I = Y V) applied to u (dim); ivm = 1 / |V|.
-__device__ void jvp(const NrDev& d, const double* Vr, const double* Vi, const double* Ir,
-                    const double* Ii, const double* ivm, const double* u, double* dVr,
-                    double* dVi, double* out) {
+template <class T>
+__device__ void jvp(const NrDev& d, const T* Vr, const T* Vi, const T* Ir, const T* Ii,
+                    const T* ivm, const T* u, T* dVr, T* dVi, T* out) {
   const int t = threadIdx.x;
+  const typename Cx<T>::type* yv = yval<T>(d);
   for (int i = t; i < d.N; i += NR_THREADS) {
     const int pt = d.pos_t[i], pq = d.pos_q[i];
-    const double dth = pt >= 0 ? u[pt] : 0.0;
-    const double a = pq >= 0 ? u[d.nt + pq] * ivm[i] : 0.0;
+    const T dth = pt >= 0 ? u[pt] : T(0);
+    const T a = pq >= 0 ? u[d.nt + pq] * ivm[i] : T(0);
     dVr[i] = Vr[i] * a - Vi[i] * dth;
     dVi[i] = Vi[i] * a + Vr[i] * dth;
   }
@@ -210,16 +244,16 @@ __device__ void jvp(const NrDev& d, const double* Vr, const double* Vi, const do
   for (int i = t; i < d.N; i += NR_THREADS) {
     const int pt = d.pos_t[i], pq = d.pos_q[i];
     if (pt < 0 && pq < 0) continue;
-    double yr = 0.0, yi = 0.0;
+    T yr = 0, yi = 0;
     for (int e = d.y_ptr[i]; e < d.y_ptr[i + 1]; ++e) {
-      const double2 y = d.y_val[e];
+      const auto y = yv[e];
       const int j = d.y_col[e];
       yr += y.x * dVr[j] - y.y * dVi[j];
       yi += y.x * dVi[j] + y.y * dVr[j];
     }
     // dS = dV conj(I) + V conj(Y dV)
-    const double sr = dVr[i] * Ir[i] + dVi[i] * Ii[i] + Vr[i] * yr + Vi[i] * yi;
-    const double si = dVi[i] * Ir[i] - dVr[i] * Ii[i] + Vi[i] * yr - Vr[i] * yi;
+    const T sr = dVr[i] * Ir[i] + dVi[i] * Ii[i] + Vr[i] * yr + Vi[i] * yi;
+    const T si = dVi[i] * Ir[i] - dVr[i] * Ii[i] + Vi[i] * yr - Vr[i] * yi;
     if (pt >= 0) out[pt] = sr;
     if (pq >= 0) out[d.nt + pq] = si;
   }
@@ -243,7 +277,20 @@ struct SolveArgs {
   int32_t* gmres;
 };
 
+// Per-CTA scratch: the FP64 state (7 N + dim doubles), then the Krylov-
+// precision arrays (FP32 copies of V, I, 1/|V| for the mixed form; dV;
+// right-hand side, solution, work vectors; the basis).
+__host__ __device__ constexpr int64_t state_doubles(int64_t N, int64_t dim) {
+  return 7 * N + dim;
+}
+template <class T>
+__host__ __device__ constexpr int64_t krylov_values(int64_t N, int64_t dim, int m) {
+  return (sizeof(T) == 4 ? 5 * N : 0) + 2 * N + 5 * dim + (int64_t)(m + 1) * dim;
+}
+
+template <class T>
 __global__ void __launch_bounds__(NR_THREADS, NR_MIN_CTAS) k_nr_solve(NrDev d, SolveArgs a) {
+  constexpr bool MIXED = sizeof(T) == 4;
   extern __shared__ double sm[];
   const int m = d.m;
   double* H = sm;                          // [(m + 1) * m], column j at H[j * (m + 1)]
@@ -252,7 +299,7 @@ __global__ void __launch_bounds__(NR_THREADS, NR_MIN_CTAS) k_nr_solve(NrDev d, S
   double* gv = sn + m;                     // [m + 1]
   double* hh = gv + m + 1;                 // [m + 1] this step's Gram-Schmidt coefficients
   double* red = hh + m + 1;                // [(m + 1) * NR_WARPS]
-  double* y = red + (m + 1) * NR_WARPS;    // [N] factor work space (the levels' reads)
+  T* y = reinterpret_cast<T*>(red + (m + 1) * NR_WARPS);   // [N] factor work space
   __shared__ int s_flag;
   __shared__ int s_jd;
 
@@ -265,15 +312,32 @@ __global__ void __launch_bounds__(NR_THREADS, NR_MIN_CTAS) k_nr_solve(NrDev d, S
   double* Ii = Ir + N;
   double* vm = Ii + N;
   double* va = vm + N;
-  double* dVr = va + N;
-  double* dVi = dVr + N;
-  double* ivm = dVi + N;                   // N, 1 / |V| of the current iterate
+  double* ivm = va + N;                    // N, 1 / |V| of the current iterate
   double* F = ivm + N;                     // dim
-  double* bv = F + dim;
-  double* x = bv + dim;
-  double* wv = x + dim;
-  double* tmp = wv + dim;
-  double* Vk = tmp + dim;                  // basis, (m + 1) * dim
+  T* kb = reinterpret_cast<T*>(F + dim);
+  const T *VrT, *ViT, *IrT, *IiT, *ivmT;   // the state in the Krylov precision
+  T *VrW = nullptr, *ViW = nullptr, *IrW = nullptr, *IiW = nullptr, *ivmW = nullptr;
+  if constexpr (MIXED) {
+    VrW = kb;
+    ViW = VrW + N;
+    IrW = ViW + N;
+    IiW = IrW + N;
+    ivmW = IiW + N;
+    kb = ivmW + N;
+    VrT = VrW, ViT = ViW, IrT = IrW, IiT = IiW, ivmT = ivmW;
+  } else {
+    VrT = reinterpret_cast<const T*>(Vr), ViT = reinterpret_cast<const T*>(Vi);
+    IrT = reinterpret_cast<const T*>(Ir), IiT = reinterpret_cast<const T*>(Ii);
+    ivmT = reinterpret_cast<const T*>(ivm);
+  }
+  T* dVr = kb;
+  T* dVi = dVr + N;
+  T* bv = dVi + N;
+  T* x = bv + dim;
+  T* wv = x + dim;
+  T* tmp = wv + dim;
+  T* work = tmp + dim;
+  T* Vk = work + dim;                      // basis, (m + 1) * dim
 
   for (int b = blockIdx.x; b < a.B; b += gridDim.x) {
     const double* P = a.P + (int64_t)b * N;
@@ -285,13 +349,18 @@ __global__ void __launch_bounds__(NR_THREADS, NR_MIN_CTAS) k_nr_solve(NrDev d, S
     int gm_total = 0, it = 0, ok = 0;
     __syncthreads();
     for (int k = 0;; ++k) {
-      // V, I = Y V, mismatch F and its max
+      // V, I = Y V, mismatch F and its max (FP64)
       for (int i = t; i < N; i += NR_THREADS) {
         double s, c;
         sincos(va[i], &s, &c);
         Vr[i] = vm[i] * c;
         Vi[i] = vm[i] * s;
         ivm[i] = 1.0 / vm[i];
+        if constexpr (MIXED) {
+          VrW[i] = (T)Vr[i];
+          ViW[i] = (T)Vi[i];
+          ivmW[i] = (T)ivm[i];
+        }
       }
       __syncthreads();
       double fmax = 0.0;
@@ -305,6 +374,10 @@ __global__ void __launch_bounds__(NR_THREADS, NR_MIN_CTAS) k_nr_solve(NrDev d, S
         }
         Ir[i] = ir;
         Ii[i] = ii;
+        if constexpr (MIXED) {
+          IrW[i] = (T)ir;
+          IiW[i] = (T)ii;
+        }
         const double sr = Vr[i] * ir + Vi[i] * ii;   // V conj(I)
         const double si = Vi[i] * ir - Vr[i] * ii;
         const int pt = d.pos_t[i], pq = d.pos_q[i];
@@ -329,29 +402,29 @@ __global__ void __launch_bounds__(NR_THREADS, NR_MIN_CTAS) k_nr_solve(NrDev d, S
       }
       // GMRES on M^-1 J dx = M^-1 (-F), x0 = 0
       for (int e = t; e < dim; e += NR_THREADS) {
-        wv[e] = -F[e];
-        x[e] = 0.0;
+        wv[e] = (T)(-F[e]);
+        x[e] = T(0);
       }
       __syncthreads();
-      precondition(d, ivm, wv, bv, tmp, y);
-      double nb = 0.0;
+      precondition<T>(d, ivmT, wv, bv, tmp, y);
+      T nb = 0;
       for (int e = t; e < dim; e += NR_THREADS) nb += bv[e] * bv[e];
-      const double beta0 = sqrt(block_sum(nb, red));
+      const double beta0 = sqrt(block_sum((double)nb, red));
       bool done = !(beta0 > 0.0);
       for (int rs = 0; rs < a.max_restart && !done; ++rs) {
         // r = b - A x (x = 0 on the first pass)
         if (rs > 0) {
-          jvp(d, Vr, Vi, Ir, Ii, ivm, x, dVr, dVi, tmp);
-          precondition(d, ivm, tmp, wv, F, y);   // F is free now: work space
+          jvp<T>(d, VrT, ViT, IrT, IiT, ivmT, x, dVr, dVi, tmp);
+          precondition<T>(d, ivmT, tmp, wv, work, y);
           for (int e = t; e < dim; e += NR_THREADS) Vk[e] = bv[e] - wv[e];
         } else {
           for (int e = t; e < dim; e += NR_THREADS) Vk[e] = bv[e];
         }
-        double nr = 0.0;
+        T nr = 0;
         for (int e = t; e < dim; e += NR_THREADS) nr += Vk[e] * Vk[e];
-        const double beta = sqrt(block_sum(nr, red));
+        const double beta = sqrt(block_sum((double)nr, red));
         if (!(beta > a.eta * beta0)) break;
-        const double ib = 1.0 / beta;
+        const T ib = (T)(1.0 / beta);
         for (int e = t; e < dim; e += NR_THREADS) Vk[e] *= ib;
         if (t == 0) {
           gv[0] = beta;
@@ -360,19 +433,20 @@ __global__ void __launch_bounds__(NR_THREADS, NR_MIN_CTAS) k_nr_solve(NrDev d, S
         }
         __syncthreads();
         for (int j = 0; j < m; ++j) {
-          double* vj = Vk + (int64_t)j * dim;
-          jvp(d, Vr, Vi, Ir, Ii, ivm, vj, dVr, dVi, tmp);
-          precondition(d, ivm, tmp, wv, F, y);   // F doubles as work space
-          // classical Gram-Schmidt, twice
+          T* vj = Vk + (int64_t)j * dim;
+          jvp<T>(d, VrT, ViT, IrT, IiT, ivmT, vj, dVr, dVi, tmp);
+          precondition<T>(d, ivmT, tmp, wv, work, y);
+          // classical Gram-Schmidt, twice; products in T, sums across the
+          // warp and the CTA in FP64
           for (int i = t; i <= j; i += NR_THREADS) H[j * (m + 1) + i] = 0.0;
           __syncthreads();
           for (int pass = 0; pass < 2; ++pass) {
             for (int i = 0; i <= j; ++i) {
-              const double* vi = Vk + (int64_t)i * dim;
-              double s = 0.0;
+              const T* vi = Vk + (int64_t)i * dim;
+              T s = 0;
               for (int e = t; e < dim; e += NR_THREADS) s += vi[e] * wv[e];
-              s = warp_sum(s);
-              if (l == 0) red[i * NR_WARPS + w] = s;
+              const double sw = warp_sum((double)s);
+              if (l == 0) red[i * NR_WARPS + w] = sw;
             }
             __syncthreads();
             for (int i = t; i <= j; i += NR_THREADS) {
@@ -383,17 +457,17 @@ __global__ void __launch_bounds__(NR_THREADS, NR_MIN_CTAS) k_nr_solve(NrDev d, S
             }
             __syncthreads();
             for (int e = t; e < dim; e += NR_THREADS) {
-              double s = wv[e];
-              for (int i = 0; i <= j; ++i) s -= hh[i] * Vk[(int64_t)i * dim + e];
+              T s = wv[e];
+              for (int i = 0; i <= j; ++i) s -= (T)hh[i] * Vk[(int64_t)i * dim + e];
               wv[e] = s;
             }
             __syncthreads();
           }
-          double nw = 0.0;
+          T nw = 0;
           for (int e = t; e < dim; e += NR_THREADS) nw += wv[e] * wv[e];
-          const double hn = sqrt(block_sum(nw, red));
-          double* vn = Vk + (int64_t)(j + 1) * dim;
-          const double inv = hn > 0.0 ? 1.0 / hn : 0.0;
+          const double hn = sqrt(block_sum((double)nw, red));
+          T* vn = Vk + (int64_t)(j + 1) * dim;
+          const T inv = hn > 0.0 ? (T)(1.0 / hn) : T(0);
           for (int e = t; e < dim; e += NR_THREADS) vn[e] = wv[e] * inv;
           if (t == 0) {
             double* h = H + j * (m + 1);
@@ -429,16 +503,16 @@ __global__ void __launch_bounds__(NR_THREADS, NR_MIN_CTAS) k_nr_solve(NrDev d, S
         }
         __syncthreads();
         for (int e = t; e < dim; e += NR_THREADS) {
-          double s = x[e];
-          for (int i = 0; i < jd; ++i) s += hh[i] * Vk[(int64_t)i * dim + e];
+          T s = x[e];
+          for (int i = 0; i < jd; ++i) s += (T)hh[i] * Vk[(int64_t)i * dim + e];
           x[e] = s;
         }
         __syncthreads();
         if (s_flag) done = true;
       }
-      // Newton update
-      for (int p = t; p < nt; p += NR_THREADS) va[d.t_bus[p]] += x[p];
-      for (int p = t; p < d.nq; p += NR_THREADS) vm[d.q_bus[p]] += x[nt + p];
+      // Newton update (FP64 state)
+      for (int p = t; p < nt; p += NR_THREADS) va[d.t_bus[p]] += (double)x[p];
+      for (int p = t; p < d.nq; p += NR_THREADS) vm[d.q_bus[p]] += (double)x[nt + p];
       __syncthreads();
     }
     double2* Vo = a.V + (int64_t)b * N;
@@ -613,6 +687,10 @@ zbus_status upload(zbus_nr_network net, T** dst, const std::vector<T>& src, cuda
   return ZBUS_OK;
 }
 
+std::vector<float> to_float(const std::vector<double>& v) {
+  return std::vector<float>(v.begin(), v.end());
+}
+
 zbus_status upload_factor(zbus_nr_network net, const HostFactor& hf, Factor& f, cudaStream_t st) {
   f.n = hf.n;
   ZB_CHECK(upload(net, &f.perm, hf.perm, st));
@@ -623,6 +701,9 @@ zbus_status upload_factor(zbus_nr_network net, const HostFactor& hf, Factor& f, 
   ZB_CHECK(upload(net, &f.u_col, hf.u_col, st));
   ZB_CHECK(upload(net, &f.u_val, hf.u_val, st));
   ZB_CHECK(upload(net, &f.dinv, hf.dinv, st));
+  ZB_CHECK(upload(net, &f.l_val_f, to_float(hf.l_val), st));
+  ZB_CHECK(upload(net, &f.u_val_f, to_float(hf.u_val), st));
+  ZB_CHECK(upload(net, &f.dinv_f, to_float(hf.dinv), st));
   ZB_CHECK(upload(net, &f.fl_ptr, hf.fl_ptr, st));
   ZB_CHECK(upload(net, &f.fl_row, hf.fl_row, st));
   ZB_CHECK(upload(net, &f.bl_ptr, hf.bl_ptr, st));
@@ -633,14 +714,16 @@ zbus_status upload_factor(zbus_nr_network net, const HostFactor& hf, Factor& f, 
   return ZBUS_OK;
 }
 
-size_t smem_bytes(int m, int N) {
-  return sizeof(double) *
-         ((size_t)(m + 1) * m + 2 * m + 2 * (m + 1) + (size_t)(m + 1) * NR_WARPS + N);
+size_t smem_bytes(int m, int N, bool mixed) {
+  return sizeof(double) * ((size_t)(m + 1) * m + 2 * m + 2 * (m + 1) + (size_t)(m + 1) * NR_WARPS) +
+         (mixed ? sizeof(float) : sizeof(double)) * (size_t)N;
 }
 
-int64_t scratch_doubles(const zbus_nr_network net, int m) {
-  const int64_t dim = net->nt + net->nq;
-  const int64_t s = 9 * (int64_t)net->N + 5 * dim + (int64_t)(m + 1) * dim;
+int64_t scratch_doubles(const zbus_nr_network net, int m, bool mixed) {
+  const int64_t N = net->N, dim = net->nt + net->nq;
+  const int64_t kv = mixed ? (krylov_values<float>(N, dim, m) + 1) / 2
+                           : krylov_values<double>(N, dim, m);
+  const int64_t s = state_doubles(N, dim) + kv;
   return (s + 31) / 32 * 32;
 }
 
@@ -659,6 +742,7 @@ void zbus_nr_opts_default(zbus_nr_opts* o) {
   o->gmres_restart = 30;
   o->gmres_max_restarts = 4;
   o->gmres_tol = 1e-6;
+  o->precision = ZBUS_NR_FP64;
 }
 
 zbus_status zbus_nr_network_create(int32_t N, int64_t nnz, const int32_t* row,
@@ -765,12 +849,17 @@ zbus_status zbus_nr_network_create(int32_t N, int64_t nnz, const int32_t* row,
   int32_t *y_ptr, *y_col, *bt_d, *pt_d, *pq_d, *tb_d, *qb_d, *g_ptr, *g_col;
   double2* y_val;
   double *vs_d, *g_val;
+  float2* y_val_f;
+  float* g_val_f;
+  std::vector<float2> yvf(yv.size());
+  for (size_t e = 0; e < yv.size(); ++e) yvf[e] = make_float2((float)yv[e].x, (float)yv[e].y);
   if ((s = upload(net, &y_ptr, yp, st)) || (s = upload(net, &y_col, yc, st)) ||
       (s = upload(net, &y_val, yv, st)) || (s = upload(net, &bt_d, bt, st)) ||
       (s = upload(net, &vs_d, vs, st)) || (s = upload(net, &pt_d, pos_t, st)) ||
       (s = upload(net, &pq_d, pos_q, st)) || (s = upload(net, &tb_d, t_bus, st)) ||
       (s = upload(net, &qb_d, q_bus, st)) || (s = upload(net, &g_ptr, gp, st)) ||
       (s = upload(net, &g_col, gc, st)) || (s = upload(net, &g_val, gval, st)) ||
+      (s = upload(net, &y_val_f, yvf, st)) || (s = upload(net, &g_val_f, to_float(gval), st)) ||
       (s = upload_factor(net, fp, d.Bp, st)) ||
       (net->nq > 0 && (s = upload_factor(net, fpp, d.Bpp, st))))
     return bail(s);
@@ -786,6 +875,8 @@ zbus_status zbus_nr_network_create(int32_t N, int64_t nnz, const int32_t* row,
   d.g_ptr = g_ptr;
   d.g_col = g_col;
   d.g_val = g_val;
+  d.y_val_f = y_val_f;
+  d.g_val_f = g_val_f;
   ce = cudaStreamSynchronize(st);
   if (ce != cudaSuccess) return bail(cuda_fail(ce, "setup copies", __FILE__, __LINE__));
   int dev = net->device;
@@ -830,6 +921,8 @@ zbus_status zbus_nr_solve(zbus_nr_network net, int64_t B, const double* P, const
   if (o.gmres_max_restarts < 1) return fail(ZBUS_ERR_ARG, "gmres_max_restarts must be >= 1");
   if (!(o.gmres_tol > 0.0) || !(o.gmres_tol < 1.0))
     return fail(ZBUS_ERR_ARG, "gmres_tol must be in (0, 1)");
+  if (o.precision != ZBUS_NR_FP64 && o.precision != ZBUS_NR_MIXED)
+    return fail(ZBUS_ERR_ARG, "unknown NR precision");
   if (B == 0) return ZBUS_OK;
   if (!P || !Q || !V_out || !iters || !converged)
     return fail(ZBUS_ERR_ARG, "P, Q, V_out, iters and converged are required");
@@ -838,18 +931,19 @@ zbus_status zbus_nr_solve(zbus_nr_network net, int64_t B, const double* P, const
   if (dev != net->device) return fail(ZBUS_ERR_ARG, "current CUDA device differs from the network's");
   cudaStream_t st = (cudaStream_t)cuda_stream;
   const int m = o.gmres_restart;
-  const size_t smem = smem_bytes(m, net->N);
+  const bool mixed = o.precision == ZBUS_NR_MIXED;
+  const size_t smem = smem_bytes(m, net->N, mixed);
   if (smem > 227 * 1024)
     return fail(ZBUS_ERR_ARG, "grid too large for the per-CTA shared work space");
-  if (net->smem_set < smem) {
-    ZB_CUDA(cudaFuncSetAttribute(k_nr_solve, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                 (int)smem));
-    net->smem_set = smem;
+  const void* kern = mixed ? (const void*)k_nr_solve<float> : (const void*)k_nr_solve<double>;
+  if (net->smem_set[mixed] < smem) {
+    ZB_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    net->smem_set[mixed] = smem;
   }
   int per = 0;
-  ZB_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_nr_solve, NR_THREADS, smem));
+  ZB_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, kern, NR_THREADS, smem));
   const int64_t ctas = std::min<int64_t>(B, (int64_t)net->sms * std::max(1, per));
-  const int64_t stride = scratch_doubles(net, m);
+  const int64_t stride = scratch_doubles(net, m, mixed);
   if (net->scratch_ctas < ctas || net->scratch_stride < stride) {
     ZB_CUDA(cudaStreamSynchronize(st));
     cudaFree(net->scratch);
@@ -875,7 +969,10 @@ zbus_status zbus_nr_solve(zbus_nr_network net, int64_t B, const double* P, const
   a.iters = iters;
   a.conv = converged;
   a.gmres = gmres_iters;
-  k_nr_solve<<<(int)ctas, NR_THREADS, smem, st>>>(d, a);
+  if (mixed)
+    k_nr_solve<float><<<(int)ctas, NR_THREADS, smem, st>>>(d, a);
+  else
+    k_nr_solve<double><<<(int)ctas, NR_THREADS, smem, st>>>(d, a);
   ZB_CUDA(cudaGetLastError());
   return ZBUS_OK;
 }

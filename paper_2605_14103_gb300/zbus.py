@@ -63,7 +63,11 @@ class zbus_serve_config(C.Structure):
 
 class zbus_nr_opts(C.Structure):
     _fields_ = [("gmres_restart", C.c_int32), ("gmres_max_restarts", C.c_int32),
-                ("gmres_tol", C.c_double), ("reserved", C.c_double * 4)]
+                ("gmres_tol", C.c_double), ("precision", C.c_int32), ("reserved0", C.c_int32),
+                ("reserved", C.c_double * 3)]
+
+
+NR_PRECISION = {"fp64": 0, "mixed": 1}
 
 
 SOURCE_FN = C.CFUNCTYPE(C.c_int32, C.c_void_p, C.c_double, C.POINTER(zbus_request))
@@ -650,7 +654,7 @@ class NrNetwork:
         return zbus_nr_network_info(self.handle)
 
     def solve(self, P, Q, tol=1e-10, max_iter=20, gmres_restart=30, gmres_max_restarts=4,
-              gmres_tol=1e-6, out=None, stream=None):
+              gmres_tol=1e-6, precision="fp64", out=None, stream=None):
         """Returns (V [B,N] complex128, iters, converged, gmres_iters) on P's device."""
         import torch
         B = P.shape[0]
@@ -663,6 +667,7 @@ class NrNetwork:
         o.gmres_restart = gmres_restart
         o.gmres_max_restarts = gmres_max_restarts
         o.gmres_tol = gmres_tol
+        o.precision = NR_PRECISION[precision]
         V, it, cv, gm = out
         zbus_nr_solve(self.handle, self.N, P, Q, tol, max_iter, o, V, it, cv, gm, stream)
         return V, it, cv, gm

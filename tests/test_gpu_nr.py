@@ -1,7 +1,9 @@
 """GPU parity of the batched Newton-Raphson power flow (zbus_nr_solve) against
 the FP64 Newton-Raphson oracle, through the C ABI.
 
-Bar (per scenario): converged flags identical; on converged scenarios
+Both arithmetic forms of the Newton direction are checked (FP64, and FP32
+GMRES under the FP64 mismatch).  Bar (per scenario): converged flags
+identical; on converged scenarios
 max |V_gpu - V_oracle| <= 1e-6 pu (checked tighter, 1e-8: both sides stop
 at max |F| <= 1e-10 and the solution moves by about |J^-1| times that),
 Newton step counts within one of the oracle's (GMRES solves each Newton
@@ -55,13 +57,17 @@ def compare(g, P, Q, V, it, cv, ref, idx=None):
     assert cpu_mismatch(g, V[m], P[m], Q[m]).max() <= 1e-9
 
 
+PRECISIONS = ["fp64", "mixed"]
+
+
+@pytest.mark.parametrize("prec", PRECISIONS)
 @pytest.mark.parametrize("N,B,seed", [(14, 7, 1), (30, 33, 2), (118, 64, 611), (300, 5, 9)])
-def test_parity_against_the_oracle(N, B, seed):
+def test_parity_against_the_oracle(N, B, seed, prec):
     g = G.make_grid(N, seed)
     P, Q = G.make_injections(g, B)
     ref = O.solve_batch(g.N, g.Y_row, g.Y_col, g.Y_val, g.bus_type, g.v_set, P, Q)
     net = zbus.NrNetwork.from_grid(g)
-    V, it, cv, gm = net.solve(dev(P), dev(Q))
+    V, it, cv, gm = net.solve(dev(P), dev(Q), precision=prec)
     compare(g, P, Q, V, it, cv, ref)
     gm = gm.cpu().numpy()
     assert (gm >= it.cpu().numpy()).all() and gm.max() < 40 * 20
@@ -70,13 +76,14 @@ def test_parity_against_the_oracle(N, B, seed):
     net.close()
 
 
+@pytest.mark.parametrize("prec", PRECISIONS)
 @pytest.mark.parametrize("name,sample", [("grid1354_b1000", 2), ("grid2224_b1000", 2)])
-def test_large_grids_full_batch_sampled(name, sample):
+def test_large_grids_full_batch_sampled(name, sample, prec):
     """The benchmark's grids at their full 1000 scenarios; the oracle checks a
     sample, the CPU mismatch every scenario."""
     g, P, Q, w = G.make_grid_workload(name)
     net = zbus.NrNetwork.from_grid(g)
-    V, it, cv, gm = net.solve(dev(P), dev(Q), tol=w.tol, max_iter=w.max_iter)
+    V, it, cv, gm = net.solve(dev(P), dev(Q), tol=w.tol, max_iter=w.max_iter, precision=prec)
     assert cv.cpu().numpy().all()
     pick = np.random.default_rng(5).choice(P.shape[0], sample, replace=False)
     ref = O.solve_batch(g.N, g.Y_row, g.Y_col, g.Y_val, g.bus_type, g.v_set, P[pick], Q[pick])
@@ -115,17 +122,19 @@ def test_two_bus_closed_form_and_pv_only_grid():
     assert np.abs(V3.cpu().numpy()[0] - Vo).max() <= TOL_TIGHT
 
 
-def test_batch_independence_and_short_gmres_cycles():
+@pytest.mark.parametrize("prec", PRECISIONS)
+def test_batch_independence_and_short_gmres_cycles(prec):
     g = G.make_grid(90, 17)
     P, Q = G.make_injections(g, 40)
     net = zbus.NrNetwork.from_grid(g)
-    V, it, cv, gm = net.solve(dev(P), dev(Q))
+    V, it, cv, gm = net.solve(dev(P), dev(Q), precision=prec)
     perm = np.random.default_rng(2).permutation(40)[:13]
-    V2, it2, cv2, gm2 = net.solve(dev(P[perm]), dev(Q[perm]))
+    V2, it2, cv2, gm2 = net.solve(dev(P[perm]), dev(Q[perm]), precision=prec)
     idx = torch.from_numpy(perm).cuda()
     assert torch.equal(V2, V[idx]) and torch.equal(it2, it[idx]) and torch.equal(gm2, gm[idx])
     # two Krylov vectors per cycle: restarts do the work, same solution
-    V3, it3, cv3, gm3 = net.solve(dev(P), dev(Q), gmres_restart=2, gmres_max_restarts=40)
+    V3, it3, cv3, gm3 = net.solve(dev(P), dev(Q), gmres_restart=2, gmres_max_restarts=40,
+                                  precision=prec)
     assert cv3.cpu().numpy().all()
     assert (V3 - V).abs().max().item() <= TOL_TIGHT
 
@@ -159,3 +168,11 @@ def test_argument_errors():
         net.solve(dev(P), dev(Q), gmres_restart=0)
     with pytest.raises(zbus.ZbusError):
         net.solve(dev(P), dev(Q), gmres_tol=2.0)
+    o = zbus.zbus_nr_opts_default()
+    o.precision = 7
+    B = P.shape[0]
+    outs = (torch.empty((B, g.N), dtype=torch.complex128, device="cuda"),
+            torch.empty((B,), dtype=torch.int32, device="cuda"),
+            torch.empty((B,), dtype=torch.uint8, device="cuda"))
+    with pytest.raises(zbus.ZbusError):
+        zbus.zbus_nr_solve(net.handle, g.N, dev(P), dev(Q), 1e-10, 20, o, *outs)
