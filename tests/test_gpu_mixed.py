@@ -94,6 +94,33 @@ def test_mixed_1024bus(mode):
     check(net, f, Sw, Sd, ref, V, it, cv)
 
 
+@pytest.fixture(scope="module")
+def full1024():
+    """The 1024-bus workload at its full 16384 scenarios (host arrays) and its
+    network; built once for the three forms."""
+    f, Sw, Sd, w = F.make_workload("feeder1024_b16384")
+    net = zbus.Network.from_feeder(f)
+    idx = np.random.default_rng(3).choice(w.B, 6, replace=False)
+    ref = oracle(f, Sw[idx], Sd[idx])
+    return f, Sw, Sd, w, net, dev(Sw), dev(Sd), idx, ref
+
+
+@pytest.mark.parametrize("mode", MODES)
+def test_mixed_full_size_1024bus_sampled(mode, full1024):
+    """1024 buses x 16384 scenarios in the launch configuration the benchmark
+    times; every scenario converged with FP64 mismatch <= 1e-6, and the
+    oracle checks a sample one scenario at a time."""
+    f, Sw, Sd, w, net, Swd, Sdd, idx, ref = full1024
+    net.reserve(w.B, mode)
+    V, it, cv = net.solve(Swd, Sdd, tol=w.tol, max_iter=w.max_iter, precision=mode)
+    assert cv.cpu().numpy().all()
+    mm = net.power_mismatch(V, Swd, Sdd).cpu().numpy()
+    assert mm.max() <= 1e-6
+    ti = torch.from_numpy(idx).cuda()
+    check(net, f, Sw[idx], Sd[idx], ref, V[ti].contiguous(), it[ti].contiguous(),
+          cv[ti].contiguous())
+
+
 @pytest.mark.parametrize("mode", MODES)
 def test_mixed_full_size_128bus_sampled(mode):
     f, Sw, Sd, w = F.make_workload("feeder128_b4096")
