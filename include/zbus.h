@@ -541,7 +541,9 @@ zbus_status zbus_nr_network_info(zbus_nr_network net, int32_t* n_theta, int32_t*
  * CTA, dim = n_theta + n_q; up to eight CTAs per SM) grows on demand with a
  * synchronous allocation.  Device buffers only.  B = 0 is a no-op.  Returns
  * ZBUS_ERR_ARG for a grid whose per-CTA shared work space (N + a few
- * (gmres_restart + 1)^2 doubles) exceeds 227 KB (N above about 27000).
+ * (gmres_restart + 1)^2 doubles) exceeds 227 KB (N above about 27000).  The
+ * scratch belongs to the grid: solves of one grid must not overlap on the
+ * GPU (other streams or host threads); solves of different grids may.
  */
 zbus_status zbus_nr_solve(zbus_nr_network net, int64_t B, const double* P, const double* Q,
                           double tol, int32_t max_iter, const zbus_nr_opts* opts,
