@@ -415,6 +415,15 @@ zbus_status zbus_solve_noalloc(zbus_network net, int64_t B,
  *                   is scaled to max_j |G_bj| = 1 (a tolerance relative to
  *                   each scenario's loss gradient); >= 0
  *   max_iter        iteration cap, >= 1
+ *   opts            NULL, or opts->precision: ZBUS_FP64 (default; the dense
+ *                   Z^T sweeps above) or ZBUS_TREE_SWEEP (radial networks
+ *                   with reciprocal branches: the defect iteration
+ *                   rho = conj(G/s + A^T mu) - Y_LL^T mu, mu += T^T rho, with
+ *                   Y_LL^T mu from the sparse branch blocks and T^T the
+ *                   backward / forward sweep of the transposed series network,
+ *                   O(n) per scenario and sweep, FP64, one CTA per scenario;
+ *                   same fixed point; ZBUS_ERR_UNSUPPORTED for a meshed
+ *                   network); other fields are ignored
  *   dS_wye          device [B][n] complex dL/dS_wye, or NULL; defined for
  *                   every slot (the sensitivity to adding a load there)
  *   dS_delta        device [B][n] complex dL/dS_delta, or NULL; slot x is the
@@ -436,6 +445,7 @@ zbus_status zbus_solve_adjoint(zbus_network net, int64_t B,
                                const double* S_wye, const double* S_delta,
                                const double* V, const double* G,
                                double tol, int32_t max_iter,
+                               const zbus_solve_opts* opts,
                                double* dS_wye, double* dS_delta,
                                int32_t* iters, uint8_t* converged,
                                void* cuda_stream);

@@ -34,6 +34,10 @@ __device__ __forceinline__ double2 cmul(double2 a, double2 b) {
   return make_double2(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x);
 }
 __device__ __forceinline__ double2 cconj(double2 a) { return make_double2(a.x, -a.y); }
+// acc + a b with four FMAs
+__device__ __forceinline__ double2 cfma(double2 a, double2 b, double2 acc) {
+  return make_double2(fma(a.x, b.x, fma(-a.y, b.y, acc.x)), fma(a.x, b.y, fma(a.y, b.x, acc.y)));
+}
 __device__ __forceinline__ double2 csub(double2 a, double2 b) {
   return make_double2(a.x - b.x, a.y - b.y);
 }
@@ -229,6 +233,254 @@ __global__ void k_adj_out(const double2* __restrict__ mu, const double2* __restr
   }
 }
 
+// ---------------------------------------------------------------------------
+// Tree form of the adjoint (radial networks): the defect iteration
+//     rho = conj(G / s + A^T mu) - Y_LL^T mu,     mu <- mu + T^T rho,
+// T^T the backward / forward sweep of the transposed series network (subtree
+// sums of rho, then path sums of z_c^T times them), FP64 throughout.  Its
+// fixed point is that of the dense adjoint (rho = 0 <=> Y^T mu =
+// conj(lambda)); without shunts T^T = Z^T and each sweep equals a dense
+// adjoint sweep.  Y_LL^T mu in branch form: with reciprocal branches
+// (Y_ba = Y_ab, which the radial detection checks),
+//     (Y_LL^T mu)_a = sum_b Y_ab^T (mu_b - mu_a) - Y_as^T mu_a + Sh_a^T mu_a.
+// One CTA per scenario runs every sweep (block barriers per tree level).
+// Each tree branch's product is formed once: with J_c = Y_cp^T (mu_p - mu_c)
+// for bus c and its parent p (mu = 0 at the slack), the branch contributes
+// J_c at c and -J_c at p, so the backward sweep forms the subtree sums as
+//     S_c = P_c + sum over children k of (S_k + J_k),
+//     P_c = conj(lambda_c) - J_c - (shunt terms of c).
+// ---------------------------------------------------------------------------
+constexpr int AT_THREADS = 128;
+constexpr int AT_WARPS = AT_THREADS / 32;
+
+struct AdjTree {
+  int n, nb, depth, B, max_iter;
+  int onchip;             // mu and r in shared memory (else in the scratch slice)
+  double tol;
+  const int4* node;       // per breadth-first position: bus, parent position, children range
+  const int32_t* lvl;     // [depth + 1]
+  const uint8_t* mask;    // phases of each position's parent line
+  const double2* z;       // [nb][9] z_c of each position's parent line (FP64)
+  const int32_t* pblk;    // [nb] branch-form block of each position's parent line
+  const int32_t* bptr;    // branch-form blocks per bus
+  const int32_t* bcol;
+  const double2* bval;
+  const double2* Sw;
+  const double2* Sd;
+  const double2* V;
+  const double2* G;
+  double2* Hw;
+  double2* Hd;
+  int32_t* iters;
+  uint8_t* conv;
+  double2* scratch;       // per CTA: mu, r, wye slopes, delta slopes, J (5 n)
+  int64_t stride;
+};
+
+__device__ double at_block_max(double v, double* red) {
+  for (int o = 16; o > 0; o >>= 1) {
+    const double y = __shfl_xor_sync(0xffffffffu, v, o);
+    v = (y > v || y != y) ? y : v;
+  }
+  __syncthreads();
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = v;
+  __syncthreads();
+  double m = 0.0;
+#pragma unroll
+  for (int k = 0; k < AT_WARPS; ++k) m = (red[k] > m || red[k] != red[k]) ? red[k] : m;
+  return m;
+}
+
+__global__ void __launch_bounds__(AT_THREADS) k_adj_tree(AdjTree a) {
+  __shared__ double red[AT_WARPS];
+  extern __shared__ double2 at_smem[];   // mu and r when they fit (a.onchip)
+  const int t = threadIdx.x;
+  const int n = a.n, nb = a.nb;
+  double2* g = a.scratch + (int64_t)blockIdx.x * a.stride;
+  double2* mu = a.onchip ? at_smem : g;
+  double2* r = a.onchip ? at_smem + n : g + n;
+  double2* aw = g + 2 * n;
+  double2* cd = g + 3 * n;
+  double2* jb = g + 4 * n;   // J of each bus's parent branch
+  for (int b = blockIdx.x; b < a.B; b += gridDim.x) {
+    const int64_t off = (int64_t)b * n;
+    const double2* V = a.V + off;
+    const double2* G = a.G + off;
+    // scale of G, load slopes at V, mu = 0
+    double gm = 0.0;
+    for (int j = t; j < n; j += AT_THREADS) {
+      const double x = hypot(G[j].x, G[j].y);
+      gm = (x > gm || x != x) ? x : gm;
+    }
+    gm = at_block_max(gm, red);
+    const double s = gm == 0.0 ? 1.0 : gm;
+    const double inv_s = 1.0 / s;
+    for (int c = t; c < nb; c += AT_THREADS) {
+      const int j0 = 3 * c;
+      double2 v[3];
+#pragma unroll
+      for (int p = 0; p < 3; ++p) {
+        v[p] = V[j0 + p];
+        aw[j0 + p] = a.Sw ? load_slope(a.Sw[off + j0 + p], v[p]) : make_double2(0.0, 0.0);
+        mu[j0 + p] = make_double2(0.0, 0.0);
+      }
+#pragma unroll
+      for (int x = 0; x < 3; ++x) {
+        const int y = x == 2 ? 0 : x + 1;
+        cd[j0 + x] = a.Sd ? load_slope(a.Sd[off + j0 + x], csub(v[x], v[y]))
+                          : make_double2(0.0, 0.0);
+      }
+    }
+    __syncthreads();
+    int it = 0, ok = 0;
+    for (int k = 1; k <= a.max_iter; ++k) {
+      // P_c = conj(G / s + A^T mu)_c - J_c - (shunt terms), per breadth-first
+      // position (bus c, parent p)
+      for (int i = t; i < nb; i += AT_THREADS) {
+        const int4 nd = a.node[i];
+        const int c = nd.x;
+        const int j0 = 3 * c;
+        double2 u[3], lam[3], yt[3];
+#pragma unroll
+        for (int q = 0; q < 3; ++q) {
+          u[q] = mu[j0 + q];
+          const double2 gq = G[j0 + q];
+          lam[q] = cfma(aw[j0 + q], u[q], make_double2(gq.x * inv_s, gq.y * inv_s));
+          yt[q] = make_double2(0.0, 0.0);
+        }
+#pragma unroll
+        for (int x = 0; x < 3; ++x) {
+          const int y = x == 2 ? 0 : x + 1;
+          const double2 d = cmul(cd[j0 + x], csub(u[x], u[y]));
+          lam[x].x += d.x;
+          lam[x].y += d.y;
+          lam[y].x -= d.x;
+          lam[y].y -= d.y;
+        }
+        {   // J_c = Y_cp^T (mu_p - mu_c)
+          const double2* Yb = a.bval + (int64_t)a.pblk[i] * 9;
+          double2 w[3];
+#pragma unroll
+          for (int q = 0; q < 3; ++q)
+            w[q] = nd.y >= 0 ? csub(mu[3 * a.node[nd.y].x + q], u[q])
+                             : make_double2(-u[q].x, -u[q].y);
+#pragma unroll
+          for (int p = 0; p < 3; ++p)
+#pragma unroll
+            for (int q = 0; q < 3; ++q) yt[p] = cfma(Yb[3 * q + p], w[q], yt[p]);
+#pragma unroll
+          for (int p = 0; p < 3; ++p) jb[j0 + p] = yt[p];
+        }
+        for (int e = a.bptr[c]; e < a.bptr[c + 1]; ++e) {   // shunts: Sh_c^T mu_c
+          if (a.bcol[e] != -2) continue;
+          const double2* Yb = a.bval + (int64_t)e * 9;
+#pragma unroll
+          for (int p = 0; p < 3; ++p)
+#pragma unroll
+            for (int q = 0; q < 3; ++q) yt[p] = cfma(Yb[3 * q + p], u[q], yt[p]);
+        }
+#pragma unroll
+        for (int p = 0; p < 3; ++p) r[j0 + p] = make_double2(lam[p].x - yt[p].x, -lam[p].y - yt[p].y);
+      }
+      __syncthreads();
+      // backward: S_c = P_c + sum over children of (S_k + J_k), deepest first
+      for (int L = a.depth - 2; L >= 0; --L) {
+        for (int i = a.lvl[L] + t; i < a.lvl[L + 1]; i += AT_THREADS) {
+          const int4 nd = a.node[i];
+          if (nd.z == nd.w) continue;
+          double2* own = r + 3 * nd.x;
+          double2 acc[3] = {own[0], own[1], own[2]};
+          for (int ch = nd.z; ch < nd.w; ++ch) {
+            const int kb = 3 * a.node[ch].x;
+            const int cm = a.mask[ch];   // a phase the child's line lacks stays below
+#pragma unroll
+            for (int p = 0; p < 3; ++p)
+              if ((cm >> p) & 1) {
+                acc[p].x += r[kb + p].x + jb[kb + p].x;
+                acc[p].y += r[kb + p].y + jb[kb + p].y;
+              }
+          }
+#pragma unroll
+          for (int p = 0; p < 3; ++p) own[p] = acc[p];
+        }
+        __syncthreads();
+      }
+      // forward: X_c = X_parent + z_c^T S_c on the phases of c's line, in place
+      for (int L = 0; L < a.depth; ++L) {
+        for (int i = a.lvl[L] + t; i < a.lvl[L + 1]; i += AT_THREADS) {
+          const int4 nd = a.node[i];
+          double2* own = r + 3 * nd.x;
+          const double2 sv[3] = {own[0], own[1], own[2]};
+          double2 xp[3] = {make_double2(0.0, 0.0), make_double2(0.0, 0.0), make_double2(0.0, 0.0)};
+          const int cm = a.mask[i];
+          if (nd.y >= 0) {
+            const double2* pa = r + 3 * a.node[nd.y].x;
+#pragma unroll
+            for (int p = 0; p < 3; ++p)
+              if ((cm >> p) & 1) xp[p] = pa[p];
+          }
+          const double2* z = a.z + (int64_t)i * 9;
+#pragma unroll
+          for (int p = 0; p < 3; ++p) {
+            double2 x = xp[p];
+#pragma unroll
+            for (int q = 0; q < 3; ++q) x = cfma(z[3 * q + p], sv[q], x);
+            own[p] = (cm >> p) & 1 ? x : make_double2(0.0, 0.0);
+          }
+        }
+        __syncthreads();
+      }
+      // mu += X, squared step size
+      double dmax = 0.0;
+      for (int j = t; j < n; j += AT_THREADS) {
+        const double2 x = r[j];
+        mu[j].x += x.x;
+        mu[j].y += x.y;
+        double st = fma(x.x, x.x, x.y * x.y);
+        if (st != st) st = INFINITY;
+        dmax = fmax(dmax, st);
+      }
+      dmax = at_block_max(dmax, red);
+      it = k;
+      if (dmax <= a.tol * a.tol) {
+        ok = 1;
+        break;
+      }
+      if (isinf(dmax)) break;
+    }
+    // dL/dS = s D^T mu
+    for (int c = t; c < nb; c += AT_THREADS) {
+      const int j0 = 3 * c;
+      double2 v[3], u[3];
+#pragma unroll
+      for (int p = 0; p < 3; ++p) {
+        v[p] = V[j0 + p];
+        u[p] = mu[j0 + p];
+      }
+      if (a.Hw) {
+#pragma unroll
+        for (int p = 0; p < 3; ++p) {
+          const double2 h = div_conj(u[p], v[p]);
+          a.Hw[off + j0 + p] = make_double2(-s * h.x, -s * h.y);
+        }
+      }
+      if (a.Hd) {
+#pragma unroll
+        for (int x = 0; x < 3; ++x) {
+          const int y = x == 2 ? 0 : x + 1;
+          const double2 h = div_conj(csub(u[y], u[x]), csub(v[x], v[y]));
+          a.Hd[off + j0 + x] = make_double2(s * h.x, s * h.y);
+        }
+      }
+    }
+    if (t == 0) {
+      a.iters[b] = it;
+      a.conv[b] = (uint8_t)ok;
+    }
+    __syncthreads();
+  }
+}
+
 int grid_1d(int64_t tot, int cap) {
   return (int)std::min<int64_t>(cap, std::max<int64_t>(1, (tot + 255) / 256));
 }
@@ -324,6 +576,75 @@ zbus_status adjoint_device(zbus_network net, int64_t B, const double* S_wye,
   return ZBUS_OK;
 }
 
+// The tree form on padded device arrays (radial networks).
+zbus_status adjoint_tree_device(zbus_network net, int64_t B, const double* S_wye,
+                                const double* S_delta, const double* V, const double* G,
+                                double tol, int32_t max_iter, double* dS_wye, double* dS_delta,
+                                int32_t* iters, uint8_t* converged, cudaStream_t st) {
+  net->last_group = nullptr;
+  // the iterate and the residual on chip up to 96 KB (two CTAs per SM at the
+  // largest such feeder, ~1000 buses), else in the scratch slice
+  const size_t onchip = 2 * (size_t)net->n * sizeof(double2);
+  const size_t smem = onchip <= 96 * 1024 ? onchip : 0;
+  if (smem > 48 * 1024)
+    ZB_CUDA(cudaFuncSetAttribute(k_adj_tree, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)smem));
+  int per = 0, sms = 0;
+  ZB_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_adj_tree, AT_THREADS, smem));
+  ZB_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, net->device));
+  const int64_t ctas = std::min<int64_t>(B, (int64_t)sms * std::max(1, per));
+  const int64_t stride = 5 * (int64_t)net->n;
+  if (net->adj_tree_ctas < ctas) {
+    ZB_CUDA(cudaStreamSynchronize(st));
+    cudaFree(net->adj_tree_scratch);
+    net->adj_tree_scratch = nullptr;
+    net->adj_tree_ctas = 0;
+    ZB_CUDA(cudaMalloc((void**)&net->adj_tree_scratch,
+                       (size_t)ctas * stride * sizeof(double2)));
+    net->adj_tree_ctas = ctas;
+  }
+  AdjTree a;
+  a.n = net->n;
+  a.nb = net->nbus;
+  a.depth = net->depth;
+  a.B = (int)B;
+  a.max_iter = max_iter;
+  a.tol = tol;
+  a.node = net->t_node;
+  a.lvl = net->t_lvl;
+  a.mask = net->t_mask;
+  a.z = net->t_z64;
+  a.pblk = net->t_pblk;
+  a.bptr = net->bsr_ptr;
+  a.bcol = net->bsr_col;
+  a.bval = net->bsr_val;
+  a.Sw = (const double2*)S_wye;
+  a.Sd = (const double2*)S_delta;
+  a.V = (const double2*)V;
+  a.G = (const double2*)G;
+  a.Hw = (double2*)dS_wye;
+  a.Hd = (double2*)dS_delta;
+  a.iters = iters;
+  a.conv = converged;
+  a.scratch = net->adj_tree_scratch;
+  a.stride = stride;
+  a.onchip = smem > 0 ? 1 : 0;
+  k_adj_tree<<<(int)ctas, AT_THREADS, smem, st>>>(a);
+  ZB_CUDA(cudaGetLastError());
+  return ZBUS_OK;
+}
+
+zbus_status adjoint_any(zbus_network net, bool tree, int64_t B, const double* S_wye,
+                        const double* S_delta, const double* V, const double* G, double tol,
+                        int32_t max_iter, double* dS_wye, double* dS_delta, int32_t* iters,
+                        uint8_t* converged, cudaStream_t st) {
+  if (tree)
+    return adjoint_tree_device(net, B, S_wye, S_delta, V, G, tol, max_iter, dS_wye, dS_delta,
+                               iters, converged, st);
+  return adjoint_device(net, B, S_wye, S_delta, V, G, tol, max_iter, dS_wye, dS_delta, iters,
+                        converged, st);
+}
+
 bool on_device(const void* p) {
   if (!p) return true;
   cudaPointerAttributes a;
@@ -348,6 +669,9 @@ void free_adjoint(zbus_network net) {
   net->adj_mu = nullptr;
   net->adj_scale = nullptr;
   net->adj_cap = 0;
+  cudaFree(net->adj_tree_scratch);
+  net->adj_tree_scratch = nullptr;
+  net->adj_tree_ctas = 0;
 }
 
 }  // namespace zbus
@@ -357,13 +681,21 @@ using namespace zbus;
 extern "C" zbus_status zbus_solve_adjoint(zbus_network net, int64_t B, const double* S_wye,
                                           const double* S_delta, const double* V,
                                           const double* G, double tol, int32_t max_iter,
-                                          double* dS_wye, double* dS_delta, int32_t* iters,
-                                          uint8_t* converged, void* cuda_stream) {
+                                          const zbus_solve_opts* opts, double* dS_wye,
+                                          double* dS_delta, int32_t* iters, uint8_t* converged,
+                                          void* cuda_stream) {
   set_error("");
   if (!net) return fail(ZBUS_ERR_ARG, "network is NULL");
   if (B < 0 || B > INT32_MAX / 4) return fail(ZBUS_ERR_ARG, "B out of range");
   if (!(tol >= 0.0) || !std::isfinite(tol)) return fail(ZBUS_ERR_ARG, "tol must be finite, >= 0");
   if (max_iter < 1) return fail(ZBUS_ERR_ARG, "max_iter must be >= 1");
+  const int32_t prec = opts ? opts->precision : ZBUS_FP64;
+  if (prec != ZBUS_FP64 && prec != ZBUS_TREE_SWEEP)
+    return fail(ZBUS_ERR_UNSUPPORTED, "the adjoint runs in FP64 (dense) or as a tree sweep");
+  const bool tree = prec == ZBUS_TREE_SWEEP;
+  if (tree && !net->radial)
+    return fail(ZBUS_ERR_UNSUPPORTED, "the tree form needs a radial network with reciprocal "
+                                      "branches");
   if (B == 0) return ZBUS_OK;
   if (!V || !G || !iters || !converged)
     return fail(ZBUS_ERR_ARG, "V, G, iters and converged are required");
@@ -377,8 +709,8 @@ extern "C" zbus_status zbus_solve_adjoint(zbus_network net, int64_t B, const dou
   if (dev != net->device) return fail(ZBUS_ERR_ARG, "current CUDA device differs from the network's");
   cudaStream_t st = (cudaStream_t)cuda_stream;
   if (!net->phased)
-    return adjoint_device(net, B, S_wye, S_delta, V, G, tol, max_iter, dS_wye, dS_delta, iters,
-                          converged, st);
+    return adjoint_any(net, tree, B, S_wye, S_delta, V, G, tol, max_iter, dS_wye, dS_delta, iters,
+                       converged, st);
   // partial-phase network: into the padded layout; the gradients come back
   // through the buffers of the loads, which the last kernel no longer reads
   double* buf[4];
@@ -387,9 +719,9 @@ extern "C" zbus_status zbus_solve_adjoint(zbus_network net, int64_t B, const dou
   if (S_delta) ZB_CHECK(phased_in(net, B, S_delta, buf[1], true, st));
   ZB_CHECK(phased_in(net, B, V, buf[2], false, st));
   ZB_CHECK(phased_in(net, B, G, buf[3], false, st));
-  ZB_CHECK(adjoint_device(net, B, S_wye ? buf[0] : nullptr, S_delta ? buf[1] : nullptr, buf[2],
-                          buf[3], tol, max_iter, dS_wye ? buf[0] : nullptr,
-                          dS_delta ? buf[1] : nullptr, iters, converged, st));
+  ZB_CHECK(adjoint_any(net, tree, B, S_wye ? buf[0] : nullptr, S_delta ? buf[1] : nullptr,
+                       buf[2], buf[3], tol, max_iter, dS_wye ? buf[0] : nullptr,
+                       dS_delta ? buf[1] : nullptr, iters, converged, st));
   if (dS_wye) ZB_CHECK(phased_out(net, B, buf[0], dS_wye, st));
   if (dS_delta) ZB_CHECK(phased_out_delta(net, B, buf[1], dS_delta, st));
   return ZBUS_OK;

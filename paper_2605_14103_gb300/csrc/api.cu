@@ -467,6 +467,8 @@ void zbus_network_destroy(zbus_network net) {
   cudaFree(net->t_mask);
   cudaFree(net->t_z);
   cudaFree(net->t_zs);
+  cudaFree(net->t_z64);
+  cudaFree(net->t_pblk);
   delete net;
 }
 

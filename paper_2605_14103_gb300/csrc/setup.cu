@@ -273,6 +273,8 @@ zbus_status build_tree(zbus_network net, const std::vector<int32_t>& bp,
   for (int L = 1; L <= levels; ++L) lvl[L] = std::max(lvl[L], lvl[L - 1]);
   std::vector<int4> node(nb);        // per breadth-first position
   std::vector<float2> z((size_t)nb * 9);
+  std::vector<double2> z64((size_t)nb * 9);   // the same impedances in FP64, unscaled
+  std::vector<int32_t> pblk(nb);              // branch-form block of each position's parent line
   std::vector<float> zs(nb);
   std::vector<uint8_t> mask(nb);     // phases the parent line carries
   int next = (int)roots.size();
@@ -286,6 +288,7 @@ zbus_status build_tree(zbus_network net, const std::vector<int32_t>& bp,
       if (par[queue[q]] != c) return ZBUS_OK;   // children not contiguous: not expected
     next += cnt;
     const int t = block_of(c, p >= 0 ? p : -1);
+    pblk[i] = t;
     if (p >= 0) {
       const int u = block_of(p, c);
       if (t < 0 || u < 0) return ZBUS_OK;
@@ -311,6 +314,7 @@ zbus_status build_tree(zbus_network net, const std::vector<int32_t>& bp,
     if (!(m > 0.0) || !std::isfinite(m)) return ZBUS_OK;
     const int ex = std::ilogb(m);
     zs[i] = std::ldexp(1.0f, ex);
+    for (int e = 0; e < 9; ++e) z64[(size_t)i * 9 + e] = zi[e];
     for (int e = 0; e < 9; ++e)
       z[(size_t)i * 9 + e] =
           make_float2((float)std::ldexp(zi[e].x, -ex), (float)std::ldexp(zi[e].y, -ex));
@@ -320,6 +324,8 @@ zbus_status build_tree(zbus_network net, const std::vector<int32_t>& bp,
   ZB_CHECK(upload(&net->t_node, node, st));
   ZB_CHECK(upload(&net->t_z, z, st));
   ZB_CHECK(upload(&net->t_zs, zs, st));
+  ZB_CHECK(upload(&net->t_z64, z64, st));
+  ZB_CHECK(upload(&net->t_pblk, pblk, st));
   net->depth = levels;
   net->radial = true;
   return ZBUS_OK;

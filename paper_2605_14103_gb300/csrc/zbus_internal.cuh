@@ -204,6 +204,8 @@ struct zbus_network_s {
   uint8_t* t_mask = nullptr;    // [nbus] phases (bits 0..2) of each position's parent line
   float2* t_z = nullptr;        // [nbus][9] z = y^{-1} of the parent branch, scaled by 2^-e
   float* t_zs = nullptr;        // [nbus] 2^e
+  double2* t_z64 = nullptr;     // [nbus][9] the same z in FP64 (the load-gradient sweep)
+  int32_t* t_pblk = nullptr;    // [nbus] branch-form block of each position's parent line
   zbus::Workspace ws;
   zbus::MixedOperands mixed[2];   // [0] FP16 row-scaled, [1] BF16 hi + lo
   struct zbus::Group* group1 = nullptr;   // single-network mixed solves
@@ -230,6 +232,8 @@ struct zbus_network_s {
   double2* adj_mu = nullptr;      // [adj_cap][n]
   double* adj_scale = nullptr;    // [adj_cap]
   int64_t adj_cap = 0;
+  double2* adj_tree_scratch = nullptr;   // tree form: [adj_tree_ctas][5 n]
+  int64_t adj_tree_ctas = 0;
 };
 
 namespace zbus {

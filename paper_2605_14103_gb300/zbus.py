@@ -100,8 +100,8 @@ _SIGS = {
     "zbus_serve": (C.c_int, [C.POINTER(zbus_serve_config), C.POINTER(C.c_void_p), C.c_int32,
                              SOURCE_FN, SINK_FN, C.c_void_p, C.c_void_p]),
     "zbus_last_device_status": (C.c_int, [_P, _P]),
-    "zbus_solve_adjoint": (C.c_int, [_P, C.c_int64, _P, _P, _P, _P, C.c_double, C.c_int32, _P,
-                                     _P, _P, _P, _P]),
+    "zbus_solve_adjoint": (C.c_int, [_P, C.c_int64, _P, _P, _P, _P, C.c_double, C.c_int32,
+                                     C.POINTER(zbus_solve_opts), _P, _P, _P, _P, _P]),
     "zbus_nr_opts_default": (None, [C.POINTER(zbus_nr_opts)]),
     "zbus_nr_network_create": (C.c_int, [C.c_int32, C.c_int64, _P, _P, _P, _P, _P, C.c_double,
                                          _P, C.POINTER(_P)]),
@@ -254,7 +254,7 @@ def zbus_solve_noalloc(h, S_wye, S_delta, V_init, tol, max_iter, rule, V_out, it
         _dptr(converged, "converged", torch.uint8, (B,)), _stream(stream)))
 
 
-def zbus_solve_adjoint(h, S_wye, S_delta, V, G, tol, max_iter, dS_wye, dS_delta, iters,
+def zbus_solve_adjoint(h, S_wye, S_delta, V, G, tol, max_iter, opts, dS_wye, dS_delta, iters,
                        converged, stream=None):
     """Load gradient dL/dS at converged voltages V given G = dL/dV (device tensors)."""
     import torch
@@ -264,7 +264,7 @@ def zbus_solve_adjoint(h, S_wye, S_delta, V, G, tol, max_iter, dS_wye, dS_delta,
     _check(lib().zbus_solve_adjoint(
         h, int(B), _dptr(S_wye, "S_wye", c128, (B, n)), _dptr(S_delta, "S_delta", c128, (B, n)),
         _dptr(V, "V", c128, (B, n)), _dptr(G, "G", c128, (B, n)), float(tol), int(max_iter),
-        _dptr(dS_wye, "dS_wye", c128, (B, n)), _dptr(dS_delta, "dS_delta", c128, (B, n)),
+        C.byref(opts) if opts is not None else None, _dptr(dS_wye, "dS_wye", c128, (B, n)), _dptr(dS_delta, "dS_delta", c128, (B, n)),
         _dptr(iters, "iters", torch.int32, (B,)), _dptr(converged, "converged", torch.uint8, (B,)),
         _stream(stream)))
 
@@ -518,8 +518,9 @@ class Network:
         return out
 
     def solve_adjoint(self, V, G, S_wye=None, S_delta=None, tol=1e-12, max_iter=200,
-                      wye=True, delta=True, stream=None):
-        """Load gradient at converged voltages V given G = dL/dV.  Returns
+                      wye=True, delta=True, precision="fp64", stream=None):
+        """Load gradient at converged voltages V given G = dL/dV; precision
+        "fp64" (dense Z^T sweeps) or "tree" (radial networks).  Returns
         (dS_wye or None, dS_delta or None, iters, converged)."""
         import torch
         B = V.shape[0]
@@ -528,7 +529,9 @@ class Network:
         dd = torch.empty((B, self.n), dtype=c128, device=V.device) if delta else None
         it = torch.empty((B,), dtype=torch.int32, device=V.device)
         cv = torch.empty((B,), dtype=torch.uint8, device=V.device)
-        zbus_solve_adjoint(self.handle, S_wye, S_delta, V, G, tol, max_iter, dw, dd, it, cv,
+        o = zbus_solve_opts_default()
+        o.precision = PRECISION[precision]
+        zbus_solve_adjoint(self.handle, S_wye, S_delta, V, G, tol, max_iter, o, dw, dd, it, cv,
                            stream)
         return dw, dd, it, cv
 
@@ -541,12 +544,12 @@ def _solve_function():
 
         @staticmethod
         def forward(ctx, S_wye, S_delta, net, opts):
-            tol, max_iter, precision, adj_tol, adj_max_iter = opts
+            tol, max_iter, precision, adj_tol, adj_max_iter, adj_precision = opts
             V, it, cv = net.solve(S_wye, S_delta, tol=tol, max_iter=max_iter,
                                   precision=precision)
             ctx.save_for_backward(S_wye, S_delta, V)
             ctx.net = net
-            ctx.adj = (adj_tol, adj_max_iter)
+            ctx.adj = (adj_tol, adj_max_iter, adj_precision)
             ctx.mark_non_differentiable(it, cv)
             return V, it, cv
 
@@ -556,7 +559,7 @@ def _solve_function():
             want_w, want_d = ctx.needs_input_grad[0], ctx.needs_input_grad[1]
             dw, dd, it, cv = ctx.net.solve_adjoint(
                 V, gV.contiguous(), S_wye, S_delta, tol=ctx.adj[0], max_iter=ctx.adj[1],
-                wye=want_w, delta=want_d)
+                wye=want_w, delta=want_d, precision=ctx.adj[2])
             ctx.net.last_adjoint = (it, cv)
             return dw, dd, None, None
 
@@ -567,15 +570,16 @@ _SOLVE_FN = None
 
 
 def solve_differentiable(net, S_wye, S_delta=None, tol=1e-10, max_iter=50, precision="fp64",
-                         adj_tol=1e-12, adj_max_iter=200):
+                         adj_tol=1e-12, adj_max_iter=200, adj_precision="fp64"):
     """(V, iters, converged) of net.solve, with V differentiable in S_wye and
-    S_delta through zbus_solve_adjoint (torch autograd).  After a backward
-    pass, net.last_adjoint holds the adjoint's (iters, converged)."""
+    S_delta through zbus_solve_adjoint (torch autograd; adj_precision "fp64"
+    or "tree").  After a backward pass, net.last_adjoint holds the adjoint's
+    (iters, converged)."""
     global _SOLVE_FN
     if _SOLVE_FN is None:
         _SOLVE_FN = _solve_function()
     return _SOLVE_FN.apply(S_wye, S_delta, net,
-                           (tol, max_iter, precision, adj_tol, adj_max_iter))
+                           (tol, max_iter, precision, adj_tol, adj_max_iter, adj_precision))
 
 
 # ---------------------------------------------------------------------------

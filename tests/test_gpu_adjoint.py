@@ -9,7 +9,10 @@ adjoint converged on every scenario.  Also: the autograd wrapper against
 central differences of the GPU forward solve, batch independence (bitwise),
 host-driven and graph loops equal, zero G, a scenario with non-finite
 voltages, partial-phase feeders and the bench's 128-bus workload at full
-batch (sampled).
+batch (sampled).  Both forms of the adjoint are checked: the dense FP64 Z^T
+sweeps and the tree form (defect iteration with the exact Y^T residual and
+the transposed tree sweep, radial networks), also with shunts, and the tree
+form's refusal of a meshed network.
 """
 import os
 
@@ -24,6 +27,7 @@ from paper_2605_14103_gb300 import zbus                  # noqa: E402
 
 pytestmark = pytest.mark.gpu
 REL = 1e-9
+FORMS = ["fp64", "tree"]
 
 
 @pytest.fixture(scope="module", autouse=True)
@@ -58,16 +62,18 @@ def assert_close(H, Href):
         assert err <= REL * scale, (b, err, scale)
 
 
+@pytest.mark.parametrize("form", FORMS)
 @pytest.mark.parametrize("N,B,delta,seed", [(13, 5, 0.0, 101), (40, 33, 0.4, 7),
                                             (128, 17, 0.3, 202), (200, 3, 0.3, 9)])
-def test_parity_against_the_oracle(N, B, delta, seed):
+def test_parity_against_the_oracle(N, B, delta, seed, form):
     f = F.make_feeder(N, seed, delta_frac=delta, mult_hi=1.5)
     Sw, Sd = F.make_scenarios(f, B, 0.5, 1.5)
     r = forward_oracle(f, Sw, Sd)
     G = loss_grad(Sw.shape, seed)
     Hw, Hd = O.solve_adjoint(r["Z"], r["V"], Sw, Sd, G)
     net = zbus.Network.from_feeder(f)
-    dw, dd, it, cv = net.solve_adjoint(dev(r["V"]), dev(G), dev(Sw), dev(Sd), tol=1e-13)
+    dw, dd, it, cv = net.solve_adjoint(dev(r["V"]), dev(G), dev(Sw), dev(Sd), tol=1e-13,
+                                       precision=form)
     assert cv.cpu().numpy().all()
     assert it.cpu().numpy().max() < 200
     assert_close(dw.cpu().numpy(), Hw)
@@ -90,14 +96,16 @@ def test_wye_only_and_one_output():
     assert_close(dd2.cpu().numpy(), Hd)
 
 
-def test_autograd_against_finite_differences_of_the_gpu_solve():
+@pytest.mark.parametrize("form", FORMS)
+def test_autograd_against_finite_differences_of_the_gpu_solve(form):
     f = F.make_feeder(20, 44, delta_frac=0.5)
     Sw, Sd = F.make_scenarios(f, 4, 0.8, 1.2)
     net = zbus.Network.from_feeder(f)
     G = dev(loss_grad(Sw.shape, 5))
     sw = dev(Sw).requires_grad_(True)
     sd = dev(Sd).requires_grad_(True)
-    V, it, cv = zbus.solve_differentiable(net, sw, sd, tol=1e-13, max_iter=300)
+    V, it, cv = zbus.solve_differentiable(net, sw, sd, tol=1e-13, max_iter=300,
+                                          adj_precision=form)
     assert cv.all()
     L = (torch.conj(G) * V).real.sum()
     L.backward()
@@ -122,24 +130,28 @@ def test_autograd_against_finite_differences_of_the_gpu_solve():
         assert abs(ad - fd) <= 1e-5 * max(1.0, abs(fd)), (wye, ad, fd)
 
 
-def test_batch_independence_and_loop_forms(monkeypatch):
+@pytest.mark.parametrize("form", FORMS)
+def test_batch_independence_and_loop_forms(monkeypatch, form):
     f, Sw, Sd, w = F.make_workload("feeder128_b4096", B=100)
     r = forward_oracle(f, Sw, Sd)
     G = loss_grad(Sw.shape, 11)
     net = zbus.Network.from_feeder(f)
-    dw, dd, it, cv = net.solve_adjoint(dev(r["V"]), dev(G), dev(Sw), dev(Sd))
+    dw, dd, it, cv = net.solve_adjoint(dev(r["V"]), dev(G), dev(Sw), dev(Sd), precision=form)
     perm = np.random.default_rng(0).permutation(100)[:37]
     dw2, dd2, it2, cv2 = net.solve_adjoint(dev(r["V"][perm]), dev(G[perm]), dev(Sw[perm]),
-                                           dev(Sd[perm]))
+                                           dev(Sd[perm]), precision=form)
     idx = torch.from_numpy(perm).cuda()
     assert torch.equal(dw2, dw[idx]) and torch.equal(dd2, dd[idx])     # bitwise
     assert torch.equal(it2, it[idx])
+    if form == "tree":
+        return   # one launch, no sweep loop on the host side
     monkeypatch.setenv("ZBUS_NO_GRAPH", "1")
     dw3, dd3, it3, cv3 = net.solve_adjoint(dev(r["V"]), dev(G), dev(Sw), dev(Sd))
     assert torch.equal(dw3, dw) and torch.equal(dd3, dd) and torch.equal(it3, it)
 
 
-def test_zero_gradient_and_non_finite_voltages():
+@pytest.mark.parametrize("form", FORMS)
+def test_zero_gradient_and_non_finite_voltages(form):
     f = F.make_feeder(30, 12, delta_frac=0.3)
     Sw, Sd = F.make_scenarios(f, 6, 0.8, 1.2)
     r = forward_oracle(f, Sw, Sd)
@@ -148,7 +160,8 @@ def test_zero_gradient_and_non_finite_voltages():
     G[2] = 0
     V = r["V"].copy()
     V[4, 7] = np.nan
-    dw, dd, it, cv = net.solve_adjoint(dev(V), dev(G), dev(Sw), dev(Sd), tol=1e-13)
+    dw, dd, it, cv = net.solve_adjoint(dev(V), dev(G), dev(Sw), dev(Sd), tol=1e-13,
+                                       precision=form)
     cv, it = cv.cpu().numpy(), it.cpu().numpy()
     assert cv[2] == 1 and it[2] == 1
     assert not np.any(dw.cpu().numpy()[2]) and not np.any(dd.cpu().numpy()[2])
@@ -160,33 +173,88 @@ def test_zero_gradient_and_non_finite_voltages():
     assert_close(dd.cpu().numpy()[ok], Hd)
 
 
+@pytest.mark.parametrize("form", FORMS)
 @pytest.mark.parametrize("N,B,seed", [(12, 4, 3), (90, 20, 77)])
-def test_partial_phase_feeders(N, B, seed):
+def test_partial_phase_feeders(N, B, seed, form):
     f = F.make_partial_feeder(N, seed, lateral_frac=0.8, delta_frac=0.5, mult_hi=1.5)
     Sw, Sd = F.make_partial_scenarios(f, B, 0.5, 1.5)
     r = forward_oracle(f, Sw, Sd, f.bus_phase)
     G = loss_grad(Sw.shape, seed)
     Hw, Hd = O.solve_adjoint(r["Z"], r["V"], Sw, Sd, G, bus_phase=r["bus_phase"])
     net = zbus.Network.from_feeder(f)
-    dw, dd, it, cv = net.solve_adjoint(dev(r["V"]), dev(G), dev(Sw), dev(Sd), tol=1e-13)
+    dw, dd, it, cv = net.solve_adjoint(dev(r["V"]), dev(G), dev(Sw), dev(Sd), tol=1e-13,
+                                       precision=form)
     assert cv.cpu().numpy().all()
     assert_close(dw.cpu().numpy(), Hw)
     assert_close(dd.cpu().numpy(), Hd)
 
 
-def test_bench_workload_full_batch_sampled():
+@pytest.mark.parametrize("form", FORMS)
+def test_bench_workload_full_batch_sampled(form):
     """The 128-bus workload at its full 4096 scenarios, in the launch
     configuration the benchmark times; the oracle checks a sample."""
     f, Sw, Sd, w = F.make_workload("feeder128_b4096")
     r = forward_oracle(f, Sw, Sd)
     G = loss_grad(Sw.shape, 2024)
     net = zbus.Network.from_feeder(f)
-    dw, dd, it, cv = net.solve_adjoint(dev(r["V"]), dev(G), dev(Sw), dev(Sd), tol=1e-12)
+    dw, dd, it, cv = net.solve_adjoint(dev(r["V"]), dev(G), dev(Sw), dev(Sd), tol=1e-12,
+                                       precision=form)
     assert cv.cpu().numpy().all()
     pick = np.random.default_rng(1).choice(Sw.shape[0], 6, replace=False)
     Hw, Hd = O.solve_adjoint(r["Z"], r["V"][pick], Sw[pick], Sd[pick], G[pick])
     assert_close(dw.cpu().numpy()[pick], Hw)
     assert_close(dd.cpu().numpy()[pick], Hd)
+
+
+def with_extra(f, extra):
+    row = list(f.Y_row) + [r for r, c in extra]
+    col = list(f.Y_col) + [c for r, c in extra]
+    val = list(f.Y_val) + list(extra.values())
+    return (np.asarray(row, np.int32), np.asarray(col, np.int32),
+            np.asarray(val, np.complex128))
+
+
+def test_tree_form_with_shunts_and_refusal_of_a_meshed_network():
+    # capacitive shunts: the transposed sweep inverts only the series part,
+    # the exact Y^T residual keeps them
+    f = F.make_feeder(90, 12, delta_frac=0.4)
+    extra = {(3 * bus + p, 3 * bus + p): 0.02j for bus in (3, 9, 20, 33, 71) for p in range(3)}
+    row, col, val = with_extra(f, extra)
+    Sw, Sd = F.make_scenarios(f, 20, 0.8, 1.2, seed=4)
+    r = O.solve_coo(f.n_total, row, col, val, f.slack_idx, f.v_slack, Sw, Sd, tol=1e-14,
+                    max_iter=300)
+    assert r["converged"].all()
+    G = loss_grad(Sw.shape, 8)
+    Hw, Hd = O.solve_adjoint(r["Z"], r["V"], Sw, Sd, G)
+    net = zbus.Network(f.n_total, row, col, val, f.slack_idx, f.v_slack)
+    dw, dd, it, cv = net.solve_adjoint(dev(r["V"]), dev(G), dev(Sw), dev(Sd), tol=1e-13,
+                                       precision="tree")
+    assert cv.cpu().numpy().all()
+    assert_close(dw.cpu().numpy(), Hw)
+    assert_close(dd.cpu().numpy(), Hd)
+    # a loop: the tree form refuses, the dense form still answers
+    a, b = 5, 17
+    y = np.linalg.inv(f.z_line[4])
+    mesh = {}
+    for p in range(3):
+        for q in range(3):
+            mesh[(3 * a + p, 3 * a + q)] = y[p, q]
+            mesh[(3 * b + p, 3 * b + q)] = y[p, q]
+            mesh[(3 * a + p, 3 * b + q)] = -y[p, q]
+            mesh[(3 * b + p, 3 * a + q)] = -y[p, q]
+    row, col, val = with_extra(f, mesh)
+    netm = zbus.Network(f.n_total, row, col, val, f.slack_idx, f.v_slack)
+    rm = O.solve_coo(f.n_total, row, col, val, f.slack_idx, f.v_slack, Sw[:3], Sd[:3],
+                     tol=1e-14, max_iter=300)
+    with pytest.raises(zbus.ZbusError) as e:
+        netm.solve_adjoint(dev(rm["V"]), dev(G[:3]), dev(Sw[:3]), dev(Sd[:3]), precision="tree")
+    assert e.value.status == 7
+    dw, dd, it, cv = netm.solve_adjoint(dev(rm["V"]), dev(G[:3]), dev(Sw[:3]), dev(Sd[:3]),
+                                        tol=1e-13)
+    Hw, Hd = O.solve_adjoint(rm["Z"], rm["V"], Sw[:3], Sd[:3], G[:3])
+    assert_close(dw.cpu().numpy(), Hw)
+    with pytest.raises(zbus.ZbusError):
+        net.solve_adjoint(dev(r["V"]), dev(G), dev(Sw), dev(Sd), precision="fp16_scaled")
 
 
 def test_argument_errors():
@@ -195,11 +263,11 @@ def test_argument_errors():
     net = zbus.Network.from_feeder(f)
     V = dev(Sw)
     with pytest.raises(zbus.ZbusError):
-        zbus.zbus_solve_adjoint(net.handle, None, None, V, V, -1.0, 10, None, None,
+        zbus.zbus_solve_adjoint(net.handle, None, None, V, V, -1.0, 10, None, None, None,
                                 torch.empty(2, dtype=torch.int32, device="cuda"),
                                 torch.empty(2, dtype=torch.uint8, device="cuda"))
     with pytest.raises(zbus.ZbusError):
-        zbus.zbus_solve_adjoint(net.handle, None, None, V, V, 1e-10, 0, None, None,
+        zbus.zbus_solve_adjoint(net.handle, None, None, V, V, 1e-10, 0, None, None, None,
                                 torch.empty(2, dtype=torch.int32, device="cuda"),
                                 torch.empty(2, dtype=torch.uint8, device="cuda"))
     assert os.environ.get("ZBUS_NO_GRAPH") != "1"
