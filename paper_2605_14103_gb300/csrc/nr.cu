@@ -299,7 +299,8 @@ __global__ void __launch_bounds__(NR_THREADS, NR_MIN_CTAS) k_nr_solve(NrDev d, S
   double* gv = sn + m;                     // [m + 1]
   double* hh = gv + m + 1;                 // [m + 1] this step's Gram-Schmidt coefficients
   double* red = hh + m + 1;                // [(m + 1) * NR_WARPS]
-  T* y = reinterpret_cast<T*>(red + (m + 1) * NR_WARPS);   // [N] factor work space
+  T* hT = reinterpret_cast<T*>(red + (m + 1) * NR_WARPS);  // [m + 1] hh in T, converted once
+  T* y = hT + m + 2;                       // [N] factor work space
   __shared__ int s_flag;
   __shared__ int s_jd;
 
@@ -453,12 +454,13 @@ __global__ void __launch_bounds__(NR_THREADS, NR_MIN_CTAS) k_nr_solve(NrDev d, S
               double s = 0.0;
               for (int q = 0; q < NR_WARPS; ++q) s += red[i * NR_WARPS + q];
               hh[i] = s;
+              hT[i] = (T)s;
               H[j * (m + 1) + i] += s;
             }
             __syncthreads();
             for (int e = t; e < dim; e += NR_THREADS) {
               T s = wv[e];
-              for (int i = 0; i <= j; ++i) s -= (T)hh[i] * Vk[(int64_t)i * dim + e];
+              for (int i = 0; i <= j; ++i) s -= hT[i] * Vk[(int64_t)i * dim + e];
               wv[e] = s;
             }
             __syncthreads();
@@ -499,12 +501,13 @@ __global__ void __launch_bounds__(NR_THREADS, NR_MIN_CTAS) k_nr_solve(NrDev d, S
             double s = gv[i];
             for (int c = i + 1; c < jd; ++c) s -= H[c * (m + 1) + i] * hh[c];
             hh[i] = s / H[i * (m + 1) + i];
+            hT[i] = (T)hh[i];
           }
         }
         __syncthreads();
         for (int e = t; e < dim; e += NR_THREADS) {
           T s = x[e];
-          for (int i = 0; i < jd; ++i) s += (T)hh[i] * Vk[(int64_t)i * dim + e];
+          for (int i = 0; i < jd; ++i) s += hT[i] * Vk[(int64_t)i * dim + e];
           x[e] = s;
         }
         __syncthreads();
@@ -716,7 +719,7 @@ zbus_status upload_factor(zbus_nr_network net, const HostFactor& hf, Factor& f, 
 
 size_t smem_bytes(int m, int N, bool mixed) {
   return sizeof(double) * ((size_t)(m + 1) * m + 2 * m + 2 * (m + 1) + (size_t)(m + 1) * NR_WARPS) +
-         (mixed ? sizeof(float) : sizeof(double)) * (size_t)N;
+         (mixed ? sizeof(float) : sizeof(double)) * ((size_t)N + m + 2);
 }
 
 int64_t scratch_doubles(const zbus_nr_network net, int m, bool mixed) {
