@@ -185,21 +185,21 @@ __device__ void factor_solve(const Factor& f, const T* in, T* y, T* out) {
   __syncthreads();
   for (int l = 0; l < f.n_fl; ++l) {
     for (int k = f.fl_ptr[l] + t; k < f.fl_ptr[l + 1]; k += NR_THREADS) {
-      const int i = f.fl_row[k];
-      const int e0 = f.l_ptr[k], e1 = f.l_ptr[k + 1];
+      const int i = __ldg(f.fl_row + k);
+      const int e0 = __ldg(f.l_ptr + k), e1 = __ldg(f.l_ptr + k + 1);
       T s = y[i];
-      for (int e = e0; e < e1; ++e) s -= lv[e] * y[f.l_col[e]];
+      for (int e = e0; e < e1; ++e) s -= __ldg(lv + e) * y[__ldg(f.l_col + e)];
       y[i] = s;
     }
     __syncthreads();
   }
   for (int l = 0; l < f.n_bl; ++l) {
     for (int k = f.bl_ptr[l] + t; k < f.bl_ptr[l + 1]; k += NR_THREADS) {
-      const int i = f.bl_row[k];
-      const int e0 = f.u_ptr[k], e1 = f.u_ptr[k + 1];
-      const T di = dv[k];
+      const int i = __ldg(f.bl_row + k);
+      const int e0 = __ldg(f.u_ptr + k), e1 = __ldg(f.u_ptr + k + 1);
+      const T di = __ldg(dv + k);
       T s = y[i];
-      for (int e = e0; e < e1; ++e) s -= uv[e] * y[f.u_col[e]];
+      for (int e = e0; e < e1; ++e) s -= __ldg(uv + e) * y[__ldg(f.u_col + e)];
       y[i] = s * di;
     }
     __syncthreads();
@@ -219,7 +219,8 @@ __device__ void precondition(const NrDev& d, const T* ivm, const T* r, T* z, T* 
     const T* gv = gval<T>(d);
     for (int p = t; p < d.nq; p += NR_THREADS) {
       T s = r[d.nt + p];
-      for (int e = d.g_ptr[p]; e < d.g_ptr[p + 1]; ++e) s -= gv[e] * z[d.g_col[e]];
+      for (int e = __ldg(d.g_ptr + p); e < __ldg(d.g_ptr + p + 1); ++e)
+        s -= __ldg(gv + e) * z[__ldg(d.g_col + e)];
       tmp[d.nt + p] = s * ivm[d.q_bus[p]];
     }
     __syncthreads();
@@ -246,8 +247,8 @@ __device__ void jvp(const NrDev& d, const T* Vr, const T* Vi, const T* Ir, const
     if (pt < 0 && pq < 0) continue;
     T yr = 0, yi = 0;
     for (int e = d.y_ptr[i]; e < d.y_ptr[i + 1]; ++e) {
-      const auto y = yv[e];
-      const int j = d.y_col[e];
+      const auto y = __ldg(yv + e);
+      const int j = __ldg(d.y_col + e);
       yr += y.x * dVr[j] - y.y * dVi[j];
       yi += y.x * dVi[j] + y.y * dVr[j];
     }
