@@ -560,6 +560,22 @@ zbus_status zbus_nr_solve(zbus_nr_network net, int64_t B, const double* P, const
                           double* V_out, int32_t* iters, uint8_t* converged,
                           int32_t* gmres_iters, void* cuda_stream);
 
+/*
+ * zbus_checked_status -- 1 if this library is the checked build (compiled
+ * with -DZBUS_CHECKED, libzbus_checked.so), else 0.  In the checked build
+ * every index the kernels read from a table (columns, active lists, tree
+ * nodes, maps, permutations, level lists) is tested against its buffer
+ * before use; a bad one records a code (0x1nn plain FP64 kernels, 0x2nn
+ * tensor-core and tree engine, 0x3nn load gradient, 0x4nn Newton-Raphson,
+ * 0x5nn partial-phase maps) and the access is skipped instead of faulting.
+ * *word (may be NULL) receives the first code recorded since the last call,
+ * 0 if none (always 0 in the normal build), and the codes are cleared.
+ * Synchronises the current device.  Project-written: the paper has no
+ * counterpart (it stands in for a memory checker on machines where none may
+ * run).
+ */
+int32_t zbus_checked_status(uint32_t* word);
+
 /* Human-readable name of a status code (static storage). */
 const char* zbus_status_string(zbus_status s);
 

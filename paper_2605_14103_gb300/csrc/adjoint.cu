@@ -143,7 +143,7 @@ __global__ void k_adj_rhs(const SolveCtx* __restrict__ ctx, int n, int n_pad) {
     const int j0 = 3 * k;
     const int64_t o = (int64_t)slot * n_pad + j0;
     double2 lam[3] = {make_double2(0.0, 0.0), make_double2(0.0, 0.0), make_double2(0.0, 0.0)};
-    if (j0 < n) {
+    if (j0 < n && ZB_IN(ctx->list[slot], ctx->B, 0x301u)) {
       const int b = ctx->list[slot];
       const int m = min(3, n - j0);
       const int64_t e = (int64_t)b * n + j0;
@@ -255,6 +255,7 @@ constexpr int AT_WARPS = AT_THREADS / 32;
 
 struct AdjTree {
   int n, nb, depth, B, max_iter;
+  int64_t nblk;           // branch-form blocks (checked build)
   int onchip;             // mu and r in shared memory (else in the scratch slice)
   double tol;
   const int4* node;       // per breadth-first position: bus, parent position, children range
@@ -338,6 +339,9 @@ __global__ void __launch_bounds__(AT_THREADS) k_adj_tree(AdjTree a) {
       // position (bus c, parent p)
       for (int i = t; i < nb; i += AT_THREADS) {
         const int4 nd = a.node[i];
+        if (!ZB_IN(nd.x, nb, 0x302u) || !ZB_IN(nd.y + 1, nb + 1, 0x303u) ||
+            !ZB_IN(a.pblk[i], a.nblk, 0x304u))
+          continue;
         const int c = nd.x;
         const int j0 = 3 * c;
         double2 u[3], lam[3], yt[3];
@@ -387,10 +391,11 @@ __global__ void __launch_bounds__(AT_THREADS) k_adj_tree(AdjTree a) {
       for (int L = a.depth - 2; L >= 0; --L) {
         for (int i = a.lvl[L] + t; i < a.lvl[L + 1]; i += AT_THREADS) {
           const int4 nd = a.node[i];
-          if (nd.z == nd.w) continue;
+          if (nd.z == nd.w || !ZB_IN(nd.x, nb, 0x307u)) continue;
           double2* own = r + 3 * nd.x;
           double2 acc[3] = {own[0], own[1], own[2]};
           for (int ch = nd.z; ch < nd.w; ++ch) {
+            if (!ZB_IN(ch, nb, 0x305u) || !ZB_IN(a.node[ch].x, nb, 0x306u)) continue;
             const int kb = 3 * a.node[ch].x;
             const int cm = a.mask[ch];   // a phase the child's line lacks stays below
 #pragma unroll
@@ -409,6 +414,7 @@ __global__ void __launch_bounds__(AT_THREADS) k_adj_tree(AdjTree a) {
       for (int L = 0; L < a.depth; ++L) {
         for (int i = a.lvl[L] + t; i < a.lvl[L + 1]; i += AT_THREADS) {
           const int4 nd = a.node[i];
+          if (!ZB_IN(nd.x, nb, 0x308u) || !ZB_IN(nd.y + 1, nb + 1, 0x309u)) continue;
           double2* own = r + 3 * nd.x;
           const double2 sv[3] = {own[0], own[1], own[2]};
           double2 xp[3] = {make_double2(0.0, 0.0), make_double2(0.0, 0.0), make_double2(0.0, 0.0)};
@@ -615,6 +621,7 @@ zbus_status adjoint_tree_device(zbus_network net, int64_t B, const double* S_wye
   a.mask = net->t_mask;
   a.z = net->t_z64;
   a.pblk = net->t_pblk;
+  a.nblk = net->nblk;
   a.bptr = net->bsr_ptr;
   a.bcol = net->bsr_col;
   a.bval = net->bsr_val;
@@ -673,6 +680,8 @@ void free_adjoint(zbus_network net) {
   net->adj_tree_scratch = nullptr;
   net->adj_tree_ctas = 0;
 }
+
+ZB_CHECK_WORD_ACCESSOR(check_word_adjoint)
 
 }  // namespace zbus
 

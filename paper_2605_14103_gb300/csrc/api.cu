@@ -341,6 +341,23 @@ const char* zbus_status_string(zbus_status s) {
 
 const char* zbus_last_error(void) { return g_last_error.c_str(); }
 
+int32_t zbus_checked_status(uint32_t* word) {
+  cudaDeviceSynchronize();
+  uint32_t (*const words[])(bool) = {check_word_f64, check_word_group, check_word_adjoint,
+                                     check_word_nr, check_word_phased};
+  uint32_t first = 0;
+  for (auto fn : words) {
+    const uint32_t w = fn(true);
+    if (!first) first = w;
+  }
+  if (word) *word = first;
+#ifdef ZBUS_CHECKED
+  return 1;
+#else
+  return 0;
+#endif
+}
+
 zbus_status zbus_network_create(int32_t n_total, int64_t nnz, const int32_t* row,
                                 const int32_t* col, const double* val_reim,
                                 const int32_t* slack_idx, const double* v_slack_reim,

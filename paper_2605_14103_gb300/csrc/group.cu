@@ -217,6 +217,7 @@ k_residual_group(GroupState* __restrict__ gs, const ItemDesc* __restrict__ items
         for (int p = 0; p < 3; ++p) ah[p][0] = al[p][0] = ah[p][1] = al[p][1] = 0.f;
         for (int t = bptr[a]; t < bptr[a + 1]; ++t) {
           const int cb = bcol[t];   // the same for the whole warp
+          if (cb >= 0 && !ZB_IN(cb, nb, 0x201u)) continue;
           float dh[3][2], dl[3][2];   // vector multiplied by the block, double-float
           if (cb >= 0) {
 #pragma unroll
@@ -621,7 +622,13 @@ k_tree_group(GroupState* __restrict__ gs, const ItemDesc* __restrict__ items,
   float* zst = reinterpret_cast<float*>(zt + 9 * nb);        // [nb]
   uint8_t* pmask = reinterpret_cast<uint8_t*>(zst + nb);     // [nb] phases of the parent line
   for (int i = threadIdx.x; i < nb; i += blockDim.x) {
-    node[i] = it.t_node[i];
+    int4 nd = it.t_node[i];
+    // checked build: a node out of range becomes a leaf hanging off the slack
+    if (!ZB_IN(nd.x, nb, 0x202u) || !ZB_IN(nd.y + 1, nb + 1, 0x203u) ||
+        !ZB_IN(nd.z, nb + 1, 0x204u) || !ZB_IN(nd.w, nb + 1, 0x205u) ||
+        !ZB_IN(nd.w - nd.z, nb + 1, 0x206u))
+      nd = make_int4(0, -1, 0, 0);
+    node[i] = nd;
     zst[i] = it.t_zs[i];
     pmask[i] = it.t_mask[i];
   }
@@ -995,6 +1002,7 @@ k_check(const double2* __restrict__ V, const double2* __restrict__ Sw,
     const int t1 = bptr[a + 1];
     for (int t = bptr[a]; t < t1; ++t) {
       const int cb = bcol[t];
+      if (cb >= 0 && !ZB_IN(cb, nb, 0x207u)) continue;
       double dr[3], di[3];
       if (cb >= 0) {
 #pragma unroll
@@ -1483,4 +1491,8 @@ zbus_status group_collect(Group* g, int k, int64_t s0, int64_t B, double* V_out,
   return ZBUS_OK;
 }
 
+}  // namespace zbus
+
+namespace zbus {
+ZB_CHECK_WORD_ACCESSOR(check_word_group)
 }  // namespace zbus

@@ -63,7 +63,7 @@ __global__ void k_currents_f64(const SolveCtx* __restrict__ ctx, int n, int n_pa
     const int j0 = 3 * k;
     const int64_t o = (int64_t)slot * n_pad + j0;
     double2 inj[3] = {make_double2(0.0, 0.0), make_double2(0.0, 0.0), make_double2(0.0, 0.0)};
-    if (j0 < n) {
+    if (j0 < n && ZB_IN(ctx->list[slot], ctx->B, 0x101u)) {
       const int b = ctx->list[slot];
       const int m = min(3, n - j0);
       const int64_t e = (int64_t)b * n + j0;
@@ -190,7 +190,7 @@ k_gemm3m_f64(const SolveCtx* __restrict__ ctx, const double* __restrict__ Zr,
       const int r = tm * TM + a;
       const int slot = slot0 + r;
       double dmax = 0.0, dsum = 0.0;
-      if (slot < count) {
+      if (slot < count && ZB_IN(list[slot], ctx->B, 0x102u)) {
         const int b = list[slot];
 #pragma unroll
         for (int c = 0; c < TN; ++c) {
@@ -241,6 +241,7 @@ __global__ void k_decide(SolveCtx* __restrict__ ctx) {
   const int it = ctx->iter + 1;
   const int ntn = ctx->ntn;
   const int b = ctx->list[slot];
+  if (!ZB_IN(b, ctx->B, 0x103u)) return;
   const double* part = ctx->part + (int64_t)slot * ntn * 2;
   double dmax = 0.0, dsum = 0.0;
   for (int t = 0; t < ntn; ++t) {
@@ -346,6 +347,7 @@ __global__ void k_mismatch(const double2* __restrict__ V, const double2* __restr
       const int j = j0 + p;
       double2 acc = ys[j];
       for (int t = ptr[j]; t < ptr[j + 1]; ++t) {
+        if (!ZB_IN(col[t], n, 0x104u)) continue;
         const double2 y = val[t], x = v[col[t]];
         acc.x += y.x * x.x - y.y * x.y;
         acc.y += y.x * x.y + y.y * x.x;
@@ -405,4 +407,8 @@ void launch_mismatch(const double2* V, const double2* S_wye, const double2* S_de
   k_mismatch<<<B, 256, 0, st>>>(V, S_wye, S_del, ptr, col, val, ys, n, out);
 }
 
+}  // namespace zbus
+
+namespace zbus {
+ZB_CHECK_WORD_ACCESSOR(check_word_f64)
 }  // namespace zbus

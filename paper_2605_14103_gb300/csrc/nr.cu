@@ -181,14 +181,17 @@ __device__ void factor_solve(const Factor& f, const T* in, T* y, T* out) {
   const T* lv = lval<T>(f);
   const T* uv = uval<T>(f);
   const T* dv = dval<T>(f);
-  for (int i = t; i < f.n; i += NR_THREADS) y[i] = in[f.perm[i]];
+  for (int i = t; i < f.n; i += NR_THREADS)
+    y[i] = ZB_IN(f.perm[i], f.n, 0x401u) ? in[f.perm[i]] : T(0);
   __syncthreads();
   for (int l = 0; l < f.n_fl; ++l) {
     for (int k = f.fl_ptr[l] + t; k < f.fl_ptr[l + 1]; k += NR_THREADS) {
       const int i = __ldg(f.fl_row + k);
       const int e0 = __ldg(f.l_ptr + k), e1 = __ldg(f.l_ptr + k + 1);
+      if (!ZB_IN(i, f.n, 0x402u)) continue;
       T s = y[i];
-      for (int e = e0; e < e1; ++e) s -= __ldg(lv + e) * y[__ldg(f.l_col + e)];
+      for (int e = e0; e < e1; ++e)
+        if (ZB_IN(__ldg(f.l_col + e), f.n, 0x403u)) s -= __ldg(lv + e) * y[__ldg(f.l_col + e)];
       y[i] = s;
     }
     __syncthreads();
@@ -198,13 +201,16 @@ __device__ void factor_solve(const Factor& f, const T* in, T* y, T* out) {
       const int i = __ldg(f.bl_row + k);
       const int e0 = __ldg(f.u_ptr + k), e1 = __ldg(f.u_ptr + k + 1);
       const T di = __ldg(dv + k);
+      if (!ZB_IN(i, f.n, 0x404u)) continue;
       T s = y[i];
-      for (int e = e0; e < e1; ++e) s -= __ldg(uv + e) * y[__ldg(f.u_col + e)];
+      for (int e = e0; e < e1; ++e)
+        if (ZB_IN(__ldg(f.u_col + e), f.n, 0x405u)) s -= __ldg(uv + e) * y[__ldg(f.u_col + e)];
       y[i] = s * di;
     }
     __syncthreads();
   }
-  for (int i = t; i < f.n; i += NR_THREADS) out[f.perm[i]] = y[i];
+  for (int i = t; i < f.n; i += NR_THREADS)
+    if (ZB_IN(f.perm[i], f.n, 0x406u)) out[f.perm[i]] = y[i];
   __syncthreads();
 }
 
@@ -212,7 +218,8 @@ __device__ void factor_solve(const Factor& f, const T* in, T* y, T* out) {
 template <class T>
 __device__ void precondition(const NrDev& d, const T* ivm, const T* r, T* z, T* tmp, T* y) {
   const int t = threadIdx.x;
-  for (int p = t; p < d.nt; p += NR_THREADS) tmp[p] = r[p] * ivm[d.t_bus[p]];
+  for (int p = t; p < d.nt; p += NR_THREADS)
+    tmp[p] = ZB_IN(d.t_bus[p], d.N, 0x407u) ? r[p] * ivm[d.t_bus[p]] : T(0);
   __syncthreads();
   factor_solve<T>(d.Bp, tmp, y, z);
   if (d.nq > 0) {
@@ -220,8 +227,8 @@ __device__ void precondition(const NrDev& d, const T* ivm, const T* r, T* z, T* 
     for (int p = t; p < d.nq; p += NR_THREADS) {
       T s = r[d.nt + p];
       for (int e = __ldg(d.g_ptr + p); e < __ldg(d.g_ptr + p + 1); ++e)
-        s -= __ldg(gv + e) * z[__ldg(d.g_col + e)];
-      tmp[d.nt + p] = s * ivm[d.q_bus[p]];
+        if (ZB_IN(__ldg(d.g_col + e), d.nt, 0x408u)) s -= __ldg(gv + e) * z[__ldg(d.g_col + e)];
+      tmp[d.nt + p] = ZB_IN(d.q_bus[p], d.N, 0x409u) ? s * ivm[d.q_bus[p]] : T(0);
     }
     __syncthreads();
     factor_solve<T>(d.Bpp, tmp + d.nt, y, z + d.nt);
@@ -249,6 +256,7 @@ __device__ void jvp(const NrDev& d, const T* Vr, const T* Vi, const T* Ir, const
     for (int e = d.y_ptr[i]; e < d.y_ptr[i + 1]; ++e) {
       const auto y = __ldg(yv + e);
       const int j = __ldg(d.y_col + e);
+      if (!ZB_IN(j, d.N, 0x40au)) continue;
       yr += y.x * dVr[j] - y.y * dVi[j];
       yi += y.x * dVi[j] + y.y * dVr[j];
     }
@@ -371,6 +379,7 @@ __global__ void __launch_bounds__(NR_THREADS, NR_MIN_CTAS) k_nr_solve(NrDev d, S
         for (int e = d.y_ptr[i]; e < d.y_ptr[i + 1]; ++e) {
           const double2 yv = d.y_val[e];
           const int j = d.y_col[e];
+          if (!ZB_IN(j, N, 0x40bu)) continue;
           ir += yv.x * Vr[j] - yv.y * Vi[j];
           ii += yv.x * Vi[j] + yv.y * Vr[j];
         }
@@ -515,8 +524,10 @@ __global__ void __launch_bounds__(NR_THREADS, NR_MIN_CTAS) k_nr_solve(NrDev d, S
         if (s_flag) done = true;
       }
       // Newton update (FP64 state)
-      for (int p = t; p < nt; p += NR_THREADS) va[d.t_bus[p]] += (double)x[p];
-      for (int p = t; p < d.nq; p += NR_THREADS) vm[d.q_bus[p]] += (double)x[nt + p];
+      for (int p = t; p < nt; p += NR_THREADS)
+        if (ZB_IN(d.t_bus[p], N, 0x40cu)) va[d.t_bus[p]] += (double)x[p];
+      for (int p = t; p < d.nq; p += NR_THREADS)
+        if (ZB_IN(d.q_bus[p], N, 0x40du)) vm[d.q_bus[p]] += (double)x[nt + p];
       __syncthreads();
     }
     double2* Vo = a.V + (int64_t)b * N;
@@ -733,6 +744,9 @@ int64_t scratch_doubles(const zbus_nr_network net, int m, bool mixed) {
 
 }  // namespace
 }  // namespace nr
+
+ZB_CHECK_WORD_ACCESSOR(check_word_nr)
+
 }  // namespace zbus
 
 using namespace zbus;

@@ -27,6 +27,7 @@ __global__ void k_ph_scatter(const double2* __restrict__ src, double2* __restric
     const int64_t b = t / n_user;
     const int j = (int)(t - b * n_user);
     if (keep && !keep[j]) continue;
+    if (!ZB_IN(map[j], n, 0x501u)) continue;
     dst[b * n + map[j]] = src[t];
   }
 }
@@ -40,7 +41,8 @@ __global__ void k_ph_gather(const double2* __restrict__ src, double2* __restrict
        t += (int64_t)gridDim.x * blockDim.x) {
     const int64_t b = t / n_user;
     const int j = (int)(t - b * n_user);
-    dst[t] = (keep && !keep[j]) ? make_double2(0.0, 0.0) : src[b * n + map[j]];
+    dst[t] = (keep && !keep[j]) || !ZB_IN(map[j], n, 0x502u) ? make_double2(0.0, 0.0)
+                                                              : src[b * n + map[j]];
   }
 }
 
@@ -51,7 +53,8 @@ __global__ void k_ph_gather_z(const double2* __restrict__ Z, double2* __restrict
   for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < total;
        t += (int64_t)gridDim.x * blockDim.x) {
     const int i = (int)(t / n_user), j = (int)(t - (int64_t)i * n_user);
-    Zu[t] = Z[(int64_t)map[i] * n + map[j]];
+    Zu[t] = ZB_IN(map[i], n, 0x503u) && ZB_IN(map[j], n, 0x504u) ? Z[(int64_t)map[i] * n + map[j]]
+                                                                 : make_double2(0.0, 0.0);
   }
 }
 
@@ -205,4 +208,8 @@ void phased_free(zbus_network net) {
   net->ph_cap = 0;
 }
 
+}  // namespace zbus
+
+namespace zbus {
+ZB_CHECK_WORD_ACCESSOR(check_word_phased)
 }  // namespace zbus

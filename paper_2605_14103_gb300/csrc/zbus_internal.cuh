@@ -42,6 +42,44 @@ constexpr int F64_PAD = 48;  // n is padded to a multiple of this
 inline int round_up(int x, int m) { return (x + m - 1) / m * m; }
 
 // ---------------------------------------------------------------------------
+// Checked build (-DZBUS_CHECKED): every index read from a table (columns,
+// active lists, tree nodes, maps, permutations, level lists) is tested
+// against the size of the buffer it addresses before the access; a bad one
+// records its code in this translation unit's check word and the access is
+// skipped.  Nothing traps; zbus_checked_status reports the words.  The normal
+// build compiles every test away.
+// ---------------------------------------------------------------------------
+#ifdef ZBUS_CHECKED
+static __device__ unsigned int g_zb_check_word;
+__device__ __forceinline__ bool zb_in(long long i, long long n, unsigned int code) {
+  if (i >= 0 && i < n) return true;
+  atomicCAS(&g_zb_check_word, 0u, code);
+  return false;
+}
+#define ZB_IN(i, n, code) ::zbus::zb_in((long long)(i), (long long)(n), (code))
+#define ZB_CHECK_WORD_ACCESSOR(fn)                                        \
+  uint32_t fn(bool clear) {                                              \
+    uint32_t v = 0;                                                      \
+    cudaMemcpyFromSymbol(&v, g_zb_check_word, sizeof(v));                \
+    if (clear) {                                                         \
+      const uint32_t z = 0;                                              \
+      cudaMemcpyToSymbol(g_zb_check_word, &z, sizeof(z));                \
+    }                                                                    \
+    return v;                                                            \
+  }
+#else
+#define ZB_IN(i, n, code) true
+#define ZB_CHECK_WORD_ACCESSOR(fn) \
+  uint32_t fn(bool) { return 0; }
+#endif
+// the check words of the translation units (0 in the normal build)
+uint32_t check_word_f64(bool clear);
+uint32_t check_word_group(bool clear);
+uint32_t check_word_adjoint(bool clear);
+uint32_t check_word_nr(bool clear);
+uint32_t check_word_phased(bool clear);
+
+// ---------------------------------------------------------------------------
 // Per-solve device context.  Kernels read pointers and sizes from it, so a
 // captured graph does not depend on the caller's buffers.
 // ---------------------------------------------------------------------------

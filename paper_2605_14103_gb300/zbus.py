@@ -13,7 +13,8 @@ import os
 import numpy as np
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
-LIB_PATH = os.path.join(_HERE, "libzbus.so")
+# ZBUS_LIB selects another build of the library (the checked build)
+LIB_PATH = os.environ.get("ZBUS_LIB") or os.path.join(_HERE, "libzbus.so")
 
 ZBUS_OK = 0
 STATUS = {0: "ZBUS_OK", 1: "ZBUS_ERR_ARG", 2: "ZBUS_ERR_SINGULAR", 3: "ZBUS_ERR_OOM",
@@ -110,6 +111,7 @@ _SIGS = {
                                        C.POINTER(C.c_int64), C.POINTER(C.c_int32)]),
     "zbus_nr_solve": (C.c_int, [_P, C.c_int64, _P, _P, C.c_double, C.c_int32,
                                 C.POINTER(zbus_nr_opts), _P, _P, _P, _P, _P]),
+    "zbus_checked_status": (C.c_int32, [C.POINTER(C.c_uint32)]),
     "zbus_status_string": (C.c_char_p, [C.c_int]),
     "zbus_last_error": (C.c_char_p, []),
 }
@@ -433,6 +435,13 @@ def serve(networks, requests, hbm_budget_bytes=120 << 30, max_slots=4096,
         if out[i] is not None:
             out[i].update(V=V, iters=it, converged=cv)
     return out
+
+
+def zbus_checked_status():
+    """(1 if the checked build else 0, first check code recorded since the last call)."""
+    w = C.c_uint32(0)
+    flag = lib().zbus_checked_status(C.byref(w))
+    return int(flag), int(w.value)
 
 
 def zbus_status_string(s: int) -> str:
