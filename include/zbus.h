@@ -54,7 +54,8 @@ typedef enum {
   ZBUS_ERR_CUDA = 4,        /* a CUDA runtime call failed */
   ZBUS_ERR_TIMEOUT = 5,     /* a bounded device wait gave up */
   ZBUS_ERR_DEVICE = 6,      /* a kernel reported an internal error word */
-  ZBUS_ERR_UNSUPPORTED = 7  /* option not available for this network / device */
+  ZBUS_ERR_UNSUPPORTED = 7, /* option not available for this network / device */
+  ZBUS_ERR_SOURCE = 8       /* zbus_serve: the request source reported a failure */
 } zbus_status;
 
 typedef enum {
@@ -291,7 +292,9 @@ typedef struct {
 
 /* Polled by the serving loop with the current serving-clock time (seconds
  * since the loop started): return 1 and fill *req if a request is ready, 0 if
- * none is ready now, -1 when no further request will come. */
+ * none is ready now, -1 when no further request will come, -2 (or below) if
+ * the source failed: no further request is taken, the requests it had
+ * delivered are still served, and zbus_serve returns ZBUS_ERR_SOURCE. */
 typedef int32_t (*zbus_request_source)(void* user, double now, zbus_request* req);
 /* Called once per request when its results are complete on the device. */
 typedef void (*zbus_completion_sink)(void* user, const zbus_request* req,

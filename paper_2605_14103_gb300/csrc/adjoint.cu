@@ -693,6 +693,7 @@ extern "C" zbus_status zbus_solve_adjoint(zbus_network net, int64_t B, const dou
                                           const zbus_solve_opts* opts, double* dS_wye,
                                           double* dS_delta, int32_t* iters, uint8_t* converged,
                                           void* cuda_stream) {
+  NvtxRange nvtx_range("zbus_solve_adjoint");
   set_error("");
   if (!net) return fail(ZBUS_ERR_ARG, "network is NULL");
   if (B < 0 || B > INT32_MAX / 4) return fail(ZBUS_ERR_ARG, "B out of range");

@@ -335,6 +335,7 @@ const char* zbus_status_string(zbus_status s) {
     case ZBUS_ERR_TIMEOUT: return "ZBUS_ERR_TIMEOUT";
     case ZBUS_ERR_DEVICE: return "ZBUS_ERR_DEVICE";
     case ZBUS_ERR_UNSUPPORTED: return "ZBUS_ERR_UNSUPPORTED";
+    case ZBUS_ERR_SOURCE: return "ZBUS_ERR_SOURCE";
   }
   return "ZBUS_UNKNOWN_STATUS";
 }
@@ -362,6 +363,7 @@ zbus_status zbus_network_create(int32_t n_total, int64_t nnz, const int32_t* row
                                 const int32_t* col, const double* val_reim,
                                 const int32_t* slack_idx, const double* v_slack_reim,
                                 void* cuda_stream, zbus_network* out) {
+  NvtxRange nvtx_range("zbus_network_create");
   g_last_error.clear();
   if (!out) return fail(ZBUS_ERR_ARG, "out is NULL");
   *out = nullptr;
@@ -714,6 +716,7 @@ zbus_status zbus_solve(zbus_network net, int64_t B, const double* S_wye, const d
                        const double* V_init, double tol, int32_t max_iter,
                        const zbus_solve_opts* opts, double* V_out, int32_t* iters,
                        uint8_t* converged, void* cuda_stream) {
+  NvtxRange nvtx_range("zbus_solve");
   g_last_error.clear();
   if (!net) return fail(ZBUS_ERR_ARG, "network is NULL");
   if (B < 0 || B > INT32_MAX / 4) return fail(ZBUS_ERR_ARG, "B out of range");
@@ -751,6 +754,7 @@ zbus_status zbus_solve(zbus_network net, int64_t B, const double* S_wye, const d
 
 zbus_status zbus_solve_batched(const zbus_batch_item* items, int32_t n_items, double tol,
                                int32_t max_iter, const zbus_solve_opts* opts, void* cuda_stream) {
+  NvtxRange nvtx_range("zbus_solve_batched");
   g_last_error.clear();
   if (n_items < 0 || (n_items > 0 && !items)) return fail(ZBUS_ERR_ARG, "items is NULL");
   if (n_items == 0) return ZBUS_OK;
@@ -841,6 +845,7 @@ zbus_status zbus_last_profile(zbus_network net, int32_t max_n, float* ms, int32_
 zbus_status zbus_power_mismatch(zbus_network net, int64_t B, const double* V,
                                 const double* S_wye, const double* S_delta, double* out,
                                 void* cuda_stream) {
+  NvtxRange nvtx_range("zbus_power_mismatch");
   g_last_error.clear();
   if (!net) return fail(ZBUS_ERR_ARG, "network is NULL");
   if (B < 0 || B > INT32_MAX) return fail(ZBUS_ERR_ARG, "B out of range");

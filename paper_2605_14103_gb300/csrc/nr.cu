@@ -767,6 +767,7 @@ zbus_status zbus_nr_network_create(int32_t N, int64_t nnz, const int32_t* row,
                                    const int32_t* col, const double* val_reim,
                                    const int32_t* bus_type, const double* v_set, double eps,
                                    void* cuda_stream, zbus_nr_network* out) {
+  NvtxRange nvtx_range("zbus_nr_network_create");
   set_error("");
   if (!out) return fail(ZBUS_ERR_ARG, "out is NULL");
   *out = nullptr;
@@ -926,6 +927,7 @@ zbus_status zbus_nr_solve(zbus_nr_network net, int64_t B, const double* P, const
                           double tol, int32_t max_iter, const zbus_nr_opts* opts, double* V_out,
                           int32_t* iters, uint8_t* converged, int32_t* gmres_iters,
                           void* cuda_stream) {
+  NvtxRange nvtx_range("zbus_nr_solve");
   set_error("");
   if (!net) return fail(ZBUS_ERR_ARG, "network is NULL");
   if (B < 0 || B > INT32_MAX) return fail(ZBUS_ERR_ARG, "B out of range");

@@ -62,6 +62,7 @@ using namespace zbus;
 extern "C" zbus_status zbus_serve(const zbus_serve_config* cfg, zbus_network* pool,
                                   int32_t n_pool, zbus_request_source src,
                                   zbus_completion_sink sink, void* user, void* cuda_stream) {
+  NvtxRange nvtx_range("zbus_serve");
   set_error("");
   if (!cfg || !pool || n_pool <= 0 || !src || !sink) return fail(ZBUS_ERR_ARG, "bad arguments");
   if (cfg->precision != ZBUS_MIXED_FP16_SCALED && cfg->precision != ZBUS_MIXED_BF16X2 &&
@@ -163,6 +164,7 @@ extern "C" zbus_status zbus_serve(const zbus_serve_config* cfg, zbus_network* po
   const auto t0 = std::chrono::steady_clock::now();
   std::deque<zbus_request> pending;
   bool ended = false;
+  bool source_failed = false;
   int64_t live_total = 0;
   std::vector<int32_t> h_it;
   std::vector<uint8_t> h_cv;
@@ -172,9 +174,14 @@ extern "C" zbus_status zbus_serve(const zbus_serve_config* cfg, zbus_network* po
       zbus_request r;
       std::memset(&r, 0, sizeof(r));
       const int32_t got = src(user, now, &r);
-      if (got == 1) pending.push_back(r);
-      else if (got < 0) ended = true;
-      else break;
+      if (got == 1) {
+        pending.push_back(r);
+      } else if (got < 0) {
+        ended = true;
+        source_failed = got <= -2;
+      } else {
+        break;
+      }
     }
     // admissions, in arrival order, first fit
     bool admitted = false;
@@ -215,7 +222,10 @@ extern "C" zbus_status zbus_serve(const zbus_serve_config* cfg, zbus_network* po
       std::this_thread::sleep_for(std::chrono::microseconds(50));
       continue;
     }
-    SV_CHECK(group_sweep(&g, 0, false, st));
+    {
+      NvtxRange sweep_range("zbus_serve sweep");
+      SV_CHECK(group_sweep(&g, 0, false, st));
+    }
     for (size_t k = 0; k < nets.size(); ++k)
       if (!fd[k].live.empty())
         SV_CUDA(cudaMemcpyAsync(fd[k].h_st, g.h_items[k].st, (size_t)fd[k].cap,
@@ -290,6 +300,9 @@ extern "C" zbus_status zbus_serve(const zbus_serve_config* cfg, zbus_network* po
     }
   }
   cleanup();
+  if (source_failed)
+    return fail(ZBUS_ERR_SOURCE, "the request source reported a failure; the requests it had "
+                                 "delivered were served");
   return ZBUS_OK;
 #undef SV_CHECK
 #undef SV_CUDA

@@ -3,6 +3,7 @@
 
 #include <cuda.h>
 #include <cuda_runtime.h>
+#include <nvtx3/nvToolsExt.h>
 #include <stdint.h>
 
 #include <string>
@@ -40,6 +41,15 @@ constexpr int F64_BK = 16;   // k step
 constexpr int F64_PAD = 48;  // n is padded to a multiple of this
 
 inline int round_up(int x, int m) { return (x + m - 1) / m * m; }
+
+// A named range on the host timeline of profilers (NVTX; no cost without a
+// tool attached) around each entry point and each serving sweep.
+struct NvtxRange {
+  explicit NvtxRange(const char* name) { nvtxRangePushA(name); }
+  ~NvtxRange() { nvtxRangePop(); }
+  NvtxRange(const NvtxRange&) = delete;
+  NvtxRange& operator=(const NvtxRange&) = delete;
+};
 
 // ---------------------------------------------------------------------------
 // Checked build (-DZBUS_CHECKED): every index read from a table (columns,

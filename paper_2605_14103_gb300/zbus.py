@@ -19,7 +19,7 @@ LIB_PATH = os.environ.get("ZBUS_LIB") or os.path.join(_HERE, "libzbus.so")
 ZBUS_OK = 0
 STATUS = {0: "ZBUS_OK", 1: "ZBUS_ERR_ARG", 2: "ZBUS_ERR_SINGULAR", 3: "ZBUS_ERR_OOM",
           4: "ZBUS_ERR_CUDA", 5: "ZBUS_ERR_TIMEOUT", 6: "ZBUS_ERR_DEVICE",
-          7: "ZBUS_ERR_UNSUPPORTED"}
+          7: "ZBUS_ERR_UNSUPPORTED", 8: "ZBUS_ERR_SOURCE"}
 PRECISION = {"fp64": 0, "bf16x2": 1, "fp16_scaled": 2, "tree": 3}
 RULE = {"maxabs": 0, "summag": 1}
 
@@ -352,10 +352,15 @@ def solve_batched(networks, loads, tol=1e-8, max_iter=50, precision="fp16_scaled
 def zbus_serve(cfg, pool_handles, source, sink, stream=None):
     """Raw call: source(now) -> zbus_request | None | -1; sink(req, res)."""
     arr = (C.c_void_p * len(pool_handles))(*pool_handles)
+    errors = []   # exceptions of the callbacks, raised again when the loop returns
 
     @SOURCE_FN
     def _src(user, now, out):
-        r = source(now)
+        try:
+            r = source(now)
+        except BaseException as e:   # the source failed: stop taking requests
+            errors.append(e)
+            return -2
         if r is None:
             return 0
         if isinstance(r, int):
@@ -365,10 +370,16 @@ def zbus_serve(cfg, pool_handles, source, sink, stream=None):
 
     @SINK_FN
     def _snk(user, req, res):
-        sink(req[0], res[0])
+        try:
+            sink(req[0], res[0])
+        except BaseException as e:
+            errors.append(e)
 
-    _check(lib().zbus_serve(C.byref(cfg), arr, len(pool_handles), _src, _snk, None,
-                            _stream(stream)))
+    status = lib().zbus_serve(C.byref(cfg), arr, len(pool_handles), _src, _snk, None,
+                              _stream(stream))
+    if errors:
+        raise errors[0]
+    _check(status)
 
 
 def serve(networks, requests, hbm_budget_bytes=120 << 30, max_slots=4096,
