@@ -233,3 +233,35 @@ def test_jacobian_and_solution_with_a_phase_shifter():
     np.testing.assert_allclose(J, Jfd, rtol=0, atol=1e-7 * np.abs(J).max())
     V, it, cv = O.newton(Y, g.bus_type, g.v_set, P[0], Q[0], tol=1e-12)
     assert cv == 1 and it <= 8
+
+
+@pytest.mark.parametrize("N,seed", [(118, 611), (1354, 612)])
+def test_grid_generator_structure(N, seed):
+    g = G.make_grid(N, seed)
+    # connected: a search from the slack reaches every bus
+    adj = [[] for _ in range(N)]
+    for f, t in zip(g.from_bus, g.to_bus):
+        adj[f].append(t)
+        adj[t].append(f)
+    seen, stack = {0}, [0]
+    while stack:
+        a = stack.pop()
+        for b in adj[a]:
+            if b not in seen:
+                seen.add(b)
+                stack.append(b)
+    assert len(seen) == N
+    assert 1.3 <= g.n_branch / N <= 1.7
+    assert (g.bus_type == G.SLACK).sum() == 1 and g.bus_type[0] == G.SLACK
+    assert abs((g.bus_type == G.PV).sum() - round(0.15 * N)) <= 1
+    Y = O.dense_Y(N, g.Y_row, g.Y_col, g.Y_val)
+    np.testing.assert_allclose(Y, Y.T, rtol=0, atol=1e-9)
+    assert (g.x > 0).all() and (g.r > 0).all() and (g.b >= 0).all()
+    # scenarios: loads within +-20 %, generation scaled with the total load
+    P, Q = G.make_injections(g, 50)
+    mult = np.divide(-Q, g.Q_load[None, :], out=np.ones_like(Q), where=g.Q_load[None, :] > 0)
+    assert mult.min() >= 0.8 - 1e-12 and mult.max() <= 1.2 + 1e-12
+    pl = mult * g.P_load[None, :]
+    gen_total = (P + pl).sum(axis=1)
+    np.testing.assert_allclose(gen_total, pl.sum(axis=1) * g.P_gen.sum() / g.P_load.sum(),
+                               rtol=1e-12)
