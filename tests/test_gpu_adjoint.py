@@ -271,3 +271,37 @@ def test_argument_errors():
                                 torch.empty(2, dtype=torch.int32, device="cuda"),
                                 torch.empty(2, dtype=torch.uint8, device="cuda"))
     assert os.environ.get("ZBUS_NO_GRAPH") != "1"
+
+
+def test_dense_form_on_a_non_reciprocal_network():
+    """Feeder matrices are symmetric (Z^T = Z), so a transposition mistake in
+    the device's Z^T would pass every other case.  A phase-shifting element
+    on one line (Y_ab != Y_ba) makes Y and Z non-symmetric; the dense form
+    must still match the oracle, and the tree form must refuse."""
+    f = F.make_feeder(25, 61, delta_frac=0.4)
+    a = 9
+    p = int(f.parent[a])
+    y = np.linalg.inv(f.z_line[a])
+    extra = {}
+    for i in range(3):
+        for j in range(3):
+            extra[(3 * a + i, 3 * p + j)] = 0.08j * y[i, j]
+            extra[(3 * p + i, 3 * a + j)] = -0.08j * y[i, j]
+    row, col, val = with_extra(f, extra)
+    Y = O.dense_from_coo(f.n_total, row, col, val)
+    assert np.abs(Y - Y.T).max() > 1.0
+    Sw, Sd = F.make_scenarios(f, 9, 0.8, 1.2)
+    r = O.solve_coo(f.n_total, row, col, val, f.slack_idx, f.v_slack, Sw, Sd, tol=1e-14,
+                    max_iter=300)
+    assert r["converged"].all()
+    assert np.abs(r["Z"] - r["Z"].T).max() > 1e-4
+    G = loss_grad(Sw.shape, 17)
+    Hw, Hd = O.solve_adjoint(r["Z"], r["V"], Sw, Sd, G)
+    net = zbus.Network(f.n_total, row, col, val, f.slack_idx, f.v_slack)
+    dw, dd, it, cv = net.solve_adjoint(dev(r["V"]), dev(G), dev(Sw), dev(Sd), tol=1e-13)
+    assert cv.cpu().numpy().all()
+    assert_close(dw.cpu().numpy(), Hw)
+    assert_close(dd.cpu().numpy(), Hd)
+    with pytest.raises(zbus.ZbusError) as e:
+        net.solve_adjoint(dev(r["V"]), dev(G), dev(Sw), dev(Sd), precision="tree")
+    assert e.value.status == 7

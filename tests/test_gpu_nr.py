@@ -176,3 +176,43 @@ def test_argument_errors():
             torch.empty((B,), dtype=torch.uint8, device="cuda"))
     with pytest.raises(zbus.ZbusError):
         zbus.zbus_nr_solve(net.handle, g.N, dev(P), dev(Q), 1e-10, 20, o, *outs)
+
+
+@pytest.mark.parametrize("prec", PRECISIONS)
+def test_phase_shifter_makes_y_non_symmetric(prec):
+    """A phase-shifting transformer (complex tap) between two PQ buses: Y,
+    B' and G_Q,Theta are no longer symmetric; both forms still match the
+    oracle."""
+    g = G.make_grid(60, 13)
+    br = next(k for k in range(g.n_branch)
+              if g.bus_type[g.from_bus[k]] == G.PQ and g.bus_type[g.to_bus[k]] == G.PQ)
+    f, t = int(g.from_bus[br]), int(g.to_bus[br])
+    y = 1.0 / (g.r[br] + 1j * g.x[br])
+    tap = np.exp(1j * 0.15)
+    row = np.concatenate([g.Y_row, [f, t]]).astype(np.int32)
+    col = np.concatenate([g.Y_col, [t, f]]).astype(np.int32)
+    val = np.concatenate([g.Y_val, [y - y / np.conj(tap), y - y / tap]])
+    Y = O.dense_Y(g.N, row, col, val)
+    assert np.abs(Y - Y.T).max() > 1.0
+    P, Q = G.make_injections(g, 6)
+    ref = O.solve_batch(g.N, row, col, val, g.bus_type, g.v_set, P, Q)
+    assert ref["converged"].all()
+    net = zbus.NrNetwork(g.N, row, col, val, g.bus_type, g.v_set)
+    V, it, cv, gm = net.solve(dev(P), dev(Q), precision=prec)
+    np.testing.assert_array_equal(cv.cpu().numpy(), ref["converged"])
+    assert np.abs(V.cpu().numpy() - ref["V"]).max() <= TOL_TIGHT
+    assert np.abs(it.cpu().numpy() - ref["iters"]).max() <= 1
+
+
+def test_golden_grid14():
+    """The GPU against the stored Newton-Raphson oracle solution."""
+    import json
+    import os
+    gd = json.load(open(os.path.join(os.path.dirname(__file__), "golden", "grid14_b4.json")))
+    g = G.make_grid(14, 1)
+    P, Q = G.make_injections(g, 4)
+    net = zbus.NrNetwork.from_grid(g)
+    V, it, cv, gm = net.solve(dev(P), dev(Q), tol=gd["tol"], max_iter=gd["max_iter"])
+    Vg = np.asarray(gd["V_re"]) + 1j * np.asarray(gd["V_im"])
+    np.testing.assert_array_equal(cv.cpu().numpy(), gd["converged"])
+    assert np.abs(V.cpu().numpy() - Vg).max() <= TOL_TIGHT

@@ -265,3 +265,18 @@ def test_grid_generator_structure(N, seed):
     gen_total = (P + pl).sum(axis=1)
     np.testing.assert_allclose(gen_total, pl.sum(axis=1) * g.P_gen.sum() / g.P_load.sum(),
                                rtol=1e-12)
+
+
+def test_golden_grid14_regression():
+    """The stored Newton-Raphson oracle solution (tests/golden/write_golden.py) still holds."""
+    import json
+    import os
+    gd = json.load(open(os.path.join(os.path.dirname(__file__), "golden", "grid14_b4.json")))
+    g = G.make_grid(14, 1)
+    P, Q = G.make_injections(g, 4)
+    r = O.solve_batch(g.N, g.Y_row, g.Y_col, g.Y_val, g.bus_type, g.v_set, P, Q,
+                      tol=gd["tol"], max_iter=gd["max_iter"])
+    V = np.asarray(gd["V_re"]) + 1j * np.asarray(gd["V_im"])
+    np.testing.assert_allclose(r["V"], V, rtol=0, atol=1e-13)
+    np.testing.assert_array_equal(r["iters"], gd["iters"])
+    np.testing.assert_array_equal(r["converged"], gd["converged"])
