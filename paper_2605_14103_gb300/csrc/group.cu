@@ -1090,7 +1090,7 @@ k_check(const double2* __restrict__ V, const double2* __restrict__ Sw,
   }
 }
 
-// Verdict per scenario: mm = sqrt(max |dS|^2); a converged flag with mm above
+// Outcome per scenario: mm = sqrt(max |dS|^2); a converged flag with mm above
 // mtol is cleared; mm_out[b] = mm, or -1 for a scenario that was not checked.
 // mm_out may alias mmax (each thread reads its entry before writing it).
 __global__ void k_check_finish(const unsigned long long* mmax, uint8_t* __restrict__ conv, int B,
