@@ -202,7 +202,7 @@ k_residual_group(GroupState* __restrict__ gs, const ItemDesc* __restrict__ items
       const int a = ch * CHUNK_BUS + q;
       float2 r[3] = {make_float2(0.f, 0.f), make_float2(0.f, 0.f), make_float2(0.f, 0.f)};
       if (a < nb && act) {
-        float2 ah3[3], al3[3], sw[3], sd[3], inj[3];   // own state (hi, lo), loads
+        float2 ah3[3], al3[3], sw[3], sd[3], inj[3], injl[3];   // own state, loads
 #pragma unroll
         for (int p = 0; p < 3; ++p) {
           const int64_t g = (int64_t)(3 * a + p) * Bp + b;
@@ -211,7 +211,7 @@ k_residual_group(GroupState* __restrict__ gs, const ItemDesc* __restrict__ items
           sw[p] = Sw[g];
           sd[p] = Sd[g];
         }
-        bus_injection_f(ah3, sw, sd, 3, inj);
+        bus_injection_df(ah3, al3, sw, sd, 3, inj, injl);
         float ah[3][2], al[3][2];   // accumulators (re, im) per phase, hi / lo
 #pragma unroll
         for (int p = 0; p < 3; ++p) ah[p][0] = al[p][0] = ah[p][1] = al[p][1] = 0.f;
@@ -256,8 +256,9 @@ k_residual_group(GroupState* __restrict__ gs, const ItemDesc* __restrict__ items
         }
 #pragma unroll
         for (int p = 0; p < 3; ++p) {
-          r[p] = make_float2(__fsub_rn(__fsub_rn(inj[p].x, ah[p][0]), al[p][0]),
-                             __fsub_rn(__fsub_rn(inj[p].y, ah[p][1]), al[p][1]));
+          // inj - (ah + al), the leading difference exact near the fixed point
+          r[p] = make_float2(__fadd_rn(__fsub_rn(inj[p].x, ah[p][0]), __fsub_rn(injl[p].x, al[p][0])),
+                             __fadd_rn(__fsub_rn(inj[p].y, ah[p][1]), __fsub_rn(injl[p].y, al[p][1])));
           const float m = fmaxf(fabsf(r[p].x), fabsf(r[p].y));
           amax = (m == m) ? fmaxf(amax, m) : __int_as_float(0x7f800000);
         }

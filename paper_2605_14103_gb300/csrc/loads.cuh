@@ -1,5 +1,5 @@
-// Constant-power load currents (Sec. II-B), shared by the FP64 and the mixed
-// sweeps and by the mismatch checks.
+// Constant-power load currents (Sec. II-B): FP64 for the FP64 sweeps and the
+// mismatch checks, double-float for the residual of the mixed defect forms.
 #pragma once
 
 #include <cuda_runtime.h>
@@ -39,29 +39,83 @@ __device__ __forceinline__ void bus_injection(const double2* v, const double2* s
   for (int p = 0; p < 3; ++p) inj[p] = make_double2(-d[p].x, -d[p].y);
 }
 
-// FP32 versions for the mixed sweeps: conj(S / v) with a rounded reciprocal.
-__device__ __forceinline__ float2 load_draw_f(float2 S, float2 v) {
-  if (S.x == 0.f && S.y == 0.f) return make_float2(0.f, 0.f);
-  const float inv = __frcp_rn(__fmaf_rn(v.x, v.x, v.y * v.y));
-  return make_float2((S.x * v.x + S.y * v.y) * inv, (S.x * v.y - S.y * v.x) * inv);
+// Double-float versions for the defect residual.  The current drawn by a
+// load, conj(S / v), is formed at the double-float voltage v = vh + vl: the
+// FP32 quotient at vh, then one correction step on the remainder
+// e = conj(S) - d conj(v), whose leading terms are formed error-free (FMA
+// products, two-sums), so the result (dh + dl) is accurate to the
+// double-float level and continuous in v.  A current formed from vh alone
+// would jump whenever the rounding of vh changes, and the iteration could
+// settle into a small cycle instead of its fixed point.
+__device__ __forceinline__ void df_two_sum(float a, float b, float& s, float& e) {
+  s = __fadd_rn(a, b);
+  const float bb = __fsub_rn(s, a);
+  e = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb));
 }
 
-__device__ __forceinline__ void bus_injection_f(const float2* v, const float2* sw,
-                                                const float2* sd, int m, float2* inj) {
-  float2 d[3];
+__device__ __forceinline__ float4 load_draw_df(float2 S, float2 vh, float2 vl) {
+  if (S.x == 0.f && S.y == 0.f) return make_float4(0.f, 0.f, 0.f, 0.f);
+  const float inv = __frcp_rn(__fmaf_rn(vh.x, vh.x, vh.y * vh.y));
+  const float2 d = make_float2((S.x * vh.x + S.y * vh.y) * inv, (S.x * vh.y - S.y * vh.x) * inv);
+  // real part: S.x - d.x vh.x - d.y vh.y - (d.x vl.x + d.y vl.y)
+  const float p1 = d.x * vh.x, e1 = __fmaf_rn(d.x, vh.x, -p1);
+  const float p2 = d.y * vh.y, e2 = __fmaf_rn(d.y, vh.y, -p2);
+  float s1, t1, s2, t2;
+  df_two_sum(S.x, -p1, s1, t1);
+  df_two_sum(s1, -p2, s2, t2);
+  const float er = s2 + (((t1 + t2) - (e1 + e2)) - (d.x * vl.x + d.y * vl.y));
+  // imaginary part: -S.y - d.y vh.x + d.x vh.y - (d.y vl.x - d.x vl.y)
+  const float q1 = d.y * vh.x, f1 = __fmaf_rn(d.y, vh.x, -q1);
+  const float q2 = d.x * vh.y, f2 = __fmaf_rn(d.x, vh.y, -q2);
+  df_two_sum(-S.y, -q1, s1, t1);
+  df_two_sum(s1, q2, s2, t2);
+  const float ei = s2 + (((t1 + t2) - f1 + f2) - (d.y * vl.x - d.x * vl.y));
+  // d + e / conj(vh) = d + e vh / |vh|^2
+  return make_float4(d.x, (er * vh.x - ei * vh.y) * inv, d.y, (er * vh.y + ei * vh.x) * inv);
+}
+
+// Injection of one bus with every current in double-float: inj[p] and
+// injl[p] the hi and lo parts (rules of bus_injection, m == 3 for delta).
+__device__ __forceinline__ void bus_injection_df(const float2* vh, const float2* vl,
+                                                 const float2* sw, const float2* sd, int m,
+                                                 float2* inj, float2* injl) {
+  float4 dw[3];
 #pragma unroll
   for (int p = 0; p < 3; ++p)
-    d[p] = (p < m && sw) ? load_draw_f(sw[p], v[p]) : make_float2(0.f, 0.f);
+    dw[p] = (p < m && sw) ? load_draw_df(sw[p], vh[p], vl[p]) : make_float4(0.f, 0.f, 0.f, 0.f);
   if (sd && m == 3) {
-    const float2 iab = load_draw_f(sd[0], make_float2(v[0].x - v[1].x, v[0].y - v[1].y));
-    const float2 ibc = load_draw_f(sd[1], make_float2(v[1].x - v[2].x, v[1].y - v[2].y));
-    const float2 ica = load_draw_f(sd[2], make_float2(v[2].x - v[0].x, v[2].y - v[0].y));
-    d[0].x += iab.x - ica.x; d[0].y += iab.y - ica.y;
-    d[1].x += ibc.x - iab.x; d[1].y += ibc.y - iab.y;
-    d[2].x += ica.x - ibc.x; d[2].y += ica.y - ibc.y;
+    float4 ib[3];   // branches ab, bc, ca on the double-float line-to-line voltages
+#pragma unroll
+    for (int x = 0; x < 3; ++x) {
+      const int y = x == 2 ? 0 : x + 1;
+      float uhx, ulx, uhy, uly;
+      df_two_sum(vh[x].x, -vh[y].x, uhx, ulx);
+      df_two_sum(vh[x].y, -vh[y].y, uhy, uly);
+      ulx += vl[x].x - vl[y].x;
+      uly += vl[x].y - vl[y].y;
+      ib[x] = load_draw_df(sd[x], make_float2(uhx, uhy), make_float2(ulx, uly));
+    }
+    // phase x draws branch x and returns branch x - 1
+#pragma unroll
+    for (int x = 0; x < 3; ++x) {
+      const int w = x == 0 ? 2 : x - 1;
+      float h, l;
+      df_two_sum(dw[x].x, ib[x].x, h, l);
+      float h2, l2;
+      df_two_sum(h, -ib[w].x, h2, l2);
+      dw[x].x = h2;
+      dw[x].y += l + l2 + ib[x].y - ib[w].y;
+      df_two_sum(dw[x].z, ib[x].z, h, l);
+      df_two_sum(h, -ib[w].z, h2, l2);
+      dw[x].z = h2;
+      dw[x].w += l + l2 + ib[x].w - ib[w].w;
+    }
   }
 #pragma unroll
-  for (int p = 0; p < 3; ++p) inj[p] = make_float2(-d[p].x, -d[p].y);
+  for (int p = 0; p < 3; ++p) {
+    inj[p] = make_float2(-dw[p].x, -dw[p].z);
+    injl[p] = make_float2(-dw[p].y, -dw[p].w);
+  }
 }
 
 }  // namespace zbus

@@ -305,3 +305,18 @@ def test_dense_form_on_a_non_reciprocal_network():
     with pytest.raises(zbus.ZbusError) as e:
         net.solve_adjoint(dev(r["V"]), dev(G), dev(Sw), dev(Sd), precision="tree")
     assert e.value.status == 7
+
+
+@pytest.mark.parametrize("form", FORMS)
+def test_iteration_cap(form):
+    """With one sweep allowed the adjoint cannot meet a tight tolerance: the
+    flags say so and the call returns (the partial gradient is not used)."""
+    f = F.make_feeder(30, 14, delta_frac=0.4)
+    Sw, Sd = F.make_scenarios(f, 5, 0.8, 1.2)
+    r = forward_oracle(f, Sw, Sd)
+    net = zbus.Network.from_feeder(f)
+    G = loss_grad(Sw.shape, 6)
+    dw, dd, it, cv = net.solve_adjoint(dev(r["V"]), dev(G), dev(Sw), dev(Sd), tol=1e-13,
+                                       max_iter=1, precision=form)
+    assert not cv.cpu().numpy().any()
+    assert (it.cpu().numpy() == 1).all()

@@ -213,3 +213,17 @@ def test_device_status_is_clean_after_solves():
         V, it, cv = net.solve(dev(Sw), dev(Sd), precision=mode)
         assert net.device_status() == 0, mode
         assert cv.cpu().numpy().all()
+
+
+@pytest.mark.parametrize("mode", MODES)
+def test_paper_stop_rule_sum_of_magnitudes(mode):
+    """The paper's stop rule (the change of the sum of voltage magnitudes,
+    Sec. II-B) in the defect forms: flags equal to the oracle's under the
+    same rule, voltages within 1e-6 pu, sweep counts within one."""
+    f, Sw, Sd, w = F.make_workload("feeder128_b4096", B=96)
+    ref = O.solve_coo(f.n_total, f.Y_row, f.Y_col, f.Y_val, f.slack_idx, f.v_slack, Sw, Sd,
+                      tol=w.tol, max_iter=w.max_iter, rule="summag")
+    net = zbus.Network.from_feeder(f)
+    V, it, cv = net.solve(dev(Sw), dev(Sd), tol=w.tol, max_iter=w.max_iter, precision=mode,
+                          rule="summag")
+    check(net, f, Sw, Sd, ref, V, it, cv)
