@@ -153,8 +153,8 @@ __global__ void k_group_params(GroupState* gs, double tol, int max_iter, int rul
 //   r_a = i_a(v) - [sum_b Y_ab (v_b - v_a) + Y_as (v_s - v_a) + Sh_a v_a]
 // The admittance sum (currents up to ~10 pu cancelling to ~1e-10 near the
 // solution) runs in double-float with the blocks loaded once per warp for 32
-// slots; the load
-// current (~1e-2, no cancellation) in FP32 from the hi part.  R[b][2j],
+// slots; the load currents in double-float at hi + lo (bus_injection_df), so
+// the residual is continuous in v.  R[b][2j],
 // R[b][2j+1] = round(c_b Re r_j), round(c_b Im r_j) with c_b = 2^(12 -
 // floor(log2 amax_prev_b)) from the previous sweep's max |r| (the residual
 // shrinks from sweep to sweep; values beyond the FP16 range saturate, which
