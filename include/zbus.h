@@ -254,6 +254,28 @@ zbus_status zbus_autotune(const zbus_batch_item* items, int32_t n_items,
                           int32_t reps, void* cuda_stream, int32_t* best_BN,
                           int32_t* best_stages);
 
+/*
+ * zbus_tune_variants -- the compiled tensor-core contraction variants of a
+ * mixed precision (ZBUS_MIXED_BF16X2 or ZBUS_MIXED_FP16_SCALED): up to `max`
+ * (N-tile, pipeline stages) pairs into the caller's host arrays BN[] and
+ * stages[] (either may be NULL to count only).  Returns the number of
+ * variants, 0 for a precision without tensor-core tiles, -1 for max < 0.
+ */
+int32_t zbus_tune_variants(int32_t precision, int32_t* BN, int32_t* stages, int32_t max);
+
+/*
+ * zbus_tune_set -- record the contraction variant (BN, stages) for the size
+ * bucket of (max_n, total_B), the same buckets as zbus_autotune, in this
+ * process's table (not written to the cache file).  Every later
+ * mixed-precision solve or serving loop in that bucket uses it.  BN = 0
+ * removes the entry (the built-in choice applies again).  ZBUS_ERR_ARG for
+ * a precision without tensor-core tiles, max_n or total_B below 1, or a
+ * (BN, stages) pair that is not compiled (zbus_tune_variants).
+ * Project-written; the paper has no counterpart.
+ */
+zbus_status zbus_tune_set(int32_t precision, int32_t max_n, int64_t total_B, int32_t BN,
+                          int32_t stages);
+
 /* ---------------------------------------------------------------------------
  * Serving: a request loop over a pool of networks with continuous batching.
  * ------------------------------------------------------------------------- */

@@ -47,8 +47,8 @@ void drop_graphs(zbus_network net) {
 }
 
 int max_ntn(const zbus_network net) {
-  // the FP64 contraction tiles outputs by 48, the tensor-core one by >= 128 reals
-  return std::max(net->n_pad / F64_BN, round_up(2 * net->n, 256) / 128);
+  // the FP64 contraction tiles outputs by 48, the tensor-core one by >= 64 reals
+  return std::max(net->n_pad / F64_BN, round_up(2 * net->n, 256) / 64);
 }
 
 int k_pad_tc(const zbus_network net) { return round_up(2 * net->n, 64); }

@@ -109,7 +109,11 @@ zbus_status tune_lookup(int32_t precision, int max_n, int64_t total_B, int* BN, 
 void tune_set(int32_t precision, int max_n, int64_t total_B, int BN, int stages, double ms) {
   std::lock_guard<std::mutex> lk(g_mu);
   load_locked();
-  g_table[std::make_tuple((int)precision, bucket(max_n), bucket(total_B))] = Choice{BN, stages, ms};
+  const auto key = std::make_tuple((int)precision, bucket(max_n), bucket(total_B));
+  if (BN == 0)
+    g_table.erase(key);
+  else
+    g_table[key] = Choice{BN, stages, ms};
   ++g_gen;
 }
 
@@ -179,5 +183,29 @@ extern "C" zbus_status zbus_autotune(const zbus_batch_item* items, int32_t n_ite
   tune_save();
   if (best_BN) *best_BN = bbn;
   if (best_stages) *best_stages = bst;
+  return ZBUS_OK;
+}
+
+extern "C" int32_t zbus_tune_variants(int32_t precision, int32_t* BN, int32_t* stages,
+                                      int32_t max) {
+  if (max < 0) return -1;
+  int bn[16], st[16];
+  const int nv = tc_variants(precision, bn, st, 16);
+  for (int v = 0; v < nv && v < max; ++v) {
+    if (BN) BN[v] = bn[v];
+    if (stages) stages[v] = st[v];
+  }
+  return nv;
+}
+
+extern "C" zbus_status zbus_tune_set(int32_t precision, int32_t max_n, int64_t total_B,
+                                     int32_t BN, int32_t stages) {
+  set_error("");
+  if (precision != ZBUS_MIXED_BF16X2 && precision != ZBUS_MIXED_FP16_SCALED)
+    return fail(ZBUS_ERR_ARG, "only the tensor-core precisions have contraction variants");
+  if (max_n < 1 || total_B < 1) return fail(ZBUS_ERR_ARG, "max_n and total_B must be >= 1");
+  if (BN != 0 && !tc_config_ok(precision, BN, stages))
+    return fail(ZBUS_ERR_ARG, "(BN, stages) is not a compiled variant of this precision");
+  tune_set(precision, max_n, total_B, BN, stages, 0.0);
   return ZBUS_OK;
 }

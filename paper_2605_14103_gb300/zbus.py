@@ -98,6 +98,9 @@ _SIGS = {
     "zbus_autotune": (C.c_int, [C.POINTER(zbus_batch_item), C.c_int32,
                                 C.POINTER(zbus_solve_opts), C.c_double, C.c_int32, C.c_int32,
                                 _P, C.POINTER(C.c_int32), C.POINTER(C.c_int32)]),
+    "zbus_tune_variants": (C.c_int32, [C.c_int32, C.POINTER(C.c_int32), C.POINTER(C.c_int32),
+                                       C.c_int32]),
+    "zbus_tune_set": (C.c_int, [C.c_int32, C.c_int32, C.c_int64, C.c_int32, C.c_int32]),
     "zbus_serve": (C.c_int, [C.POINTER(zbus_serve_config), C.POINTER(C.c_void_p), C.c_int32,
                              SOURCE_FN, SINK_FN, C.c_void_p, C.c_void_p]),
     "zbus_last_device_status": (C.c_int, [_P, _P]),
@@ -326,6 +329,24 @@ def zbus_autotune(items, opts, tol, max_iter, reps=3, stream=None):
     _check(lib().zbus_autotune(arr, len(items), C.byref(opts), float(tol), int(max_iter),
                                int(reps), _stream(stream), C.byref(bn), C.byref(stg)))
     return bn.value, stg.value
+
+
+def zbus_tune_variants(precision):
+    """The compiled contraction variants of a mixed precision: [(BN, stages)]."""
+    p = PRECISION[precision] if isinstance(precision, str) else int(precision)
+    m = lib().zbus_tune_variants(p, None, None, 0)
+    if m <= 0:
+        return []
+    bn = (C.c_int32 * m)()
+    st = (C.c_int32 * m)()
+    lib().zbus_tune_variants(p, bn, st, m)
+    return list(zip(bn, st))
+
+
+def zbus_tune_set(precision, max_n, total_B, BN, stages):
+    """Use variant (BN, stages) for the size bucket of (max_n, total_B); BN = 0 clears it."""
+    p = PRECISION[precision] if isinstance(precision, str) else int(precision)
+    _check(lib().zbus_tune_set(p, int(max_n), int(total_B), int(BN), int(stages)))
 
 
 def solve_batched(networks, loads, tol=1e-8, max_iter=50, precision="fp16_scaled",

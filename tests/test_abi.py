@@ -125,3 +125,23 @@ def test_create_phased_rejects_bad_maps(lib):
                                           val.ctypes.data, sl.ctypes.data, vs.ctypes.data,
                                           None, None, C.byref(out)) == 1
     assert not out.value
+
+
+def test_tune_variants_and_override_without_a_gpu(lib):
+    """The contraction variants are listed and an override is checked on the
+    host: a pair that is not compiled, or a precision without tensor-core
+    tiles, is refused; BN = 0 clears an entry."""
+    fp16 = zbus.zbus_tune_variants("fp16_scaled")
+    bf16 = zbus.zbus_tune_variants("bf16x2")
+    assert fp16 and bf16 and zbus.zbus_tune_variants("fp64") == []
+    assert all(bn in (64, 128, 256) and st >= 2 for bn, st in fp16 + bf16)
+    assert lib.zbus_tune_variants(2, None, None, -1) == -1
+    bn, st = fp16[0]
+    zbus.zbus_tune_set("fp16_scaled", 381, 4096, bn, st)
+    zbus.zbus_tune_set("fp16_scaled", 381, 4096, 0, 0)
+    for args in (("fp16_scaled", 381, 4096, 96, 4), ("fp64", 381, 4096, bn, st),
+                 ("tree", 381, 4096, bn, st), ("fp16_scaled", 0, 4096, bn, st),
+                 ("fp16_scaled", 381, 0, bn, st)):
+        with pytest.raises(zbus.ZbusError) as ei:
+            zbus.zbus_tune_set(*args)
+        assert ei.value.status == 1

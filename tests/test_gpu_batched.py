@@ -100,7 +100,7 @@ def test_autotune_records_a_compiled_variant(tmp_path, monkeypatch):
                       torch.empty((B,), dtype=torch.int32, device="cuda"),
                       torch.empty((B,), dtype=torch.uint8, device="cuda")))
     bn, stages = zbus.zbus_autotune(items, o, 1e-8, 50, reps=2)
-    assert bn in (128, 256) and stages >= 2
+    assert (bn, stages) in zbus.zbus_tune_variants("fp16_scaled")
     # the cache is written only if the library resolved the same path at first use;
     # the returned choice is what matters, and later solves still agree with FP64
     outs = zbus.solve_batched(nets, [(it[1], it[2]) for it in items])

@@ -71,6 +71,36 @@ def test_one_defect_step_matches_fp64_step(mode, N, B, seed):
     assert (it.cpu().numpy() == 1).all()
 
 
+@pytest.mark.parametrize("mode", ["fp16_scaled", "bf16x2"])
+@pytest.mark.parametrize("N,B,seed", [(128, 300, 202), (300, 130, 9)])
+def test_every_contraction_variant(mode, N, B, seed):
+    """Each compiled (N-tile, stages) variant of the tensor-core contraction,
+    forced through zbus_tune_set: one defect step against the FP64 step and a
+    full solve against the oracle (ragged batches: 300 = 2 x 128 + 44 slots;
+    n = 381 and 897 give 12 / 6 / 3 and 28 / 14 / 7 N-tiles of 64 / 128 / 256
+    columns)."""
+    f = F.make_feeder(N, seed, delta_frac=0.3)
+    Sw, Sd = F.make_scenarios(f, B, 0.8, 1.2)
+    V0 = oracle(f, 0.7 * Sw, 0.7 * Sd)["V"]
+    ref1 = oracle(f, Sw, Sd, tol=0.0, max_iter=1, V0=V0)["V"]
+    ref = oracle(f, Sw, Sd)
+    net = zbus.Network.from_feeder(f)
+    variants = zbus.zbus_tune_variants(mode)
+    assert (64, 8 if mode == "fp16_scaled" else 6) in variants and len(variants) >= 4
+    step = np.abs(ref1 - V0).max(axis=1, keepdims=True)
+    try:
+        for bn, st in variants:
+            zbus.zbus_tune_set(mode, net.n, B, bn, st)
+            V, it, cv = net.solve(dev(Sw), dev(Sd), V_init=dev(V0), tol=0.0, max_iter=1,
+                                  precision=mode)
+            err = np.abs(V.cpu().numpy() - ref1) / step
+            assert err.max() <= STEP_RTOL[mode], (bn, st, err.max())
+            V, it, cv = net.solve(dev(Sw), dev(Sd), precision=mode)
+            check(net, f, Sw, Sd, ref, V, it, cv)
+    finally:
+        zbus.zbus_tune_set(mode, net.n, B, 0, 0)
+
+
 @pytest.mark.parametrize("mode", MODES)
 @pytest.mark.parametrize("N,B,delta,seed", [(13, 8, 0.4, 101), (17, 1, 0.5, 3),
                                              (40, 7, 0.3, 4), (128, 129, 0.3, 202),
