@@ -141,11 +141,14 @@ def allreduce_sum(x, ws):
 # the oracle legs (CPU)
 # ---------------------------------------------------------------------------
 def oracle_setup(f):
+    """(Z, w, bus_phase of the load unknowns or None) of the oracle."""
+    import numpy as np
     from oracle import zbus_oracle as O
     Y = O.dense_from_coo(f.n_total, f.Y_row, f.Y_col, f.Y_val)
-    Y_LL, Y_Ls, _ = O.partition(Y, f.slack_idx)
+    Y_LL, Y_Ls, load_idx = O.partition(Y, f.slack_idx)
     Z, w = O.reduced_impedance(Y_LL, Y_Ls, f.v_slack)
-    return Z, w
+    bp = getattr(f, "bus_phase", None)
+    return Z, w, (None if bp is None else np.asarray(bp)[load_idx])
 
 
 def cpu_cores():
@@ -159,7 +162,7 @@ def cpu_baseline(f, Sw, Sd, wl, seconds, V_gpu, it_gpu, cv_gpu):
     """The oracle as it stands, timed on this host on a bounded sample of the batch."""
     import numpy as np
     from oracle import zbus_oracle as O
-    Z, w = oracle_setup(f)
+    Z, w, bp = oracle_setup(f)
     B = Sw.shape[0]
     bs = min(B, 1024)
     reps, solved, t_total = 0, 0, 0.0
@@ -168,7 +171,7 @@ def cpu_baseline(f, Sw, Sd, wl, seconds, V_gpu, it_gpu, cv_gpu):
         lo = (reps * bs) % B
         idx = np.arange(lo, min(B, lo + bs))
         t0 = time.perf_counter()
-        V, it, cv = O.fixed_point(Z, w, Sw[idx], Sd[idx], wl.tol, wl.max_iter)
+        V, it, cv = O.fixed_point(Z, w, Sw[idx], Sd[idx], wl.tol, wl.max_iter, bus_phase=bp)
         t_total += time.perf_counter() - t0
         solved += int(cv.sum())
         if first is None:
@@ -199,15 +202,16 @@ def run_reference(args):
     from paper_2605_14103_gb300 import feeders as F
     workload = args.workload if args.workload in F.WORKLOADS else "feeder128_b4096"
     f, Sw, Sd, wl = F.make_workload(workload)
-    Z, w = oracle_setup(f)
+    Z, w, bp = oracle_setup(f)
     bs = min(wl.B, 512)
     for s in range(args.warmup):
-        O.fixed_point(Z, w, Sw[:bs], Sd[:bs], wl.tol, wl.max_iter)
+        O.fixed_point(Z, w, Sw[:bs], Sd[:bs], wl.tol, wl.max_iter, bus_phase=bp)
     times, solved = [], 0
     for s in range(args.steps):
         lo = (s * bs) % wl.B
         t0 = time.perf_counter()
-        V, it, cv = O.fixed_point(Z, w, Sw[lo:lo + bs], Sd[lo:lo + bs], wl.tol, wl.max_iter)
+        V, it, cv = O.fixed_point(Z, w, Sw[lo:lo + bs], Sd[lo:lo + bs], wl.tol, wl.max_iter,
+                                  bus_phase=bp)
         times.append(time.perf_counter() - t0)
         solved += int(cv.sum())
     total = sum(times)
@@ -216,7 +220,7 @@ def run_reference(args):
            "n_gpus": ws, "steps": args.steps, "warmup": args.warmup,
            "ms_per_step": 1e3 * total / args.steps, "higher_is_better": True,
            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-           "config": {"workload": workload, "feeder_buses": wl.N, "unknowns": 3 * (wl.N - 1),
+           "config": {"workload": workload, "feeder_buses": wl.N, "unknowns": int(Sw.shape[1]),
                       "scenarios_per_step": bs, "tol": wl.tol},
            "cpu_baseline": {"value": value, "unit": UNIT, "cores": cpu_cores(), "kind": "oracle",
                             "sample": f"{bs} scenarios of the {wl.B}-scenario batch per step"},
@@ -323,8 +327,11 @@ def load_peaks():
     return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "src": "fallback"}
 
 
-def measure(net, form, Sw, Sd, wl, n, steps, warmup, flush, ws, peaks):
-    """Timed solves of one precision form: value, step times, kernel shares, roofline."""
+def measure(net, form, Sw, Sd, wl, n, steps, warmup, flush, ws, peaks, extra_launches=0):
+    """Timed solves of one precision form: value, step times, kernel shares, roofline.
+    extra_launches: kernels per solve around the form's own (the scatter of
+    the loads into, and the gather of the voltages out of, a partial-phase
+    network's padded layout)."""
     import torch
     B = Sw.shape[0]
     net.reserve(B, form)
@@ -401,7 +408,8 @@ def measure(net, form, Sw, Sd, wl, n, steps, warmup, flush, ws, peaks):
             "step_ms_p50": statistics.median(step_ms),
             "step_ms_p99": float(np.percentile(step_ms, 99)), "converged_per_step": good,
             "max_iters": max_iters, "mean_iters": float(it.float().mean().item()),
-            "gpu_launches": steps * (OUTSIDE[form][1] + (2 if form == "tree" else 4) * max_iters),
+            "gpu_launches": steps * (OUTSIDE[form][1] + extra_launches +
+                                     (2 if form == "tree" else 4) * max_iters),
             "kernels": kernels, "roofline": roof}, (V, it, cv)
 
 
@@ -491,11 +499,13 @@ def run_ours(args):
     f, _, _, wl = F.make_workload(args.workload, B=1)
     Bw = args.batch if args.batch > 0 else wl.B
     from paper_2605_14103_gb300 import dist as D
-    Sw_h, Sd_h = F.make_scenarios(f, Bw, wl.mult[0], wl.mult[1], seed=D.rank_seed(f.seed + 1, rank))
+    Sw_h, Sd_h = F.workload_scenarios(f, Bw, wl.mult[0], wl.mult[1],
+                                      seed=D.rank_seed(f.seed + 1, rank))
     B, n = Sw_h.shape
     Sw = torch.from_numpy(Sw_h).cuda()
     Sd = torch.from_numpy(Sd_h).cuda()
     net = zbus.Network.from_feeder(f)
+    phased = getattr(f, "bus_phase", None) is not None
     flush = torch.empty(512 * 1024 * 1024, dtype=torch.uint8, device="cuda")
 
     forms = [args.precision] + ([m for m in ("fp64", "fp16_scaled", "bf16x2", "tree")
@@ -507,7 +517,8 @@ def run_ours(args):
     head_out = None
     for form in forms:
         steps = args.steps if form == args.precision else max(3, args.steps // 2)
-        r, out = measure(net, form, Sw, Sd, wl, n, steps, args.warmup, flush, ws, peaks)
+        r, out = measure(net, form, Sw, Sd, wl, n, steps, args.warmup, flush, ws, peaks,
+                         extra_launches=3 if phased else 0)
         results[form] = r
         if form == args.precision:
             head_out = tuple(x.clone() for x in out)
@@ -577,6 +588,9 @@ def run_ours(args):
                        "d2h_bytes_per_step": B * n * 16 + B * 4 + B},
                "clocks": clk, "cpu_baseline": cpu, "parity": parity,
                "peaks": peaks["src"], "forms": forms_out}
+        if phased:
+            # the device solves the network padded to three phase slots per bus
+            out["config"]["padded_unknowns"] = 3 * (wl.N - 1)
         if grad is not None:
             for k in ("fp64", "tree"):
                 if "ms_per_step" in grad.get(k, {}):

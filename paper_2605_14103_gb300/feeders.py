@@ -326,6 +326,7 @@ class Workload:
     seed: int
     tol: float = 1e-8
     max_iter: int = 50
+    lateral_frac: float = 0.0   # > 0: partial-phase laterals (make_partial_feeder)
 
 
 WORKLOADS = {
@@ -335,15 +336,31 @@ WORKLOADS = {
     "feeder128_b4096": Workload("feeder128_b4096", 128, 4096, 0.3, (0.5, 1.5), 202),
     # 1024 buses (3069 unknowns), 16384 scenarios, 70 / 30, U(0.8, 1.2).
     "feeder1024_b16384": Workload("feeder1024_b16384", 1024, 16384, 0.3, (0.8, 1.2), 303),
+    # the same feeder with single- and two-phase laterals (30 % of the small
+    # subtrees start one), 16384 scenarios: a stand-in for the paper's feeder
+    # counted in phase connections (Sec. III)
+    "partial1024_b16384": Workload("partial1024_b16384", 1024, 16384, 0.3, (0.8, 1.2), 303,
+                                   lateral_frac=0.3),
 }
 
 
 def make_workload(name: str, B: int | None = None):
     """(feeder, S_wye, S_delta, workload) for a named workload; B overrides the batch."""
     w = WORKLOADS[name]
-    f = make_feeder(w.N, w.seed, delta_frac=w.delta_frac, mult_hi=w.mult[1])
-    S_wye, S_delta = make_scenarios(f, w.B if B is None else B, w.mult[0], w.mult[1])
+    if w.lateral_frac > 0:
+        f = make_partial_feeder(w.N, w.seed, lateral_frac=w.lateral_frac,
+                                delta_frac=w.delta_frac, mult_hi=w.mult[1])
+    else:
+        f = make_feeder(w.N, w.seed, delta_frac=w.delta_frac, mult_hi=w.mult[1])
+    S_wye, S_delta = workload_scenarios(f, w.B if B is None else B, w.mult[0], w.mult[1])
     return f, S_wye, S_delta, w
+
+
+def workload_scenarios(f, B: int, mult_lo: float, mult_hi: float, seed: int | None = None):
+    """Scenarios of a three-phase (make_scenarios) or partial-phase feeder."""
+    if isinstance(f, PhasedFeeder):
+        return make_partial_scenarios(f, B, mult_lo, mult_hi, seed=seed)
+    return make_scenarios(f, B, mult_lo, mult_hi, seed=seed)
 
 
 def heterogeneous_set(n_feeders: int = 64, seed: int = 404, n_lo: int = 50,

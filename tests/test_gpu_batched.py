@@ -63,6 +63,32 @@ def test_batched_equals_single_and_oracle(mode):
         assert np.abs(it.cpu().numpy()[m] - ref["iters"][m]).max() <= 1
 
 
+@pytest.mark.parametrize("mode", ["fp16_scaled", "bf16x2"])
+def test_every_contraction_variant_batched(mode):
+    """Feeders of uneven size (different N-tile counts per item) through each
+    compiled contraction variant, forced with zbus_tune_set: the K order of
+    the product does not depend on the tile, so every variant gives the
+    default's voltages (1e-12) and counts, and the FP64 method's flags."""
+    fs = make_set(SPECS)
+    nets = [zbus.Network.from_feeder(f) for f, _, _ in fs]
+    loads = [(dev(Sw), dev(Sd)) for _, Sw, Sd in fs]
+    max_n = max(net.n for net in nets)
+    total_B = sum(Sw.shape[0] for _, Sw, _ in fs)
+    base = zbus.solve_batched(nets, loads, precision=mode)
+    ref = zbus.solve_batched(nets, loads, precision="fp64")
+    try:
+        for bn, st in zbus.zbus_tune_variants(mode):
+            zbus.zbus_tune_set(mode, max_n, total_B, bn, st)
+            outs = zbus.solve_batched(nets, loads, precision=mode)
+            for (V, it, cv), (V0, it0, cv0), (Vr, _, cr) in zip(outs, base, ref):
+                assert torch.equal(cv, cv0) and torch.equal(it, it0), (bn, st)
+                assert (V - V0).abs().max().item() <= 1e-12, (bn, st)
+                assert torch.equal(cv, cr)
+                assert (V - Vr).abs().max().item() <= 1e-6
+    finally:
+        zbus.zbus_tune_set(mode, max_n, total_B, 0, 0)
+
+
 def test_batched_repeat_and_fp64():
     fs = make_set([(40, 20), (80, 50)], seed0=70)
     nets = [zbus.Network.from_feeder(f) for f, _, _ in fs]

@@ -104,3 +104,24 @@ def test_calls_that_take_three_phase_networks_refuse_it():
         zbus.solve_batched([net], [(dev(Sw), dev(Sd))], precision="fp16_scaled")
     with pytest.raises(zbus.ZbusError):
         zbus.serve([net], [{"feeder": 0, "S_wye": dev(Sw), "S_delta": dev(Sd), "arrival": 0.0}])
+
+
+@pytest.mark.parametrize("mode", FORMS)
+def test_benchmark_workload_full_batch_sampled(mode):
+    """The partial-phase benchmark workload (1024 buses with laterals, 16384
+    scenarios) in the launch configuration the bench times: every scenario
+    converged with its FP64 mismatch <= 1e-6 pu; 96 sampled scenarios
+    against the oracle (flags, |dV| <= 1e-6 pu, iterations within one)."""
+    f, Sw, Sd, w = F.make_workload("partial1024_b16384")
+    net = zbus.Network.from_feeder(f)
+    sw, sd = dev(Sw), dev(Sd)
+    V, it, cv = net.solve(sw, sd, tol=w.tol, max_iter=w.max_iter, precision=mode)
+    mm = net.power_mismatch(V, sw, sd)
+    assert bool((cv == 1).all()) and mm.max().item() <= 1e-6
+    pick = np.sort(np.random.default_rng(11).choice(Sw.shape[0], 96, replace=False))
+    ref = oracle(f, Sw[pick], Sd[pick], tol=w.tol, max_iter=w.max_iter)
+    Vs, its, cvs = V.cpu().numpy()[pick], it.cpu().numpy()[pick], cv.cpu().numpy()[pick]
+    np.testing.assert_array_equal(cvs, ref["converged"])
+    assert np.abs(Vs - ref["V"]).max() <= 1e-6
+    assert np.abs(its - ref["iters"]).max() <= 1
+    net.close()
