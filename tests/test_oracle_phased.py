@@ -65,6 +65,25 @@ def test_generator_structure():
         assert f.phases[bp[j] // 3].all()
 
 
+def test_partial_benchmark_workload_is_the_three_phase_feeder_with_laterals():
+    """partial1024_b16384: the tree, impedances and loads of feeder1024_b16384
+    (same seed and multipliers) with laterals; three-phase buses keep their
+    wye or delta loads, lateral buses carry their loads as wye on the
+    present phases."""
+    f, Sw, Sd, w = F.make_workload("partial1024_b16384", B=5)
+    g, Sw3, Sd3, w3 = F.make_workload("feeder1024_b16384", B=5)
+    assert isinstance(f, F.PhasedFeeder) and (w.N, w.B, w.seed) == (w3.N, w3.B, w3.seed)
+    np.testing.assert_array_equal(f.parent, g.parent)
+    assert f.n < g.n and Sw.shape == (5, f.n) and Sd.shape == (5, f.n)
+    bp = f.bus_phase[3:]
+    j3 = 3 * (bp // 3 - 1) + bp % 3            # the same (bus, phase) in the three-phase feeder
+    three = f.phases[bp // 3].all(axis=1)
+    np.testing.assert_array_equal(Sw[:, three], Sw3[:, j3[three]])
+    np.testing.assert_array_equal(Sd[:, three], Sd3[:, j3[three]])
+    np.testing.assert_array_equal(Sw[:, ~three], (Sw3 + Sd3)[:, j3[~three]])
+    assert not Sd[:, ~three].any()
+
+
 @pytest.mark.parametrize("N,seed,kappa", [(3, 41, 25.0), (5, 42, 15.0), (7, 43, 10.0)])
 def test_against_bruteforce_newton(N, seed, kappa):
     base = F.make_partial_feeder(N, seed, lateral_frac=1.0, delta_frac=0.6)
