@@ -974,10 +974,12 @@ __device__ __forceinline__ double2 draw64(double2 S, double2 v) {
 // Lanes are scenarios and every lane of a warp works on the same bus, so the
 // loop over a bus's blocks is uniform and the 3x3 blocks are broadcast loads;
 // the FP64 pipe (2 operations per clock per SM) only sees useful work.  Grid
-// (ceil(B / 32), ny), block (32, CHECK_WARPS): the warps of the grid's y
-// extent interleave over the buses.  Each block folds its max |dS|^2 per
-// scenario into mmax[b] (non-negative doubles order like their bit patterns;
-// NaN counts as +inf); mmax is zeroed by k_slot_merge.
+// ceil(B / 32) x ny blocks of (32, CHECK_WARPS), the ny blocks of one group
+// of 32 scenarios consecutive, so they run together and share that group's
+// rows (its neighbour voltages) in L2; their warps interleave over the
+// buses.  Each block folds its max |dS|^2 per scenario into mmax[b]
+// (non-negative doubles order like their bit patterns; NaN counts as +inf);
+// mmax is zeroed by k_slot_merge.
 constexpr int CHECK_WARPS = 4;
 
 __global__ void __launch_bounds__(32 * CHECK_WARPS)
@@ -985,17 +987,18 @@ k_check(const double2* __restrict__ V, const double2* __restrict__ Sw,
         const double2* __restrict__ Sd, const uint8_t* __restrict__ conv, int B, int n,
         const int32_t* __restrict__ bptr, const int32_t* __restrict__ bcol,
         const double2* __restrict__ bval, double2 vs0, double2 vs1, double2 vs2,
-        unsigned long long* __restrict__ mmax) {
+        unsigned long long* __restrict__ mmax, int ny) {
   __shared__ double red[CHECK_WARPS][32];
   const int lane = threadIdx.x, ty = threadIdx.y;
-  const int b = blockIdx.x * 32 + lane;
+  const int bx = blockIdx.x / ny, by = blockIdx.x % ny;   // scenario group, bus stride
+  const int b = bx * 32 + lane;
   const bool live = b < B && conv[b] != 0;
   if (__ballot_sync(0xffffffffu, live) == 0u) return;   // same for every warp of the block
   const int64_t row = (int64_t)(b < B ? b : B - 1) * n;
   const double2* vg = V + row;
   double worst = 0.0;   // max |dS|^2
   const int nb = n / 3;
-  for (int a = blockIdx.y * CHECK_WARPS + ty; a < nb; a += gridDim.y * CHECK_WARPS) {
+  for (int a = by * CHECK_WARPS + ty; a < nb; a += ny * CHECK_WARPS) {
     double2 va[3];
 #pragma unroll
     for (int p = 0; p < 3; ++p) va[p] = vg[3 * a + p];
@@ -1488,10 +1491,10 @@ zbus_status group_collect(Group* g, int k, int64_t s0, int64_t B, double* V_out,
   const int nb = net->n / 3;
   const int ny = std::max(1, std::min((nb + CHECK_WARPS - 1) / CHECK_WARPS,
                                       (8 * g->num_sms + gx - 1) / gx));
-  k_check<<<dim3((unsigned)gx, (unsigned)ny), dim3(32, CHECK_WARPS), 0, st>>>(
+  k_check<<<(unsigned)((int64_t)gx * ny), dim3(32, CHECK_WARPS), 0, st>>>(
       (const double2*)V_out, (const double2*)S_wye, (const double2*)S_delta, converged, (int)B,
       net->n, net->bsr_ptr, net->bsr_col, net->bsr_val, net->v_slack[0], net->v_slack[1],
-      net->v_slack[2], mmax);
+      net->v_slack[2], mmax, ny);
   k_check_finish<<<(unsigned)((B + 255) / 256), 256, 0, st>>>(mmax, converged, (int)B, mtol,
                                                                mm_out);
   ZB_CUDA(cudaGetLastError());
