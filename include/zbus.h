@@ -79,11 +79,15 @@ typedef struct {
   double mismatch_tol;     /* mixed modes: a converged scenario must also have
                               max_j |v_j conj(r_j)| <= mismatch_tol (FP64);
                               <= 0 selects 1e-6 */
-  int32_t max_correction;  /* reserved, accepted and unused: the defect forms
-                              converge to the fixed point of the exact
-                              (double-float) residual, so no separate
-                              correction sweeps run; a scenario that fails
-                              the FP64 mismatch test keeps its flag cleared */
+  int32_t max_correction;  /* mixed modes: a scenario that met the stop rule
+                              but fails the FP64 mismatch test gets up to
+                              max_correction FP64 correction sweeps (r =
+                              i(v) - Y_LL v - Y_Ls v_s in FP64, v += Z r with
+                              the FP64 Z, then the test again); it keeps its
+                              flag once the test passes and loses it if none
+                              does.  Each sweep counts as an iteration.
+                              <= 0: none (the flag is cleared at once);
+                              default 8 */
   int32_t profile;         /* 1: run the sweeps from the host with CUDA events
                               around every kernel on cuda_stream, for
                               zbus_last_profile; 0: device-resident loop */
@@ -333,7 +337,9 @@ typedef struct {
   double tol;
   double mismatch_tol;         /* <= 0 selects 1e-6 */
   int32_t max_admit_per_sweep; /* <= 0: unlimited */
-  int32_t reserved0;
+  int32_t max_correction;      /* FP64 correction sweeps per scenario, as in
+                                  zbus_solve_opts (<= 0: none, the flag of a
+                                  scenario above mismatch_tol is cleared) */
 } zbus_serve_config;
 
 /*
@@ -342,7 +348,8 @@ typedef struct {
  * requests into free scenario slots of their feeder (first fit, in arrival
  * order), runs one sweep of the grouped mixed-precision engine over every
  * active slot of every feeder, and completes the requests whose scenarios
- * have all stopped (FP64 mismatch test, results to the caller, sink call).
+ * have all stopped (FP64 mismatch test and correction sweeps, results to the
+ * caller, sink call).
  * Requests that arrive while others are on the GPU join at the next sweep
  * (continuous batching); per-scenario arithmetic does not depend on the mix,
  * so a result is the same alone and in the mix.  Slot capacity per feeder is
@@ -389,22 +396,26 @@ zbus_status zbus_last_profile(zbus_network net, int32_t max_n, float* ms, int32_
  *
  * It calls no cudaMalloc, cudaFree or allocating library routine: its scratch
  * (solve context, active list, per-tile partials, contraction operands) lives
- * in one static 16 MiB device array that every GPU loading the library holds
- * until the process exits.  The network must exist already (create it at
- * start-up).  The sweeps are launched from the host (max_iter sweeps; once no
- * scenario is active the remaining launches return at once).
+ * in one static 16 MiB device array.  zbus_network_create loads that array on
+ * its device and looks up its address (with that device current), so every
+ * device on which a network was created holds the 16 MiB from then until the
+ * process exits, and this call itself loads nothing.  The network must exist
+ * already (create it at start-up, before any stream capture).  The sweeps are
+ * launched from the host (max_iter sweeps; once no scenario is active the
+ * remaining launches return at once).
  *
- *   arguments as zbus_solve, with conv_rule (zbus_conv_rule) in place of opts.
- *   Returns ZBUS_ERR_ARG, launching nothing, when the batch needs more than
- *   the 16 MiB: about 16 MiB / (24 n_pad + 16 ceil(n/48) + 5) bytes per
- *   scenario, n_pad = n rounded up to a multiple of 48 (about 1790 scenarios
- *   for n = 381).
+ *   arguments as zbus_solve, with conv_rule (zbus_conv_rule) in place of
+ *   opts, but device memory only: a host array (pinned or pageable) returns
+ *   ZBUS_ERR_ARG, launching nothing.  Also ZBUS_ERR_ARG, launching nothing,
+ *   when the batch needs more than the 16 MiB: about 16 MiB / (24 n_pad +
+ *   16 ceil(n/48) + 5) bytes per scenario, n_pad = n rounded up to a multiple
+ *   of 48 (about 1790 scenarios for n = 381).  Partial-phase networks:
+ *   ZBUS_ERR_UNSUPPORTED.  After this call zbus_last_device_status reports
+ *   ZBUS_OK (the FP64 sweeps have no device-side waits).
  *
- * The first call on a device looks up the array's device address (with that
- * device current) and caches it; make that first call before any stream
- * capture.  All calls share the array and it keeps the last call's contents;
- * every call rewrites what it reads, but calls that overlap on the GPU (other
- * streams or other host threads) race on it.
+ * All calls share the array and it keeps the last call's contents; every call
+ * rewrites what it reads, but calls that overlap on the GPU (other streams or
+ * other host threads) race on it.
  */
 zbus_status zbus_solve_noalloc(zbus_network net, int64_t B,
                                const double* S_wye, const double* S_delta,
@@ -600,6 +611,31 @@ zbus_status zbus_nr_solve(zbus_nr_network net, int64_t B, const double* P, const
  * run).
  */
 int32_t zbus_checked_status(uint32_t* word);
+
+/*
+ * zbus_checked_set_wait -- checked build only: the time limit, in
+ * nanoseconds, of every wait of the tensor-core pipeline (default 2e9).  0
+ * makes a wait that is not complete at its first test give up at once, so a
+ * test can make the pipeline give up without a fault: the kernel records
+ * ZBUS_ERR_TIMEOUT for zbus_last_device_status, waits (2 s at most) for the
+ * MMAs and TMA loads it already issued, frees its tensor memory and ends the
+ * sweep loop.  Synchronous.  ZBUS_ERR_UNSUPPORTED in the normal build.
+ * Project-written: the paper has no counterpart.
+ */
+zbus_status zbus_checked_set_wait(uint64_t wait_ns);
+
+/*
+ * zbus_probe_fp64_rate -- measure the FP64 fused multiply-add rate of the
+ * current device: one launch of 8 blocks per SM x 256 threads, each running
+ * eight independent DFMA chains (no memory traffic), after a short warm-up
+ * launch, timed with CUDA events on cuda_stream.  *tflops (may be NULL)
+ * receives 2 flop per DFMA / the kernel's duration, in TFLOP/s; *ms (may be
+ * NULL) the duration.  Synchronous; allocates and frees a few KB on the
+ * stream.  The roofline denominator of the FP64 kernels (the plain method's
+ * contraction, the mismatch test); project-written, the paper has no
+ * counterpart.
+ */
+zbus_status zbus_probe_fp64_rate(double* tflops, float* ms, void* cuda_stream);
 
 /* Human-readable name of a status code (static storage). */
 const char* zbus_status_string(zbus_status s);

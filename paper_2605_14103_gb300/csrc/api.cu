@@ -44,6 +44,10 @@ void drop_graphs(zbus_network net) {
     if (g.graph) cudaGraphDestroy(g.graph);
   }
   net->graphs.clear();
+  if (net->corr_exec) cudaGraphExecDestroy(net->corr_exec);
+  if (net->corr_graph) cudaGraphDestroy(net->corr_graph);
+  net->corr_exec = nullptr;
+  net->corr_graph = nullptr;
 }
 
 int max_ntn(const zbus_network net) {
@@ -283,7 +287,7 @@ zbus_status run_group(Group* g, const std::vector<zbus_network>& nets, const std
   }
   for (size_t k = 0; k < nets.size(); ++k)
     ZB_CHECK(group_collect(g, (int)k, 0, Bs[k], Vout[k], iters[k], conv[k], Sw[k], Sd[k], mtol,
-                           k == 0 ? nets[k]->ws.mm : nullptr, st));
+                           nullptr, o.max_correction, st));
   return ZBUS_OK;
 }
 
@@ -298,6 +302,19 @@ zbus_status check_device(zbus_network net) {
 }
 
 }  // namespace
+
+// Where a caller buffer lives: 1 device (or managed) memory, 0 host memory
+// (pinned or pageable), -1 null.
+int buffer_kind(const void* p) {
+  if (!p) return -1;
+  cudaPointerAttributes a;
+  if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+    cudaGetLastError();
+    return 0;
+  }
+  return (a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged) ? 1 : 0;
+}
+
 }  // namespace zbus
 
 using namespace zbus;
@@ -394,6 +411,9 @@ zbus_status zbus_network_create(int32_t n_total, int64_t nnz, const int32_t* row
   }
   zbus_status s = build_network(net, n_total, nnz, row, col, val_reim, slack_idx, v_slack_reim,
                                 (cudaStream_t)cuda_stream);
+  // the allocation-free solve's static array is loaded now, while the caller
+  // still allocates, not at its first zbus_solve_noalloc call
+  if (s == ZBUS_OK) s = noalloc_prepare(net->device);
   if (s != ZBUS_OK) {
     std::string msg = g_last_error;
     cudaStreamSynchronize((cudaStream_t)cuda_stream);
@@ -514,6 +534,12 @@ zbus_status zbus_network_get_z(zbus_network net, double* Z_out, double* w_out, v
   return ZBUS_OK;
 }
 
+zbus_status zbus_probe_fp64_rate(double* tflops, float* ms, void* cuda_stream) {
+  g_last_error.clear();
+  if (!tflops && !ms) return fail(ZBUS_ERR_ARG, "both outputs are NULL");
+  return probe_fp64_rate(tflops, ms, (cudaStream_t)cuda_stream);
+}
+
 zbus_status zbus_network_reserve(zbus_network net, int64_t B, int32_t precision) {
   g_last_error.clear();
   if (!net) return fail(ZBUS_ERR_ARG, "network is NULL");
@@ -610,18 +636,6 @@ zbus_status solve_device_user(zbus_network net, int64_t B, const double* S_wye,
                         V_init ? buf[2] : nullptr, tol, max_iter, o, buf[3], iters, converged,
                         st));
   return phased_out(net, B, buf[3], V_out, st);
-}
-
-// Where a caller buffer lives: 1 device (or managed) memory, 0 host memory
-// (pinned or pageable), -1 null.
-int buffer_kind(const void* p) {
-  if (!p) return -1;
-  cudaPointerAttributes a;
-  if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
-    cudaGetLastError();
-    return 0;
-  }
-  return (a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged) ? 1 : 0;
 }
 
 // Staging of host-buffer solves: two sets of device buffers (loads, warm

@@ -321,7 +321,31 @@ k_residual_group(GroupState* __restrict__ gs, const ItemDesc* __restrict__ items
 // 1 = TMEM owner and MMA issuer, 2..5 = epilogue (warp w reads TMEM lanes
 // 32 (w % 4) .. + 31).  Barriers: full / empty per stage (TMA -> MMA -> TMA),
 // tfull / tempty per accumulator (MMA -> epilogue -> MMA).
+//
+// L2: every CTA re-reads Z_emb (75 MB at 3069 unknowns) during the launch,
+// while the epilogue streams the double-float state (16 B per unknown and
+// slot each way); Z's tiles are loaded with an evict-last policy and the
+// state with streaming (evict-first) accesses, so Z stays in L2.
+//
+// Giving up: every pipeline wait is bounded (tc_wait_ns()).  A role whose
+// wait runs out records its code in gs->err and stops issuing; then, before
+// the CTA frees its tensor memory and exits, the MMA issuer waits for all
+// of its committed MMAs (a final tcgen05.commit on the drain barrier) and
+// the producer for every TMA load it issued (the last fill of each stage),
+// each with its own fixed limit (DRAIN_NS), so nothing lands in tensor or
+// shared memory after the CTA is gone.
 // ---------------------------------------------------------------------------
+constexpr unsigned long long DRAIN_NS = 2000000000ull;
+
+#ifdef ZBUS_CHECKED
+// checked build: the pipeline waits' limit can be lowered by
+// zbus_checked_set_wait (0: a wait not complete at its first test gives up)
+__device__ unsigned long long g_tc_wait_ns = WAIT_NS;
+__device__ __forceinline__ unsigned long long tc_wait_ns() { return g_tc_wait_ns; }
+#else
+__device__ __forceinline__ unsigned long long tc_wait_ns() { return WAIT_NS; }
+#endif
+
 template <int BN, int ZP, int STAGES, bool BF>
 __global__ void __launch_bounds__(TC_THREADS, 1)
 k_contract_group(GroupState* __restrict__ gs, const ItemDesc* __restrict__ items,
@@ -336,12 +360,14 @@ k_contract_group(GroupState* __restrict__ gs, const ItemDesc* __restrict__ items
   uint64_t* empty = full + STAGES;
   uint64_t* tfull = empty + STAGES;
   uint64_t* tempty = tfull + 2;
-  uint32_t* tmem_holder = (uint32_t*)(tempty + 2);
+  uint64_t* drain = tempty + 2;
+  uint32_t* tmem_holder = (uint32_t*)(drain + 1);
 
   const int total = gs->n_tiles;
   if ((int)blockIdx.x >= total) return;   // whole block, before any barrier
   const uint64_t* __restrict__ tiles = gs->tiles;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const unsigned long long wait_ns = tc_wait_ns();
 
   if (threadIdx.x == 0) {
     for (int s = 0; s < STAGES; ++s) {
@@ -352,6 +378,7 @@ k_contract_group(GroupState* __restrict__ gs, const ItemDesc* __restrict__ items
       mbar_init(&tfull[u], 1);
       mbar_init(&tempty[u], 4);
     }
+    mbar_init(drain, 1);
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
   if (warp == 1) {
@@ -367,7 +394,8 @@ k_contract_group(GroupState* __restrict__ gs, const ItemDesc* __restrict__ items
 
   if (warp == 0) {
     if (lane == 0) {
-      uint32_t kc = 0;
+      const uint64_t zpol = policy_evict_last();
+      uint32_t kc = 0;   // stage fills issued
       bool ok = true;
       for (int g = blockIdx.x; g < total && ok; g += gridDim.x) {
         const uint64_t e = tiles[g];
@@ -376,10 +404,10 @@ k_contract_group(GroupState* __restrict__ gs, const ItemDesc* __restrict__ items
         const CUtensorMap* mR = tmR + k;
         const CUtensorMap* mZ0 = tmZ0 + k;
         const CUtensorMap* mZ1 = tmZ1 + k;
-        for (int kb = 0; kb < num_kb; ++kb, ++kc) {
+        for (int kb = 0; kb < num_kb; ++kb) {
           const int s = kc % STAGES;
           const uint32_t round = kc / STAGES;
-          if (!mbar_wait(&empty[s], (round & 1) ^ 1)) {
+          if (!mbar_wait(&empty[s], (round & 1) ^ 1, wait_ns)) {
             atomicCAS(&gs->err, 0, 101);
             ok = false;
             break;
@@ -387,10 +415,20 @@ k_contract_group(GroupState* __restrict__ gs, const ItemDesc* __restrict__ items
           uint8_t* st = smem + s * STAGE_BYTES;
           mbar_expect_tx(&full[s], STAGE_BYTES);
           tma_load_2d(st, mR, &full[s], kb * BK, mt * BM);
-          tma_load_2d(st + A_BYTES, mZ0, &full[s], kb * BK, nt * BN);
-          if (ZP == 2) tma_load_2d(st + A_BYTES + B_BYTES, mZ1, &full[s], kb * BK, nt * BN);
+          tma_load_2d_hint(st + A_BYTES, mZ0, &full[s], kb * BK, nt * BN, zpol);
+          if (ZP == 2)
+            tma_load_2d_hint(st + A_BYTES + B_BYTES, mZ1, &full[s], kb * BK, nt * BN, zpol);
+          ++kc;
         }
       }
+      // drain: the last fill of every stage has landed (fills complete in
+      // order per stage; nothing refills a stage after this point)
+      const uint32_t first = kc > (uint32_t)STAGES ? kc - STAGES : 0u;
+      for (uint32_t j = first; j < kc; ++j)
+        if (!mbar_wait(&full[j % STAGES], (j / STAGES) & 1, DRAIN_NS)) {
+          atomicCAS(&gs->err, 0, 105);
+          break;
+        }
     }
   } else if (warp == 1) {
     if (lane == 0) {
@@ -398,14 +436,14 @@ k_contract_group(GroupState* __restrict__ gs, const ItemDesc* __restrict__ items
       const uint32_t idesc = (1u << 4) | ((BF ? 1u : 0u) << 7) | ((BF ? 1u : 0u) << 10) |
                              ((uint32_t)(BN >> 3) << 17) | ((uint32_t)(BM >> 4) << 24);
       uint32_t kc = 0;
-      bool ok = true;
+      bool ok = true, issued = false;
       int i = 0;
       for (int g = blockIdx.x; g < total && ok; g += gridDim.x, ++i) {
         const int k = (int)(tiles[g] >> 32);
         const int num_kb = items[k].K_pad / BK;
         const int buf = i & 1;
         const uint32_t use = (uint32_t)(i >> 1);
-        if (!mbar_wait(&tempty[buf], (use & 1) ^ 1)) {
+        if (!mbar_wait(&tempty[buf], (use & 1) ^ 1, wait_ns)) {
           atomicCAS(&gs->err, 0, 104);
           break;
         }
@@ -414,7 +452,7 @@ k_contract_group(GroupState* __restrict__ gs, const ItemDesc* __restrict__ items
         for (int kb = 0; kb < num_kb; ++kb, ++kc) {
           const int s = kc % STAGES;
           const uint32_t round = kc / STAGES;
-          if (!mbar_wait(&full[s], round & 1)) {
+          if (!mbar_wait(&full[s], round & 1, wait_ns)) {
             atomicCAS(&gs->err, 0, 102);
             ok = false;
             break;
@@ -430,9 +468,16 @@ k_contract_group(GroupState* __restrict__ gs, const ItemDesc* __restrict__ items
                        (kb | kk | p) != 0 ? 1u : 0u);
             }
           }
+          issued = true;
           umma_commit(&empty[s]);
         }
         if (ok) umma_commit(&tfull[buf]);
+      }
+      // drain: every MMA this thread issued has completed before the
+      // tensor memory is freed
+      if (issued) {
+        umma_commit(drain);
+        if (!mbar_wait(drain, 0, DRAIN_NS)) atomicCAS(&gs->err, 0, 106);
       }
     }
   } else {
@@ -446,7 +491,7 @@ k_contract_group(GroupState* __restrict__ gs, const ItemDesc* __restrict__ items
       const ItemDesc& it = items[k];
       const int buf = i & 1;
       const uint32_t use = (uint32_t)(i >> 1);
-      const bool ok = mbar_wait(&tfull[buf], use & 1);
+      const bool ok = mbar_wait(&tfull[buf], use & 1, wait_ns);
       tc_fence_after();
       if (!ok) {
         if (lane == 0) atomicCAS(&gs->err, 0, 103);
@@ -472,8 +517,8 @@ k_contract_group(GroupState* __restrict__ gs, const ItemDesc* __restrict__ items
           const int oi = i0 + t;
           const bool in = valid && oi < n;
           const int64_t gi = (int64_t)(in ? oi : 0) * Bp;
-          h[t] = in ? Vh[gi] : make_float2(0.f, 0.f);
-          l[t] = in ? Vl[gi] : make_float2(0.f, 0.f);
+          h[t] = in ? __ldcs(Vh + gi) : make_float2(0.f, 0.f);
+          l[t] = in ? __ldcs(Vl + gi) : make_float2(0.f, 0.f);
           zs[t] = in ? zinv[oi] : 0.f;
         }
         float v[32];
@@ -498,8 +543,8 @@ k_contract_group(GroupState* __restrict__ gs, const ItemDesc* __restrict__ items
               fast_two_sum(sr, __fadd_rn(er, l[t].x), nh.x, nl.x);
               fast_two_sum(si, __fadd_rn(ei, l[t].y), nh.y, nl.y);
               const int64_t gi = (int64_t)oi * Bp;
-              Vh[gi] = nh;
-              Vl[gi] = nl;
+              __stcs(Vh + gi, nh);
+              __stcs(Vl + gi, nl);
               float step = sqrtf(__fmaf_rn(dr, dr, di * di));
               if (step != step) step = __int_as_float(0x7f800000);
               dmax = fmaxf(dmax, step);
@@ -598,7 +643,7 @@ __device__ void tree_block_done(GroupState* gs, int still_active, cudaGraphCondi
   gs->sweep = gs->sweep + 1;
   gs->tree_active = 0;
   gs->tree_done = 0;
-  if (use_handle) cudaGraphSetConditional(h, total > 0 ? 1u : 0u);
+  if (use_handle) cudaGraphSetConditional(h, (total > 0 && gs->err == 0) ? 1u : 0u);
 }
 
 template <int TREE_WARPS, int MINB, bool ONCHIP>
@@ -905,7 +950,9 @@ k_finish_group(GroupState* __restrict__ gs, const ItemDesc* __restrict__ items, 
     if (!initial && gs->hist && gs->sweep < gs->hist_n) gs->hist[gs->sweep] = gs->active;
     gs->active = sactive;
     if (!initial) gs->sweep = gs->sweep + 1;
-    if (use_handle) cudaGraphSetConditional(h, sactive > 0 ? 1u : 0u);
+    // a pipeline wait that gave up ends the loop (zbus_last_device_status
+    // reports it); the slots still active keep their flags cleared
+    if (use_handle) cudaGraphSetConditional(h, (sactive > 0 && gs->err == 0) ? 1u : 0u);
   }
 }
 
@@ -965,11 +1012,121 @@ __device__ __forceinline__ double2 draw64(double2 S, double2 v) {
   return make_double2(fma(S.x, v.x, S.y * v.y) * inv, fma(S.x, v.y, -S.y * v.x) * inv);
 }
 
-// FP64 check of converged scenarios, in power form: for every unknown j,
+// FP64 admittance sum of bus a of one scenario (row vg of the [B][n] voltages):
+//   acc_p = (Y_LL v + Y_Ls v_s)_{3a+p}
+//         = sum_b Y_ab (v_b - v_a) + Y_as (v_s - v_a) + Sh_a v_a   (branch form)
+// va = the bus's own voltages.  The 3x3 blocks are the same for every lane of
+// a warp working on bus a (broadcast loads).
+__device__ __forceinline__ void admittance_sum_f64(const double2* __restrict__ vg, int a, int nb,
+                                                   const int32_t* __restrict__ bptr,
+                                                   const int32_t* __restrict__ bcol,
+                                                   const double2* __restrict__ bval,
+                                                   const double2 (&vs)[3], const double2 (&va)[3],
+                                                   double (&ar)[3], double (&ai)[3]) {
+#pragma unroll
+  for (int p = 0; p < 3; ++p) ar[p] = ai[p] = 0.0;
+  const int t1 = bptr[a + 1];
+  for (int t = bptr[a]; t < t1; ++t) {
+    const int cb = bcol[t];
+    if (cb >= 0 && !ZB_IN(cb, nb, 0x207u)) continue;
+    double dr[3], di[3];
+    if (cb >= 0) {
+#pragma unroll
+      for (int q = 0; q < 3; ++q) {
+        const double2 x = vg[3 * cb + q];
+        dr[q] = x.x - va[q].x;
+        di[q] = x.y - va[q].y;
+      }
+    } else if (cb == -1) {
+#pragma unroll
+      for (int q = 0; q < 3; ++q) {
+        dr[q] = vs[q].x - va[q].x;
+        di[q] = vs[q].y - va[q].y;
+      }
+    } else {
+#pragma unroll
+      for (int q = 0; q < 3; ++q) {
+        dr[q] = va[q].x;
+        di[q] = va[q].y;
+      }
+    }
+    const double2* y = bval + (int64_t)t * 9;
+#pragma unroll
+    for (int p = 0; p < 3; ++p)
+#pragma unroll
+      for (int q = 0; q < 3; ++q) {
+        const double2 yy = y[p * 3 + q];
+        ar[p] = fma(yy.x, dr[q], fma(-yy.y, di[q], ar[p]));
+        ai[p] = fma(yy.x, di[q], fma(yy.y, dr[q], ai[p]));
+      }
+  }
+}
+
+// FP64 check of one bus of one scenario, in power form: for its unknowns j,
 //   dS_j = v_j conj((Y_LL v + Y_Ls v_s)_j) - v_j conj(i_j(v)),  |dS_j| = |v_j| |r_j|
-// with the admittance rows summed in FP64 from the branch-form blocks, the wye
-// term exactly S_j (v conj(conj(S / v)) = S, no division) and the delta term
-// v_j conj(drawn) from FP64 branch currents.
+// with the wye term exactly S_j (v conj(conj(S / v)) = S, no division) and the
+// delta term v_j conj(drawn) from FP64 branch currents.  Returns the largest
+// |dS_j|^2 of the bus (+inf for a NaN).  sw, sd: the scenario's load rows or
+// null.
+__device__ __forceinline__ double check_bus_f64(const double2* __restrict__ vg,
+                                                const double2* __restrict__ sw,
+                                                const double2* __restrict__ sd, int a, int nb,
+                                                const int32_t* __restrict__ bptr,
+                                                const int32_t* __restrict__ bcol,
+                                                const double2* __restrict__ bval,
+                                                const double2 (&vs)[3]) {
+  double2 va[3];
+#pragma unroll
+  for (int p = 0; p < 3; ++p) va[p] = vg[3 * a + p];
+  double ar[3], ai[3];
+  admittance_sum_f64(vg, a, nb, bptr, bcol, bval, vs, va, ar, ai);
+  // dS_p = v_p conj(acc_p) + S_wye_p + v_p conj(drawn_delta_p)
+  double sr[3], si[3];
+#pragma unroll
+  for (int p = 0; p < 3; ++p) {
+    sr[p] = fma(va[p].x, ar[p], va[p].y * ai[p]);
+    si[p] = fma(va[p].y, ar[p], -va[p].x * ai[p]);
+  }
+  if (sw) {
+#pragma unroll
+    for (int p = 0; p < 3; ++p) {
+      const double2 x = sw[3 * a + p];
+      sr[p] += x.x;
+      si[p] += x.y;
+    }
+  }
+  if (sd) {
+    const double2 s0 = sd[3 * a], s1 = sd[3 * a + 1], s2 = sd[3 * a + 2];
+    const bool any = (__double_as_longlong(s0.x) | __double_as_longlong(s0.y) |
+                      __double_as_longlong(s1.x) | __double_as_longlong(s1.y) |
+                      __double_as_longlong(s2.x) | __double_as_longlong(s2.y)) != 0;
+    if (any) {
+      double2 ib[3];
+      const double2 ss[3] = {s0, s1, s2};
+#pragma unroll
+      for (int p = 0; p < 3; ++p) {
+        const int q = (p + 1) % 3;
+        ib[p] = draw64(ss[p], make_double2(va[p].x - va[q].x, va[p].y - va[q].y));
+      }
+#pragma unroll
+      for (int p = 0; p < 3; ++p) {
+        const int m = (p + 2) % 3;   // branch p leaves phase p, branch m returns into it
+        const double gx = ib[p].x - ib[m].x, gy = ib[p].y - ib[m].y;
+        sr[p] += fma(va[p].x, gx, va[p].y * gy);
+        si[p] += fma(va[p].y, gx, -va[p].x * gy);
+      }
+    }
+  }
+  double worst = 0.0;
+#pragma unroll
+  for (int p = 0; p < 3; ++p) {
+    const double e = fma(sr[p], sr[p], si[p] * si[p]);
+    worst = (e != e) ? INFINITY : fmax(worst, e);
+  }
+  return worst;
+}
+
+// FP64 check of converged scenarios (every bus, check_bus_f64).
 //
 // Lanes are scenarios and every lane of a warp works on the same bus, so the
 // loop over a bus's blocks is uniform and the 3x3 blocks are broadcast loads;
@@ -995,95 +1152,12 @@ k_check(const double2* __restrict__ V, const double2* __restrict__ Sw,
   const bool live = b < B && conv[b] != 0;
   if (__ballot_sync(0xffffffffu, live) == 0u) return;   // same for every warp of the block
   const int64_t row = (int64_t)(b < B ? b : B - 1) * n;
-  const double2* vg = V + row;
+  const double2 vs[3] = {vs0, vs1, vs2};
   double worst = 0.0;   // max |dS|^2
   const int nb = n / 3;
-  for (int a = by * CHECK_WARPS + ty; a < nb; a += ny * CHECK_WARPS) {
-    double2 va[3];
-#pragma unroll
-    for (int p = 0; p < 3; ++p) va[p] = vg[3 * a + p];
-    double ar[3] = {0.0, 0.0, 0.0}, ai[3] = {0.0, 0.0, 0.0};
-    const int t1 = bptr[a + 1];
-    for (int t = bptr[a]; t < t1; ++t) {
-      const int cb = bcol[t];
-      if (cb >= 0 && !ZB_IN(cb, nb, 0x207u)) continue;
-      double dr[3], di[3];
-      if (cb >= 0) {
-#pragma unroll
-        for (int q = 0; q < 3; ++q) {
-          const double2 x = vg[3 * cb + q];
-          dr[q] = x.x - va[q].x;
-          di[q] = x.y - va[q].y;
-        }
-      } else if (cb == -1) {
-        const double2 vs[3] = {vs0, vs1, vs2};
-#pragma unroll
-        for (int q = 0; q < 3; ++q) {
-          dr[q] = vs[q].x - va[q].x;
-          di[q] = vs[q].y - va[q].y;
-        }
-      } else {
-#pragma unroll
-        for (int q = 0; q < 3; ++q) {
-          dr[q] = va[q].x;
-          di[q] = va[q].y;
-        }
-      }
-      const double2* y = bval + (int64_t)t * 9;
-#pragma unroll
-      for (int p = 0; p < 3; ++p)
-#pragma unroll
-        for (int q = 0; q < 3; ++q) {
-          const double2 yy = y[p * 3 + q];
-          ar[p] = fma(yy.x, dr[q], fma(-yy.y, di[q], ar[p]));
-          ai[p] = fma(yy.x, di[q], fma(yy.y, dr[q], ai[p]));
-        }
-    }
-    // dS_p = v_p conj(acc_p) + S_wye_p + v_p conj(drawn_delta_p)
-    double sr[3], si[3];
-#pragma unroll
-    for (int p = 0; p < 3; ++p) {
-      sr[p] = fma(va[p].x, ar[p], va[p].y * ai[p]);
-      si[p] = fma(va[p].y, ar[p], -va[p].x * ai[p]);
-    }
-    if (Sw) {
-      const double2* sw = Sw + row + 3 * a;
-#pragma unroll
-      for (int p = 0; p < 3; ++p) {
-        const double2 x = sw[p];
-        sr[p] += x.x;
-        si[p] += x.y;
-      }
-    }
-    if (Sd) {
-      const double2* sd = Sd + row + 3 * a;
-      const double2 s0 = sd[0], s1 = sd[1], s2 = sd[2];
-      const bool any = (__double_as_longlong(s0.x) | __double_as_longlong(s0.y) |
-                        __double_as_longlong(s1.x) | __double_as_longlong(s1.y) |
-                        __double_as_longlong(s2.x) | __double_as_longlong(s2.y)) != 0;
-      if (any) {
-        double2 ib[3];
-        const double2 ss[3] = {s0, s1, s2};
-#pragma unroll
-        for (int p = 0; p < 3; ++p) {
-          const int q = (p + 1) % 3;
-          ib[p] = draw64(ss[p], make_double2(va[p].x - va[q].x, va[p].y - va[q].y));
-        }
-#pragma unroll
-        for (int p = 0; p < 3; ++p) {
-          const int m = (p + 2) % 3;   // branch p leaves phase p, branch m returns into it
-          const double gx = ib[p].x - ib[m].x, gy = ib[p].y - ib[m].y;
-          sr[p] += fma(va[p].x, gx, va[p].y * gy);
-          si[p] += fma(va[p].y, gx, -va[p].x * gy);
-        }
-      }
-    }
-#pragma unroll
-    for (int p = 0; p < 3; ++p) {
-      const double e = fma(sr[p], sr[p], si[p] * si[p]);
-      worst = (e != e) ? INFINITY : fmax(worst, e);
-    }
-  }
+  for (int a = by * CHECK_WARPS + ty; a < nb; a += ny * CHECK_WARPS)
+    worst = fmax(worst, check_bus_f64(V + row, Sw ? Sw + row : nullptr, Sd ? Sd + row : nullptr,
+                                      a, nb, bptr, bcol, bval, vs));
   red[ty][lane] = worst;
   __syncthreads();
   if (ty == 0 && live) {
@@ -1096,7 +1170,6 @@ k_check(const double2* __restrict__ V, const double2* __restrict__ Sw,
 
 // Outcome per scenario: mm = sqrt(max |dS|^2); a converged flag with mm above
 // mtol is cleared; mm_out[b] = mm, or -1 for a scenario that was not checked.
-// mm_out may alias mmax (each thread reads its entry before writing it).
 __global__ void k_check_finish(const unsigned long long* mmax, uint8_t* __restrict__ conv, int B,
                                double mtol, double* mm_out) {
   const int b = blockIdx.x * blockDim.x + threadIdx.x;
@@ -1108,6 +1181,210 @@ __global__ void k_check_finish(const unsigned long long* mmax, uint8_t* __restri
   const double mm = sqrt(__longlong_as_double((long long)mmax[b]));
   if (mm_out) mm_out[b] = mm;
   if (!(mm <= mtol)) conv[b] = 0;
+}
+
+// ---------------------------------------------------------------------------
+// FP64 correction of the mixed forms: a converged scenario whose FP64
+// mismatch exceeds mtol gets up to max_correction FP64 defect sweeps
+//   r = i(v) - Y_LL v - Y_Ls v_s   (FP64, branch-form blocks)
+//   v <- v + Z r                   (the FP64 3M contraction, exact Z)
+// each followed by the FP64 check; it keeps its flag once the check passes,
+// and loses it if none of the sweeps brings it below mtol.  Each sweep counts
+// as an iteration.  The per-call arguments arrive in the solve context
+// (k_corr_setup); the select kernel, a WHILE node over the sweep (residual,
+// contraction, check, update) and the end kernel form one graph per network
+// and workspace.  With nothing to correct the graph runs two small kernels.
+// ---------------------------------------------------------------------------
+__global__ void k_corr_setup(SolveCtx* ctx, SolveCtx h) { *ctx = h; }
+
+// One block of 1024 threads: stable compaction of the index range [0, n) by a
+// predicate into list; returns the count (valid in every thread).
+template <typename Pred>
+__device__ int block_compact(int n, int32_t* __restrict__ list, Pred pred, const int32_t* src) {
+  __shared__ int swarp[32];
+  __shared__ int sbase, stotal;
+  const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
+  if (tid == 0) sbase = 0;
+  __syncthreads();
+  for (int base = 0; base < n; base += 1024) {
+    const int i = base + tid;
+    int keep = 0, v = -1;
+    if (i < n) {
+      v = src ? src[i] : i;
+      keep = pred(v) ? 1 : 0;
+    }
+    const unsigned bal = __ballot_sync(0xffffffffu, keep);
+    const int wpre = __popc(bal & ((1u << lane) - 1u));
+    if (lane == 0) swarp[wid] = __popc(bal);
+    __syncthreads();
+    if (wid == 0) {
+      const int x = swarp[lane];
+      int incl = x;
+      for (int o = 1; o < 32; o <<= 1) {
+        const int y = __shfl_up_sync(0xffffffffu, incl, o);
+        if (lane >= o) incl += y;
+      }
+      swarp[lane] = incl - x;
+      if (lane == 31) stotal = incl;
+    }
+    __syncthreads();
+    // in place (src == list) is safe: every read of this chunk happened
+    // before the barriers, every write lands at or before its own index
+    if (keep) list[sbase + swarp[wid] + wpre] = v;
+    __syncthreads();
+    if (tid == 0) sbase += stotal;
+    __syncthreads();
+  }
+  return sbase;
+}
+
+// Scenarios to correct: converged by the stop rule, FP64 mismatch above mtol.
+// The others get their outcome (mm_out); the selected ones start from a zero
+// mismatch record.
+__global__ void __launch_bounds__(1024)
+k_corr_select(SolveCtx* __restrict__ ctx, cudaGraphConditionalHandle h) {
+  const int B = ctx->B;
+  const double mtol = ctx->mismatch_tol;
+  uint8_t* conv = ctx->conv;
+  unsigned long long* mmax = ctx->mmax;
+  double* mm_out = ctx->mm_out;
+  for (int b = threadIdx.x; b < B; b += blockDim.x) {
+    if (conv[b] == 0) {
+      if (mm_out) mm_out[b] = -1.0;
+    } else {
+      const double mm = sqrt(__longlong_as_double((long long)mmax[b]));
+      if (mm_out) mm_out[b] = mm;
+    }
+  }
+  __syncthreads();
+  const int cnt = block_compact(B, ctx->list, [&](int b) {
+    return conv[b] != 0 && !(sqrt(__longlong_as_double((long long)mmax[b])) <= mtol);
+  }, nullptr);
+  __syncthreads();
+  for (int i = threadIdx.x; i < cnt; i += blockDim.x) mmax[ctx->list[i]] = 0ull;
+  if (threadIdx.x == 0) {
+    ctx->count = cnt;
+    ctx->iter = 0;
+    cudaGraphSetConditional(h, (cnt > 0 && ctx->max_iter > 0) ? 1u : 0u);
+  }
+}
+
+// FP64 residual of every listed scenario, per (slot, bus), into the 3M
+// operands [slot][n_pad] (Re, Im, Re + Im; zero in the padding).
+__global__ void __launch_bounds__(256)
+k_corr_resid(const SolveCtx* __restrict__ ctx, int n, int n_pad, const int32_t* __restrict__ bptr,
+             const int32_t* __restrict__ bcol, const double2* __restrict__ bval, double2 vs0,
+             double2 vs1, double2 vs2) {
+  const int count = ctx->count;
+  const int nbp = n_pad / 3, nb = n / 3;
+  const int64_t tot = (int64_t)count * nbp;
+  const int64_t plane = (int64_t)ctx->B * n_pad;
+  double* Ir = ctx->Iop;
+  double* Ii = Ir + plane;
+  double* Is = Ii + plane;
+  const double2 vs[3] = {vs0, vs1, vs2};
+  for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < tot;
+       t += (int64_t)gridDim.x * blockDim.x) {
+    const int slot = (int)(t / nbp);
+    const int a = (int)(t % nbp);
+    const int64_t o = (int64_t)slot * n_pad + 3 * a;
+    double rr[3] = {0.0, 0.0, 0.0}, ri[3] = {0.0, 0.0, 0.0};
+    if (a < nb && ZB_IN(ctx->list[slot], ctx->B, 0x209u)) {
+      const int b = ctx->list[slot];
+      const int64_t row = (int64_t)b * n;
+      const double2* vg = ctx->V + row;
+      double2 va[3], sw[3], sd[3], inj[3];
+#pragma unroll
+      for (int p = 0; p < 3; ++p) {
+        va[p] = vg[3 * a + p];
+        sw[p] = ctx->S_wye ? ctx->S_wye[row + 3 * a + p] : make_double2(0.0, 0.0);
+        sd[p] = ctx->S_del ? ctx->S_del[row + 3 * a + p] : make_double2(0.0, 0.0);
+      }
+      bus_injection(va, ctx->S_wye ? sw : nullptr, ctx->S_del ? sd : nullptr, 3, inj);
+      double ar[3], ai[3];
+      admittance_sum_f64(vg, a, nb, bptr, bcol, bval, vs, va, ar, ai);
+#pragma unroll
+      for (int p = 0; p < 3; ++p) {
+        rr[p] = inj[p].x - ar[p];
+        ri[p] = inj[p].y - ai[p];
+      }
+    }
+#pragma unroll
+    for (int p = 0; p < 3; ++p) {
+      Ir[o + p] = rr[p];
+      Ii[o + p] = ri[p];
+      Is[o + p] = rr[p] + ri[p];
+    }
+  }
+}
+
+// End of a correction sweep (one block of 1024): every listed scenario took
+// one more iteration; those whose check passed keep their flag and leave the
+// list (stable compaction); the others start the next check from zero.
+__global__ void __launch_bounds__(1024)
+k_corr_update(SolveCtx* __restrict__ ctx, cudaGraphConditionalHandle h) {
+  const int cnt0 = ctx->count;
+  const double mtol = ctx->mismatch_tol;
+  int32_t* list = ctx->list;
+  unsigned long long* mmax = ctx->mmax;
+  double* mm_out = ctx->mm_out;
+  for (int i = threadIdx.x; i < cnt0; i += blockDim.x) {
+    const int b = list[i];
+    ctx->iters[b] += 1;
+    if (mm_out) mm_out[b] = sqrt(__longlong_as_double((long long)mmax[b]));
+  }
+  __syncthreads();
+  const int cnt = block_compact(cnt0, list, [&](int b) {
+    return !(sqrt(__longlong_as_double((long long)mmax[b])) <= mtol);
+  }, list);
+  __syncthreads();
+  for (int i = threadIdx.x; i < cnt; i += blockDim.x) mmax[list[i]] = 0ull;
+  if (threadIdx.x == 0) {
+    const int it = ctx->iter + 1;
+    ctx->iter = it;
+    ctx->count = cnt;
+    cudaGraphSetConditional(h, (cnt > 0 && it < ctx->max_iter) ? 1u : 0u);
+  }
+}
+
+// The FP64 check (k_check's layout) of the listed scenarios: lane slot i of
+// the grid checks scenario list[i] for i < count.
+__global__ void __launch_bounds__(32 * CHECK_WARPS)
+k_corr_check(const SolveCtx* __restrict__ ctx, int n, const int32_t* __restrict__ bptr,
+             const int32_t* __restrict__ bcol, const double2* __restrict__ bval, double2 vs0,
+             double2 vs1, double2 vs2, int ny) {
+  __shared__ double red[CHECK_WARPS][32];
+  const int lane = threadIdx.x, ty = threadIdx.y;
+  const int bx = blockIdx.x / ny, by = blockIdx.x % ny;
+  const int i = bx * 32 + lane;
+  const int B = ctx->B;
+  const bool live = i < ctx->count && ZB_IN(ctx->list[i], B, 0x208u);
+  if (__ballot_sync(0xffffffffu, live) == 0u) return;
+  const int b = live ? ctx->list[i] : 0;
+  const int64_t row = (int64_t)b * n;
+  const double2 vs[3] = {vs0, vs1, vs2};
+  const double2* Sw = ctx->S_wye;
+  const double2* Sd = ctx->S_del;
+  double worst = 0.0;
+  const int nb = n / 3;
+  for (int a = by * CHECK_WARPS + ty; a < nb; a += ny * CHECK_WARPS)
+    worst = fmax(worst, check_bus_f64(ctx->V + row, Sw ? Sw + row : nullptr,
+                                      Sd ? Sd + row : nullptr, a, nb, bptr, bcol, bval, vs));
+  red[ty][lane] = worst;
+  __syncthreads();
+  if (ty == 0 && live) {
+    double x = red[0][lane];
+#pragma unroll
+    for (int w = 1; w < CHECK_WARPS; ++w) x = fmax(x, red[w][lane]);
+    if (x > 0.0) atomicMax(&ctx->mmax[b], (unsigned long long)__double_as_longlong(x));
+  }
+}
+
+// Scenarios still above mtol after the correction sweeps lose their flag.
+__global__ void k_corr_end(const SolveCtx* __restrict__ ctx) {
+  const int cnt = ctx->count;
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < cnt; i += gridDim.x * blockDim.x)
+    ctx->conv[ctx->list[i]] = 0;
 }
 
 // ---------------------------------------------------------------------------
@@ -1472,32 +1749,130 @@ zbus_status group_device_status(Group* g, cudaStream_t st) {
   ZB_CUDA(cudaMemcpyAsync(&err, group_error_word(g), sizeof(err), cudaMemcpyDeviceToHost, st));
   ZB_CUDA(cudaStreamSynchronize(st));
   if (err == 0) return ZBUS_OK;
-  if (err >= 101 && err <= 104)
+  if (err >= 101 && err <= 106)
     return fail(ZBUS_ERR_TIMEOUT, "a bounded wait of the tensor-core pipeline gave up (code " +
                                       std::to_string(err) + ")");
   return fail(ZBUS_ERR_DEVICE, "device error word " + std::to_string(err));
 }
 
+namespace {
+
+// Grid of k_check over B scenarios (32 per group, ny blocks per group).
+void check_grid(int64_t B, int n, int num_sms, int* gx, int* ny) {
+  *gx = (int)((B + 31) / 32);
+  const int nb = n / 3;
+  *ny = std::max(1, std::min((nb + CHECK_WARPS - 1) / CHECK_WARPS, (8 * num_sms + *gx - 1) / *gx));
+}
+
+// The correction graph of a network for its current workspace: select, then
+// WHILE (residual, contraction, check, update), then end.  Every per-call
+// argument is read from the workspace's solve context.
+zbus_status corr_graph(zbus_network net, int num_sms) {
+  if (net->corr_exec && net->corr_gen == net->ws.gen) return ZBUS_OK;
+  if (net->corr_exec) cudaGraphExecDestroy(net->corr_exec);
+  if (net->corr_graph) cudaGraphDestroy(net->corr_graph);
+  net->corr_exec = nullptr;
+  net->corr_graph = nullptr;
+  if (!net->cap_stream) ZB_CUDA(cudaStreamCreateWithFlags(&net->cap_stream, cudaStreamNonBlocking));
+  cudaStream_t cs = net->cap_stream;
+  SolveCtx* ctx = net->ws.ctx;
+  const int64_t cap = net->ws.cap_B;
+  const int n = net->n, n_pad = net->n_pad;
+  cudaGraph_t graph = nullptr;
+  ZB_CUDA(cudaGraphCreate(&graph, 0));
+  net->corr_graph = graph;
+  cudaGraphConditionalHandle h;
+  ZB_CUDA(cudaGraphConditionalHandleCreate(&h, graph, 0, cudaGraphCondAssignDefault));
+  cudaGraph_t out = nullptr;
+  ZB_CUDA(cudaStreamBeginCaptureToGraph(cs, graph, nullptr, nullptr, 0,
+                                        cudaStreamCaptureModeThreadLocal));
+  k_corr_select<<<1, 1024, 0, cs>>>(ctx, h);
+  cudaError_t ce = cudaStreamEndCapture(cs, &out);
+  if (ce != cudaSuccess) return cuda_fail(ce, "capture (correction select)", __FILE__, __LINE__);
+  cudaGraphNode_t sel = nullptr;
+  size_t num = 1;
+  ZB_CUDA(cudaGraphGetNodes(graph, &sel, &num));
+  cudaGraphNodeParams cp = {cudaGraphNodeTypeConditional};
+  cp.conditional.handle = h;
+  cp.conditional.type = cudaGraphCondTypeWhile;
+  cp.conditional.size = 1;
+  cudaGraphNode_t cond = nullptr;
+  ZB_CUDA(cudaGraphAddNode(&cond, graph, &sel, nullptr, 1, &cp));
+  cudaGraph_t body = cp.conditional.phGraph_out[0];
+  ZB_CUDA(cudaStreamBeginCaptureToGraph(cs, body, nullptr, nullptr, 0,
+                                        cudaStreamCaptureModeThreadLocal));
+  {
+    const int64_t tot = cap * (n_pad / 3);
+    const int grid = (int)std::min<int64_t>(152 * 16, std::max<int64_t>(1, (tot + 255) / 256));
+    k_corr_resid<<<grid, 256, 0, cs>>>(ctx, n, n_pad, net->bsr_ptr, net->bsr_col, net->bsr_val,
+                                       net->v_slack[0], net->v_slack[1], net->v_slack[2]);
+    launch_gemm_f64(ctx, net->Zr, net->Zi, net->Zs, nullptr, n, n_pad,
+                    gemm_f64_grid((int)cap, n_pad), cs);
+    int gx = 0, ny = 0;
+    check_grid(cap, n, num_sms, &gx, &ny);
+    k_corr_check<<<(unsigned)((int64_t)gx * ny), dim3(32, CHECK_WARPS), 0, cs>>>(
+        ctx, n, net->bsr_ptr, net->bsr_col, net->bsr_val, net->v_slack[0], net->v_slack[1],
+        net->v_slack[2], ny);
+    k_corr_update<<<1, 1024, 0, cs>>>(ctx, h);
+  }
+  ce = cudaStreamEndCapture(cs, &out);
+  if (ce != cudaSuccess) return cuda_fail(ce, "capture (correction sweep)", __FILE__, __LINE__);
+  ZB_CUDA(cudaStreamBeginCaptureToGraph(cs, graph, &cond, nullptr, 1,
+                                        cudaStreamCaptureModeThreadLocal));
+  k_corr_end<<<(unsigned)std::max<int64_t>(1, std::min<int64_t>(64, (cap + 255) / 256)), 256, 0,
+               cs>>>(ctx);
+  ce = cudaStreamEndCapture(cs, &out);
+  if (ce != cudaSuccess) return cuda_fail(ce, "capture (correction end)", __FILE__, __LINE__);
+  ce = cudaGraphInstantiate(&net->corr_exec, graph, 0);
+  if (ce != cudaSuccess) return cuda_fail(ce, "cudaGraphInstantiate(correction)", __FILE__, __LINE__);
+  net->corr_gen = net->ws.gen;
+  return ZBUS_OK;
+}
+
+}  // namespace
+
 zbus_status group_collect(Group* g, int k, int64_t s0, int64_t B, double* V_out, int32_t* iters,
                           uint8_t* converged, const double* S_wye, const double* S_delta,
-                          double mtol, double* mm_out, cudaStream_t st) {
+                          double mtol, double* mm_out, int32_t max_corr, cudaStream_t st) {
   if (B <= 0) return ZBUS_OK;
   zbus_network net = g->nets[k];
   if (!net->ws.mm || B > net->ws.cap_B) return fail(ZBUS_ERR_ARG, "collect: batch above workspace");
   unsigned long long* mmax = reinterpret_cast<unsigned long long*>(net->ws.mm);
   k_slot_merge<<<dim3((net->n + 31) / 32, (unsigned)((B + 31) / 32)), dim3(32, 8), 0, st>>>(
       g->d_items, k, (int)s0, (int)B, (double2*)V_out, iters, converged, mmax);
-  const int gx = (int)((B + 31) / 32);
-  const int nb = net->n / 3;
-  const int ny = std::max(1, std::min((nb + CHECK_WARPS - 1) / CHECK_WARPS,
-                                      (8 * g->num_sms + gx - 1) / gx));
+  int gx = 0, ny = 0;
+  check_grid(B, net->n, g->num_sms, &gx, &ny);
   k_check<<<(unsigned)((int64_t)gx * ny), dim3(32, CHECK_WARPS), 0, st>>>(
       (const double2*)V_out, (const double2*)S_wye, (const double2*)S_delta, converged, (int)B,
       net->n, net->bsr_ptr, net->bsr_col, net->bsr_val, net->v_slack[0], net->v_slack[1],
       net->v_slack[2], mmax, ny);
-  k_check_finish<<<(unsigned)((B + 255) / 256), 256, 0, st>>>(mmax, converged, (int)B, mtol,
-                                                               mm_out);
+  if (max_corr <= 0) {
+    k_check_finish<<<(unsigned)((B + 255) / 256), 256, 0, st>>>(mmax, converged, (int)B, mtol,
+                                                                 mm_out);
+    ZB_CUDA(cudaGetLastError());
+    return ZBUS_OK;
+  }
+  SolveCtx h;
+  std::memset(&h, 0, sizeof(h));
+  h.S_wye = (const double2*)S_wye;
+  h.S_del = (const double2*)S_delta;
+  h.V = (double2*)V_out;
+  h.iters = iters;
+  h.conv = converged;
+  h.list = net->ws.list;
+  h.keep = net->ws.keep;
+  h.part = net->ws.part;
+  h.Iop = net->ws.Iop;
+  h.mismatch_tol = mtol;
+  h.B = (int32_t)B;
+  h.max_iter = max_corr;
+  h.ntn = net->n_pad / F64_BN;
+  h.mmax = mmax;
+  h.mm_out = mm_out;
+  ZB_CHECK(corr_graph(net, g->num_sms));
+  k_corr_setup<<<1, 1, 0, st>>>(net->ws.ctx, h);
   ZB_CUDA(cudaGetLastError());
+  ZB_CUDA(cudaGraphLaunch(net->corr_exec, st));
   return ZBUS_OK;
 }
 
@@ -1506,3 +1881,16 @@ zbus_status group_collect(Group* g, int k, int64_t s0, int64_t B, double* V_out,
 namespace zbus {
 ZB_CHECK_WORD_ACCESSOR(check_word_group)
 }  // namespace zbus
+
+extern "C" zbus_status zbus_checked_set_wait(uint64_t wait_ns) {
+#ifdef ZBUS_CHECKED
+  zbus::set_error("");
+  cudaError_t e = cudaMemcpyToSymbol(zbus::g_tc_wait_ns, &wait_ns, sizeof(wait_ns));
+  if (e != cudaSuccess)
+    return zbus::cuda_fail(e, "cudaMemcpyToSymbol(wait limit)", __FILE__, __LINE__);
+  return ZBUS_OK;
+#else
+  (void)wait_ns;
+  return zbus::fail(ZBUS_ERR_UNSUPPORTED, "the wait limit is settable in the checked build only");
+#endif
+}

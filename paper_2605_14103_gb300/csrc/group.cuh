@@ -139,11 +139,13 @@ zbus_status group_sweep(Group* g, cudaGraphConditionalHandle h, bool use_handle,
 // Device-resident loop: sweeps until no slot is active (CUDA graph WHILE).
 zbus_status group_run(Group* g, cudaStream_t st);
 // Results of item k, slots [s0, s0 + B): merged FP64 voltages, iteration
-// counts and flags into caller arrays, then the FP64 mismatch test (flags of
-// scenarios above mtol cleared; mm_out may be null).
+// counts and flags into caller arrays, then the FP64 mismatch test; a
+// converged scenario above mtol gets up to max_corr FP64 correction sweeps
+// and loses its flag if it stays above (mm_out, may be null: the final
+// mismatch, -1 where not checked).
 zbus_status group_collect(Group* g, int k, int64_t s0, int64_t B, double* V_out, int32_t* iters,
                           uint8_t* converged, const double* S_wye, const double* S_delta,
-                          double mtol, double* mm_out, cudaStream_t st);
+                          double mtol, double* mm_out, int32_t max_corr, cudaStream_t st);
 // Shared memory of the position tables of a tree-sweep block for a feeder of
 // nbus buses: per bus its node record (16 B), FP16 z block (36 B), scale
 // (4 B) and parent-line phase mask (1 B), padded to 16 B.

@@ -90,8 +90,9 @@ __global__ void k_currents_f64(const SolveCtx* __restrict__ ctx, int n, int n_pa
 // K2: FP64 3M contraction over active scenarios.
 //   T1 = Zr Ir, T2 = Zi Ii, T3 = (Zr + Zi)(Ir + Ii);  D = (T1 - T2, T3 - T1 - T2)
 // Tile: BM scenarios x BN outputs, k in steps of BK, each thread TM x TN.
-// Epilogue: v <- w + D in place, partials (max |dv|, sum |v_new| - |v_old|)
-// per (slot, N-tile), summed in a fixed order.
+// Epilogue: v <- w + D in place (w null: v <- v + D, the defect update of
+// the FP64 correction sweeps), partials (max |dv|, sum |v_new| - |v_old|) per
+// (slot, N-tile), summed in a fixed order.
 // ---------------------------------------------------------------------------
 constexpr int TM = 2, TN = 4;
 constexpr int THR_M = F64_BM / TM;   // 16
@@ -198,9 +199,9 @@ k_gemm3m_f64(const SolveCtx* __restrict__ ctx, const double* __restrict__ Zr,
           if (i < n) {
             const double dr = a1[a][c] - a2[a][c];
             const double di = a3[a][c] - a1[a][c] - a2[a][c];
-            const double2 wi = w[i];
             const int64_t g = (int64_t)b * n + i;
             const double2 vo = V[g];
+            const double2 wi = w ? w[i] : vo;
             const double2 vn = make_double2(wi.x + dr, wi.y + di);
             V[g] = vn;
             double step = hypot(vn.x - vo.x, vn.y - vo.y);
@@ -369,7 +370,58 @@ __global__ void k_mismatch(const double2* __restrict__ V, const double2* __restr
   }
 }
 
+// ---------------------------------------------------------------------------
+// FP64 rate probe: eight independent DFMA chains per thread (no memory
+// traffic in the loop), the roofline denominator of the FP64 kernels.  The
+// values stay bounded (x <- x a + c with a < 1) and are summed into out only
+// when the sum is negative, which it never is, so the chains are kept.
+// ---------------------------------------------------------------------------
+constexpr int PROBE_CHAINS = 8;
+
+__global__ void __launch_bounds__(256) k_probe_dfma(double* out, int iters, double a, double c) {
+  double x[PROBE_CHAINS];
+#pragma unroll
+  for (int i = 0; i < PROBE_CHAINS; ++i) x[i] = 1.0 + 1e-3 * (threadIdx.x + i);
+  for (int k = 0; k < iters; ++k) {
+#pragma unroll
+    for (int i = 0; i < PROBE_CHAINS; ++i) x[i] = fma(x[i], a, c);
+  }
+  double s = 0.0;
+#pragma unroll
+  for (int i = 0; i < PROBE_CHAINS; ++i) s += x[i];
+  if (s < 0.0) out[blockIdx.x] = s;
+}
+
 }  // namespace
+
+zbus_status probe_fp64_rate(double* tflops, float* ms_out, cudaStream_t st) {
+  int dev = 0, sms = 0;
+  ZB_CUDA(cudaGetDevice(&dev));
+  ZB_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+  const int blocks = 8 * sms, threads = 256;
+  double* out = nullptr;   // written only on a negative sum (never)
+  ZB_CUDA(cudaMallocAsync((void**)&out, (size_t)blocks * sizeof(double), st));
+  cudaEvent_t e0, e1;
+  ZB_CUDA(cudaEventCreate(&e0));
+  ZB_CUDA(cudaEventCreate(&e1));
+  k_probe_dfma<<<blocks, threads, 0, st>>>(out, 256, 0.999999, 1e-7);   // warm-up
+  const int iters = 16384;
+  ZB_CUDA(cudaEventRecord(e0, st));
+  k_probe_dfma<<<blocks, threads, 0, st>>>(out, iters, 0.999999, 1e-7);
+  ZB_CUDA(cudaEventRecord(e1, st));
+  cudaError_t ce = cudaEventSynchronize(e1);
+  float ms = 0.f;
+  if (ce == cudaSuccess) ce = cudaEventElapsedTime(&ms, e0, e1);
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  cudaFreeAsync(out, st);
+  if (ce != cudaSuccess) return cuda_fail(ce, "FP64 probe", __FILE__, __LINE__);
+  ZB_CUDA(cudaStreamSynchronize(st));
+  const double flops = 2.0 * PROBE_CHAINS * (double)iters * blocks * threads;
+  if (tflops) *tflops = ms > 0.f ? flops / (ms * 1e-3) / 1e12 : 0.0;
+  if (ms_out) *ms_out = ms;
+  return ZBUS_OK;
+}
 
 void launch_init(SolveCtx* ctx, const SolveCtx& h, const double2* w, int n, int B,
                  cudaStream_t st) {

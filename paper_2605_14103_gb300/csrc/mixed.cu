@@ -13,7 +13,7 @@
 
 #include "df.cuh"
 #include "group.cuh"
-#include "mixed.cuh"
+#include "zbus_internal.cuh"
 
 namespace zbus {
 namespace {

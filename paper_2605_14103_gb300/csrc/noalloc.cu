@@ -9,10 +9,15 @@
 // at start-up (zbus_network_create allocates) and then calls this entry point,
 // which calls no cudaMalloc, cudaFree or allocating library routine.
 //
-// The scratch array is STATIC_SCRATCH_BYTES (16 MiB) and is held by every GPU
-// that loads the library until the process exits.  All calls share it and it
-// keeps the last call's contents, so calls that overlap on the GPU (on
-// different streams, or from several host threads) race on it.
+// The scratch array is STATIC_SCRATCH_BYTES (16 MiB).  The CUDA runtime loads
+// it on a device lazily, when its address is first asked for; so that this
+// never happens inside a call that must not allocate, zbus_network_create
+// asks for it (noalloc_prepare), and every device on which a network was
+// created holds the array from then until the process exits.  All calls share
+// it and it keeps the last call's contents, so calls that overlap on the GPU
+// (on different streams, or from several host threads) race on it.  Every
+// array argument must be device memory: the sweeps read and write the
+// caller's arrays directly, with no staging.
 #include <cmath>
 #include <cstring>
 #include <mutex>
@@ -49,6 +54,12 @@ zbus_status scratch_address(int dev, void** out) {
 }
 
 }  // namespace
+
+zbus_status noalloc_prepare(int dev) {
+  void* p = nullptr;
+  return scratch_address(dev, &p);
+}
+
 }  // namespace zbus
 
 using namespace zbus;
@@ -91,6 +102,12 @@ extern "C" zbus_status zbus_solve_noalloc(zbus_network net, int64_t B, const dou
   int dev = -1;
   ZB_CUDA(cudaGetDevice(&dev));
   if (dev != net->device) return fail(ZBUS_ERR_ARG, "current device differs from the network's");
+  // no staging here: host arrays are refused (cudaPointerGetAttributes
+  // allocates nothing)
+  const void* arrays[] = {S_wye, S_delta, V_init, V_out, iters, converged};
+  for (const void* a : arrays)
+    if (buffer_kind(a) == 0)
+      return fail(ZBUS_ERR_ARG, "the allocation-free solve takes device memory only");
   void* base = nullptr;
   ZB_CHECK(scratch_address(dev, &base));
   char* p = (char*)base;
@@ -115,6 +132,9 @@ extern "C" zbus_status zbus_solve_noalloc(zbus_network net, int64_t B, const dou
   h.ntn = ntn;
   SolveCtx* ctx = (SolveCtx*)p;
   cudaStream_t st = (cudaStream_t)cuda_stream;
+  // the FP64 sweeps have no device-side waits: zbus_last_device_status must
+  // not report the error word of an earlier mixed-precision solve
+  net->last_group = nullptr;
   // The run start writes the whole context, the active list, iters and flags,
   // so nothing left in the array by an earlier call is read: every partial,
   // keep mark and operand element (padding included) is written in a sweep

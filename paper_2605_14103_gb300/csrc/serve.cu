@@ -259,7 +259,7 @@ extern "C" zbus_status zbus_serve(const zbus_serve_config* cfg, zbus_network* po
         int32_t* itp = fl.req.V_out && fl.req.iters ? fl.req.iters : f.res_it + fl.s0;
         uint8_t* cvp = fl.req.V_out && fl.req.converged ? fl.req.converged : f.res_cv + fl.s0;
         SV_CHECK(group_collect(&g, (int)k, fl.s0, fl.req.B, V, itp, cvp, fl.req.S_wye,
-                               fl.req.S_delta, mtol, nullptr, st));
+                               fl.req.S_delta, mtol, nullptr, cfg->max_correction, st));
         done.push_back(Done{k, fl, V, itp, cvp});
         f.live.erase(f.live.begin() + q);
       }

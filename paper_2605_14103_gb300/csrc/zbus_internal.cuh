@@ -111,9 +111,11 @@ struct SolveCtx {
   int32_t max_iter;
   int32_t rule;
   int32_t ntn;            // N-tiles of the contraction
-  int32_t phase;          // mixed modes: 0 = sweeping, 1 = correction
-  int32_t corr_left;
   int32_t err;            // device error word (0 = fine)
+  // FP64 correction of the mixed forms: max |dS|^2 per scenario (bit
+  // patterns of non-negative doubles) and the reported mismatch (or null)
+  unsigned long long* mmax;
+  double* mm_out;
   int32_t* hist;          // profile mode: active count of sweep k (else nullptr)
   int32_t hist_n;
   uint8_t* keep;          // [B] stop decision of the current sweep, by slot
@@ -259,6 +261,11 @@ struct zbus_network_s {
   struct zbus::Group* group1 = nullptr;   // single-network mixed solves
   struct zbus::Group* last_group = nullptr;   // group of the last mixed solve (error word)
   std::vector<zbus::GraphEntry> graphs;
+  // FP64 correction loop of the mixed forms (group.cu), built for the
+  // workspace generation corr_gen
+  cudaGraph_t corr_graph = nullptr;
+  cudaGraphExec_t corr_exec = nullptr;
+  uint64_t corr_gen = 0;
   cudaStream_t cap_stream = nullptr;  // private stream used only to capture graphs
   zbus::Profile prof;
   zbus::HostStage stage;
@@ -286,12 +293,21 @@ struct zbus_network_s {
 
 namespace zbus {
 
+// api.cu: where a caller buffer lives (1 device or managed memory, 0 host
+// memory, pinned or pageable; -1 null)
+int buffer_kind(const void* p);
+
+// noalloc.cu: loads the allocation-free solve's static scratch array on the
+// current device and caches its address (called once per network creation)
+zbus_status noalloc_prepare(int dev);
+
 // setup.cu
 zbus_status build_network(zbus_network net, int32_t n_total, int64_t nnz, const int32_t* row,
                           const int32_t* col, const double* val, const int32_t* slack,
                           const double* vs, cudaStream_t st);
 
 // kernels_f64.cu
+zbus_status probe_fp64_rate(double* tflops, float* ms, cudaStream_t st);
 void launch_init(SolveCtx* ctx, const SolveCtx& h, const double2* w, int n, int B,
                  cudaStream_t st);
 void launch_currents_f64(SolveCtx* ctx, int n, int n_pad, int B, cudaStream_t st);

@@ -59,7 +59,7 @@ class zbus_serve_config(C.Structure):
     _fields_ = [("hbm_budget_bytes", C.c_uint64), ("max_slots", C.c_int32),
                 ("precision", C.c_int32), ("conv_rule", C.c_int32), ("max_iter", C.c_int32),
                 ("tol", C.c_double), ("mismatch_tol", C.c_double),
-                ("max_admit_per_sweep", C.c_int32), ("reserved0", C.c_int32)]
+                ("max_admit_per_sweep", C.c_int32), ("max_correction", C.c_int32)]
 
 
 class zbus_nr_opts(C.Structure):
@@ -104,6 +104,8 @@ _SIGS = {
     "zbus_serve": (C.c_int, [C.POINTER(zbus_serve_config), C.POINTER(C.c_void_p), C.c_int32,
                              SOURCE_FN, SINK_FN, C.c_void_p, C.c_void_p]),
     "zbus_last_device_status": (C.c_int, [_P, _P]),
+    "zbus_probe_fp64_rate": (C.c_int, [C.POINTER(C.c_double), C.POINTER(C.c_float), _P]),
+    "zbus_checked_set_wait": (C.c_int, [C.c_uint64]),
     "zbus_solve_adjoint": (C.c_int, [_P, C.c_int64, _P, _P, _P, _P, C.c_double, C.c_int32,
                                      C.POINTER(zbus_solve_opts), _P, _P, _P, _P, _P]),
     "zbus_nr_opts_default": (None, [C.POINTER(zbus_nr_opts)]),
@@ -245,6 +247,14 @@ def zbus_last_device_status(h, stream=None) -> int:
     return int(lib().zbus_last_device_status(h, _stream(stream)))
 
 
+def zbus_probe_fp64_rate(stream=None):
+    """(TFLOP/s, ms) of the device's FP64 fused multiply-add rate (DFMA chains)."""
+    t = C.c_double(0.0)
+    ms = C.c_float(0.0)
+    _check(lib().zbus_probe_fp64_rate(C.byref(t), C.byref(ms), _stream(stream)))
+    return t.value, ms.value
+
+
 def zbus_solve_noalloc(h, S_wye, S_delta, V_init, tol, max_iter, rule, V_out, iters, converged,
                        stream=None):
     """The FP64 solve with library-static scratch (no device allocation)."""
@@ -350,13 +360,14 @@ def zbus_tune_set(precision, max_n, total_B, BN, stages):
 
 
 def solve_batched(networks, loads, tol=1e-8, max_iter=50, precision="fp16_scaled",
-                  rule="maxabs", mismatch_tol=1e-6, stream=None):
+                  rule="maxabs", mismatch_tol=1e-6, max_correction=8, stream=None):
     """networks: [Network]; loads: [(S_wye, S_delta)] device tensors.  Returns [(V, iters, conv)]."""
     import torch
     o = zbus_solve_opts_default()
     o.precision = PRECISION[precision]
     o.conv_rule = RULE[rule]
     o.mismatch_tol = mismatch_tol
+    o.max_correction = max_correction
     items, outs = [], []
     for net, (sw, sd) in zip(networks, loads):
         ref = sw if sw is not None else sd
@@ -405,7 +416,7 @@ def zbus_serve(cfg, pool_handles, source, sink, stream=None):
 
 def serve(networks, requests, hbm_budget_bytes=120 << 30, max_slots=4096,
           precision="fp16_scaled", tol=1e-8, max_iter=50, mismatch_tol=1e-6, rule="maxabs",
-          keep_results=True, max_admit_per_sweep=0, stream=None):
+          keep_results=True, max_admit_per_sweep=0, max_correction=8, stream=None):
     """Serve a list of requests over a pool of networks.
 
     requests: dicts with keys feeder, S_wye, S_delta (device tensors [B, n]),
@@ -462,6 +473,7 @@ def serve(networks, requests, hbm_budget_bytes=120 << 30, max_slots=4096,
     cfg.tol = float(tol)
     cfg.mismatch_tol = float(mismatch_tol)
     cfg.max_admit_per_sweep = int(max_admit_per_sweep)
+    cfg.max_correction = int(max_correction)
     zbus_serve(cfg, [net.handle for net in networks], source, sink, stream)
     for i, V, it, cv in keep:
         if out[i] is not None:

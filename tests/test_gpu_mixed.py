@@ -227,12 +227,69 @@ def test_final_mismatch_test_agrees_with_oracle(mode):
     mm = O.power_mismatch(ref["Y_LL"], ref["Y_Ls"], f.v_slack, V.cpu().numpy(), Sw, Sd)
     thr = float(np.sqrt(mm.min() * mm.max()))
     assert mm.min() < thr < mm.max()
-    V2, it2, cv2 = net.solve(dev(Sw), dev(Sd), tol=1e-7, precision=mode, mismatch_tol=thr)
+    V2, it2, cv2 = net.solve(dev(Sw), dev(Sd), tol=1e-7, precision=mode, mismatch_tol=thr,
+                             max_correction=0)
     assert torch.equal(V2, V)
     want = (mm <= thr).astype(np.uint8)
     # both sides sum in FP64 in different orders: leave out near-ties
     clear = np.abs(mm / thr - 1.0) > 1e-3
     np.testing.assert_array_equal(cv2.cpu().numpy()[clear], want[clear])
+
+
+@pytest.mark.parametrize("mode", MODES)
+def test_fp64_correction_sweeps(mode):
+    """The final FP64 correction of the mixed forms.
+
+    A loose stop tolerance (1e-5) leaves every scenario with an FP64 power
+    mismatch of about 5e-7 .. 1e-6.  With the gate between the smallest and
+    the largest of the oracle's mismatches of those voltages:
+      * max_correction = 0: exactly the scenarios the oracle puts above the
+        gate lose their flag, voltages unchanged;
+      * max_correction = 8: every scenario keeps its flag; those below the
+        gate are untouched (voltages bitwise, same iteration counts), those
+        above took one or more FP64 correction sweeps (counted as
+        iterations), and now pass the gate by the oracle's mismatch and lie
+        within 1e-6 pu of the oracle's tight solution;
+      * an unreachable gate: every flag is cleared after the allowed sweeps.
+    """
+    f = F.make_feeder(90, 31, delta_frac=0.5)
+    Sw, Sd = F.make_scenarios(f, 64, 0.8, 1.2)
+    net = zbus.Network.from_feeder(f)
+    V, it, cv = net.solve(dev(Sw), dev(Sd), tol=1e-5, precision=mode, mismatch_tol=1.0,
+                          max_correction=0)
+    assert cv.cpu().numpy().all()
+    ref = oracle(f, Sw, Sd, tol=1e-12, max_iter=100)
+    mm = O.power_mismatch(ref["Y_LL"], ref["Y_Ls"], f.v_slack, V.cpu().numpy(), Sw, Sd)
+    thr = float(np.sqrt(mm.min() * mm.max()))
+    assert mm.min() < thr < mm.max()
+    clear = np.abs(mm / thr - 1.0) > 1e-3   # FP64 sums in different orders: no near-ties
+    above = (mm > thr) & clear
+    below = (mm <= thr) & clear
+    assert above.any() and below.any()
+
+    V0, it0, cv0 = net.solve(dev(Sw), dev(Sd), tol=1e-5, precision=mode, mismatch_tol=thr,
+                             max_correction=0)
+    assert torch.equal(V0, V) and torch.equal(it0, it)
+    np.testing.assert_array_equal(cv0.cpu().numpy()[clear], below[clear].astype(np.uint8))
+
+    V8, it8, cv8 = net.solve(dev(Sw), dev(Sd), tol=1e-5, precision=mode, mismatch_tol=thr,
+                             max_correction=8)
+    V8h, it8h, ith = V8.cpu().numpy(), it8.cpu().numpy(), it.cpu().numpy()
+    assert cv8.cpu().numpy().all()
+    np.testing.assert_array_equal(V8h[below], V.cpu().numpy()[below])
+    np.testing.assert_array_equal(it8h[below], ith[below])
+    assert (it8h[above] > ith[above]).all() and (it8h[above] <= ith[above] + 8).all()
+    mm8 = O.power_mismatch(ref["Y_LL"], ref["Y_Ls"], f.v_slack, V8h, Sw, Sd)
+    assert mm8[above].max() <= thr * (1 + 1e-3)
+    assert np.abs(V8h - ref["V"]).max() <= 1e-6
+    err_before = np.abs(V.cpu().numpy() - ref["V"]).max(axis=1)
+    err_after = np.abs(V8h - ref["V"]).max(axis=1)
+    assert (err_after[above] < err_before[above]).all()
+
+    Vx, itx, cvx = net.solve(dev(Sw), dev(Sd), tol=1e-5, precision=mode, mismatch_tol=1e-300,
+                             max_correction=2)
+    assert not cvx.cpu().numpy().any()
+    np.testing.assert_array_equal(itx.cpu().numpy(), ith + 2)
 
 
 def test_device_status_is_clean_after_solves():
