@@ -135,6 +135,7 @@ zbus_status ensure_workspace(zbus_network net, int64_t B) {
   ws.keep = (uint8_t*)(p + L.keep);
   ws.part = (double*)(p + L.part);
   ws.Iop = (double*)(p + L.iop);
+  ws.iop_bytes = L.R - L.iop;
   ws.R = (void*)(p + L.R);
   ws.rinv = (float*)(p + L.rinv);
   ws.mm = (double*)(p + L.mm);
@@ -501,6 +502,8 @@ void zbus_network_destroy(zbus_network net) {
   cudaFree(net->bsr_ptr);
   cudaFree(net->bsr_col);
   cudaFree(net->bsr_val);
+  cudaFree(net->br_tab);
+  cudaFree(net->bsr_br);
   cudaFree(net->t_node);
   cudaFree(net->t_lvl);
   cudaFree(net->t_mask);

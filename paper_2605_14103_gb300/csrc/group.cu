@@ -324,8 +324,10 @@ k_residual_group(GroupState* __restrict__ gs, const ItemDesc* __restrict__ items
 //
 // L2: every CTA re-reads Z_emb (75 MB at 3069 unknowns) during the launch,
 // while the epilogue streams the double-float state (16 B per unknown and
-// slot each way); Z's tiles are loaded with an evict-last policy and the
-// state with streaming (evict-first) accesses, so Z stays in L2.
+// slot each way); Z's tiles are loaded with an evict-last policy and, where
+// the state is larger than L2 keeps between kernels (gs->stream_state), the
+// state with streaming (evict-first) accesses, so Z stays in L2.  A state
+// that fits is left to the default policy: the next residual re-reads it.
 //
 // Giving up: every pipeline wait is bounded (tc_wait_ns()).  A role whose
 // wait runs out records its code in gs->err and stops issuing; then, before
@@ -484,6 +486,7 @@ k_contract_group(GroupState* __restrict__ gs, const ItemDesc* __restrict__ items
     const int q = warp & 3;
     const int row = q * 32 + lane;
     const bool summag = gs->rule == ZBUS_CONV_SUMMAG;
+    const bool stream = gs->stream_state != 0;
     int i = 0;
     for (int g = blockIdx.x; g < total; g += gridDim.x, ++i) {
       const uint64_t e = tiles[g];
@@ -517,8 +520,8 @@ k_contract_group(GroupState* __restrict__ gs, const ItemDesc* __restrict__ items
           const int oi = i0 + t;
           const bool in = valid && oi < n;
           const int64_t gi = (int64_t)(in ? oi : 0) * Bp;
-          h[t] = in ? __ldcs(Vh + gi) : make_float2(0.f, 0.f);
-          l[t] = in ? __ldcs(Vl + gi) : make_float2(0.f, 0.f);
+          h[t] = in ? (stream ? __ldcs(Vh + gi) : Vh[gi]) : make_float2(0.f, 0.f);
+          l[t] = in ? (stream ? __ldcs(Vl + gi) : Vl[gi]) : make_float2(0.f, 0.f);
           zs[t] = in ? zinv[oi] : 0.f;
         }
         float v[32];
@@ -543,8 +546,13 @@ k_contract_group(GroupState* __restrict__ gs, const ItemDesc* __restrict__ items
               fast_two_sum(sr, __fadd_rn(er, l[t].x), nh.x, nl.x);
               fast_two_sum(si, __fadd_rn(ei, l[t].y), nh.y, nl.y);
               const int64_t gi = (int64_t)oi * Bp;
-              __stcs(Vh + gi, nh);
-              __stcs(Vl + gi, nl);
+              if (stream) {
+                __stcs(Vh + gi, nh);
+                __stcs(Vl + gi, nl);
+              } else {
+                Vh[gi] = nh;
+                Vl[gi] = nl;
+              }
               float step = sqrtf(__fmaf_rn(dr, dr, di * di));
               if (step != step) step = __int_as_float(0x7f800000);
               dmax = fmaxf(dmax, step);
@@ -1017,18 +1025,38 @@ __device__ __forceinline__ double2 draw64(double2 S, double2 v) {
 //         = sum_b Y_ab (v_b - v_a) + Y_as (v_s - v_a) + Sh_a v_a   (branch form)
 // va = the bus's own voltages.  The 3x3 blocks are the same for every lane of
 // a warp working on bus a (broadcast loads).
+//
+// With a branch row jg (the scenario's branch terms J_k = Y_ab (v_b - v_a),
+// k_branch_f64) and the block-to-branch map br, a neighbour block adds +J_k
+// (block (a, b)) or -J_k (its mirror) instead of forming the product.
 __device__ __forceinline__ void admittance_sum_f64(const double2* __restrict__ vg, int a, int nb,
                                                    const int32_t* __restrict__ bptr,
                                                    const int32_t* __restrict__ bcol,
                                                    const double2* __restrict__ bval,
                                                    const double2 (&vs)[3], const double2 (&va)[3],
-                                                   double (&ar)[3], double (&ai)[3]) {
+                                                   double (&ar)[3], double (&ai)[3],
+                                                   const double2* __restrict__ jg = nullptr,
+                                                   const int32_t* __restrict__ br = nullptr,
+                                                   int nbr = 0) {
 #pragma unroll
   for (int p = 0; p < 3; ++p) ar[p] = ai[p] = 0.0;
   const int t1 = bptr[a + 1];
   for (int t = bptr[a]; t < t1; ++t) {
     const int cb = bcol[t];
     if (cb >= 0 && !ZB_IN(cb, nb, 0x207u)) continue;
+    if (jg && cb >= 0) {
+      const int k = br[t];
+      const int kk = k >= 0 ? k : -k - 1;
+      if (!ZB_IN(kk, nbr, 0x20au)) continue;
+      const double sg = k >= 0 ? 1.0 : -1.0;
+#pragma unroll
+      for (int p = 0; p < 3; ++p) {
+        const double2 x = jg[3 * kk + p];
+        ar[p] = fma(sg, x.x, ar[p]);
+        ai[p] = fma(sg, x.y, ai[p]);
+      }
+      continue;
+    }
     double dr[3], di[3];
     if (cb >= 0) {
 #pragma unroll
@@ -1074,12 +1102,15 @@ __device__ __forceinline__ double check_bus_f64(const double2* __restrict__ vg,
                                                 const int32_t* __restrict__ bptr,
                                                 const int32_t* __restrict__ bcol,
                                                 const double2* __restrict__ bval,
-                                                const double2 (&vs)[3]) {
+                                                const double2 (&vs)[3],
+                                                const double2* __restrict__ jg = nullptr,
+                                                const int32_t* __restrict__ br = nullptr,
+                                                int nbr = 0) {
   double2 va[3];
 #pragma unroll
   for (int p = 0; p < 3; ++p) va[p] = vg[3 * a + p];
   double ar[3], ai[3];
-  admittance_sum_f64(vg, a, nb, bptr, bcol, bval, vs, va, ar, ai);
+  admittance_sum_f64(vg, a, nb, bptr, bcol, bval, vs, va, ar, ai, jg, br, nbr);
   // dS_p = v_p conj(acc_p) + S_wye_p + v_p conj(drawn_delta_p)
   double sr[3], si[3];
 #pragma unroll
@@ -1137,14 +1168,60 @@ __device__ __forceinline__ double check_bus_f64(const double2* __restrict__ vg,
 // buses.  Each block folds its max |dS|^2 per scenario into mmax[b]
 // (non-negative doubles order like their bit patterns; NaN counts as +inf);
 // mmax is zeroed by k_slot_merge.
+//
+// With branch rows J ([B][nbr][3], k_branch_f64 of the same grid), each
+// line's block product is formed once, by k_branch_f64, and both of its
+// buses add it (identical mirror blocks, build_branches): about a third
+// fewer FP64 operations.
 constexpr int CHECK_WARPS = 4;
+
+// Branch terms J_k = Y_ab (v_b - v_a) of every live scenario, FP64, in the
+// check's layout (lanes = 32 scenarios, warps over the branches).
+__global__ void __launch_bounds__(32 * CHECK_WARPS)
+k_branch_f64(const double2* __restrict__ V, const uint8_t* __restrict__ conv, int B, int n,
+             const int4* __restrict__ tab, int nbr, const double2* __restrict__ bval,
+             double2* __restrict__ J, int ny) {
+  const int lane = threadIdx.x, ty = threadIdx.y;
+  const int bx = blockIdx.x / ny, by = blockIdx.x % ny;
+  const int b = bx * 32 + lane;
+  const bool live = b < B && conv[b] != 0;
+  if (__ballot_sync(0xffffffffu, live) == 0u) return;
+  if (!live) return;
+  const double2* vg = V + (int64_t)b * n;
+  double2* jg = J + (int64_t)b * nbr * 3;
+  const int nb = n / 3;
+  for (int k = by * CHECK_WARPS + ty; k < nbr; k += ny * CHECK_WARPS) {
+    const int4 e = tab[k];
+    if (!ZB_IN(e.x, nb, 0x20bu) || !ZB_IN(e.y, nb, 0x20cu)) continue;
+    double dr[3], di[3];
+#pragma unroll
+    for (int q = 0; q < 3; ++q) {
+      const double2 xb = vg[3 * e.y + q], xa = vg[3 * e.x + q];
+      dr[q] = xb.x - xa.x;
+      di[q] = xb.y - xa.y;
+    }
+    const double2* y = bval + (int64_t)e.z * 9;
+#pragma unroll
+    for (int p = 0; p < 3; ++p) {
+      double ar = 0.0, ai = 0.0;
+#pragma unroll
+      for (int q = 0; q < 3; ++q) {
+        const double2 yy = y[p * 3 + q];
+        ar = fma(yy.x, dr[q], fma(-yy.y, di[q], ar));
+        ai = fma(yy.x, di[q], fma(yy.y, dr[q], ai));
+      }
+      jg[3 * k + p] = make_double2(ar, ai);
+    }
+  }
+}
 
 __global__ void __launch_bounds__(32 * CHECK_WARPS)
 k_check(const double2* __restrict__ V, const double2* __restrict__ Sw,
         const double2* __restrict__ Sd, const uint8_t* __restrict__ conv, int B, int n,
         const int32_t* __restrict__ bptr, const int32_t* __restrict__ bcol,
         const double2* __restrict__ bval, double2 vs0, double2 vs1, double2 vs2,
-        unsigned long long* __restrict__ mmax, int ny) {
+        unsigned long long* __restrict__ mmax, int ny, const double2* __restrict__ J,
+        const int32_t* __restrict__ br, int nbr) {
   __shared__ double red[CHECK_WARPS][32];
   const int lane = threadIdx.x, ty = threadIdx.y;
   const int bx = blockIdx.x / ny, by = blockIdx.x % ny;   // scenario group, bus stride
@@ -1155,9 +1232,10 @@ k_check(const double2* __restrict__ V, const double2* __restrict__ Sw,
   const double2 vs[3] = {vs0, vs1, vs2};
   double worst = 0.0;   // max |dS|^2
   const int nb = n / 3;
+  const double2* jg = J ? J + (int64_t)(b < B ? b : B - 1) * nbr * 3 : nullptr;
   for (int a = by * CHECK_WARPS + ty; a < nb; a += ny * CHECK_WARPS)
     worst = fmax(worst, check_bus_f64(V + row, Sw ? Sw + row : nullptr, Sd ? Sd + row : nullptr,
-                                      a, nb, bptr, bcol, bval, vs));
+                                      a, nb, bptr, bcol, bval, vs, jg, br, nbr));
   red[ty][lane] = worst;
   __syncthreads();
   if (ty == 0 && live) {
@@ -1628,6 +1706,16 @@ zbus_status group_build(Group* g, const std::vector<zbus_network>& nets,
   s.dec_blocks = dec;
   s.tree_groups = tb;
   s.tiles = g->d_tiles;
+  {
+    // double-float state of every slot (hi and lo, 16 B per unknown): streamed
+    // when it is more than a third of L2
+    size_t state = 0;
+    for (size_t k = 0; k < nets.size(); ++k)
+      state += (size_t)g->h_items[k].Bp * (size_t)g->h_items[k].n * 16;
+    int l2 = 0;
+    ZB_CUDA(cudaDeviceGetAttribute(&l2, cudaDevAttrL2CacheSize, dev));
+    s.stream_state = state > (size_t)l2 / 3 ? 1 : 0;
+  }
   ZB_CUDA(cudaMemcpyAsync(g->d_items, g->h_items.data(), nets.size() * sizeof(ItemDesc),
                           cudaMemcpyHostToDevice, st));
   ZB_CUDA(cudaMemcpyAsync(g->d_state, &s, sizeof(s), cudaMemcpyHostToDevice, st));
@@ -1842,10 +1930,18 @@ zbus_status group_collect(Group* g, int k, int64_t s0, int64_t B, double* V_out,
       g->d_items, k, (int)s0, (int)B, (double2*)V_out, iters, converged, mmax);
   int gx = 0, ny = 0;
   check_grid(B, net->n, g->num_sms, &gx, &ny);
+  // branch terms once per line, in the FP64 scratch (free between sweeps)
+  double2* J = nullptr;
+  if (net->nbr > 0 && (size_t)B * net->nbr * 3 * sizeof(double2) <= net->ws.iop_bytes) {
+    J = reinterpret_cast<double2*>(net->ws.Iop);
+    k_branch_f64<<<(unsigned)((int64_t)gx * ny), dim3(32, CHECK_WARPS), 0, st>>>(
+        (const double2*)V_out, converged, (int)B, net->n, net->br_tab, net->nbr, net->bsr_val, J,
+        ny);
+  }
   k_check<<<(unsigned)((int64_t)gx * ny), dim3(32, CHECK_WARPS), 0, st>>>(
       (const double2*)V_out, (const double2*)S_wye, (const double2*)S_delta, converged, (int)B,
       net->n, net->bsr_ptr, net->bsr_col, net->bsr_val, net->v_slack[0], net->v_slack[1],
-      net->v_slack[2], mmax, ny);
+      net->v_slack[2], mmax, ny, J, net->bsr_br, net->nbr);
   if (max_corr <= 0) {
     k_check_finish<<<(unsigned)((B + 255) / 256), 256, 0, st>>>(mmax, converged, (int)B, mtol,
                                                                  mm_out);

@@ -73,6 +73,8 @@ struct GroupState {
   int32_t tree_groups;      // tree-sweep blocks over all items
   int32_t tree_done;        // tree-sweep blocks finished in this sweep
   int32_t tree_active;      // slots still active after this sweep (tree blocks' sum)
+  int32_t stream_state;     // 1: the slot state exceeds what L2 keeps between kernels, so
+                            // the contraction epilogue streams it (evict-first)
   int32_t* hist;            // profile mode: active slots of sweep k
   int32_t hist_n;
   uint64_t* tiles;          // (item << 32) | (mt << 16) | nt of every active tile

@@ -7,6 +7,7 @@
 #include <algorithm>
 #include <cmath>
 #include <complex>
+#include <cstring>
 #include <numeric>
 
 #include "zbus_internal.cuh"
@@ -220,6 +221,50 @@ bool inv3(const double2* a, double2* out) {
     for (int j = 0; j < m; ++j)
       out[3 * ph[i] + ph[j]] = make_double2(g[i][m + j].real(), g[i][m + j].imag());
   return true;
+}
+
+// Branches of the branch form, for the FP64 mismatch test that forms each
+// line's term once: where every neighbour block has an identical mirror
+// (Y_ab == Y_ba, bit for bit: lines with symmetric series matrices), the term
+// of bus b in row a is the negative of that of bus a in row b,
+//   Y_ba (v_a - v_b) = -Y_ab (v_b - v_a).
+// Branch k = (a, b, block of Y_ab) with a < b; br_of[t] = k for the block
+// (a, b) and -(k + 1) for its mirror (b, a); 0 for slack and shunt blocks.
+// Leaves net->nbr = 0 when a block has no identical mirror.
+zbus_status build_branches(zbus_network net, const std::vector<int32_t>& bp,
+                           const std::vector<int32_t>& bc, const std::vector<double2>& bv,
+                           cudaStream_t st) {
+  const int nb = net->nbus;
+  std::vector<int32_t> br_of(bc.size(), 0);
+  std::vector<int4> tab;
+  for (int a = 0; a < nb; ++a)
+    for (int t = bp[a]; t < bp[a + 1]; ++t) {
+      const int b = bc[t];
+      if (b < 0) continue;
+      int u = -1;
+      for (int x = bp[b]; x < bp[b + 1]; ++x)
+        if (bc[x] == a) u = x;
+      if (u < 0) return ZBUS_OK;
+      if (std::memcmp(&bv[(size_t)t * 9], &bv[(size_t)u * 9], 9 * sizeof(double2)) != 0)
+        return ZBUS_OK;
+      if (b > a) {
+        br_of[t] = (int32_t)tab.size();
+        tab.push_back(make_int4(a, b, t, 0));
+      }
+    }
+  // mirrors: the block (b, a) with b > a refers to branch (a, b)
+  for (int b = 0; b < nb; ++b)
+    for (int t = bp[b]; t < bp[b + 1]; ++t) {
+      const int a = bc[t];
+      if (a < 0 || a > b) continue;
+      for (int x = bp[a]; x < bp[a + 1]; ++x)
+        if (bc[x] == b) br_of[t] = -(br_of[x] + 1);
+    }
+  if (tab.empty()) return ZBUS_OK;
+  ZB_CHECK(upload(&net->br_tab, tab, st));
+  ZB_CHECK(upload(&net->bsr_br, br_of, st));
+  net->nbr = (int)tab.size();
+  return ZBUS_OK;
 }
 
 // Radial structure of the branch form, when the buses form a tree hanging off
@@ -470,6 +515,7 @@ zbus_status build_network(zbus_network net, int32_t n_total, int64_t nnz, const 
     ZB_CHECK(upload(&net->bsr_ptr, bp, st));
     ZB_CHECK(upload(&net->bsr_col, bc, st));
     ZB_CHECK(upload(&net->bsr_val, bv, st));
+    ZB_CHECK(build_branches(net, bp, bc, bv, st));
     ZB_CHECK(build_tree(net, bp, bc, bv, st));
   }
 

@@ -147,6 +147,7 @@ struct Workspace {
   int32_t* list = nullptr;
   double* part = nullptr;    // [cap_B][max N-tiles][2]
   double* Iop = nullptr;     // FP64: 3 x [cap_B][n_pad]
+  size_t iop_bytes = 0;      // bytes of that region
   void* R = nullptr;         // mixed: [cap_B][K_pad] fp16 / bf16 residual rows
   float* rinv = nullptr;     // mixed: [cap_B] inverse residual scales
   double* mm = nullptr;      // mixed: [cap_B] final FP64 mismatch (-1 if not checked)
@@ -242,6 +243,12 @@ struct zbus_network_s {
   double2* bsr_val = nullptr;   // [nblk][3][3] row-major complex
   int64_t nblk = 0;
   float4* bsr_df = nullptr;     // [nblk][9] double-float copy (mixed sweeps)
+  // branches (pairs of identical mirror blocks), for the FP64 test that forms
+  // each line's term once: (a, b, block of Y_ab) with a < b, and per block
+  // its branch (k, or -(k + 1) for the mirror); nbr = 0 where not available
+  int nbr = 0;
+  int4* br_tab = nullptr;       // [nbr]
+  int32_t* bsr_br = nullptr;    // [nblk]
   // radial structure (buses form a tree hanging off the slack, reciprocal
   // branches), for the tree-sweep application of Z: breadth-first positions,
   // levels, children ranges, and the inverse series block of each bus's

@@ -236,6 +236,35 @@ def test_final_mismatch_test_agrees_with_oracle(mode):
     np.testing.assert_array_equal(cv2.cpu().numpy()[clear], want[clear])
 
 
+@pytest.mark.parametrize("mode", ["fp16_scaled", "bf16x2"])
+def test_final_mismatch_test_without_identical_mirror_blocks(mode):
+    """The FP64 test on a network whose line blocks are not all mirrored
+    (Y_ab != Y_ba for one line, as with a non-reciprocal element): each block
+    product is formed at its own bus (the line-once form needs identical
+    mirrors), and the test still decides like the oracle's mismatch."""
+    f = F.make_feeder(90, 31, delta_frac=0.5)
+    r0, c0 = next((r, c) for r, c in zip(f.Y_row, f.Y_col)
+                  if r // 3 != c // 3 and min(r, c) >= 3)
+    row = np.append(f.Y_row, r0).astype(np.int32)
+    col = np.append(f.Y_col, c0).astype(np.int32)
+    val = np.append(f.Y_val, 0.5 + 0.25j)
+    Sw, Sd = F.make_scenarios(f, 64, 0.8, 1.2)
+    net = zbus.Network(f.n_total, row, col, val, f.slack_idx, f.v_slack)
+    V, it, cv = net.solve(dev(Sw), dev(Sd), tol=1e-7, precision=mode, mismatch_tol=1.0,
+                          max_correction=0)
+    ref = O.solve_coo(f.n_total, row, col, val, f.slack_idx, f.v_slack, Sw, Sd, tol=1e-12,
+                      max_iter=100)
+    assert ref["converged"].all() and cv.cpu().numpy().all()
+    assert np.abs(V.cpu().numpy() - ref["V"]).max() <= 1e-6
+    mm = O.power_mismatch(ref["Y_LL"], ref["Y_Ls"], f.v_slack, V.cpu().numpy(), Sw, Sd)
+    thr = float(np.sqrt(mm.min() * mm.max()))
+    V2, it2, cv2 = net.solve(dev(Sw), dev(Sd), tol=1e-7, precision=mode, mismatch_tol=thr,
+                             max_correction=0)
+    assert torch.equal(V2, V)
+    clear = np.abs(mm / thr - 1.0) > 1e-3
+    np.testing.assert_array_equal(cv2.cpu().numpy()[clear], (mm <= thr).astype(np.uint8)[clear])
+
+
 @pytest.mark.parametrize("mode", MODES)
 def test_fp64_correction_sweeps(mode):
     """The final FP64 correction of the mixed forms.
