@@ -929,6 +929,7 @@ def run_serve(args, compact=False):
         return {"requests": len(res), "scenarios": scen, "converged": good,
                 "throughput": good / span, "p50_ms": float(np.percentile(lat, 50) * 1e3),
                 "p99_ms": float(np.percentile(lat, 99) * 1e3), "wall_s": wall,
+                "operands_formed": int(sum(r.get("operands_formed", 0) for r in res)),
                 "all_ok": all(r["status"] == 0 for r in res)}
 
     zbus.serve(nets, requests(np.zeros(32)), keep_results=False, precision=prec)   # warm-up
@@ -948,6 +949,7 @@ def run_serve(args, compact=False):
                 "latency_ms": {k: {"p50": v["p50_ms"], "p99": v["p99_ms"]}
                                for k, v in runs.items()},
                 "throughput": {k: v["throughput"] for k, v in runs.items()},
+                "operands_formed": {k: v["operands_formed"] for k, v in runs.items()},
                 "all_ok": all(v["all_ok"] for v in runs.values())}
     out = {"metric": METRIC, "value": sat["throughput"], "unit": UNIT, "n_gpus": 1,
            "steps": 1, "warmup": 1, "ms_per_step": sat["wall_s"] * 1e3,

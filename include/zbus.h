@@ -308,7 +308,8 @@ typedef struct {
                               never fit (B above the slot capacity, bad feeder) */
   int32_t n_converged;     /* scenarios flagged converged (after the FP64 test) */
   int32_t max_iters;       /* largest iteration count of its scenarios */
-  int32_t reserved0;
+  int32_t operands_formed; /* 1: its admission formed the feeder's operands
+                              (a miss of the serving loop's operand cache) */
   double t_admit;          /* seconds on the serving clock */
   double t_done;           /* results complete on the device */
   const double* V;         /* device [B][n] results (V_out or the library buffer) */
@@ -352,16 +353,38 @@ typedef struct {
  * caller, sink call).
  * Requests that arrive while others are on the GPU join at the next sweep
  * (continuous batching); per-scenario arithmetic does not depend on the mix,
- * so a result is the same alone and in the mix.  Slot capacity per feeder is
- * the largest multiple of 128 (<= max_slots) whose state fits the budget
- * left after the pool's operands; ZBUS_ERR_OOM if not even 128 fit.  The
- * pool's operands stay resident; each feeder keeps its last converged
- * voltage for warm starts.  Runs on the calling thread; the callbacks run on
- * it too.
+ * so a result is the same alone and in the mix.
+ *
+ * HBM budget (hbm_budget_bytes): every feeder gets the same slot capacity,
+ * the largest multiple of 128 (<= max_slots) whose state, over all feeders,
+ * leaves room for the largest feeder's operands while they are formed
+ * (ZBUS_ERR_OOM if not even 128 do).  The rest of the budget is an operand
+ * cache (the Z_LL cache): a resident feeder holds its tensor-core Z and the
+ * FP64 3M copies of Z (for the correction sweeps); its complex FP64 Z is
+ * released once those are formed.  At the start the pool's feeders are made
+ * resident in pool order while they fit; the others release their dense
+ * operands.  A request for a feeder that is not resident evicts idle
+ * feeders (no request in flight), least recently used first, until the
+ * feeder's operands can be formed on the device (Z_LL^-1 again by
+ * Gauss-Jordan, then its copies), and waits while they cannot; requests of
+ * other feeders are admitted meanwhile.  Released operands of a pool network
+ * are formed again on demand by any later call that needs them.  Each feeder
+ * keeps its last converged voltage for warm starts.  Runs on the calling
+ * thread; the callbacks run on it too.
  */
 zbus_status zbus_serve(const zbus_serve_config* cfg, zbus_network* pool, int32_t n_pool,
                        zbus_request_source src, zbus_completion_sink sink, void* user,
                        void* cuda_stream);
+
+/*
+ * zbus_serve_footprint -- what zbus_serve counts against its HBM budget for
+ * one pool network in a precision: the operand bytes it holds while resident
+ * in the operand cache, the extra bytes a formation needs while it runs, and
+ * the bytes of one scenario slot.  Any output may be NULL.  Host only.
+ * Project-written sizing query.
+ */
+zbus_status zbus_serve_footprint(zbus_network net, int32_t precision, uint64_t* operand_bytes,
+                                 uint64_t* formation_bytes, uint64_t* slot_bytes);
 
 /*
  * zbus_power_mismatch -- per-scenario FP64 power mismatch of given voltages,

@@ -494,6 +494,7 @@ int grid_1d(int64_t tot, int cap) {
 // Z^T operands, the zero no-load term, and per-scenario scratch for B.
 zbus_status ensure_adjoint(zbus_network net, int64_t B, cudaStream_t st) {
   const int np = net->n_pad;
+  ZB_CHECK(ensure_3m(net, st));
   if (!net->ZrT) {
     const size_t bytes = (size_t)np * np * sizeof(double);
     ZB_CUDA(cudaMalloc((void**)&net->ZrT, bytes));

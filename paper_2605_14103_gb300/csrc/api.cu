@@ -38,6 +38,8 @@ bool known_precision(int32_t p) {
          p == ZBUS_TREE_SWEEP;
 }
 
+}  // namespace
+
 void drop_graphs(zbus_network net) {
   for (auto& g : net->graphs) {
     if (g.exec) cudaGraphExecDestroy(g.exec);
@@ -49,6 +51,8 @@ void drop_graphs(zbus_network net) {
   net->corr_exec = nullptr;
   net->corr_graph = nullptr;
 }
+
+namespace {
 
 int max_ntn(const zbus_network net) {
   // the FP64 contraction tiles outputs by 48, the tensor-core one by >= 64 reals
@@ -259,7 +263,9 @@ bool group_current(const Group* g, const std::vector<zbus_network>& nets,
   if (!g || g->precision != precision || g->nets != nets) return false;
   if (g->tune_gen != tune_generation()) return false;
   for (size_t k = 0; k < nets.size(); ++k)
-    if (g->ws_gen[k] != nets[k]->ws.gen || g->h_items[k].Bp < Bs[k]) return false;
+    if (g->ws_gen[k] != nets[k]->ws.gen || g->op_gen[k] != nets[k]->op_gen ||
+        g->h_items[k].Bp < Bs[k])
+      return false;
   return true;
 }
 
@@ -523,6 +529,7 @@ zbus_status zbus_network_get_z(zbus_network net, double* Z_out, double* w_out, v
   if (!net) return fail(ZBUS_ERR_ARG, "network is NULL");
   ZB_CHECK(check_device(net));
   cudaStream_t st = (cudaStream_t)cuda_stream;
+  ZB_CHECK(ensure_z(net, st));
   if (net->phased) {   // the caller's unknowns only
     if (Z_out) ZB_CHECK(phased_z(net, Z_out, st));
     if (w_out) ZB_CHECK(phased_out(net, 1, (const double*)net->w, w_out, st));
@@ -550,6 +557,7 @@ zbus_status zbus_network_reserve(zbus_network net, int64_t B, int32_t precision)
   if (!known_precision(precision)) return fail(ZBUS_ERR_ARG, "unknown precision");
   ZB_CHECK(check_device(net));
   ZB_CHECK(ensure_workspace(net, B));
+  ZB_CHECK(ensure_3m(net, nullptr));
   if (precision == ZBUS_TREE_SWEEP) ZB_CHECK(prepare_tree(net, nullptr));
   else if (precision != ZBUS_FP64) ZB_CHECK(prepare_mixed(net, precision, nullptr));
   return ZBUS_OK;
@@ -566,6 +574,9 @@ zbus_status solve_device(zbus_network net, int64_t B, const double* S_wye, const
                          const zbus_solve_opts& o, double* V_out, int32_t* iters,
                          uint8_t* converged, cudaStream_t st) {
   ZB_CHECK(ensure_workspace(net, B));
+  // the FP64 operands (the plain method's contraction, the mixed forms'
+  // correction sweeps), formed again if a serving cache released them
+  ZB_CHECK(ensure_3m(net, st));
   if (o.precision != ZBUS_FP64) {
     // mixed precision: a group of one feeder
     if (!net->group1) net->group1 = new Group();

@@ -326,8 +326,8 @@ k_residual_group(GroupState* __restrict__ gs, const ItemDesc* __restrict__ items
 // while the epilogue streams the double-float state (16 B per unknown and
 // slot each way); Z's tiles are loaded with an evict-last policy and, where
 // the state is larger than L2 keeps between kernels (gs->stream_state), the
-// state with streaming (evict-first) accesses, so Z stays in L2.  A state
-// that fits is left to the default policy: the next residual re-reads it.
+// state with an evict-first policy, so Z stays in L2.  A state that fits is
+// left to the normal policy: the next residual re-reads it.
 //
 // Giving up: every pipeline wait is bounded (tc_wait_ns()).  A role whose
 // wait runs out records its code in gs->err and stops issuing; then, before
@@ -486,7 +486,8 @@ k_contract_group(GroupState* __restrict__ gs, const ItemDesc* __restrict__ items
     const int q = warp & 3;
     const int row = q * 32 + lane;
     const bool summag = gs->rule == ZBUS_CONV_SUMMAG;
-    const bool stream = gs->stream_state != 0;
+    // evict-first for a state larger than L2 keeps, else the default
+    const uint64_t spol = gs->stream_state != 0 ? policy_evict_first() : policy_evict_normal();
     int i = 0;
     for (int g = blockIdx.x; g < total; g += gridDim.x, ++i) {
       const uint64_t e = tiles[g];
@@ -520,8 +521,8 @@ k_contract_group(GroupState* __restrict__ gs, const ItemDesc* __restrict__ items
           const int oi = i0 + t;
           const bool in = valid && oi < n;
           const int64_t gi = (int64_t)(in ? oi : 0) * Bp;
-          h[t] = in ? (stream ? __ldcs(Vh + gi) : Vh[gi]) : make_float2(0.f, 0.f);
-          l[t] = in ? (stream ? __ldcs(Vl + gi) : Vl[gi]) : make_float2(0.f, 0.f);
+          h[t] = in ? ld_f2_hint(Vh + gi, spol) : make_float2(0.f, 0.f);
+          l[t] = in ? ld_f2_hint(Vl + gi, spol) : make_float2(0.f, 0.f);
           zs[t] = in ? zinv[oi] : 0.f;
         }
         float v[32];
@@ -546,13 +547,8 @@ k_contract_group(GroupState* __restrict__ gs, const ItemDesc* __restrict__ items
               fast_two_sum(sr, __fadd_rn(er, l[t].x), nh.x, nl.x);
               fast_two_sum(si, __fadd_rn(ei, l[t].y), nh.y, nl.y);
               const int64_t gi = (int64_t)oi * Bp;
-              if (stream) {
-                __stcs(Vh + gi, nh);
-                __stcs(Vl + gi, nl);
-              } else {
-                Vh[gi] = nh;
-                Vl[gi] = nl;
-              }
+              st_f2_hint(Vh + gi, nh, spol);
+              st_f2_hint(Vl + gi, nl, spol);
               float step = sqrtf(__fmaf_rn(dr, dr, di * di));
               if (step != step) step = __int_as_float(0x7f800000);
               dmax = fmaxf(dmax, step);
@@ -1553,7 +1549,8 @@ void group_free(Group* g) {
 }
 
 zbus_status group_build(Group* g, const std::vector<zbus_network>& nets,
-                        const std::vector<int64_t>& Bs, int32_t precision, cudaStream_t st) {
+                        const std::vector<int64_t>& Bs, int32_t precision, cudaStream_t st,
+                        bool lazy_ops) {
   group_free(g);
   g->nets = nets;
   g->Bs = Bs;
@@ -1562,8 +1559,15 @@ zbus_status group_build(Group* g, const std::vector<zbus_network>& nets,
   const bool tree = precision == ZBUS_TREE_SWEEP;
   int max_n = 0;
   int64_t total_B = 0;
+  const int pi = precision == ZBUS_MIXED_BF16X2 ? 1 : 0;
   for (size_t k = 0; k < nets.size(); ++k) {
-    ZB_CHECK(tree ? prepare_tree(nets[k], st) : prepare_mixed(nets[k], precision, st));
+    // the double-float branch blocks, slack and no-load voltages every item's
+    // residual and admission read (also for an item whose Z comes later)
+    ZB_CHECK(prepare_df(nets[k], st));
+    if (tree) ZB_CHECK(prepare_tree(nets[k], st));
+    else if (!lazy_ops || nets[k]->mixed[pi].ready) ZB_CHECK(prepare_mixed(nets[k], precision, st));
+    // the FP64 correction sweeps use the FP64 Z (formed again if released)
+    if (!lazy_ops) ZB_CHECK(ensure_3m(nets[k], st));
     ZB_CHECK(ensure_workspace(nets[k], Bs[k]));
     max_n = std::max(max_n, nets[k]->n);
     total_B += Bs[k];
@@ -1585,6 +1589,7 @@ zbus_status group_build(Group* g, const std::vector<zbus_network>& nets,
 
   g->h_items.resize(nets.size());
   g->ws_gen.resize(nets.size());
+  g->op_gen.resize(nets.size());
   int res = 0, dec = 0, mt = 0, tiles = 0, tb = 0;
   g->tree_smem = 0;
   // tree-sweep blocks of 32 slots: 16 warps per block while the blocks are
@@ -1624,10 +1629,11 @@ zbus_status group_build(Group* g, const std::vector<zbus_network>& nets,
       tb += d.Bp / 32;
       g->tree_smem = std::max(g->tree_smem, tree_table_bytes(net->nbus));
     } else {
+      // the operand layout (K_pad, N_pad) also for an item formed later
       d.zinv = op.zinv;
-      d.K_pad = op.K_pad;
-      d.N_pad = op.N_pad;
-      d.ntn = op.N_pad / g->BN;
+      d.K_pad = round_up(2 * net->n, 64);
+      d.N_pad = round_up(2 * net->n, 256);
+      d.ntn = d.N_pad / g->BN;
     }
     d.Vh = ws.Vh;
     d.Vl = ws.Vl;
@@ -1651,6 +1657,7 @@ zbus_status group_build(Group* g, const std::vector<zbus_network>& nets,
     mt += d.Bp / 128;
     tiles += (d.Bp / 128) * d.ntn;
     g->ws_gen[k] = ws.gen;
+    g->op_gen[k] = net->op_gen;
   }
   g->res_blocks = res;
   g->dec_blocks = dec;
@@ -1688,11 +1695,13 @@ zbus_status group_build(Group* g, const std::vector<zbus_network>& nets,
   g->d_tmZ1 = g->d_tmZ0 + nets.size();
 
   std::vector<CUtensorMap> maps(3 * nets.size());
+  std::memset(maps.data(), 0, maps.size() * sizeof(CUtensorMap));
   const bool bf = precision == ZBUS_MIXED_BF16X2;
   for (size_t k = 0; k < nets.size() && !tree; ++k) {
     const MixedOperands& op = nets[k]->mixed[bf ? 1 : 0];
     const ItemDesc& d = g->h_items[k];
     ZB_CHECK(make_tmap_2d(&maps[k], d.R, bf, (uint64_t)d.K_pad, (uint64_t)d.Bp, BK, BM));
+    if (!op.ready) continue;   // lazy: encoded by group_refresh_item
     ZB_CHECK(make_tmap_2d(&maps[nets.size() + k], op.Z0, bf, (uint64_t)op.K_pad,
                           (uint64_t)op.N_pad, BK, g->BN));
     ZB_CHECK(make_tmap_2d(&maps[2 * nets.size() + k], bf ? op.Z1 : op.Z0, bf, (uint64_t)op.K_pad,
@@ -1721,6 +1730,31 @@ zbus_status group_build(Group* g, const std::vector<zbus_network>& nets,
   ZB_CUDA(cudaMemcpyAsync(g->d_state, &s, sizeof(s), cudaMemcpyHostToDevice, st));
   ZB_CUDA(cudaMemcpyAsync(g->d_tmR, maps.data(), maps.size() * sizeof(CUtensorMap),
                           cudaMemcpyHostToDevice, st));
+  ZB_CUDA(cudaStreamSynchronize(st));
+  return ZBUS_OK;
+}
+
+zbus_status group_refresh_item(Group* g, int k, cudaStream_t st) {
+  zbus_network net = g->nets[k];
+  ItemDesc& d = g->h_items[k];
+  g->op_gen[k] = net->op_gen;
+  if (!net->bsr_df || d.bsr_df != net->bsr_df || !net->w_df)
+    return fail(ZBUS_ERR_DEVICE, "group item without its double-float blocks");
+  if (g->precision == ZBUS_TREE_SWEEP) return ZBUS_OK;
+  const bool bf = g->precision == ZBUS_MIXED_BF16X2;
+  const MixedOperands& op = net->mixed[bf ? 1 : 0];
+  if (!op.ready || !op.zinv || !op.Z0 || (bf && !op.Z1))
+    return fail(ZBUS_ERR_DEVICE, "group item refreshed without its operands");
+  if (op.K_pad != d.K_pad || op.N_pad != d.N_pad)
+    return fail(ZBUS_ERR_DEVICE, "group item operand layout differs");
+  d.zinv = op.zinv;
+  CUtensorMap m[2];
+  ZB_CHECK(make_tmap_2d(&m[0], op.Z0, bf, (uint64_t)op.K_pad, (uint64_t)op.N_pad, BK, g->BN));
+  ZB_CHECK(make_tmap_2d(&m[1], bf ? op.Z1 : op.Z0, bf, (uint64_t)op.K_pad, (uint64_t)op.N_pad, BK,
+                        g->BN));
+  ZB_CUDA(cudaMemcpyAsync(g->d_items + k, &d, sizeof(ItemDesc), cudaMemcpyHostToDevice, st));
+  ZB_CUDA(cudaMemcpyAsync(g->d_tmZ0 + k, &m[0], sizeof(CUtensorMap), cudaMemcpyHostToDevice, st));
+  ZB_CUDA(cudaMemcpyAsync(g->d_tmZ1 + k, &m[1], sizeof(CUtensorMap), cudaMemcpyHostToDevice, st));
   ZB_CUDA(cudaStreamSynchronize(st));
   return ZBUS_OK;
 }

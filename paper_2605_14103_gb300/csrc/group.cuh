@@ -107,6 +107,7 @@ struct Group {
   CUtensorMap* d_tmZ1 = nullptr;
   std::vector<ItemDesc> h_items;
   std::vector<uint64_t> ws_gen;  // workspace generation of each item when built
+  std::vector<uint64_t> op_gen;  // operand generation of each item when built
   uint64_t tune_gen = 0;         // tile table generation when built
   cudaStream_t cap_stream = nullptr;
   cudaGraph_t graph = nullptr;
@@ -118,8 +119,15 @@ struct Group {
   int prof_sweeps = 0;
 };
 
+// lazy_ops: items whose tensor-core operands are not formed are built without
+// them (the serving cache forms them before the item's first admission and
+// then calls group_refresh_item).
 zbus_status group_build(Group* g, const std::vector<zbus_network>& nets,
-                        const std::vector<int64_t>& Bs, int32_t precision, cudaStream_t st);
+                        const std::vector<int64_t>& Bs, int32_t precision, cudaStream_t st,
+                        bool lazy_ops = false);
+// Item k's operand addresses (tensor maps, row scales) after its operands
+// were formed again.
+zbus_status group_refresh_item(Group* g, int k, cudaStream_t st);
 void group_free(Group* g);
 // Run start for item k: slots [s0, s0 + B) from v^0 (V0 or w) and the loads
 // (FP64 [B][n]); admitted slots become active.

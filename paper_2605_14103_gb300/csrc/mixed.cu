@@ -119,10 +119,9 @@ zbus_status make_tmap_2d(CUtensorMap* map, const void* base, bool bf16, uint64_t
   return ZBUS_OK;
 }
 
-namespace {
-
 // Double-float copies of the branch-form blocks, Y_Ls v_s and w, shared by
-// the defect forms.
+// the defect forms (independent of Z: kept when the dense operands are
+// released).
 zbus_status prepare_df(zbus_network net, cudaStream_t st) {
   if (!net->bsr_df) {
     const int64_t m = std::max<int64_t>(1, net->nblk * 9);
@@ -138,8 +137,6 @@ zbus_status prepare_df(zbus_network net, cudaStream_t st) {
   }
   return ZBUS_OK;
 }
-
-}  // namespace
 
 zbus_status prepare_tree(zbus_network net, cudaStream_t st) {
   if (!net->bus_aligned)
@@ -163,6 +160,7 @@ zbus_status prepare_mixed(zbus_network net, int32_t precision, cudaStream_t st) 
   if (net->n > 16383)
     return fail(ZBUS_ERR_UNSUPPORTED, "mixed modes support n <= 16383 unknowns");
   ZB_CHECK(prepare_df(net, st));
+  ZB_CHECK(ensure_z(net, st));
   const bool bf = precision == ZBUS_MIXED_BF16X2;
   op.bf16 = bf;
   op.zparts = bf ? 2 : 1;
@@ -182,6 +180,16 @@ zbus_status prepare_mixed(zbus_network net, int32_t precision, cudaStream_t st) 
   ZB_CUDA(cudaStreamSynchronize(st));
   op.ready = true;
   return ZBUS_OK;
+}
+
+void release_mixed_ops(zbus_network net) {
+  for (auto& op : net->mixed) {
+    cudaFree(op.Z0);
+    cudaFree(op.Z1);
+    cudaFree(op.zinv);
+    op = MixedOperands();
+  }
+  net->op_gen += 1;
 }
 
 void free_mixed(zbus_network net) {

@@ -78,6 +78,9 @@ extern "C" zbus_status zbus_solve_noalloc(zbus_network net, int64_t B, const dou
     return fail(ZBUS_ERR_ARG, "unknown convergence rule");
   if (net->phased)
     return fail(ZBUS_ERR_UNSUPPORTED, "the allocation-free solve takes three-phase networks");
+  if (!net->Zr)   // released by a serving loop: forming it again would allocate
+    return fail(ZBUS_ERR_UNSUPPORTED,
+                "the network's FP64 operands were released; zbus_network_reserve forms them");
   if (B == 0) return ZBUS_OK;
   if (!V_out || !iters || !converged) return fail(ZBUS_ERR_ARG, "an output pointer is NULL");
   if (S_delta && !net->bus_aligned)

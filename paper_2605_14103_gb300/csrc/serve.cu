@@ -16,21 +16,56 @@ double clock_s(std::chrono::steady_clock::time_point t0) {
   return std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
 }
 
-// Device bytes of the operands a network keeps resident for mixed solves.
-size_t operand_bytes(zbus_network net) {
-  const size_t n = (size_t)net->n, np = (size_t)net->n_pad;
-  size_t b = n * n * 16 + 3 * np * np * 8 + n * 48;                  // Z, Zr/Zi/Zs, w, ys
-  b += (size_t)net->nnz_ll * 20 + (size_t)net->nblk * (144 + 144);  // CSR, blocks (FP64, df)
-  for (const auto& op : net->mixed)
-    if (op.ready) b += (size_t)op.N_pad * op.K_pad * 2 * op.zparts;
-  if (net->radial) b += (size_t)net->nbus * (16 + 4 + 72 + 4) + 4 * (size_t)(net->depth + 1);
+// Device bytes of a feeder's operands while it is resident in the serving
+// cache: the tensor-core Z (mixed forms) and the FP64 3M copies (the
+// correction sweeps).  The complex FP64 Z is released once those are formed.
+size_t cache_bytes(zbus_network net, int32_t precision) {
+  const size_t np = (size_t)net->n_pad;
+  size_t b = 3 * np * np * sizeof(double);
+  if (precision != ZBUS_TREE_SWEEP) {
+    const size_t K = (size_t)round_up(2 * net->n, 64), N = (size_t)round_up(2 * net->n, 256);
+    b += N * K * 2 * (precision == ZBUS_MIXED_BF16X2 ? 2 : 1) + N / 2 * sizeof(float);
+  }
   return b;
+}
+
+// Bytes a formation needs on top of cache_bytes while it runs: the complex Z
+// and the elimination's scratch.
+size_t form_extra(zbus_network net) {
+  const size_t n = (size_t)net->n;
+  return n * n * sizeof(double2) + n * 24;
+}
+
+// Device bytes per scenario slot: the workspace of both methods plus the
+// library result buffers.
+size_t slot_bytes(zbus_network net) {
+  const size_t n = (size_t)net->n;
+  return 40 * n + 24 * (size_t)net->n_pad + 4 * (size_t)round_up(2 * net->n, 64) +
+         64 * (size_t)(round_up(2 * net->n, 256) / 128 + 1) + 16 * n + 64;
+}
+
+// Forms a feeder's resident operands (the Gauss-Jordan inverse again if it
+// was released), then drops the complex Z.
+zbus_status cache_form(zbus_network net, int32_t precision, cudaStream_t st) {
+  ZB_CHECK(ensure_3m(net, st));
+  if (precision != ZBUS_TREE_SWEEP) ZB_CHECK(prepare_mixed(net, precision, st));
+  ZB_CUDA(cudaStreamSynchronize(st));
+  release_z(net);
+  return ZBUS_OK;
+}
+
+// Frees every dense operand of a feeder (no work of it may be in flight).
+void cache_evict(zbus_network net) {
+  release_mixed_ops(net);
+  release_3m(net);
+  release_z(net);
 }
 
 struct Inflight {
   zbus_request req;
   int64_t s0;
   double t_admit;
+  int32_t formed;   // its admission formed the feeder's operands (a cache miss)
 };
 
 struct Feeder {
@@ -59,6 +94,20 @@ int64_t first_fit(const std::vector<char>& used, int64_t B) {
 
 using namespace zbus;
 
+extern "C" zbus_status zbus_serve_footprint(zbus_network net, int32_t precision,
+                                            uint64_t* operand_bytes, uint64_t* formation_bytes,
+                                            uint64_t* slot_bytes_out) {
+  set_error("");
+  if (!net) return fail(ZBUS_ERR_ARG, "network is NULL");
+  if (precision != ZBUS_MIXED_FP16_SCALED && precision != ZBUS_MIXED_BF16X2 &&
+      precision != ZBUS_TREE_SWEEP)
+    return fail(ZBUS_ERR_ARG, "serving runs the mixed precisions");
+  if (operand_bytes) *operand_bytes = cache_bytes(net, precision);
+  if (formation_bytes) *formation_bytes = form_extra(net);
+  if (slot_bytes_out) *slot_bytes_out = slot_bytes(net);
+  return ZBUS_OK;
+}
+
 extern "C" zbus_status zbus_serve(const zbus_serve_config* cfg, zbus_network* pool,
                                   int32_t n_pool, zbus_request_source src,
                                   zbus_completion_sink sink, void* user, void* cuda_stream) {
@@ -82,34 +131,50 @@ extern "C" zbus_status zbus_serve(const zbus_serve_config* cfg, zbus_network* po
   cudaStream_t st = (cudaStream_t)cuda_stream;
   const double mtol = cfg->mismatch_tol > 0 ? cfg->mismatch_tol : 1e-6;
 
-  // operands first, then the slot capacity the budget leaves
-  size_t fixed = 0;
+  // Budget: the scenario slots of every feeder (one capacity for all, the
+  // largest multiple of 128 up to max_slots that leaves room for the largest
+  // feeder's operands while they are formed) plus the operand cache.
+  for (auto net : nets)
+    if (cfg->precision == ZBUS_TREE_SWEEP) ZB_CHECK(prepare_tree(net, st));
+  size_t per_slot = 0, peak_one = 0;
   for (auto net : nets) {
-    ZB_CHECK(cfg->precision == ZBUS_TREE_SWEEP ? prepare_tree(net, st)
-                                                : prepare_mixed(net, cfg->precision, st));
-    fixed += operand_bytes(net);
+    per_slot += slot_bytes(net);
+    peak_one = std::max(peak_one, cache_bytes(net, cfg->precision) + form_extra(net));
   }
-  if (fixed >= cfg->hbm_budget_bytes)
-    return fail(ZBUS_ERR_OOM, "the pool's operands alone exceed the HBM budget (" +
-                                  std::to_string(fixed) + " bytes)");
-  const size_t share = (cfg->hbm_budget_bytes - fixed) / nets.size();
-  std::vector<int64_t> caps(nets.size());
-  std::vector<Feeder> fd(nets.size());
+  const uint64_t budget = cfg->hbm_budget_bytes;
+  int64_t cap = (int64_t)std::max(128, cfg->max_slots) / 128 * 128;
+  while (cap >= 128 && (double)per_slot * cap + peak_one > (double)budget) cap -= 128;
+  if (cap < 128)
+    return fail(ZBUS_ERR_OOM, "the HBM budget cannot hold 128 slots per feeder plus the "
+                              "operands of the largest feeder (" +
+                                  std::to_string(per_slot * 128 + peak_one) + " bytes)");
+  const size_t ops_budget = budget - (size_t)per_slot * cap;
+  // the operand cache starts with the feeders that hold their operands (or
+  // the complex Z they are packed from) and fit, in pool order; the others
+  // give their dense operands up now and are formed on demand
+  std::vector<char> resident(nets.size(), 0);
+  std::vector<int64_t> last_use(nets.size(), -1);
+  size_t used = 0;
+  const int pi = cfg->precision == ZBUS_MIXED_BF16X2 ? 1 : 0;
   for (size_t k = 0; k < nets.size(); ++k) {
-    const size_t n = (size_t)nets[k]->n;
-    // per slot: workspace of both methods plus the library result buffers
-    const size_t per = 40 * n + 24 * (size_t)nets[k]->n_pad + 4 * (size_t)round_up(2 * nets[k]->n, 64) +
-                       64 * (size_t)(round_up(2 * nets[k]->n, 256) / 128 + 1) + 16 * n + 64;
-    int64_t cap = (int64_t)std::min<size_t>((size_t)std::max(128, cfg->max_slots), share / per);
-    cap = cap / 128 * 128;
-    if (cap < 128)
-      return fail(ZBUS_ERR_OOM, "the HBM budget leaves fewer than 128 slots for feeder " +
-                                    std::to_string(k));
-    caps[k] = cap;
+    const zbus_network net = nets[k];
+    const size_t cb = cache_bytes(net, cfg->precision);
+    const bool holds = (net->Zr || net->Z) &&
+                       (cfg->precision == ZBUS_TREE_SWEEP || net->mixed[pi].ready || net->Z);
+    ZB_CUDA(cudaStreamSynchronize(st));
+    if (holds && used + cb <= ops_budget) {
+      ZB_CHECK(cache_form(nets[k], cfg->precision, st));
+      resident[k] = 1;
+      used += cb;
+    } else {
+      cache_evict(nets[k]);
+    }
   }
+  std::vector<int64_t> caps(nets.size(), cap);
+  std::vector<Feeder> fd(nets.size());
   for (size_t k = 0; k < nets.size(); ++k) ZB_CHECK(ensure_workspace(nets[k], caps[k]));
   Group g;
-  zbus_status s = group_build(&g, nets, caps, cfg->precision, st);
+  zbus_status s = group_build(&g, nets, caps, cfg->precision, st, true);
   if (s != ZBUS_OK) {
     group_free(&g);
     return s;
@@ -168,7 +233,9 @@ extern "C" zbus_status zbus_serve(const zbus_serve_config* cfg, zbus_network* po
   int64_t live_total = 0;
   std::vector<int32_t> h_it;
   std::vector<uint8_t> h_cv;
+  int64_t n_pass = 0;
   while (true) {
+    ++n_pass;
     const double now = clock_s(t0);
     while (!ended) {
       zbus_request r;
@@ -206,11 +273,47 @@ extern "C" zbus_status zbus_serve(const zbus_serve_config* cfg, zbus_network* po
         ++it;
         continue;
       }
+      int32_t formed = 0;
+      if (!resident[r.feeder]) {
+        // operand cache miss: evict idle feeders, least recently used first,
+        // until this one can be formed; else it waits for one to go idle
+        const size_t cb = cache_bytes(nets[r.feeder], cfg->precision);
+        const size_t need = cb + form_extra(nets[r.feeder]);
+        while (used + need > ops_budget) {
+          int victim = -1;
+          for (size_t j = 0; j < nets.size(); ++j)
+            if (resident[j] && fd[j].live.empty() &&
+                (victim < 0 || last_use[j] < last_use[victim]))
+              victim = (int)j;
+          if (victim < 0) break;
+          SV_CUDA(cudaStreamSynchronize(st));
+          cache_evict(nets[victim]);
+          resident[victim] = 0;
+          used -= cache_bytes(nets[victim], cfg->precision);
+        }
+        if (used + need > ops_budget) {
+          ++it;
+          continue;
+        }
+        SV_CHECK(cache_form(nets[r.feeder], cfg->precision, st));
+        SV_CHECK(group_refresh_item(&g, r.feeder, st));
+        resident[r.feeder] = 1;
+        used += cb;
+        formed = 1;
+      }
+      last_use[r.feeder] = n_pass;
+      {
+        // every pointer the sweep reads for this item is in place
+        const ItemDesc& d = g.h_items[r.feeder];
+        const bool ok = d.bsr_df && nets[r.feeder]->w_df && nets[r.feeder]->Zr &&
+                        (cfg->precision == ZBUS_TREE_SWEEP || d.zinv);
+        if (!ok) SV_CHECK(fail(ZBUS_ERR_DEVICE, "serving: a feeder's operands are missing"));
+      }
       const bool warm = r.warm_start && f.warm_valid;
       SV_CHECK(group_admit(&g, r.feeder, s0, r.B, warm ? (const double*)f.warm : nullptr,
                            r.S_wye, r.S_delta, st, true));
       std::fill(f.used.begin() + s0, f.used.begin() + s0 + r.B, 1);
-      f.live.push_back(Inflight{r, s0, clock_s(t0)});
+      f.live.push_back(Inflight{r, s0, clock_s(t0), formed});
       live_total += 1;
       admitted = true;
       ++n_adm;
@@ -279,6 +382,7 @@ extern "C" zbus_status zbus_serve(const zbus_serve_config* cfg, zbus_network* po
       res.status = ZBUS_OK;
       res.t_admit = d.fl.t_admit;
       res.t_done = t_done;
+      res.operands_formed = d.fl.formed;
       res.V = d.V;
       res.iters = d.it;
       res.converged = d.cv;

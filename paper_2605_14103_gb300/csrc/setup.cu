@@ -27,6 +27,13 @@ __global__ void k_scatter(double2* A, int n, const int32_t* r, const int32_t* c,
     A[(int64_t)r[t] * n + c[t]] = v[t];
 }
 
+// The same from the device CSR of Y_LL (one thread per row).
+__global__ void k_scatter_csr(double2* A, int n, const int32_t* ptr, const int32_t* col,
+                              const double2* v) {
+  for (int r = blockIdx.x * blockDim.x + threadIdx.x; r < n; r += gridDim.x * blockDim.x)
+    for (int t = ptr[r]; t < ptr[r + 1]; ++t) A[(int64_t)r * n + col[t]] = v[t];
+}
+
 // ys[j] = sum_p Y_Ls[j][p] v_s[p] from the slack-column entries (row-sorted,
 // so each row's terms are summed in a fixed order by one thread).
 __global__ void k_slack_injection(double2* ys, int n, const int32_t* ptr, const int32_t* sp,
@@ -425,13 +432,12 @@ zbus_status build_network(zbus_network net, int32_t n_total, int64_t nnz, const 
     lp[i + 1] += lp[i];
     sp[i + 1] += sp[i];
   }
-  std::vector<int32_t> lr(lp[n]), lc(lp[n]), sc(sp[n]);
+  std::vector<int32_t> lc(lp[n]), sc(sp[n]);
   std::vector<double2> lv(lp[n]), sv(sp[n]);
   std::vector<int32_t> fl(lp.begin(), lp.end() - 1), fs(sp.begin(), sp.end() - 1);
   for (const Entry& x : u) {
     if (x.c >= 0) {
       int t = fl[x.r]++;
-      lr[t] = x.r;
       lc[t] = x.c;
       lv[t] = make_double2(x.re, x.im);
     } else {
@@ -519,26 +525,44 @@ zbus_status build_network(zbus_network net, int32_t n_total, int64_t nnz, const 
     ZB_CHECK(build_tree(net, bp, bc, bv, st));
   }
 
-  const size_t zb = (size_t)n * n * sizeof(double2);
-  const size_t pb = (size_t)net->n_pad * net->n_pad * sizeof(double);
-  ZB_CUDA(cudaMalloc((void**)&net->Z, zb));
   ZB_CUDA(cudaMalloc((void**)&net->w, n * sizeof(double2)));
   ZB_CUDA(cudaMalloc((void**)&net->ys, n * sizeof(double2)));
-  ZB_CUDA(cudaMalloc((void**)&net->Zr, pb));
-  ZB_CUDA(cudaMalloc((void**)&net->Zi, pb));
-  ZB_CUDA(cudaMalloc((void**)&net->Zs, pb));
   ZB_CHECK(upload(&net->csr_ptr, lp, st));
   ZB_CHECK(upload(&net->csr_col, lc, st));
   ZB_CHECK(upload(&net->csr_val, lv, st));
-
-  int32_t *d_lr = nullptr, *d_sp = nullptr, *d_sc = nullptr, *d_perm = nullptr, *d_info = nullptr;
-  double2 *d_sv = nullptr, *d_colk = nullptr;
+  int32_t *d_sp = nullptr, *d_sc = nullptr;
+  double2* d_sv = nullptr;
   zbus_status s = ZBUS_OK;
   do {
-    if ((s = upload(&d_lr, lr, st)) != ZBUS_OK) break;
     if ((s = upload(&d_sp, sp, st)) != ZBUS_OK) break;
     if ((s = upload(&d_sc, sc, st)) != ZBUS_OK) break;
     if ((s = upload(&d_sv, sv, st)) != ZBUS_OK) break;
+    k_slack_injection<<<(n + 255) / 256, 256, 0, st>>>(net->ys, n, d_sp, d_sc, d_sv,
+                                                        net->v_slack[0], net->v_slack[1],
+                                                        net->v_slack[2]);
+    cudaError_t ce = cudaGetLastError();
+    if (ce != cudaSuccess) {
+      s = cuda_fail(ce, "setup kernel launch", __FILE__, __LINE__);
+      break;
+    }
+    s = ensure_3m(net, st);
+  } while (0);
+  cudaStreamSynchronize(st);
+  cudaFree(d_sp);
+  cudaFree(d_sc);
+  cudaFree(d_sv);
+  return s;
+}
+
+zbus_status ensure_z(zbus_network net, cudaStream_t st) {
+  if (net->Z) return ZBUS_OK;
+  const int n = net->n;
+  const size_t zb = (size_t)n * n * sizeof(double2);
+  ZB_CUDA(cudaMalloc((void**)&net->Z, zb));
+  int32_t *d_perm = nullptr, *d_info = nullptr;
+  double2* d_colk = nullptr;
+  zbus_status s = ZBUS_OK;
+  do {
     cudaError_t ce;
     if ((ce = cudaMalloc((void**)&d_perm, n * sizeof(int32_t))) != cudaSuccess ||
         (ce = cudaMalloc((void**)&d_info, sizeof(int32_t))) != cudaSuccess ||
@@ -548,21 +572,18 @@ zbus_status build_network(zbus_network net, int32_t n_total, int64_t nnz, const 
     }
     cudaMemsetAsync(d_info, 0, sizeof(int32_t), st);
     cudaMemsetAsync(net->Z, 0, zb, st);
-    if (lp[n] > 0)
-      k_scatter<<<std::min<int64_t>(4096, (lp[n] + 255) / 256), 256, 0, st>>>(
-          net->Z, n, d_lr, net->csr_col, net->csr_val, lp[n]);
-    k_slack_injection<<<(n + 255) / 256, 256, 0, st>>>(net->ys, n, d_sp, d_sc, d_sv,
-                                                        net->v_slack[0], net->v_slack[1],
-                                                        net->v_slack[2]);
+    k_scatter_csr<<<(n + 255) / 256, 256, 0, st>>>(net->Z, n, net->csr_ptr, net->csr_col,
+                                                    net->csr_val);
     const int gy = std::min(n, 256);
     for (int k = 0; k < n; ++k) {
       k_gj_pivot<<<1, 1024, 0, st>>>(net->Z, n, k, d_perm, d_colk, d_info);
       k_gj_update<<<dim3((n + 127) / 128, gy), 128, 0, st>>>(net->Z, n, k, d_colk);
     }
     k_gj_unpermute<<<(n + 127) / 128, 128, 0, st>>>(net->Z, n, d_perm);
+    // w = -Z Y_Ls v_s (the same value at every formation: the elimination is
+    // deterministic)
     k_noload<<<(n * 32 + 255) / 256, 256, 0, st>>>(net->Z, net->ys, net->w, n);
     k_check_finite<<<(n + 255) / 256, 256, 0, st>>>(net->w, n, d_info);
-    k_pack_f64<<<2048, 256, 0, st>>>(net->Z, n, net->n_pad, net->Zr, net->Zi, net->Zs);
     if ((ce = cudaGetLastError()) != cudaSuccess) {
       s = cuda_fail(ce, "setup kernel launch", __FILE__, __LINE__);
       break;
@@ -581,14 +602,48 @@ zbus_status build_network(zbus_network net, int32_t n_total, int64_t nnz, const 
       s = fail(ZBUS_ERR_SINGULAR, "no-load voltage is not finite (Y_LL numerically singular)");
     }
   } while (0);
-  cudaFree(d_lr);
-  cudaFree(d_sp);
-  cudaFree(d_sc);
-  cudaFree(d_sv);
   cudaFree(d_perm);
   cudaFree(d_info);
   cudaFree(d_colk);
+  if (s != ZBUS_OK) {
+    cudaFree(net->Z);
+    net->Z = nullptr;
+  }
   return s;
+}
+
+zbus_status ensure_3m(zbus_network net, cudaStream_t st) {
+  if (net->Zr) return ZBUS_OK;
+  ZB_CHECK(ensure_z(net, st));
+  const size_t pb = (size_t)net->n_pad * net->n_pad * sizeof(double);
+  zbus_status s = ZBUS_OK;
+  cudaError_t ce;
+  if ((ce = cudaMalloc((void**)&net->Zr, pb)) != cudaSuccess ||
+      (ce = cudaMalloc((void**)&net->Zi, pb)) != cudaSuccess ||
+      (ce = cudaMalloc((void**)&net->Zs, pb)) != cudaSuccess) {
+    s = cuda_fail(ce, "cudaMalloc(3M operands)", __FILE__, __LINE__);
+  } else {
+    k_pack_f64<<<2048, 256, 0, st>>>(net->Z, net->n, net->n_pad, net->Zr, net->Zi, net->Zs);
+    if ((ce = cudaGetLastError()) != cudaSuccess ||
+        (ce = cudaStreamSynchronize(st)) != cudaSuccess)
+      s = cuda_fail(ce, "3M operands", __FILE__, __LINE__);
+  }
+  if (s != ZBUS_OK) release_3m(net);
+  return s;
+}
+
+void release_z(zbus_network net) {
+  cudaFree(net->Z);
+  net->Z = nullptr;
+}
+
+void release_3m(zbus_network net) {
+  drop_graphs(net);   // their kernels hold the operand addresses
+  free_adjoint(net);
+  cudaFree(net->Zr);
+  cudaFree(net->Zi);
+  cudaFree(net->Zs);
+  net->Zr = net->Zi = net->Zs = nullptr;
 }
 
 }  // namespace zbus

@@ -265,6 +265,7 @@ struct zbus_network_s {
   int32_t* t_pblk = nullptr;    // [nbus] branch-form block of each position's parent line
   zbus::Workspace ws;
   zbus::MixedOperands mixed[2];   // [0] FP16 row-scaled, [1] BF16 hi + lo
+  uint64_t op_gen = 0;            // bumped when the tensor-core operands are freed
   struct zbus::Group* group1 = nullptr;   // single-network mixed solves
   struct zbus::Group* last_group = nullptr;   // group of the last mixed solve (error word)
   std::vector<zbus::GraphEntry> graphs;
@@ -307,6 +308,20 @@ int buffer_kind(const void* p);
 // noalloc.cu: loads the allocation-free solve's static scratch array on the
 // current device and caches its address (called once per network creation)
 zbus_status noalloc_prepare(int dev);
+
+// setup.cu: dense operands.  Z = Y_LL^-1 (complex FP64, by Gauss-Jordan from
+// the device CSR; also recomputes w) and its 3M copies (Zr, Zi, Zr + Zi) are
+// formed on demand and can be released (the serving loop's operand cache);
+// a release waits for nothing: the caller makes sure no work uses them.
+zbus_status ensure_z(zbus_network net, cudaStream_t st);
+zbus_status ensure_3m(zbus_network net, cudaStream_t st);
+void release_z(zbus_network net);
+void release_3m(zbus_network net);
+// mixed.cu: frees the tensor-core operands of both precisions
+void release_mixed_ops(zbus_network net);
+// api.cu: drops the cached sweep graphs of a network (they hold operand and
+// workspace addresses)
+void drop_graphs(zbus_network net);
 
 // setup.cu
 zbus_status build_network(zbus_network net, int32_t n_total, int64_t nnz, const int32_t* row,
@@ -371,6 +386,7 @@ void phased_free(zbus_network net);
 zbus_status make_tmap_2d(CUtensorMap* map, const void* base, bool bf16, uint64_t cols,
                          uint64_t rows, uint32_t box_cols, uint32_t box_rows);
 zbus_status prepare_mixed(zbus_network net, int32_t precision, cudaStream_t st);
+zbus_status prepare_df(zbus_network net, cudaStream_t st);
 // double-float operands of the tree sweep (radial networks only)
 zbus_status prepare_tree(zbus_network net, cudaStream_t st);
 void free_mixed(zbus_network net);

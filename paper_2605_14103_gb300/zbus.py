@@ -51,7 +51,7 @@ class zbus_request(C.Structure):
 
 class zbus_request_result(C.Structure):
     _fields_ = [("status", C.c_int), ("n_converged", C.c_int32), ("max_iters", C.c_int32),
-                ("reserved0", C.c_int32), ("t_admit", C.c_double), ("t_done", C.c_double),
+                ("operands_formed", C.c_int32), ("t_admit", C.c_double), ("t_done", C.c_double),
                 ("V", C.c_void_p), ("iters", C.c_void_p), ("converged", C.c_void_p)]
 
 
@@ -106,6 +106,8 @@ _SIGS = {
     "zbus_last_device_status": (C.c_int, [_P, _P]),
     "zbus_probe_fp64_rate": (C.c_int, [C.POINTER(C.c_double), C.POINTER(C.c_float), _P]),
     "zbus_checked_set_wait": (C.c_int, [C.c_uint64]),
+    "zbus_serve_footprint": (C.c_int, [_P, C.c_int32, C.POINTER(C.c_uint64),
+                                       C.POINTER(C.c_uint64), C.POINTER(C.c_uint64)]),
     "zbus_solve_adjoint": (C.c_int, [_P, C.c_int64, _P, _P, _P, _P, C.c_double, C.c_int32,
                                      C.POINTER(zbus_solve_opts), _P, _P, _P, _P, _P]),
     "zbus_nr_opts_default": (None, [C.POINTER(zbus_nr_opts)]),
@@ -245,6 +247,14 @@ def zbus_solve(h, S_wye, S_delta, V_init, tol, max_iter, opts, V_out, iters, con
 def zbus_last_device_status(h, stream=None) -> int:
     """ZBUS_OK (0), or the status of an error the device detected in the last solve."""
     return int(lib().zbus_last_device_status(h, _stream(stream)))
+
+
+def zbus_serve_footprint(h, precision="fp16_scaled"):
+    """(operand bytes while cached, extra bytes while forming, bytes per slot)."""
+    a, b, c = C.c_uint64(0), C.c_uint64(0), C.c_uint64(0)
+    _check(lib().zbus_serve_footprint(h, PRECISION[precision], C.byref(a), C.byref(b),
+                                      C.byref(c)))
+    return a.value, b.value, c.value
 
 
 def zbus_probe_fp64_rate(stream=None):
@@ -462,7 +472,8 @@ def serve(networks, requests, hbm_budget_bytes=120 << 30, max_slots=4096,
     def sink(req, res):
         out[req.tag] = {"status": res.status, "t_arrival": req.t_arrival, "t_admit": res.t_admit,
                         "t_done": res.t_done, "n_converged": res.n_converged,
-                        "max_iters": res.max_iters, "B": req.B}
+                        "max_iters": res.max_iters, "B": req.B,
+                        "operands_formed": res.operands_formed}
 
     cfg = zbus_serve_config()
     cfg.hbm_budget_bytes = int(hbm_budget_bytes)

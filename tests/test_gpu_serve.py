@@ -111,3 +111,54 @@ def test_budget_too_small_is_refused(pool):
     with pytest.raises(zbus.ZbusError) as ei:
         zbus.serve(nets, reqs, hbm_budget_bytes=1 << 20)
     assert ei.value.status == 3
+
+
+@pytest.mark.parametrize("mode", ["fp16_scaled", "tree"])
+def test_operand_cache_under_a_budget_below_the_pool(mode):
+    """The pool's operands exceed the budget: the serving loop keeps an
+    operand cache, evicts idle feeders (least recently used first) and forms
+    a feeder's operands on demand.  Every request completes, each equal,
+    bitwise, to its result alone and within 1e-6 pu of the oracle; operands
+    are formed more often than there are feeders; a network the loop released
+    still solves (its Z formed again, bitwise the same)."""
+    feeders = [F.make_feeder(N, 700 + N, delta_frac=0.4) for N in (200, 220, 60)]
+    nets = [zbus.Network.from_feeder(f) for f in feeders]
+    Z0, w0 = nets[1].get_z()
+    Z0, w0 = Z0.clone(), w0.clone()
+    fp = [zbus.zbus_serve_footprint(n.handle, mode) for n in nets]
+    slots = 128
+    peak = max(a + b for a, b, _ in fp)
+    budget = sum(c for _, _, c in fp) * slots + peak   # room for one large feeder at a time
+    assert fp[0][0] + fp[1][0] > peak                  # the two large ones never fit together
+    # requests far enough apart that each finds the previous one's feeder idle:
+    # the two large feeders keep evicting each other (and the small one)
+    order = [0, 1, 0, 2, 1, 1, 0, 2]
+    reqs, host = [], []
+    for i, k in enumerate(order):
+        Sw, Sd = F.make_scenarios(feeders[k], 16 + 7 * i, 0.8, 1.2, seed=50 + i)
+        reqs.append({"feeder": k, "S_wye": dev(Sw), "S_delta": dev(Sd), "arrival": 0.08 * i})
+        host.append((k, Sw, Sd))
+    mixed = zbus.serve(nets, reqs, precision=mode, max_slots=slots, hbm_budget_bytes=budget)
+    assert all(r["status"] == 0 for r in mixed)
+    assert sum(r["operands_formed"] for r in mixed) >= 4
+    for i, q in enumerate(reqs):
+        alone = zbus.serve(nets, [dict(q, arrival=0.0)], precision=mode, max_slots=slots,
+                           hbm_budget_bytes=budget)[0]
+        m = mixed[i]
+        assert torch.equal(m["V"], alone["V"]), i
+        assert torch.equal(m["iters"], alone["iters"]), i
+        assert torch.equal(m["converged"], alone["converged"]), i
+        k, Sw, Sd = host[i]
+        f = feeders[k]
+        ref = O.solve_coo(f.n_total, f.Y_row, f.Y_col, f.Y_val, f.slack_idx, f.v_slack, Sw, Sd)
+        np.testing.assert_array_equal(m["converged"].cpu().numpy(), ref["converged"])
+        assert np.abs(m["V"].cpu().numpy() - ref["V"]).max() <= 1e-6
+    # the networks the loop released form their operands again on demand
+    Z1, w1 = nets[1].get_z()
+    assert torch.equal(Z1, Z0) and torch.equal(w1, w0)
+    for k, net in enumerate(nets):
+        Sw, Sd = F.make_scenarios(feeders[k], 9, 0.8, 1.2, seed=99)
+        V, it, cv = net.solve(dev(Sw), dev(Sd), precision="fp64")
+        f = feeders[k]
+        ref = O.solve_coo(f.n_total, f.Y_row, f.Y_col, f.Y_val, f.slack_idx, f.v_slack, Sw, Sd)
+        assert np.abs(V.cpu().numpy() - ref["V"]).max() <= 1e-6
