@@ -303,6 +303,7 @@ DTYPE = {"fp64": "f64", "fp16_scaled": "fp16_scaled+f64", "bf16x2": "bf16x2+f64"
 MIXED_OUTSIDE = ("k_group_reset+k_slot_init+k_group_params+k_finish_group(start)+k_slot_merge"
                  "+k_check+k_corr_setup+k_corr_select+k_corr_end")
 # launches outside the sweep loop per solve (with no scenario to correct), and per sweep
+# (the tensor-core forms fold their stop test into the sweep end up to 1024 slots)
 OUTSIDE = {"fp64": ("k_init", 1), "tree": (MIXED_OUTSIDE, 9),
            "fp16_scaled": (MIXED_OUTSIDE, 9), "bf16x2": (MIXED_OUTSIDE, 9)}
 PER_SWEEP = {"fp64": 4, "fp16_scaled": 4, "bf16x2": 4, "tree": 2}
@@ -467,8 +468,9 @@ def measure(net, form, Sw, Sd, wl, n, steps, warmup, flush, ws, peaks, extra_lau
             "step_ms_p50": statistics.median(step_ms),
             "step_ms_p99": float(np.percentile(step_ms, 99)), "converged_per_step": good,
             "max_iters": max_iters, "mean_iters": float(it.float().mean().item()),
-            "gpu_launches": steps * (OUTSIDE[form][1] + extra_launches +
-                                     PER_SWEEP[form] * max_iters),
+            "gpu_launches": steps * (OUTSIDE[form][1] + extra_launches + max_iters * (
+                PER_SWEEP[form] - (1 if form in ("fp16_scaled", "bf16x2") and
+                                   (B + 127) // 128 * 128 <= 1024 else 0))),
             "kernels": kernels, "roofline": roof, "sample": sample}, (V, it, cv)
 
 
@@ -599,6 +601,9 @@ def run_ours(args):
         results[form] = r
         if head:
             head_out = out
+    # the load gradient of the converged solution on the plain method's workload
+    grad = (measure_gradient(net, Sw, Sd, n, args, flush, ws)
+            if "fp64" in results and args.workload == "feeder128_b4096" else None)
     clk = clocks.stop() if clocks else None
     head = results[args.precision]
 
@@ -684,6 +689,12 @@ def run_ours(args):
         if phased:
             # the device solves the network padded to three phase slots per bus
             out["config"]["padded_unknowns"] = 3 * (wl.N - 1)
+        if grad is not None:
+            for k in ("fp64", "tree"):
+                if "ms_per_step" in grad.get(k, {}):
+                    grad[k]["vs_forward_fp64_time"] = (grad[k]["ms_per_step"] /
+                                                       results["fp64"]["ms_per_step"])
+            out["gradient"] = grad
         out.update(extras)
         print(json.dumps(out), flush=True)
     if ws > 1:

@@ -5,6 +5,7 @@
 #pragma once
 
 #include <cuda_runtime.h>
+#include <stdint.h>
 
 namespace zbus {
 
@@ -41,6 +42,19 @@ __device__ __forceinline__ void df_sub(float bh, float bl, float ah, float al, f
   two_sum(bh, -ah, s, e);
   dh = s;
   dl = __fadd_rn(e, __fsub_rn(bl, al));
+}
+
+// float -> double, exact, by moving the bits (integer instructions): the
+// conversion instruction runs on this GPU's FP64 units, which also do the
+// FP64 arithmetic.  Zeros, subnormals, infinities and NaNs take the
+// conversion instruction.
+__device__ __forceinline__ double f2d_exact(float f) {
+  const uint32_t u = __float_as_uint(f);
+  const uint32_t e = (u >> 23) & 0xFFu;
+  if (e == 0u || e == 0xFFu) return (double)f;
+  const uint64_t d = ((uint64_t)(u & 0x80000000u) << 32) | ((uint64_t)(e + 896u) << 52) |
+                     ((uint64_t)(u & 0x7FFFFFu) << 29);
+  return __longlong_as_double((long long)d);
 }
 
 // Split a double into hi + lo floats.

@@ -31,6 +31,7 @@ constexpr int RES_WARPS = 4;
 constexpr int CHUNK_BUS = 4;
 constexpr int CHUNK_ROWS = 3 * CHUNK_BUS;
 constexpr int DEC_THREADS = 256;
+constexpr int64_t FUSE_DECIDE = 1024;   // slots up to which the stop test joins the sweep end
 // output of the residual: scaled FP16 / BF16 rows of R (tensor-core
 // contraction) or FP32 values, scenario-minor (tree sweep)
 constexpr int RES_FP16 = 0, RES_BF16 = 1, RES_F32 = 2;
@@ -583,11 +584,8 @@ k_contract_group(GroupState* __restrict__ gs, const ItemDesc* __restrict__ items
 // order; a slot stops when its step meets tol (converged), is not finite or
 // reaches max_iter sweeps since its admission.
 // ---------------------------------------------------------------------------
-__global__ void __launch_bounds__(DEC_THREADS)
-k_decide_group(GroupState* __restrict__ gs, const ItemDesc* __restrict__ items) {
-  const int k = find_item(items, gs->n_items, blockIdx.x, 1);
-  const ItemDesc& it = items[k];
-  const int b = (blockIdx.x - it.dec_begin) * DEC_THREADS + threadIdx.x;
+__device__ __forceinline__ void decide_slot(const GroupState* __restrict__ gs, const ItemDesc& it,
+                                            int b) {
   int keep = 0;
   if (b < it.Bp && it.st[b] == SLOT_ACTIVE) {
     const int sw = it.it[b] + 1;
@@ -611,6 +609,13 @@ k_decide_group(GroupState* __restrict__ gs, const ItemDesc* __restrict__ items) 
     it.amax[b] = it.amax[it.Bp + b];
     it.amax[it.Bp + b] = 0.f;
   }
+}
+
+__global__ void __launch_bounds__(DEC_THREADS)
+k_decide_group(GroupState* __restrict__ gs, const ItemDesc* __restrict__ items) {
+  const int k = find_item(items, gs->n_items, blockIdx.x, 1);
+  const ItemDesc& it = items[k];
+  decide_slot(gs, it, (blockIdx.x - it.dec_begin) * DEC_THREADS + threadIdx.x);
 }
 
 // ---------------------------------------------------------------------------
@@ -890,16 +895,26 @@ k_tree_group(GroupState* __restrict__ gs, const ItemDesc* __restrict__ items,
 // 128-slot tile holding an active slot, times its item's N-tiles, in a stable
 // order), the active count, the sweep counter and the graph's loop
 // condition.  initial = 1 only rebuilds the list and the count (after
-// admissions), without counting a sweep.
+// admissions), without counting a sweep.  decide = 1 first runs the stop test
+// of every slot (k_decide_group's work, for groups of at most FUSE_DECIDE
+// slots, where the extra launch costs more than the test).
 // ---------------------------------------------------------------------------
 __global__ void __launch_bounds__(1024)
 k_finish_group(GroupState* __restrict__ gs, const ItemDesc* __restrict__ items, int initial,
-               cudaGraphConditionalHandle h, int use_handle) {
+               cudaGraphConditionalHandle h, int use_handle, int decide) {
   __shared__ int swarp[32], sact[32];
   __shared__ int sbase, stotal, sactive;
   const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
   const int mt_total = gs->mt_total, n_items = gs->n_items;
   uint64_t* tiles = gs->tiles;
+  if (decide) {
+    // small groups: the stop test of every slot here, saving a launch per sweep
+    for (int k = 0; k < n_items; ++k) {
+      const ItemDesc& it = items[k];
+      for (int b = tid; b < it.Bp; b += blockDim.x) decide_slot(gs, it, b);
+    }
+    __syncthreads();
+  }
   if (tid == 0) {
     sbase = 0;
     sactive = 0;
@@ -978,7 +993,7 @@ __global__ void k_slot_merge(const ItemDesc* __restrict__ items, int k, int s0, 
     if (j < n && b < B) {
       const int64_t g = (int64_t)j * Bp + s0 + b;
       const float2 h = it.Vh[g], l = it.Vl[g];
-      v = make_double2((double)h.x + (double)l.x, (double)h.y + (double)l.y);
+      v = make_double2(f2d_exact(h.x) + f2d_exact(l.x), f2d_exact(h.y) + f2d_exact(l.y));
     }
     t[tx][r] = v;
   }
@@ -1022,9 +1037,10 @@ __device__ __forceinline__ double2 draw64(double2 S, double2 v) {
 // va = the bus's own voltages.  The 3x3 blocks are the same for every lane of
 // a warp working on bus a (broadcast loads).
 //
-// With a branch row jg (the scenario's branch terms J_k = Y_ab (v_b - v_a),
-// k_branch_f64) and the block-to-branch map br, a neighbour block adds +J_k
-// (block (a, b)) or -J_k (its mirror) instead of forming the product.
+// With branch terms (jg: the scenario's J_k = Y_ab (v_b - v_a) of phase p at
+// jg[(3 k + p) js], k_branch_f64) and the block-to-branch map br, a neighbour
+// block adds +J_k (block (a, b)) or -J_k (its mirror) instead of forming the
+// product.
 __device__ __forceinline__ void admittance_sum_f64(const double2* __restrict__ vg, int a, int nb,
                                                    const int32_t* __restrict__ bptr,
                                                    const int32_t* __restrict__ bcol,
@@ -1033,7 +1049,7 @@ __device__ __forceinline__ void admittance_sum_f64(const double2* __restrict__ v
                                                    double (&ar)[3], double (&ai)[3],
                                                    const double2* __restrict__ jg = nullptr,
                                                    const int32_t* __restrict__ br = nullptr,
-                                                   int nbr = 0) {
+                                                   int nbr = 0, int64_t js = 0) {
 #pragma unroll
   for (int p = 0; p < 3; ++p) ar[p] = ai[p] = 0.0;
   const int t1 = bptr[a + 1];
@@ -1047,7 +1063,7 @@ __device__ __forceinline__ void admittance_sum_f64(const double2* __restrict__ v
       const double sg = k >= 0 ? 1.0 : -1.0;
 #pragma unroll
       for (int p = 0; p < 3; ++p) {
-        const double2 x = jg[3 * kk + p];
+        const double2 x = jg[(3 * kk + p) * js];
         ar[p] = fma(sg, x.x, ar[p]);
         ai[p] = fma(sg, x.y, ai[p]);
       }
@@ -1101,12 +1117,12 @@ __device__ __forceinline__ double check_bus_f64(const double2* __restrict__ vg,
                                                 const double2 (&vs)[3],
                                                 const double2* __restrict__ jg = nullptr,
                                                 const int32_t* __restrict__ br = nullptr,
-                                                int nbr = 0) {
+                                                int nbr = 0, int64_t js = 0) {
   double2 va[3];
 #pragma unroll
   for (int p = 0; p < 3; ++p) va[p] = vg[3 * a + p];
   double ar[3], ai[3];
-  admittance_sum_f64(vg, a, nb, bptr, bcol, bval, vs, va, ar, ai, jg, br, nbr);
+  admittance_sum_f64(vg, a, nb, bptr, bcol, bval, vs, va, ar, ai, jg, br, nbr, js);
   // dS_p = v_p conj(acc_p) + S_wye_p + v_p conj(drawn_delta_p)
   double sr[3], si[3];
 #pragma unroll
@@ -1165,14 +1181,15 @@ __device__ __forceinline__ double check_bus_f64(const double2* __restrict__ vg,
 // (non-negative doubles order like their bit patterns; NaN counts as +inf);
 // mmax is zeroed by k_slot_merge.
 //
-// With branch rows J ([B][nbr][3], k_branch_f64 of the same grid), each
+// With branch terms J ([nbr][3][B], k_branch_f64 of the same grid), each
 // line's block product is formed once, by k_branch_f64, and both of its
 // buses add it (identical mirror blocks, build_branches): about a third
 // fewer FP64 operations.
 constexpr int CHECK_WARPS = 4;
 
 // Branch terms J_k = Y_ab (v_b - v_a) of every live scenario, FP64, in the
-// check's layout (lanes = 32 scenarios, warps over the branches).
+// check's layout (lanes = 32 scenarios, warps over the branches), stored
+// scenario-minor, J[(3 k + p) B + b], so both kernels move whole rows.
 __global__ void __launch_bounds__(32 * CHECK_WARPS)
 k_branch_f64(const double2* __restrict__ V, const uint8_t* __restrict__ conv, int B, int n,
              const int4* __restrict__ tab, int nbr, const double2* __restrict__ bval,
@@ -1184,7 +1201,7 @@ k_branch_f64(const double2* __restrict__ V, const uint8_t* __restrict__ conv, in
   if (__ballot_sync(0xffffffffu, live) == 0u) return;
   if (!live) return;
   const double2* vg = V + (int64_t)b * n;
-  double2* jg = J + (int64_t)b * nbr * 3;
+  double2* jg = J + b;
   const int nb = n / 3;
   for (int k = by * CHECK_WARPS + ty; k < nbr; k += ny * CHECK_WARPS) {
     const int4 e = tab[k];
@@ -1206,7 +1223,7 @@ k_branch_f64(const double2* __restrict__ V, const uint8_t* __restrict__ conv, in
         ar = fma(yy.x, dr[q], fma(-yy.y, di[q], ar));
         ai = fma(yy.x, di[q], fma(yy.y, dr[q], ai));
       }
-      jg[3 * k + p] = make_double2(ar, ai);
+      jg[(int64_t)(3 * k + p) * B] = make_double2(ar, ai);
     }
   }
 }
@@ -1228,10 +1245,10 @@ k_check(const double2* __restrict__ V, const double2* __restrict__ Sw,
   const double2 vs[3] = {vs0, vs1, vs2};
   double worst = 0.0;   // max |dS|^2
   const int nb = n / 3;
-  const double2* jg = J ? J + (int64_t)(b < B ? b : B - 1) * nbr * 3 : nullptr;
+  const double2* jg = J ? J + (b < B ? b : B - 1) : nullptr;
   for (int a = by * CHECK_WARPS + ty; a < nb; a += ny * CHECK_WARPS)
     worst = fmax(worst, check_bus_f64(V + row, Sw ? Sw + row : nullptr, Sd ? Sd + row : nullptr,
-                                      a, nb, bptr, bcol, bval, vs, jg, br, nbr));
+                                      a, nb, bptr, bcol, bval, vs, jg, br, nbr, (int64_t)B));
   red[ty][lane] = worst;
   __syncthreads();
   if (ty == 0 && live) {
@@ -1477,9 +1494,10 @@ cudaError_t tc_attr() {
 }
 
 template <int BN, int ZP, int STAGES, bool BF>
-void tc_launch(Group* g, int grid, cudaStream_t st) {
+cudaError_t tc_launch(Group* g, int grid, cudaStream_t st) {
   k_contract_group<BN, ZP, STAGES, BF><<<grid, TC_THREADS, tc_smem<BN, ZP, STAGES, BF>(), st>>>(
       g->d_state, g->d_items, g->d_tmR, g->d_tmZ0, g->d_tmZ1);
+  return cudaGetLastError();
 }
 
 // (precision, BN, stages) variants compiled: FP16 x1 and BF16 x2.
@@ -1487,7 +1505,7 @@ struct TcVariant {
   int32_t precision;
   int BN, stages;
   cudaError_t (*attr)();
-  void (*launch)(Group*, int, cudaStream_t);
+  cudaError_t (*launch)(Group*, int, cudaStream_t);
 };
 
 const TcVariant kVariants[] = {
@@ -1680,6 +1698,9 @@ zbus_status group_build(Group* g, const std::vector<zbus_network>& nets,
   g->mt_total = mt;
   g->max_tiles = tiles;
 
+  g->total_Bp = 0;
+  for (size_t k = 0; k < nets.size(); ++k) g->total_Bp += g->h_items[k].Bp;
+
   const size_t o_items = 0;
   const size_t o_state = a256(o_items + nets.size() * sizeof(ItemDesc));
   const size_t o_tiles = a256(o_state + sizeof(GroupState));
@@ -1785,19 +1806,19 @@ zbus_status group_start(Group* g, double tol, int32_t max_iter, int32_t rule, in
 }
 
 zbus_status group_rebuild(Group* g, cudaStream_t st) {
-  k_finish_group<<<1, 1024, 0, st>>>(g->d_state, g->d_items, 1, 0, 0);
+  k_finish_group<<<1, 1024, 0, st>>>(g->d_state, g->d_items, 1, 0, 0, 0);
   ZB_CUDA(cudaGetLastError());
   return ZBUS_OK;
 }
 
-zbus_status group_sweep(Group* g, cudaGraphConditionalHandle h, bool use_handle, cudaStream_t st,
-                        cudaEvent_t* ev) {
+namespace {
+
+// Residual of every slot on stream st.  Register budget: 4 blocks per SM at
+// small n (latency), 6 at large n (FP32 issue), measured on both workloads.
+void launch_residual(Group* g, cudaStream_t st) {
   const bool bf = g->precision == ZBUS_MIXED_BF16X2;
   const bool tree = g->precision == ZBUS_TREE_SWEEP;
-  if (ev) ZB_CUDA(cudaEventRecord(ev[0], st));
-  // register budget of the residual: 4 blocks per SM at small n (latency),
-  // 6 at large n (FP32 issue), measured on both workloads
-#define ZB_RES(OUT, M) \
+#define ZB_RES(OUT, M)                                                                     \
   k_residual_group<OUT, M><<<g->res_blocks, RES_WARPS * 32, 0, st>>>(g->d_state, g->d_items)
   const int out = tree ? RES_F32 : (bf ? RES_BF16 : RES_FP16);
   if (g->max_n > 1024) {
@@ -1810,6 +1831,15 @@ zbus_status group_sweep(Group* g, cudaGraphConditionalHandle h, bool use_handle,
     else ZB_RES(RES_FP16, 4);
   }
 #undef ZB_RES
+}
+
+}  // namespace
+
+zbus_status group_sweep(Group* g, cudaGraphConditionalHandle h, bool use_handle, cudaStream_t st,
+                        cudaEvent_t* ev) {
+  const bool tree = g->precision == ZBUS_TREE_SWEEP;
+  if (ev) ZB_CUDA(cudaEventRecord(ev[0], st));
+  launch_residual(g, st);
   if (ev) ZB_CUDA(cudaEventRecord(ev[1], st));
   if (tree) {
     // step, update, stop test and the end of the sweep in one launch
@@ -1826,10 +1856,12 @@ zbus_status group_sweep(Group* g, cudaGraphConditionalHandle h, bool use_handle,
     if (ev) ZB_CUDA(cudaEventRecord(ev[2], st));
   } else {
     const TcVariant* var = find_variant(g->precision, g->BN, g->stages);
-    var->launch(g, std::min(g->num_sms, g->max_tiles), st);
+    ZB_CUDA(var->launch(g, std::min(g->num_sms, g->max_tiles), st));
     if (ev) ZB_CUDA(cudaEventRecord(ev[2], st));
-    k_decide_group<<<g->dec_blocks, DEC_THREADS, 0, st>>>(g->d_state, g->d_items);
-    k_finish_group<<<1, 1024, 0, st>>>(g->d_state, g->d_items, 0, h, use_handle ? 1 : 0);
+    const bool fuse = g->total_Bp <= FUSE_DECIDE;
+    if (!fuse) k_decide_group<<<g->dec_blocks, DEC_THREADS, 0, st>>>(g->d_state, g->d_items);
+    k_finish_group<<<1, 1024, 0, st>>>(g->d_state, g->d_items, 0, h, use_handle ? 1 : 0,
+                                       fuse ? 1 : 0);
   }
   if (ev) ZB_CUDA(cudaEventRecord(ev[3], st));
   ZB_CUDA(cudaGetLastError());

@@ -89,6 +89,7 @@ struct Group {
   int stages = 0;
   int n_items = 0;
   int mt_total = 0;
+  int64_t total_Bp = 0;         // slots over all items
   int max_tiles = 0;
   int res_blocks = 0;
   int dec_blocks = 0;

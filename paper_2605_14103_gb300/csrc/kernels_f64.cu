@@ -232,6 +232,87 @@ k_gemm3m_f64(const SolveCtx* __restrict__ ctx, const double* __restrict__ Zr,
 }
 
 // ---------------------------------------------------------------------------
+// K2 for small batches (at most one 32-scenario tile): one block per (slot,
+// N-tile), one thread per output, so the work spreads over slots x N-tiles
+// SMs instead of the single block the tiled kernel would run (the FP64 pipe
+// does 2 DFMA per clock per SM, so one block of the tiled kernel takes tens
+// of microseconds even at 36 unknowns).  Every output's three products are
+// summed over k in the tiled kernel's order (one sequential FMA chain each)
+// and the tile partials are grouped like its block reduction (per thread
+// column tn the outputs tn, tn + 12, tn + 24, tn + 36, then tn = 0..11), so
+// the results are bitwise those of k_gemm3m_f64.
+// ---------------------------------------------------------------------------
+constexpr int SMALL_THREADS = 64;
+
+__global__ void __launch_bounds__(SMALL_THREADS)
+k_gemm3m_f64_small(const SolveCtx* __restrict__ ctx, const double* __restrict__ Zr,
+                   const double* __restrict__ Zi, const double* __restrict__ Zs,
+                   const double2* __restrict__ w, int n, int n_pad) {
+  __shared__ double sdm[F64_BN], sds[F64_BN];
+  __shared__ int sok[F64_BN];
+  const int count = ctx->count;
+  const int slot = blockIdx.x, nt = blockIdx.y;
+  if (slot >= count) return;   // whole block
+  const int ntn = n_pad / F64_BN;
+  const int64_t plane = (int64_t)ctx->B * n_pad;
+  const double* __restrict__ Ir = ctx->Iop + (int64_t)slot * n_pad;
+  const double* __restrict__ Ii = Ir + plane;
+  const double* __restrict__ Is = Ii + plane;
+  const int t = threadIdx.x;
+  if (t < F64_BN) {
+    const int i = nt * F64_BN + t;
+    const double* zr = Zr + (int64_t)i * n_pad;
+    const double* zi = Zi + (int64_t)i * n_pad;
+    const double* zs = Zs + (int64_t)i * n_pad;
+    double a1 = 0.0, a2 = 0.0, a3 = 0.0;
+    for (int k = 0; k < n_pad; ++k) {
+      a1 = fma(zr[k], Ir[k], a1);
+      a2 = fma(zi[k], Ii[k], a2);
+      a3 = fma(zs[k], Is[k], a3);
+    }
+    int ok = 0;
+    double dm = 0.0, ds = 0.0;
+    if (i < n && ZB_IN(ctx->list[slot], ctx->B, 0x105u)) {
+      const int b = ctx->list[slot];
+      const double dr = a1 - a2;
+      const double di = a3 - a1 - a2;
+      const int64_t g = (int64_t)b * n + i;
+      double2* V = ctx->V;
+      const double2 vo = V[g];
+      const double2 wi = w ? w[i] : vo;
+      const double2 vn = make_double2(wi.x + dr, wi.y + di);
+      V[g] = vn;
+      double step = hypot(vn.x - vo.x, vn.y - vo.y);
+      if (step != step) step = INFINITY;
+      dm = step;
+      ds = hypot(vn.x, vn.y) - hypot(vo.x, vo.y);
+      ok = 1;
+    }
+    sdm[t] = dm;
+    sds[t] = ds;
+    sok[t] = ok;
+  }
+  __syncthreads();
+  if (t == 0) {
+    double dmax = 0.0, dsum = 0.0;
+    for (int tn = 0; tn < F64_BN / 4; ++tn) {
+      double m = 0.0, u = 0.0;
+      for (int c = 0; c < 4; ++c) {
+        const int o = tn + (F64_BN / 4) * c;
+        if (sok[o]) {
+          m = fmax(m, sdm[o]);
+          u += sds[o];
+        }
+      }
+      dmax = fmax(dmax, m);
+      dsum += u;
+    }
+    ctx->part[((int64_t)slot * ntn + nt) * 2 + 0] = dmax;
+    ctx->part[((int64_t)slot * ntn + nt) * 2 + 1] = dsum;
+  }
+}
+
+// ---------------------------------------------------------------------------
 // K3a: stop test per active scenario (many blocks): reduce the per-tile
 // partials in a fixed order, record iters / flags, mark the slots to keep.
 // ---------------------------------------------------------------------------
@@ -436,14 +517,22 @@ void launch_currents_f64(SolveCtx* ctx, int n, int n_pad, int B, cudaStream_t st
   k_currents_f64<<<grid, 256, 0, st>>>(ctx, n, n_pad);
 }
 
+// Grid of the FP64 contraction for batches of up to B scenarios: the number
+// of blocks of the tiled kernel, or -B for batches of one tile at most (the
+// per-(slot, N-tile) kernel).
 int gemm_f64_grid(int B, int n_pad) {
+  if (B <= F64_BM) return -std::max(1, B);
   const int tiles = ((B + F64_BM - 1) / F64_BM) * (n_pad / F64_BN);
   return std::max(1, std::min(tiles, 152 * 4));
 }
 
 void launch_gemm_f64(SolveCtx* ctx, const double* Zr, const double* Zi, const double* Zs,
                      const double2* w, int n, int n_pad, int grid, cudaStream_t st) {
-  k_gemm3m_f64<<<grid, GEMM_THREADS, 0, st>>>(ctx, Zr, Zi, Zs, w, n, n_pad);
+  if (grid < 0)
+    k_gemm3m_f64_small<<<dim3(-grid, n_pad / F64_BN), SMALL_THREADS, 0, st>>>(ctx, Zr, Zi, Zs, w,
+                                                                             n, n_pad);
+  else
+    k_gemm3m_f64<<<grid, GEMM_THREADS, 0, st>>>(ctx, Zr, Zi, Zs, w, n, n_pad);
 }
 
 void launch_converge(SolveCtx* ctx, int B, cudaGraphConditionalHandle h, bool use_handle,
