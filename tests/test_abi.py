@@ -145,3 +145,19 @@ def test_tune_variants_and_override_without_a_gpu(lib):
         with pytest.raises(zbus.ZbusError) as ei:
             zbus.zbus_tune_set(*args)
         assert ei.value.status == 1
+
+
+def test_new_entry_points_refuse_bad_arguments_without_a_gpu(lib):
+    """Argument checks that run before any CUDA work: the FP64 probe with no
+    output, the serving footprint of a NULL network or a non-serving
+    precision, the wait limit outside the checked build, and the
+    allocation-free solve of a NULL network."""
+    assert lib.zbus_probe_fp64_rate(None, None, None) == 1
+    a = C.c_uint64(0)
+    assert lib.zbus_serve_footprint(None, 2, C.byref(a), None, None) == 1
+    assert lib.zbus_checked_set_wait(0) == 7                 # normal build: unsupported
+    assert lib.zbus_solve_noalloc(None, 4, None, None, None, 1e-8, 50, 0, None, None, None,
+                                  None) == 1
+    o = zbus.zbus_solve_opts_default()
+    assert o.max_correction == 8                            # FP64 correction sweeps by default
+
