@@ -313,9 +313,12 @@ k_residual_group(GroupState* __restrict__ gs, const ItemDesc* __restrict__ items
 }
 
 // ---------------------------------------------------------------------------
-// tcgen05 contraction, persistent: one CTA per SM walks the tile list (tiles
-// of one 128-slot group are consecutive, N fastest, so CTAs running together
-// share the R tile in L2).  Each tile is a 128 x BN block of D = R Z_emb^T
+// tcgen05 contraction, persistent: one CTA per SM walks the tile list (one
+// feeder with 8 or more N-tiles: groups of 128-slot tiles, N-tile by N-tile
+// within a group, so CTAs running together share a Z panel and the group's
+// R rows stay in L2 across the group; otherwise the tiles of one 128-slot
+// group are consecutive, N fastest, and CTAs running together share the R
+// tile).  Each tile is a 128 x BN block of D = R Z_emb^T
 // over K_pad of its item in steps of 64 (128-byte swizzled rows staged by
 // TMA).  Two tensor-memory accumulators (2 x BN columns) let the epilogue of
 // one tile overlap the MMAs of the next.  Warp roles: 0 = TMA producer,
@@ -327,8 +330,8 @@ k_residual_group(GroupState* __restrict__ gs, const ItemDesc* __restrict__ items
 // while the epilogue streams the double-float state (16 B per unknown and
 // slot each way); Z's tiles are loaded with an evict-last policy and, where
 // the state is larger than L2 keeps between kernels (gs->stream_state), the
-// state with an evict-first policy, so Z stays in L2.  A state that fits is
-// left to the normal policy: the next residual re-reads it.
+// state with an evict-first policy, which favours Z over the state.  A state
+// that fits is left to the normal policy: the next residual re-reads it.
 //
 // Giving up: every pipeline wait is bounded (tc_wait_ns()).  A role whose
 // wait runs out records its code in gs->err and stops issuing; then, before
@@ -906,6 +909,7 @@ k_finish_group(GroupState* __restrict__ gs, const ItemDesc* __restrict__ items, 
   __shared__ int sbase, stotal, sactive;
   const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
   const int mt_total = gs->mt_total, n_items = gs->n_items;
+  const int raster = n_items == 1 ? gs->raster : 0;
   uint64_t* tiles = gs->tiles;
   if (decide) {
     // small groups: the stop test of every slot here, saving a launch per sweep
@@ -958,11 +962,57 @@ k_finish_group(GroupState* __restrict__ gs, const ItemDesc* __restrict__ items, 
     }
     __syncthreads();
     const int pos = sbase + swarp[wid] + incl - cnt;
-    for (int t = 0; t < cnt; ++t)
-      tiles[pos + t] = ((uint64_t)k << 32) | ((uint64_t)lm << 16) | (uint64_t)t;
+    if (raster == 0)
+      for (int t = 0; t < cnt; ++t)
+        tiles[pos + t] = ((uint64_t)k << 32) | ((uint64_t)lm << 16) | (uint64_t)t;
     __syncthreads();
     if (tid == 0) sbase += stotal;
     __syncthreads();
+  }
+  if (raster > 0) {
+    // one item: the active 128-slot tiles (rank r among them, in order) in
+    // groups of `raster`; within a group, N-tile by N-tile: tile (r, t) of
+    // group g = r / raster (size sz) at g raster ntn + t sz + r % raster.
+    // Concurrent CTAs then share a group's R rows and a few Z panels in L2.
+    const int ntn = items[0].ntn;
+    const int n_act = sbase / ntn;
+    int rbase = 0;
+    for (int base = 0; base < mt_total; base += 1024) {
+      const int m = base + tid;
+      int act = 0;
+      if (m < mt_total) {
+        const uint32_t* st4 = reinterpret_cast<const uint32_t*>(items[0].st + m * 128);
+        for (int q = 0; q < 32 && !act; ++q) {
+          const uint32_t x = st4[q];
+#pragma unroll
+          for (int y = 0; y < 4; ++y) act |= ((x >> (8 * y)) & 0xFFu) == SLOT_ACTIVE;
+        }
+      }
+      const unsigned bal = __ballot_sync(0xffffffffu, act);
+      if (lane == 0) swarp[wid] = __popc(bal);
+      __syncthreads();
+      if (wid == 0) {
+        const int x = swarp[lane];
+        int inc2 = x;
+        for (int o = 1; o < 32; o <<= 1) {
+          const int y = __shfl_up_sync(0xffffffffu, inc2, o);
+          if (lane >= o) inc2 += y;
+        }
+        swarp[lane] = inc2 - x;
+        if (lane == 31) stotal = inc2;
+      }
+      __syncthreads();
+      if (act) {
+        const int r = rbase + swarp[wid] + __popc(bal & ((1u << lane) - 1u));
+        const int g = r / raster, i = r % raster;
+        const int sz = min(raster, n_act - g * raster);
+        for (int t = 0; t < ntn; ++t)
+          tiles[g * raster * ntn + t * sz + i] = ((uint64_t)m << 16) | (uint64_t)t;
+      }
+      __syncthreads();
+      rbase += stotal;
+      __syncthreads();
+    }
   }
   if (tid == 0) {
     gs->n_tiles = sbase;
@@ -1736,6 +1786,22 @@ zbus_status group_build(Group* g, const std::vector<zbus_network>& nets,
   s.dec_blocks = dec;
   s.tree_groups = tb;
   s.tiles = g->d_tiles;
+  if (!tree && nets.size() == 1) {
+    // tile groups whose R rows (128 x K_pad 16-bit values per 128-slot tile)
+    // take about a quarter of L2 (all tiles in one group below twice that),
+    // when the feeder has enough N-tiles for the grouping to matter.  At
+    // 3069 unknowns (K_pad = 6144, 24 N-tiles of 256) the contraction went
+    // from 1394-1431 to 1469-1480 TFLOP/s at 16384 scenarios (groups of 20)
+    // and from 1147 to 1219 at 4096 (one group of 32); groups sized to L2/2
+    // or L2/8, R loaded evict-last instead of Z, or Z loaded with the
+    // normal or evict-first policy, were slower.
+    int l2 = 0;
+    ZB_CUDA(cudaDeviceGetAttribute(&l2, cudaDevAttrL2CacheSize, dev));
+    const ItemDesc& d = g->h_items[0];
+    const size_t rtile = (size_t)BM * d.K_pad * 2;
+    const int gm = (int)std::max<size_t>(1, (size_t)l2 / 4 / rtile);
+    if (d.ntn >= 8) s.raster = mt >= 2 * gm ? gm : mt;
+  }
   {
     // double-float state of every slot (hi and lo, 16 B per unknown): streamed
     // when it is more than a third of L2

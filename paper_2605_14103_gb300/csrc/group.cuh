@@ -67,6 +67,8 @@ struct GroupState {
   double tol;
   int32_t err;
   int32_t n_tiles;          // entries of tiles
+  int32_t raster;           // one-item groups: 128-slot tiles per group of the tile order
+                            // (0: tile by tile, N-tiles fastest)
   int32_t mt_total;         // 128-slot tiles over all items
   int32_t res_blocks;       // residual grid size
   int32_t dec_blocks;       // stop-test grid size
