@@ -91,7 +91,21 @@ typedef struct {
   int32_t profile;         /* 1: run the sweeps from the host with CUDA events
                               around every kernel on cuda_stream, for
                               zbus_last_profile; 0: device-resident loop */
-  double reserved[4];
+  int32_t fp32_start;      /* dense mixed modes (BF16X2, FP16_SCALED), cold
+                              starts (V_init NULL): 1 (default) = a scenario's
+                              first sweeps form the defect residual in FP32
+                              (block products with the FP32 part of Y, load
+                              currents at the FP32 voltage) as long as its max
+                              |r| exceeds 2^-11 of its largest line or load
+                              current, falls from sweep to sweep and its step
+                              exceeds tol, then double-float to the stop; no
+                              scenario stops on an FP32 sweep, so the fixed
+                              point and the stop rule are those of the
+                              double-float residual.  0 = double-float from
+                              the first sweep.  Per scenario: a result does
+                              not depend on the batch around it. */
+  int32_t reserved_i;
+  double reserved[3];
 } zbus_solve_opts;
 
 /* Fill *opts with the defaults (FP64, max-step rule). */
@@ -341,6 +355,8 @@ typedef struct {
   int32_t max_correction;      /* FP64 correction sweeps per scenario, as in
                                   zbus_solve_opts (<= 0: none, the flag of a
                                   scenario above mismatch_tol is cleared) */
+  int32_t fp32_start;          /* as in zbus_solve_opts, for requests without
+                                  a warm start (0: double-float throughout) */
 } zbus_serve_config;
 
 /*

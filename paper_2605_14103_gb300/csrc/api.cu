@@ -102,7 +102,7 @@ WsLayout workspace_layout(const zbus_network net, int64_t B) {
   L.st = o;
   o += align256(Bp);
   L.amax = o;
-  o += align256(2 * Bp * sizeof(float));
+  o += align256(4 * Bp * sizeof(float));
   L.mt = o;
   o += align256(2 * (Bp / 128) * sizeof(int32_t));
   L.sit = o;
@@ -279,7 +279,8 @@ zbus_status run_group(Group* g, const std::vector<zbus_network>& nets, const std
   for (auto net : nets) net->last_group = g;
   ZB_CHECK(group_reset(g, st));
   for (size_t k = 0; k < nets.size(); ++k)
-    ZB_CHECK(group_admit(g, (int)k, 0, Bs[k], V0[k], Sw[k], Sd[k], st));
+    ZB_CHECK(group_admit(g, (int)k, 0, Bs[k], V0[k], Sw[k], Sd[k], st, false,
+                         o.fp32_start != 0));
   zbus_network pn = nets[0];
   if (o.profile == 1) {
     ZB_CHECK(ensure_profile(pn, max_iter));
@@ -335,6 +336,7 @@ void zbus_solve_opts_default(zbus_solve_opts* o) {
   o->conv_rule = ZBUS_CONV_MAXABS;
   o->mismatch_tol = 1e-6;
   o->max_correction = 8;
+  o->fp32_start = 1;
 }
 
 zbus_status zbus_last_device_status(zbus_network net, void* cuda_stream) {

@@ -63,7 +63,7 @@ __device__ __forceinline__ int find_item(const ItemDesc* items, int n_items, int
 __global__ void k_slot_init(GroupState* __restrict__ gs, const ItemDesc* __restrict__ items, int k,
                             int s0, int B, const double2* __restrict__ V0, int v0_stride,
                             const float4* __restrict__ w_df, const double2* __restrict__ Sw,
-                            const double2* __restrict__ Sd) {
+                            const double2* __restrict__ Sd, int fp32_start) {
   __shared__ double2 tv[32][33];
   __shared__ double2 tw[32][33];
   __shared__ double2 td[32][33];
@@ -114,6 +114,8 @@ __global__ void k_slot_init(GroupState* __restrict__ gs, const ItemDesc* __restr
       it.conv[slot] = 0;
       it.amax[slot] = 1.0f;
       it.amax[Bp + slot] = 0.0f;
+      it.amax[2 * Bp + slot] = 0.0f;
+      it.amax[3 * Bp + slot] = (fp32_start && !V0) ? 1.0f : 0.0f;
     }
   }
 }
@@ -169,6 +171,7 @@ k_residual_group(GroupState* __restrict__ gs, const ItemDesc* __restrict__ items
   constexpr bool BF = OUT == RES_BF16;
   __shared__ uint32_t stage[RES_WARPS][CHUNK_ROWS][32];
   __shared__ float sred[RES_WARPS][32];
+  __shared__ float smag[RES_WARPS][32];
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int k = find_item(items, gs->n_items, blockIdx.x, 0);
   const ItemDesc& it = items[k];
@@ -179,6 +182,10 @@ k_residual_group(GroupState* __restrict__ gs, const ItemDesc* __restrict__ items
   const int b = grp * 32 + lane;
   const bool act = it.st[b] == SLOT_ACTIVE;
   if (!__syncthreads_or(act)) return;   // all 32 slots of this group are idle
+  // FP32 sweep for this slot (its flag, set at a cold start and kept by the
+  // stop test while the residual stays above 2^-11 of the largest line
+  // current); lanes of a warp may differ and then take both paths
+  const bool lp = OUT != RES_F32 && act && it.amax[3 * it.Bp + b] != 0.f;
   float c = 1.f;
   if (OUT != RES_F32) {
     const float ap = it.amax[b];
@@ -197,7 +204,7 @@ k_residual_group(GroupState* __restrict__ gs, const ItemDesc* __restrict__ items
   const int nb = it.nbus;
   const int rows_pad = OUT == RES_F32 ? it.n : it.K_pad >> 1;
   const int nchunks = (rows_pad + CHUNK_ROWS - 1) / CHUNK_ROWS;
-  float amax = 0.f;
+  float amax = 0.f, mag = 0.f;
   for (int ch = ys * RES_WARPS + warp; ch < nchunks; ch += split * RES_WARPS) {
     for (int q = 0; q < CHUNK_BUS; ++q) {
       const int a = ch * CHUNK_BUS + q;
@@ -212,6 +219,55 @@ k_residual_group(GroupState* __restrict__ gs, const ItemDesc* __restrict__ items
           sw[p] = Sw[g];
           sd[p] = Sd[g];
         }
+        if (lp) {
+          // FP32: d = v_b - v_a from the hi and lo parts, block products with
+          // the hi part of Y, each line's term J = Y_ab d kept for the bound
+          bus_injection_f32(ah3, al3, sw, sd, 3, inj);
+          float2 acc[3] = {make_float2(0.f, 0.f), make_float2(0.f, 0.f), make_float2(0.f, 0.f)};
+          for (int t = bptr[a]; t < bptr[a + 1]; ++t) {
+            const int cb = bcol[t];
+            if (cb >= 0 && !ZB_IN(cb, nb, 0x202u)) continue;
+            float2 d[3];
+#pragma unroll
+            for (int q2 = 0; q2 < 3; ++q2) {
+              if (cb >= 0) {
+                const int64_t g = (int64_t)(3 * cb + q2) * Bp + b;
+                const float2 xh = Vh[g], xl = Vl[g];
+                d[q2] = make_float2((xh.x - ah3[q2].x) + (xl.x - al3[q2].x),
+                                    (xh.y - ah3[q2].y) + (xl.y - al3[q2].y));
+              } else if (cb == -1) {
+                const float4 s4 = it.vs_df[q2];
+                d[q2] = make_float2((s4.x - ah3[q2].x) + (s4.y - al3[q2].x),
+                                    (s4.z - ah3[q2].y) + (s4.w - al3[q2].y));
+              } else {
+                d[q2] = make_float2(ah3[q2].x + al3[q2].x, ah3[q2].y + al3[q2].y);
+              }
+            }
+            const float4* yb = bval + (int64_t)t * 9;
+#pragma unroll
+            for (int p = 0; p < 3; ++p) {
+              float jr = 0.f, ji = 0.f;
+#pragma unroll
+              for (int q2 = 0; q2 < 3; ++q2) {
+                const float4 y = yb[p * 3 + q2];
+                jr = __fmaf_rn(y.x, d[q2].x, jr);
+                jr = __fmaf_rn(-y.z, d[q2].y, jr);
+                ji = __fmaf_rn(y.x, d[q2].y, ji);
+                ji = __fmaf_rn(y.z, d[q2].x, ji);
+              }
+              acc[p].x += jr;
+              acc[p].y += ji;
+              mag = fmaxf(mag, fmaxf(fabsf(jr), fabsf(ji)));
+            }
+          }
+#pragma unroll
+          for (int p = 0; p < 3; ++p) {
+            r[p] = make_float2(inj[p].x - acc[p].x, inj[p].y - acc[p].y);
+            mag = fmaxf(mag, fmaxf(fabsf(inj[p].x), fabsf(inj[p].y)));
+            const float m = fmaxf(fabsf(r[p].x), fabsf(r[p].y));
+            amax = (m == m) ? fmaxf(amax, m) : __int_as_float(0x7f800000);
+          }
+        } else {
         bus_injection_df(ah3, al3, sw, sd, 3, inj, injl);
         float ah[3][2], al[3][2];   // accumulators (re, im) per phase, hi / lo
 #pragma unroll
@@ -263,6 +319,7 @@ k_residual_group(GroupState* __restrict__ gs, const ItemDesc* __restrict__ items
           const float m = fmaxf(fabsf(r[p].x), fabsf(r[p].y));
           amax = (m == m) ? fmaxf(amax, m) : __int_as_float(0x7f800000);
         }
+        }
       }
       if constexpr (OUT == RES_F32) {
         if (a < nb && act) {
@@ -304,11 +361,16 @@ k_residual_group(GroupState* __restrict__ gs, const ItemDesc* __restrict__ items
   }
   if constexpr (OUT == RES_F32) return;   // the tree sweep needs no residual scale
   sred[warp][lane] = amax;
+  smag[warp][lane] = mag == mag ? mag : __int_as_float(0x7f800000);
   __syncthreads();
   if (warp == 0 && act) {
-    float m = sred[0][lane];
-    for (int w = 1; w < RES_WARPS; ++w) m = fmaxf(m, sred[w][lane]);
+    float m = sred[0][lane], g = smag[0][lane];
+    for (int w = 1; w < RES_WARPS; ++w) {
+      m = fmaxf(m, sred[w][lane]);
+      g = fmaxf(g, smag[w][lane]);
+    }
     atomicMax(reinterpret_cast<int*>(&it.amax[Bp + b]), __float_as_int(m));
+    if (lp) atomicMax(reinterpret_cast<int*>(&it.amax[2 * Bp + b]), __float_as_int(g));
   }
 }
 
@@ -601,16 +663,31 @@ __device__ __forceinline__ void decide_slot(const GroupState* __restrict__ gs, c
       dsum += part[2 * t + 1];
     }
     const double delta = gs->rule == ZBUS_CONV_SUMMAG ? fabs(dsum) : dmax;
+    // a sweep on the FP32 residual never stops a slot
+    const bool lp = it.amax[3 * it.Bp + b] != 0.f;
     if (!isfinite(delta)) {
       it.conv[b] = 0;
-    } else if (delta <= gs->tol) {
+    } else if (delta <= gs->tol && !lp) {
       it.conv[b] = 1;
     } else if (sw < gs->max_iter) {
       keep = 1;
     }
     if (!keep) it.st[b] = SLOT_DONE;
-    it.amax[b] = it.amax[it.Bp + b];
+    const float am = it.amax[it.Bp + b], prev = it.amax[b];
+    it.amax[b] = am;
     it.amax[it.Bp + b] = 0.f;
+    if (lp) {
+      // the next sweep stays on FP32 while max |r| exceeds 2^-11 of the
+      // largest line current or load current of this one (the FP32 rounding
+      // of the block products, a few ulps of those currents, is then below
+      // 2^-10 of the residual, under the FP16 rounding of R), still falls,
+      // and the step is above the stop tolerance; once off, the slot runs
+      // double-float to its stop
+      const float g = it.amax[2 * it.Bp + b];
+      const bool more = keep && am > 0x1p-11f * g && am < prev && delta > gs->tol;
+      it.amax[3 * it.Bp + b] = more ? 1.f : 0.f;
+      it.amax[2 * it.Bp + b] = 0.f;
+    }
   }
 }
 
@@ -1855,12 +1932,13 @@ zbus_status group_reset(Group* g, cudaStream_t st) {
 
 zbus_status group_admit(Group* g, int k, int64_t s0, int64_t B, const double* V0,
                         const double* S_wye, const double* S_delta, cudaStream_t st,
-                        bool v0_broadcast) {
+                        bool v0_broadcast, bool fp32_start) {
   if (B <= 0) return ZBUS_OK;
   const ItemDesc& d = g->h_items[k];
   k_slot_init<<<dim3((d.n + 31) / 32, (unsigned)((B + 31) / 32)), dim3(32, 8), 0, st>>>(
       g->d_state, g->d_items, k, (int)s0, (int)B, (const double2*)V0, v0_broadcast ? 0 : d.n,
-      g->nets[k]->w_df, (const double2*)S_wye, (const double2*)S_delta);
+      g->nets[k]->w_df, (const double2*)S_wye, (const double2*)S_delta,
+      (fp32_start && g->tree_groups == 0) ? 1 : 0);
   ZB_CUDA(cudaGetLastError());
   return ZBUS_OK;
 }

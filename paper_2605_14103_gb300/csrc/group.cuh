@@ -37,7 +37,9 @@ struct ItemDesc {
   uint8_t* st;              // [Bp] SLOT_*
   int32_t* it;              // [Bp] sweeps since admission
   uint8_t* conv;            // [Bp] stop rule met
-  float* amax;              // [2][Bp] max |r| of the previous / current sweep
+  float* amax;              // [4][Bp] max |r| of the previous / current sweep, the
+                            // current sweep's largest line or load current (FP32
+                            // sweeps), the FP32-sweep flag (nonzero: on)
   void* R;                  // [Bp][K_pad] fp16 / bf16 residual rows
   float* rinv;              // [Bp] inverse residual scales
   double* part;             // [Bp][ntn][2] per-tile step partials
@@ -133,10 +135,11 @@ zbus_status group_build(Group* g, const std::vector<zbus_network>& nets,
 zbus_status group_refresh_item(Group* g, int k, cudaStream_t st);
 void group_free(Group* g);
 // Run start for item k: slots [s0, s0 + B) from v^0 (V0 or w) and the loads
-// (FP64 [B][n]); admitted slots become active.
+// (FP64 [B][n]); admitted slots become active.  fp32_start: a cold start
+// (no V0) of the dense mixed forms begins with FP32 residual sweeps.
 zbus_status group_admit(Group* g, int k, int64_t s0, int64_t B, const double* V0,
                         const double* S_wye, const double* S_delta, cudaStream_t st,
-                        bool v0_broadcast = false);
+                        bool v0_broadcast = false, bool fp32_start = false);
 // Rebuild the tile list and the active count from the slot states (after
 // admissions between sweeps).
 zbus_status group_rebuild(Group* g, cudaStream_t st);

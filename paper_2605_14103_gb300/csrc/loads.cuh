@@ -118,4 +118,41 @@ __device__ __forceinline__ void bus_injection_df(const float2* vh, const float2*
   }
 }
 
+// FP32 injection at v = vh + vl rounded to FP32 (rules of bus_injection),
+// for the first sweeps of a cold start, where the residual is still far
+// above the FP32 rounding of the line currents.
+__device__ __forceinline__ float2 load_draw_f32(float2 S, float2 v) {
+  if (S.x == 0.f && S.y == 0.f) return make_float2(0.f, 0.f);
+  const float inv = __frcp_rn(__fmaf_rn(v.x, v.x, v.y * v.y));
+  return make_float2(__fmaf_rn(S.x, v.x, S.y * v.y) * inv, __fmaf_rn(S.x, v.y, -S.y * v.x) * inv);
+}
+
+__device__ __forceinline__ void bus_injection_f32(const float2* vh, const float2* vl,
+                                                  const float2* sw, const float2* sd, int m,
+                                                  float2* inj) {
+  float2 d[3];
+#pragma unroll
+  for (int p = 0; p < 3; ++p)
+    d[p] = (p < m && sw) ? load_draw_f32(sw[p], make_float2(vh[p].x + vl[p].x, vh[p].y + vl[p].y))
+                         : make_float2(0.f, 0.f);
+  if (sd && m == 3) {
+    float2 ib[3];   // branches ab, bc, ca
+#pragma unroll
+    for (int x = 0; x < 3; ++x) {
+      const int y = x == 2 ? 0 : x + 1;
+      const float2 u = make_float2((vh[x].x - vh[y].x) + (vl[x].x - vl[y].x),
+                                   (vh[x].y - vh[y].y) + (vl[x].y - vl[y].y));
+      ib[x] = load_draw_f32(sd[x], u);
+    }
+#pragma unroll
+    for (int x = 0; x < 3; ++x) {
+      const int w = x == 0 ? 2 : x - 1;
+      d[x].x += ib[x].x - ib[w].x;
+      d[x].y += ib[x].y - ib[w].y;
+    }
+  }
+#pragma unroll
+  for (int p = 0; p < 3; ++p) inj[p] = make_float2(-d[p].x, -d[p].y);
+}
+
 }  // namespace zbus

@@ -41,7 +41,7 @@ size_t form_extra(zbus_network net) {
 size_t slot_bytes(zbus_network net) {
   const size_t n = (size_t)net->n;
   return 40 * n + 24 * (size_t)net->n_pad + 4 * (size_t)round_up(2 * net->n, 64) +
-         64 * (size_t)(round_up(2 * net->n, 256) / 128 + 1) + 16 * n + 64;
+         64 * (size_t)(round_up(2 * net->n, 256) / 128 + 1) + 16 * n + 72;
 }
 
 // Forms a feeder's resident operands (the Gauss-Jordan inverse again if it
@@ -311,7 +311,7 @@ extern "C" zbus_status zbus_serve(const zbus_serve_config* cfg, zbus_network* po
       }
       const bool warm = r.warm_start && f.warm_valid;
       SV_CHECK(group_admit(&g, r.feeder, s0, r.B, warm ? (const double*)f.warm : nullptr,
-                           r.S_wye, r.S_delta, st, true));
+                           r.S_wye, r.S_delta, st, true, cfg->fp32_start != 0));
       std::fill(f.used.begin() + s0, f.used.begin() + s0 + r.B, 1);
       f.live.push_back(Inflight{r, s0, clock_s(t0), formed});
       live_total += 1;

@@ -33,7 +33,8 @@ class ZbusError(RuntimeError):
 class zbus_solve_opts(C.Structure):
     _fields_ = [("precision", C.c_int32), ("conv_rule", C.c_int32),
                 ("mismatch_tol", C.c_double), ("max_correction", C.c_int32),
-                ("profile", C.c_int32), ("reserved", C.c_double * 4)]
+                ("profile", C.c_int32), ("fp32_start", C.c_int32), ("reserved_i", C.c_int32),
+                ("reserved", C.c_double * 3)]
 
 
 class zbus_batch_item(C.Structure):
@@ -59,7 +60,8 @@ class zbus_serve_config(C.Structure):
     _fields_ = [("hbm_budget_bytes", C.c_uint64), ("max_slots", C.c_int32),
                 ("precision", C.c_int32), ("conv_rule", C.c_int32), ("max_iter", C.c_int32),
                 ("tol", C.c_double), ("mismatch_tol", C.c_double),
-                ("max_admit_per_sweep", C.c_int32), ("max_correction", C.c_int32)]
+                ("max_admit_per_sweep", C.c_int32), ("max_correction", C.c_int32),
+                ("fp32_start", C.c_int32)]
 
 
 class zbus_nr_opts(C.Structure):
@@ -370,7 +372,8 @@ def zbus_tune_set(precision, max_n, total_B, BN, stages):
 
 
 def solve_batched(networks, loads, tol=1e-8, max_iter=50, precision="fp16_scaled",
-                  rule="maxabs", mismatch_tol=1e-6, max_correction=8, stream=None):
+                  rule="maxabs", mismatch_tol=1e-6, max_correction=8, fp32_start=True,
+                  stream=None):
     """networks: [Network]; loads: [(S_wye, S_delta)] device tensors.  Returns [(V, iters, conv)]."""
     import torch
     o = zbus_solve_opts_default()
@@ -378,6 +381,7 @@ def solve_batched(networks, loads, tol=1e-8, max_iter=50, precision="fp16_scaled
     o.conv_rule = RULE[rule]
     o.mismatch_tol = mismatch_tol
     o.max_correction = max_correction
+    o.fp32_start = 1 if fp32_start else 0
     items, outs = [], []
     for net, (sw, sd) in zip(networks, loads):
         ref = sw if sw is not None else sd
@@ -426,7 +430,8 @@ def zbus_serve(cfg, pool_handles, source, sink, stream=None):
 
 def serve(networks, requests, hbm_budget_bytes=120 << 30, max_slots=4096,
           precision="fp16_scaled", tol=1e-8, max_iter=50, mismatch_tol=1e-6, rule="maxabs",
-          keep_results=True, max_admit_per_sweep=0, max_correction=8, stream=None):
+          keep_results=True, max_admit_per_sweep=0, max_correction=8, fp32_start=True,
+          stream=None):
     """Serve a list of requests over a pool of networks.
 
     requests: dicts with keys feeder, S_wye, S_delta (device tensors [B, n]),
@@ -485,6 +490,7 @@ def serve(networks, requests, hbm_budget_bytes=120 << 30, max_slots=4096,
     cfg.mismatch_tol = float(mismatch_tol)
     cfg.max_admit_per_sweep = int(max_admit_per_sweep)
     cfg.max_correction = int(max_correction)
+    cfg.fp32_start = 1 if fp32_start else 0
     zbus_serve(cfg, [net.handle for net in networks], source, sink, stream)
     for i, V, it, cv in keep:
         if out[i] is not None:
@@ -547,7 +553,7 @@ class Network:
 
     def solve(self, S_wye, S_delta=None, V_init=None, tol=1e-8, max_iter=50,
               precision="fp64", rule="maxabs", mismatch_tol=1e-6, max_correction=8,
-              profile=False, out=None, stream=None):
+              profile=False, out=None, stream=None, fp32_start=True):
         """Returns (V [B,n] complex128, iters int32[B], converged uint8[B]) where the
         loads live: on the device, or in host memory (results valid once the
         stream has synchronised)."""
@@ -564,6 +570,7 @@ class Network:
         o.mismatch_tol = mismatch_tol
         o.max_correction = max_correction
         o.profile = 1 if profile else 0
+        o.fp32_start = 1 if fp32_start else 0
         V, it, cv = out
         zbus_solve(self.handle, S_wye, S_delta, V_init, tol, max_iter, o, V, it, cv, stream)
         return V, it, cv

@@ -192,11 +192,14 @@ def test_mixed_zero_load_and_divergence(mode):
     f = F.make_feeder(30, 15, delta_frac=0.3)
     z = np.zeros((5, f.n), dtype=np.complex128)
     net = zbus.Network.from_feeder(f)
-    V, it, cv = net.solve(dev(z), dev(z), precision=mode)
     _, w = net.get_z()
-    assert (cv.cpu().numpy() == 1).all() and (it.cpu().numpy() == 1).all()
-    # the FP64 residual of w is rounding noise, not exactly zero: V = w + O(1e-15)
-    assert (V - w.expand(5, -1)).abs().max().item() <= 1e-12
+    # one sweep in double-float; with the FP32 start sweeps the first sweep
+    # cannot stop a scenario, so the second one (double-float) does
+    for fp32_start, n_it in ((False, 1), (True, 1 if mode == "tree" else 2)):
+        V, it, cv = net.solve(dev(z), dev(z), precision=mode, fp32_start=fp32_start)
+        assert (cv.cpu().numpy() == 1).all() and (it.cpu().numpy() == n_it).all()
+        # the FP64 residual of w is rounding noise, not exactly zero: V = w + O(1e-15)
+        assert (V - w.expand(5, -1)).abs().max().item() <= 1e-12
     f, Sw, Sd, _ = F.make_workload("feeder128_b4096", B=6)
     Sw, Sd = Sw * 60.0, Sd * 60.0
     Sw[0] /= 60.0
@@ -351,3 +354,59 @@ def test_paper_stop_rule_sum_of_magnitudes(mode):
     V, it, cv = net.solve(dev(Sw), dev(Sd), tol=w.tol, max_iter=w.max_iter, precision=mode,
                           rule="summag")
     check(net, f, Sw, Sd, ref, V, it, cv)
+
+
+@pytest.mark.parametrize("mode", ["fp16_scaled", "bf16x2"])
+def test_fp32_start_sweeps(mode):
+    """Cold starts of the dense mixed forms begin with FP32 residual sweeps.
+
+    Against double-float from the first sweep (fp32_start=False): the same
+    flags, both within the parity bar of the oracle, iteration counts within
+    one; warm starts never take the FP32 path (bitwise equal); no scenario
+    stops on an FP32 sweep (a tolerance every step meets: one sweep without
+    the FP32 start, two with it); the results of a scenario do not depend on
+    the batch around it (lanes of a warp on different paths)."""
+    f, Sw, Sd, w = F.make_workload("feeder128_b4096", B=256)
+    net = zbus.Network.from_feeder(f)
+    ref = oracle(f, Sw, Sd)
+    V1, it1, cv1 = net.solve(dev(Sw), dev(Sd), precision=mode)
+    V0, it0, cv0 = net.solve(dev(Sw), dev(Sd), precision=mode, fp32_start=False)
+    check(net, f, Sw, Sd, ref, V1, it1, cv1)
+    check(net, f, Sw, Sd, ref, V0, it0, cv0)
+    assert torch.equal(cv1, cv0)
+    d_it = (it1 - it0).cpu().numpy()
+    assert d_it.min() >= -1 and d_it.max() <= 1
+    assert (V1 - V0).abs().max().item() <= 1e-8
+
+    Vw = dev(ref["V"] * 0.999)
+    Va, ita, cva = net.solve(dev(Sw), dev(Sd), V_init=Vw, precision=mode)
+    Vb, itb, cvb = net.solve(dev(Sw), dev(Sd), V_init=Vw, precision=mode, fp32_start=False)
+    assert torch.equal(Va, Vb) and torch.equal(ita, itb) and torch.equal(cva, cvb)
+
+    # (the FP64 test passes whatever the mismatch, so no correction sweep adds
+    # iterations)
+    loose = dict(tol=10.0, precision=mode, mismatch_tol=1e9, max_correction=0)
+    _, ita, cva = net.solve(dev(Sw[:40]), dev(Sd[:40]), fp32_start=False, **loose)
+    assert (ita.cpu().numpy() == 1).all() and cva.cpu().numpy().all()
+    _, ita, cva = net.solve(dev(Sw[:40]), dev(Sd[:40]), **loose)
+    assert (ita.cpu().numpy() == 2).all() and cva.cpu().numpy().all()
+
+    # a batch in which scenarios leave the FP32 path at different sweeps
+    # (loads scaled per scenario), solved whole and as a subset
+    scale = np.linspace(0.05, 1.6, 256)[:, None]
+    Sws, Sds = Sw * scale, Sd * scale
+    V, it, cv = net.solve(dev(Sws), dev(Sds), precision=mode)
+    perm = np.random.default_rng(5).permutation(256)[:61]
+    V2, it2, cv2 = net.solve(dev(Sws[perm]), dev(Sds[perm]), precision=mode)
+    ti = torch.from_numpy(perm).cuda()
+    assert torch.equal(V2, V[ti]) and torch.equal(it2, it[ti]) and torch.equal(cv2, cv[ti])
+    assert len(np.unique(it.cpu().numpy())) > 1
+
+
+def test_fp32_start_leaves_the_tree_form_alone():
+    f, Sw, Sd, w = F.make_workload("feeder128_b4096", B=64)
+    net = zbus.Network.from_feeder(f)
+    a = net.solve(dev(Sw), dev(Sd), precision="tree")
+    b = net.solve(dev(Sw), dev(Sd), precision="tree", fp32_start=False)
+    for x, y in zip(a, b):
+        assert torch.equal(x, y)
