@@ -91,8 +91,8 @@ typedef struct {
   int32_t profile;         /* 1: run the sweeps from the host with CUDA events
                               around every kernel on cuda_stream, for
                               zbus_last_profile; 0: device-resident loop */
-  int32_t fp32_start;      /* dense mixed modes (BF16X2, FP16_SCALED), cold
-                              starts (V_init NULL): 1 (default) = a scenario's
+  int32_t fp32_start;      /* mixed modes (BF16X2, FP16_SCALED, TREE_SWEEP),
+                              cold starts (V_init NULL): 1 (default) = a scenario's
                               first sweeps form the defect residual in FP32
                               (block products with the FP32 part of Y, load
                               currents at the FP32 voltage) as long as its max

@@ -150,6 +150,28 @@ __global__ void k_group_params(GroupState* gs, double tol, int max_iter, int rul
   gs->err = 0;
 }
 
+// One block of the FP32 residual: J = Y_ab d (d = v_b - v_a, the slack's
+// voltage minus v_a, or v_a itself for the shunt term) with the hi part of
+// Y, added to acc, the largest |Re J|, |Im J| kept in mag.
+__device__ __forceinline__ void block_f32(const float2* d, const float4* __restrict__ yb,
+                                          float2* acc, float& mag) {
+#pragma unroll
+  for (int p = 0; p < 3; ++p) {
+    float jr = 0.f, ji = 0.f;
+#pragma unroll
+    for (int q2 = 0; q2 < 3; ++q2) {
+      const float4 y = yb[p * 3 + q2];
+      jr = __fmaf_rn(y.x, d[q2].x, jr);
+      jr = __fmaf_rn(-y.z, d[q2].y, jr);
+      ji = __fmaf_rn(y.x, d[q2].y, ji);
+      ji = __fmaf_rn(y.z, d[q2].x, ji);
+    }
+    acc[p].x += jr;
+    acc[p].y += ji;
+    mag = fmaxf(mag, fmaxf(fabsf(jr), fabsf(ji)));
+  }
+}
+
 // ---------------------------------------------------------------------------
 // Defect residual, one slot per lane, double-float, branch form per bus a
 // (rows 3a..3a+2):
@@ -185,7 +207,7 @@ k_residual_group(GroupState* __restrict__ gs, const ItemDesc* __restrict__ items
   // FP32 sweep for this slot (its flag, set at a cold start and kept by the
   // stop test while the residual stays above 2^-11 of the largest line
   // current); lanes of a warp may differ and then take both paths
-  const bool lp = OUT != RES_F32 && act && it.amax[3 * it.Bp + b] != 0.f;
+  const bool lp = act && it.amax[3 * it.Bp + b] != 0.f;
   float c = 1.f;
   if (OUT != RES_F32) {
     const float ap = it.amax[b];
@@ -243,22 +265,7 @@ k_residual_group(GroupState* __restrict__ gs, const ItemDesc* __restrict__ items
                 d[q2] = make_float2(ah3[q2].x + al3[q2].x, ah3[q2].y + al3[q2].y);
               }
             }
-            const float4* yb = bval + (int64_t)t * 9;
-#pragma unroll
-            for (int p = 0; p < 3; ++p) {
-              float jr = 0.f, ji = 0.f;
-#pragma unroll
-              for (int q2 = 0; q2 < 3; ++q2) {
-                const float4 y = yb[p * 3 + q2];
-                jr = __fmaf_rn(y.x, d[q2].x, jr);
-                jr = __fmaf_rn(-y.z, d[q2].y, jr);
-                ji = __fmaf_rn(y.x, d[q2].y, ji);
-                ji = __fmaf_rn(y.z, d[q2].x, ji);
-              }
-              acc[p].x += jr;
-              acc[p].y += ji;
-              mag = fmaxf(mag, fmaxf(fabsf(jr), fabsf(ji)));
-            }
+            block_f32(d, bval + (int64_t)t * 9, acc, mag);
           }
 #pragma unroll
           for (int p = 0; p < 3; ++p) {
@@ -359,7 +366,10 @@ k_residual_group(GroupState* __restrict__ gs, const ItemDesc* __restrict__ items
     }
     __syncwarp();
   }
-  if constexpr (OUT == RES_F32) return;   // the tree sweep needs no residual scale
+  // the tree sweep needs no residual scale, only the FP32-sweep bounds
+  if constexpr (OUT == RES_F32) {
+    if (!__syncthreads_or(lp)) return;
+  }
   sred[warp][lane] = amax;
   smag[warp][lane] = mag == mag ? mag : __int_as_float(0x7f800000);
   __syncthreads();
@@ -956,14 +966,23 @@ k_tree_group(GroupState* __restrict__ gs, const ItemDesc* __restrict__ items,
       const int sw = it.it[b] + 1;
       it.it[b] = sw;
       const double delta = summag ? fabs((double)u) : (double)m;
+      const bool lp = it.amax[3 * it.Bp + b] != 0.f;   // FP32 residual (rules of decide_slot)
       if (!isfinite(delta)) {
         it.conv[b] = 0;
-      } else if (delta <= gs->tol) {
+      } else if (delta <= gs->tol && !lp) {
         it.conv[b] = 1;
       } else if (sw < gs->max_iter) {
         keep = 1;
       }
       if (!keep) it.st[b] = SLOT_DONE;
+      if (lp) {
+        const float am = it.amax[it.Bp + b], prev = it.amax[b], g = it.amax[2 * it.Bp + b];
+        const bool more = keep && am > 0x1p-11f * g && am < prev && delta > gs->tol;
+        it.amax[3 * it.Bp + b] = more ? 1.f : 0.f;
+        it.amax[b] = am;
+        it.amax[it.Bp + b] = 0.f;
+        it.amax[2 * it.Bp + b] = 0.f;
+      }
     }
     const int still = __popc(__ballot_sync(0xffffffffu, keep));
     if (lane == 0) tree_block_done(gs, still, h, use_handle);
@@ -1937,8 +1956,7 @@ zbus_status group_admit(Group* g, int k, int64_t s0, int64_t B, const double* V0
   const ItemDesc& d = g->h_items[k];
   k_slot_init<<<dim3((d.n + 31) / 32, (unsigned)((B + 31) / 32)), dim3(32, 8), 0, st>>>(
       g->d_state, g->d_items, k, (int)s0, (int)B, (const double2*)V0, v0_broadcast ? 0 : d.n,
-      g->nets[k]->w_df, (const double2*)S_wye, (const double2*)S_delta,
-      (fp32_start && g->tree_groups == 0) ? 1 : 0);
+      g->nets[k]->w_df, (const double2*)S_wye, (const double2*)S_delta, fp32_start ? 1 : 0);
   ZB_CUDA(cudaGetLastError());
   return ZBUS_OK;
 }

@@ -136,7 +136,7 @@ zbus_status group_refresh_item(Group* g, int k, cudaStream_t st);
 void group_free(Group* g);
 // Run start for item k: slots [s0, s0 + B) from v^0 (V0 or w) and the loads
 // (FP64 [B][n]); admitted slots become active.  fp32_start: a cold start
-// (no V0) of the dense mixed forms begins with FP32 residual sweeps.
+// (no V0) begins with FP32 residual sweeps.
 zbus_status group_admit(Group* g, int k, int64_t s0, int64_t B, const double* V0,
                         const double* S_wye, const double* S_delta, cudaStream_t st,
                         bool v0_broadcast = false, bool fp32_start = false);

@@ -195,7 +195,7 @@ def test_mixed_zero_load_and_divergence(mode):
     _, w = net.get_z()
     # one sweep in double-float; with the FP32 start sweeps the first sweep
     # cannot stop a scenario, so the second one (double-float) does
-    for fp32_start, n_it in ((False, 1), (True, 1 if mode == "tree" else 2)):
+    for fp32_start, n_it in ((False, 1), (True, 2)):
         V, it, cv = net.solve(dev(z), dev(z), precision=mode, fp32_start=fp32_start)
         assert (cv.cpu().numpy() == 1).all() and (it.cpu().numpy() == n_it).all()
         # the FP64 residual of w is rounding noise, not exactly zero: V = w + O(1e-15)
@@ -356,9 +356,9 @@ def test_paper_stop_rule_sum_of_magnitudes(mode):
     check(net, f, Sw, Sd, ref, V, it, cv)
 
 
-@pytest.mark.parametrize("mode", ["fp16_scaled", "bf16x2"])
+@pytest.mark.parametrize("mode", MODES)
 def test_fp32_start_sweeps(mode):
-    """Cold starts of the dense mixed forms begin with FP32 residual sweeps.
+    """Cold starts of the mixed forms begin with FP32 residual sweeps.
 
     Against double-float from the first sweep (fp32_start=False): the same
     flags, both within the parity bar of the oracle, iteration counts within
@@ -402,11 +402,3 @@ def test_fp32_start_sweeps(mode):
     assert torch.equal(V2, V[ti]) and torch.equal(it2, it[ti]) and torch.equal(cv2, cv[ti])
     assert len(np.unique(it.cpu().numpy())) > 1
 
-
-def test_fp32_start_leaves_the_tree_form_alone():
-    f, Sw, Sd, w = F.make_workload("feeder128_b4096", B=64)
-    net = zbus.Network.from_feeder(f)
-    a = net.solve(dev(Sw), dev(Sd), precision="tree")
-    b = net.solve(dev(Sw), dev(Sd), precision="tree", fp32_start=False)
-    for x, y in zip(a, b):
-        assert torch.equal(x, y)
