@@ -301,11 +301,12 @@ KERNELS = {"fp64": ("k_currents_f64", "k_gemm3m_f64", "k_decide+k_compact"),
 DTYPE = {"fp64": "f64", "fp16_scaled": "fp16_scaled+f64", "bf16x2": "bf16x2+f64",
          "tree": "f32+f64"}
 MIXED_OUTSIDE = ("k_group_reset+k_slot_init+k_group_params+k_finish_group(start)+k_slot_merge"
-                 "+k_check+k_corr_setup+k_corr_select+k_corr_end")
-# launches outside the sweep loop per solve (with no scenario to correct), and per sweep
-# (the tensor-core forms fold their stop test into the sweep end up to 1024 slots)
-OUTSIDE = {"fp64": ("k_init", 1), "tree": (MIXED_OUTSIDE, 9),
-           "fp16_scaled": (MIXED_OUTSIDE, 9), "bf16x2": (MIXED_OUTSIDE, 9)}
+                 "+k_branch_f64+k_check+k_corr_setup+k_corr_select+k_corr_end")
+# launches outside the sweep loop per solve (with no scenario to correct; k_branch_f64 runs
+# where every line's two blocks are identical, as in every feeder of the workloads), and per
+# sweep (the tensor-core forms fold their stop test into the sweep end up to 1024 slots)
+OUTSIDE = {"fp64": ("k_init", 1), "tree": (MIXED_OUTSIDE, 10),
+           "fp16_scaled": (MIXED_OUTSIDE, 10), "bf16x2": (MIXED_OUTSIDE, 10)}
 PER_SWEEP = {"fp64": 4, "fp16_scaled": 4, "bf16x2": 4, "tree": 2}
 
 
