@@ -205,7 +205,7 @@ k_residual_group(GroupState* __restrict__ gs, const ItemDesc* __restrict__ items
   const bool act = it.st[b] == SLOT_ACTIVE;
   if (!__syncthreads_or(act)) return;   // all 32 slots of this group are idle
   // FP32 sweep for this slot (its flag, set at a cold start and kept by the
-  // stop test while the residual stays above 2^-11 of the largest line
+  // stop test while the residual stays above 2^-13 of the largest line
   // current); lanes of a warp may differ and then take both paths
   const bool lp = act && it.amax[3 * it.Bp + b] != 0.f;
   float c = 1.f;
@@ -687,14 +687,14 @@ __device__ __forceinline__ void decide_slot(const GroupState* __restrict__ gs, c
     it.amax[b] = am;
     it.amax[it.Bp + b] = 0.f;
     if (lp) {
-      // the next sweep stays on FP32 while max |r| exceeds 2^-11 of the
+      // the next sweep stays on FP32 while max |r| exceeds 2^-13 of the
       // largest line current or load current of this one (the FP32 rounding
       // of the block products, a few ulps of those currents, is then below
-      // 2^-10 of the residual, under the FP16 rounding of R), still falls,
-      // and the step is above the stop tolerance; once off, the slot runs
-      // double-float to its stop
+      // 2^-8 of the residual, under 1/30 of what one sweep removes), still
+      // falls, and the step is above the stop tolerance; once off, the slot
+      // runs double-float to its stop
       const float g = it.amax[2 * it.Bp + b];
-      const bool more = keep && am > 0x1p-11f * g && am < prev && delta > gs->tol;
+      const bool more = keep && am > 0x1p-13f * g && am < prev && delta > gs->tol;
       it.amax[3 * it.Bp + b] = more ? 1.f : 0.f;
       it.amax[2 * it.Bp + b] = 0.f;
     }
@@ -977,7 +977,7 @@ k_tree_group(GroupState* __restrict__ gs, const ItemDesc* __restrict__ items,
       if (!keep) it.st[b] = SLOT_DONE;
       if (lp) {
         const float am = it.amax[it.Bp + b], prev = it.amax[b], g = it.amax[2 * it.Bp + b];
-        const bool more = keep && am > 0x1p-11f * g && am < prev && delta > gs->tol;
+        const bool more = keep && am > 0x1p-13f * g && am < prev && delta > gs->tol;
         it.amax[3 * it.Bp + b] = more ? 1.f : 0.f;
         it.amax[b] = am;
         it.amax[it.Bp + b] = 0.f;
@@ -1123,33 +1123,60 @@ k_finish_group(GroupState* __restrict__ gs, const ItemDesc* __restrict__ items, 
 
 // ---------------------------------------------------------------------------
 // Collection: slots [s0, s0 + B) of item k merged into the FP64 output
-// [B][n], with their sweep counts and flags; the slots become free.
+// [B][n], with their sweep counts and flags; the slots become free.  Tiles of
+// MERGE_T unknowns x MERGE_T slots: every thread issues its 32 loads (hi and
+// lo of 8 unknowns x 2 slots, 256-byte row pieces) before converting any, and
+// every output row goes out as 1 KB of consecutive unknowns.
 // ---------------------------------------------------------------------------
-__global__ void k_slot_merge(const ItemDesc* __restrict__ items, int k, int s0, int B,
-                             double2* __restrict__ V, int32_t* __restrict__ iters,
-                             uint8_t* __restrict__ conv, unsigned long long* __restrict__ mmax) {
-  __shared__ double2 t[32][33];
+constexpr int MERGE_T = 64;
+constexpr size_t MERGE_SMEM = (size_t)MERGE_T * (MERGE_T + 1) * sizeof(double2);
+
+__global__ void __launch_bounds__(256)
+k_slot_merge(const ItemDesc* __restrict__ items, int k, int s0, int B,
+             double2* __restrict__ V, int32_t* __restrict__ iters,
+             uint8_t* __restrict__ conv, unsigned long long* __restrict__ mmax) {
+  extern __shared__ double2 tm[];   // [MERGE_T slots][MERGE_T + 1 unknowns]
   const ItemDesc it = items[k];
   const int n = it.n, Bp = it.Bp;
-  const int j0 = blockIdx.x * 32, b0 = blockIdx.y * 32;
+  const int j0 = blockIdx.x * MERGE_T, b0 = blockIdx.y * MERGE_T;
   const int tx = threadIdx.x, ty = threadIdx.y;
-  for (int r = ty; r < 32; r += 8) {
-    const int j = j0 + r, b = b0 + tx;
-    double2 v = make_double2(0.0, 0.0);
-    if (j < n && b < B) {
-      const int64_t g = (int64_t)j * Bp + s0 + b;
-      const float2 h = it.Vh[g], l = it.Vl[g];
-      v = make_double2(f2d_exact(h.x) + f2d_exact(l.x), f2d_exact(h.y) + f2d_exact(l.y));
+  const float2* __restrict__ Vh = it.Vh;
+  const float2* __restrict__ Vl = it.Vl;
+  float2 h[8][2], l[8][2];
+#pragma unroll
+  for (int i = 0; i < 8; ++i) {
+    const int j = j0 + ty + 8 * i;
+#pragma unroll
+    for (int c = 0; c < 2; ++c) {
+      const int b = b0 + tx + 32 * c;
+      h[i][c] = l[i][c] = make_float2(0.f, 0.f);
+      if (j < n && b < B) {
+        const int64_t g = (int64_t)j * Bp + s0 + b;
+        h[i][c] = Vh[g];
+        l[i][c] = Vl[g];
+      }
     }
-    t[tx][r] = v;
   }
+#pragma unroll
+  for (int i = 0; i < 8; ++i)
+#pragma unroll
+    for (int c = 0; c < 2; ++c)
+      tm[(tx + 32 * c) * (MERGE_T + 1) + ty + 8 * i] =
+          make_double2(f2d_exact(h[i][c].x) + f2d_exact(l[i][c].x),
+                       f2d_exact(h[i][c].y) + f2d_exact(l[i][c].y));
   __syncthreads();
-  for (int r = ty; r < 32; r += 8) {
-    const int b = b0 + r, j = j0 + tx;
-    if (b < B && j < n) V[(int64_t)b * n + j] = t[r][tx];
+#pragma unroll
+  for (int i = 0; i < 8; ++i) {
+    const int r = ty + 8 * i, b = b0 + r;
+    if (b >= B) continue;
+#pragma unroll
+    for (int c = 0; c < 2; ++c) {
+      const int j = j0 + tx + 32 * c;
+      if (j < n) V[(int64_t)b * n + j] = tm[r * (MERGE_T + 1) + tx + 32 * c];
+    }
   }
-  if (blockIdx.x == 0 && ty == 0) {
-    const int b = b0 + tx;
+  if (blockIdx.x == 0 && ty < 2) {
+    const int b = b0 + tx + 32 * ty;
     if (b < B) {
       iters[b] = it.it[s0 + b];
       conv[b] = it.conv[s0 + b];
@@ -1841,6 +1868,8 @@ zbus_status group_build(Group* g, const std::vector<zbus_network>& nets,
     ZB_CUDA(cudaFuncSetAttribute(k_tree_group<8, 2, false>,
                                  cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
   }
+  ZB_CUDA(cudaFuncSetAttribute(k_slot_merge, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                               (int)MERGE_SMEM));
   g->mt_total = mt;
   g->max_tiles = tiles;
 
@@ -2154,7 +2183,8 @@ zbus_status group_collect(Group* g, int k, int64_t s0, int64_t B, double* V_out,
   zbus_network net = g->nets[k];
   if (!net->ws.mm || B > net->ws.cap_B) return fail(ZBUS_ERR_ARG, "collect: batch above workspace");
   unsigned long long* mmax = reinterpret_cast<unsigned long long*>(net->ws.mm);
-  k_slot_merge<<<dim3((net->n + 31) / 32, (unsigned)((B + 31) / 32)), dim3(32, 8), 0, st>>>(
+  k_slot_merge<<<dim3((net->n + MERGE_T - 1) / MERGE_T, (unsigned)((B + MERGE_T - 1) / MERGE_T)),
+                 dim3(32, 8), MERGE_SMEM, st>>>(
       g->d_items, k, (int)s0, (int)B, (double2*)V_out, iters, converged, mmax);
   int gx = 0, ny = 0;
   check_grid(B, net->n, g->num_sms, &gx, &ny);
