@@ -100,8 +100,8 @@ __global__ void k_slot_init(GroupState* __restrict__ gs, const ItemDesc* __restr
         it.Vh[g] = make_float2(wd.x, wd.z);
         it.Vl[g] = make_float2(wd.y, wd.w);
       }
-      it.Swf[g] = make_float2(__double2float_rn(tw[tx][r].x), __double2float_rn(tw[tx][r].y));
-      it.Sdf[g] = make_float2(__double2float_rn(td[tx][r].x), __double2float_rn(td[tx][r].y));
+      it.Swf[g] = make_float2(d2f_rn(tw[tx][r].x), d2f_rn(tw[tx][r].y));
+      it.Sdf[g] = make_float2(d2f_rn(td[tx][r].x), d2f_rn(td[tx][r].y));
     }
   }
   if (blockIdx.x == 0 && ty == 0) {
