@@ -1188,10 +1188,11 @@ k_slot_merge(const ItemDesc* __restrict__ items, int k, int s0, int B,
 
 // 1 / d: a single-precision reciprocal refined by two Newton-Raphson steps
 // r <- r (2 - d r) (quadratic convergence, 24 -> 48 -> beyond 53 bits);
-// plain division outside the single-precision range.
+// plain division outside the single-precision range.  The conversions to
+// and from float are the integer ones (the FP64 units stay on the FMAs).
 __device__ __forceinline__ double recip64(double d) {
   if (!(d > 1e-30 && d < 1e30)) return 1.0 / d;
-  double r = (double)__frcp_rn((float)d);
+  double r = f2d_exact(__frcp_rn(d2f_rn(d)));
   r = r * fma(-d, r, 2.0);
   r = r * fma(-d, r, 2.0);
   return r;
@@ -1278,10 +1279,10 @@ __device__ __forceinline__ void admittance_sum_f64(const double2* __restrict__ v
 // FP64 check of one bus of one scenario, in power form: for its unknowns j,
 //   dS_j = v_j conj((Y_LL v + Y_Ls v_s)_j) - v_j conj(i_j(v)),  |dS_j| = |v_j| |r_j|
 // with the wye term exactly S_j (v conj(conj(S / v)) = S, no division) and the
-// delta term v_j conj(drawn) from FP64 branch currents.  Returns the largest
-// |dS_j|^2 of the bus (+inf for a NaN).  sw, sd: the scenario's load rows or
-// null.
-__device__ __forceinline__ double check_bus_f64(const double2* __restrict__ vg,
+// delta term v_j conj(drawn) from FP64 branch currents.  Returns the bit
+// pattern of the largest |dS_j|^2 of the bus (+inf for a NaN), which orders
+// like the value.  sw, sd: the scenario's load rows or null.
+__device__ __forceinline__ unsigned long long check_bus_f64(const double2* __restrict__ vg,
                                                 const double2* __restrict__ sw,
                                                 const double2* __restrict__ sd, int a, int nb,
                                                 const int32_t* __restrict__ bptr,
@@ -1333,11 +1334,16 @@ __device__ __forceinline__ double check_bus_f64(const double2* __restrict__ vg,
       }
     }
   }
-  double worst = 0.0;
+  // the largest |dS_j|^2 by its bit pattern (non-negative doubles order like
+  // their bits; a NaN, whatever its sign bit, counts as +inf), compared on
+  // the integer units
+  unsigned long long worst = 0ull;
 #pragma unroll
   for (int p = 0; p < 3; ++p) {
     const double e = fma(sr[p], sr[p], si[p] * si[p]);
-    worst = (e != e) ? INFINITY : fmax(worst, e);
+    unsigned long long eb = (unsigned long long)__double_as_longlong(e) & 0x7FFFFFFFFFFFFFFFull;
+    eb = eb > 0x7FF0000000000000ull ? 0x7FF0000000000000ull : eb;
+    worst = eb > worst ? eb : worst;
   }
   return worst;
 }
@@ -1408,7 +1414,7 @@ k_check(const double2* __restrict__ V, const double2* __restrict__ Sw,
         const double2* __restrict__ bval, double2 vs0, double2 vs1, double2 vs2,
         unsigned long long* __restrict__ mmax, int ny, const double2* __restrict__ J,
         const int32_t* __restrict__ br, int nbr) {
-  __shared__ double red[CHECK_WARPS][32];
+  __shared__ unsigned long long red[CHECK_WARPS][32];
   const int lane = threadIdx.x, ty = threadIdx.y;
   const int bx = blockIdx.x / ny, by = blockIdx.x % ny;   // scenario group, bus stride
   const int b = bx * 32 + lane;
@@ -1416,19 +1422,22 @@ k_check(const double2* __restrict__ V, const double2* __restrict__ Sw,
   if (__ballot_sync(0xffffffffu, live) == 0u) return;   // same for every warp of the block
   const int64_t row = (int64_t)(b < B ? b : B - 1) * n;
   const double2 vs[3] = {vs0, vs1, vs2};
-  double worst = 0.0;   // max |dS|^2
+  unsigned long long worst = 0ull;   // max |dS|^2, as its bit pattern
   const int nb = n / 3;
   const double2* jg = J ? J + (b < B ? b : B - 1) : nullptr;
-  for (int a = by * CHECK_WARPS + ty; a < nb; a += ny * CHECK_WARPS)
-    worst = fmax(worst, check_bus_f64(V + row, Sw ? Sw + row : nullptr, Sd ? Sd + row : nullptr,
-                                      a, nb, bptr, bcol, bval, vs, jg, br, nbr, (int64_t)B));
+  for (int a = by * CHECK_WARPS + ty; a < nb; a += ny * CHECK_WARPS) {
+    const unsigned long long w =
+        check_bus_f64(V + row, Sw ? Sw + row : nullptr, Sd ? Sd + row : nullptr, a, nb, bptr,
+                      bcol, bval, vs, jg, br, nbr, (int64_t)B);
+    worst = w > worst ? w : worst;
+  }
   red[ty][lane] = worst;
   __syncthreads();
   if (ty == 0 && live) {
-    double x = red[0][lane];
+    unsigned long long x = red[0][lane];
 #pragma unroll
-    for (int w = 1; w < CHECK_WARPS; ++w) x = fmax(x, red[w][lane]);
-    if (x > 0.0) atomicMax(&mmax[b], (unsigned long long)__double_as_longlong(x));
+    for (int w = 1; w < CHECK_WARPS; ++w) x = red[w][lane] > x ? red[w][lane] : x;
+    if (x > 0ull) atomicMax(&mmax[b], x);
   }
 }
 
@@ -1617,7 +1626,7 @@ __global__ void __launch_bounds__(32 * CHECK_WARPS)
 k_corr_check(const SolveCtx* __restrict__ ctx, int n, const int32_t* __restrict__ bptr,
              const int32_t* __restrict__ bcol, const double2* __restrict__ bval, double2 vs0,
              double2 vs1, double2 vs2, int ny) {
-  __shared__ double red[CHECK_WARPS][32];
+  __shared__ unsigned long long red[CHECK_WARPS][32];
   const int lane = threadIdx.x, ty = threadIdx.y;
   const int bx = blockIdx.x / ny, by = blockIdx.x % ny;
   const int i = bx * 32 + lane;
@@ -1629,18 +1638,21 @@ k_corr_check(const SolveCtx* __restrict__ ctx, int n, const int32_t* __restrict_
   const double2 vs[3] = {vs0, vs1, vs2};
   const double2* Sw = ctx->S_wye;
   const double2* Sd = ctx->S_del;
-  double worst = 0.0;
+  unsigned long long worst = 0ull;
   const int nb = n / 3;
-  for (int a = by * CHECK_WARPS + ty; a < nb; a += ny * CHECK_WARPS)
-    worst = fmax(worst, check_bus_f64(ctx->V + row, Sw ? Sw + row : nullptr,
-                                      Sd ? Sd + row : nullptr, a, nb, bptr, bcol, bval, vs));
+  for (int a = by * CHECK_WARPS + ty; a < nb; a += ny * CHECK_WARPS) {
+    const unsigned long long w = check_bus_f64(ctx->V + row, Sw ? Sw + row : nullptr,
+                                               Sd ? Sd + row : nullptr, a, nb, bptr, bcol,
+                                               bval, vs);
+    worst = w > worst ? w : worst;
+  }
   red[ty][lane] = worst;
   __syncthreads();
   if (ty == 0 && live) {
-    double x = red[0][lane];
+    unsigned long long x = red[0][lane];
 #pragma unroll
-    for (int w = 1; w < CHECK_WARPS; ++w) x = fmax(x, red[w][lane]);
-    if (x > 0.0) atomicMax(&ctx->mmax[b], (unsigned long long)__double_as_longlong(x));
+    for (int w = 1; w < CHECK_WARPS; ++w) x = red[w][lane] > x ? red[w][lane] : x;
+    if (x > 0ull) atomicMax(&ctx->mmax[b], x);
   }
 }
 
