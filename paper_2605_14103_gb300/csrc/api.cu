@@ -688,10 +688,28 @@ zbus_status solve_host(zbus_network net, int64_t B, const double* S_wye, const d
                        const zbus_solve_opts& o, double* V_out, int32_t* iters,
                        uint8_t* converged, cudaStream_t st) {
   // four chunks for the defect forms (whose sweeps take about as long as the
-  // copies); one for the plain method, whose FP64 sweeps take some fifty
-  // times longer than its copies and run less efficiently on smaller batches
-  const int64_t C = (B <= 2048 || o.precision == ZBUS_FP64) ? B
-                                                            : std::max<int64_t>(1024, (B + 3) / 4);
+  // copies), 1/8, 3/8, 3/8 and 1/8 of the batch in multiples of 128: the
+  // small first chunk shortens the copy nothing overlaps at the start, the
+  // small last one the copy back at the end, and each middle chunk's copy
+  // fits under the solve of the chunk before it.  One chunk for the plain
+  // method, whose FP64 sweeps take some fifty times longer than its copies
+  // and run less efficiently on smaller batches, and for inputs under 256
+  // MB (about a millisecond of copies), which a chunk's fixed cost outweighs
+  const size_t n2u = (size_t)(net->phased ? net->n_user : net->n) * 2;
+  const size_t in_bytes = (size_t)B * n2u * sizeof(double) *
+                          ((S_wye ? 1 : 0) + (S_delta ? 1 : 0) + (V_init ? 1 : 0));
+  std::vector<int64_t> lo{0};
+  if (B <= 2048 || o.precision == ZBUS_FP64 || in_bytes < ((size_t)256 << 20)) {
+    lo.push_back(B);
+  } else {
+    const int64_t c0 = round_up((int)((B + 7) / 8), 128);
+    const int64_t c1 = round_up((int)((3 * B + 7) / 8), 128);
+    for (int64_t b : {c0, c0 + c1, c0 + 2 * c1})
+      if (b < B) lo.push_back(b);
+    lo.push_back(B);
+  }
+  int64_t C = 0;
+  for (size_t k = 0; k + 1 < lo.size(); ++k) C = std::max(C, lo[k + 1] - lo[k]);
   ZB_CHECK(ensure_stage(net, C));
   ZB_CHECK(ensure_workspace(net, C));
   HostStage& h = net->stage;
@@ -700,8 +718,8 @@ zbus_status solve_host(zbus_network net, int64_t B, const double* S_wye, const d
   ZB_CUDA(cudaEventRecord(h.start, st));
   ZB_CUDA(cudaStreamWaitEvent(h.h2d, h.start, 0));
   ZB_CUDA(cudaStreamWaitEvent(h.d2h, h.start, 0));
-  for (int64_t b0 = 0, k = 0; b0 < B; b0 += C, ++k) {
-    const int64_t Bk = std::min(C, B - b0);
+  for (size_t k = 0; k + 1 < lo.size(); ++k) {
+    const int64_t b0 = lo[k], Bk = lo[k + 1] - lo[k];
     const int s = (int)(k & 1);
     double* sw = h.buf[s];
     double* sd = sw + vec;
