@@ -2017,7 +2017,8 @@ zbus_status group_rebuild(Group* g, cudaStream_t st) {
 namespace {
 
 // Residual of every slot on stream st.  Register budget: 4 blocks per SM at
-// small n (latency), 6 at large n (FP32 issue), measured on both workloads.
+// small n (latency), 6 or 8 at large n (FP32 issue), measured on both
+// workloads.
 void launch_residual(Group* g, cudaStream_t st) {
   const bool bf = g->precision == ZBUS_MIXED_BF16X2;
   const bool tree = g->precision == ZBUS_TREE_SWEEP;
@@ -2025,7 +2026,10 @@ void launch_residual(Group* g, cudaStream_t st) {
   k_residual_group<OUT, M><<<g->res_blocks, RES_WARPS * 32, 0, st>>>(g->d_state, g->d_items)
   const int out = tree ? RES_F32 : (bf ? RES_BF16 : RES_FP16);
   if (g->max_n > 1024) {
-    if (out == RES_F32) ZB_RES(RES_F32, 6);
+    // the tree sweep's FP32 rows: 8 blocks (64 registers) beat 6 and 7
+    // (17.50 / 17.90 / 17.54 ms per 1024-bus x 16384 step); the FP16 and
+    // BF16 rows: 6 (18.91) against 7 (18.85) and 8 (18.93), within noise
+    if (out == RES_F32) ZB_RES(RES_F32, 8);
     else if (out == RES_BF16) ZB_RES(RES_BF16, 6);
     else ZB_RES(RES_FP16, 6);
   } else {
