@@ -276,9 +276,17 @@ k_residual_group(GroupState* __restrict__ gs, const ItemDesc* __restrict__ items
           }
         } else {
         bus_injection_df(ah3, al3, sw, sd, 3, inj, injl);
-        float ah[3][2], al[3][2];   // accumulators (re, im) per phase, hi / lo
+        // accumulators (re, im) per phase, hi / lo, started at -i(v): the
+        // block products are added to them error-free, so they end at -r
+        // and the currents need no registers during the block loop
+        float ah[3][2], al[3][2];
 #pragma unroll
-        for (int p = 0; p < 3; ++p) ah[p][0] = al[p][0] = ah[p][1] = al[p][1] = 0.f;
+        for (int p = 0; p < 3; ++p) {
+          ah[p][0] = -inj[p].x;
+          al[p][0] = -injl[p].x;
+          ah[p][1] = -inj[p].y;
+          al[p][1] = -injl[p].y;
+        }
         for (int t = bptr[a]; t < bptr[a + 1]; ++t) {
           const int cb = bcol[t];   // the same for the whole warp
           if (cb >= 0 && !ZB_IN(cb, nb, 0x201u)) continue;
@@ -320,9 +328,8 @@ k_residual_group(GroupState* __restrict__ gs, const ItemDesc* __restrict__ items
         }
 #pragma unroll
         for (int p = 0; p < 3; ++p) {
-          // inj - (ah + al), the leading difference exact near the fixed point
-          r[p] = make_float2(__fadd_rn(__fsub_rn(inj[p].x, ah[p][0]), __fsub_rn(injl[p].x, al[p][0])),
-                             __fadd_rn(__fsub_rn(inj[p].y, ah[p][1]), __fsub_rn(injl[p].y, al[p][1])));
+          // r = -(ah + al), one rounding
+          r[p] = make_float2(-__fadd_rn(ah[p][0], al[p][0]), -__fadd_rn(ah[p][1], al[p][1]));
           const float m = fmaxf(fabsf(r[p].x), fabsf(r[p].y));
           amax = (m == m) ? fmaxf(amax, m) : __int_as_float(0x7f800000);
         }
