@@ -479,16 +479,16 @@ def measure(net, form, Sw, Sd, wl, n, steps, warmup, flush, ws, peaks, extra_lau
 # (workload, scenarios, form, kernel) -> dram__bytes_read.sum + dram__bytes_write.sum per
 # launch from one ncu capture of the current kernel, with how it was taken
 TRAFFIC = {
-    ("feeder128_b4096", 4096, "fp64", "k_gemm3m_f64"): 66.378752e6 + 1.770240e6,
+    ("feeder128_b4096", 4096, "fp64", "k_gemm3m_f64"): 66.403584e6 + 1.091584e6,
     ("feeder1024_b16384", 16384, "fp16_scaled", "k_residual_group"):
-        4.0 * (404.892160e6 + 48.654848e6),
+        4.0 * (404.387840e6 + 49.560320e6),
 }
 TRAFFIC_SRC = {
     ("feeder128_b4096", 4096, "fp64", "k_gemm3m_f64"):
         "ncu capture of this launch configuration (sweep 3, all scenarios active)",
     ("feeder1024_b16384", 16384, "fp16_scaled", "k_residual_group"):
-        "ncu capture at 4096 scenarios x 4 (bytes scale with the scenarios: "
-        "measured 453.5 MB = algorithmic 452.6 MB)",
+        "ncu capture of a double-float sweep at 4096 scenarios x 4 (bytes scale with the "
+        "scenarios: measured 453.9 MB = algorithmic 452.6 MB; an FP32 start sweep 454.2 MB)",
 }
 
 
