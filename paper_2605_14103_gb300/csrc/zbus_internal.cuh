@@ -119,19 +119,6 @@ struct SolveCtx {
   int32_t* hist;          // profile mode: active count of sweep k (else nullptr)
   int32_t hist_n;
   uint8_t* keep;          // [B] stop decision of the current sweep, by slot
-  // mixed modes: double-float state (hi + lo FP32 pairs) and FP32 loads
-  float2* Vh;             // [n][B_pad] (scenario-minor)
-  float2* Vl;             // [n][B_pad]
-  float2* Swf;            // [n][B_pad] or nullptr
-  float2* Sdf;            // [n][B_pad] or nullptr
-  uint8_t* st;            // mixed: [B_pad] 0 = active, 1 = stopped
-  float* amax_prev;       // mixed: [B_pad] max |r| of the previous sweep (scale)
-  float* amax_cur;        // mixed: [B_pad] max |r| of this sweep
-  int32_t count_next;     // mixed: active scenarios after this sweep
-  int32_t B_pad;          // mixed: B rounded up to the 128-row tile
-  int32_t* mt_list;       // mixed: [B_pad / 128] tiles holding an active scenario
-  uint32_t* mt_flag;      // mixed: [B_pad / 128] set by the stop test
-  int32_t mt_count;       // mixed: entries of mt_list
   // load gradient (adjoint sweeps): V holds the adjoint iterate mu, these the
   // converged voltages, the loss gradient and its per-scenario scale
   const double2* Vf;      // [B][n]
