@@ -2,15 +2,18 @@
 // v <- v + Z_lp r(v)), for one or many feeders at once.
 //
 // Per sweep, four kernels cover every item of the group:
-//   k_residual_group   r(v) in double-float over 3x3 bus blocks, one slot per
-//                      lane, written as scaled FP16 / BF16 rows of R
+//   k_residual_group   r(v) over 3x3 bus blocks, one slot per lane, in FP32
+//                      for a cold start's first sweeps and in double-float
+//                      after them, written as scaled FP16 / BF16 rows of R
 //   k_contract_group   persistent tcgen05 contraction D = R Z_emb^T over the
 //                      list of (item, 128-slot tile, N-tile) with an active
 //                      slot; double-float epilogue v += D and step partials
 //   k_decide_group     per-slot stop test (own sweep counter per slot)
 //   k_finish_group     list of tiles for the next sweep, loop condition
-// Slots are admitted (k_slot_init) and collected (k_slot_merge + k_check, the
-// FP64 power-mismatch test) outside the loop.
+// (the tree form replaces the last three by k_tree_group).  Slots are
+// admitted (k_slot_init) and collected (k_slot_merge + k_branch_f64 +
+// k_check, the FP64 power-mismatch test, then the FP64 correction sweeps)
+// outside the loop.
 #include <cuda_bf16.h>
 #include <cuda_fp16.h>
 
