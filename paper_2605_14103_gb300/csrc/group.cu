@@ -248,32 +248,70 @@ k_residual_group(GroupState* __restrict__ gs, const ItemDesc* __restrict__ items
           // FP32: d = v_b - v_a from the hi and lo parts, block products with
           // the hi part of Y, each line's term J = Y_ab d kept for the bound
           bus_injection_f32(ah3, al3, sw, sd, 3, inj);
-          float2 acc[3] = {make_float2(0.f, 0.f), make_float2(0.f, 0.f), make_float2(0.f, 0.f)};
-          for (int t = bptr[a]; t < bptr[a + 1]; ++t) {
-            const int cb = bcol[t];
-            if (cb >= 0 && !ZB_IN(cb, nb, 0x202u)) continue;
-            float2 d[3];
+          // the accumulator starts at -i(v) (ends at -r), so the currents
+          // hold no registers in the block loop; the next block's neighbour
+          // state is requested before the current block is multiplied
+          float2 acc[3];
+#pragma unroll
+          for (int p = 0; p < 3; ++p) {
+            mag = fmaxf(mag, fmaxf(fabsf(inj[p].x), fabsf(inj[p].y)));
+            acc[p] = make_float2(-inj[p].x, -inj[p].y);
+          }
+          const int t1 = bptr[a + 1];
+          int t = bptr[a];
+          int cb = t < t1 ? bcol[t] : -3;
+          float2 xh[3], xl[3];
+#pragma unroll
+          for (int q2 = 0; q2 < 3; ++q2) xh[q2] = xl[q2] = make_float2(0.f, 0.f);
+          if (cb >= 0 && ZB_IN(cb, nb, 0x202u)) {
 #pragma unroll
             for (int q2 = 0; q2 < 3; ++q2) {
-              if (cb >= 0) {
-                const int64_t g = (int64_t)(3 * cb + q2) * Bp + b;
-                const float2 xh = Vh[g], xl = Vl[g];
-                d[q2] = make_float2((xh.x - ah3[q2].x) + (xl.x - al3[q2].x),
-                                    (xh.y - ah3[q2].y) + (xl.y - al3[q2].y));
-              } else if (cb == -1) {
-                const float4 s4 = it.vs_df[q2];
-                d[q2] = make_float2((s4.x - ah3[q2].x) + (s4.y - al3[q2].x),
-                                    (s4.z - ah3[q2].y) + (s4.w - al3[q2].y));
-              } else {
-                d[q2] = make_float2(ah3[q2].x + al3[q2].x, ah3[q2].y + al3[q2].y);
+              const int64_t g = (int64_t)(3 * cb + q2) * Bp + b;
+              xh[q2] = Vh[g];
+              xl[q2] = Vl[g];
+            }
+          }
+          for (; t < t1; ++t) {
+            const int cn = t + 1 < t1 ? bcol[t + 1] : -3;
+            float2 nh[3], nl[3];
+#pragma unroll
+            for (int q2 = 0; q2 < 3; ++q2) nh[q2] = nl[q2] = make_float2(0.f, 0.f);
+            if (cn >= 0 && ZB_IN(cn, nb, 0x203u)) {
+#pragma unroll
+              for (int q2 = 0; q2 < 3; ++q2) {
+                const int64_t g = (int64_t)(3 * cn + q2) * Bp + b;
+                nh[q2] = Vh[g];
+                nl[q2] = Vl[g];
               }
             }
-            block_f32(d, bval + (int64_t)t * 9, acc, mag);
+            if (cb >= 0 && !ZB_IN(cb, nb, 0x204u)) cb = -3;
+            if (cb != -3) {
+              float2 d[3];
+#pragma unroll
+              for (int q2 = 0; q2 < 3; ++q2) {
+                if (cb >= 0) {
+                  d[q2] = make_float2((xh[q2].x - ah3[q2].x) + (xl[q2].x - al3[q2].x),
+                                      (xh[q2].y - ah3[q2].y) + (xl[q2].y - al3[q2].y));
+                } else if (cb == -1) {
+                  const float4 s4 = it.vs_df[q2];
+                  d[q2] = make_float2((s4.x - ah3[q2].x) + (s4.y - al3[q2].x),
+                                      (s4.z - ah3[q2].y) + (s4.w - al3[q2].y));
+                } else {
+                  d[q2] = make_float2(ah3[q2].x + al3[q2].x, ah3[q2].y + al3[q2].y);
+                }
+              }
+              block_f32(d, bval + (int64_t)t * 9, acc, mag);
+            }
+            cb = cn;
+#pragma unroll
+            for (int q2 = 0; q2 < 3; ++q2) {
+              xh[q2] = nh[q2];
+              xl[q2] = nl[q2];
+            }
           }
 #pragma unroll
           for (int p = 0; p < 3; ++p) {
-            r[p] = make_float2(inj[p].x - acc[p].x, inj[p].y - acc[p].y);
-            mag = fmaxf(mag, fmaxf(fabsf(inj[p].x), fabsf(inj[p].y)));
+            r[p] = make_float2(-acc[p].x, -acc[p].y);
             const float m = fmaxf(fabsf(r[p].x), fabsf(r[p].y));
             amax = (m == m) ? fmaxf(amax, m) : __int_as_float(0x7f800000);
           }
