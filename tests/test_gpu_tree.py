@@ -67,9 +67,11 @@ def test_meshed_network_is_refused():
     assert np.abs(V.cpu().numpy() - ref).max() <= 1e-6
 
 
-def test_shunts_converge_to_the_oracle():
+@pytest.mark.parametrize("mode", ["tree", "fp16_scaled", "bf16x2"])
+def test_shunts_converge_to_the_oracle(mode):
     # capacitive shunts: the sweep inverts only the series part, the defect
-    # residual keeps them exactly
+    # residual keeps them exactly (its shunt blocks, in the FP32 start sweeps
+    # and in double-float); the dense forms invert them with Z
     f = F.make_feeder(90, 12, delta_frac=0.4)
     extra = {}
     for bus in (3, 9, 20, 33, 71):
@@ -79,7 +81,7 @@ def test_shunts_converge_to_the_oracle():
     net = zbus.Network(f.n_total, row, col, val, f.slack_idx, f.v_slack)
     Sw, Sd = F.make_scenarios(f, 70, 0.8, 1.2, seed=4)
     ref = O.solve_coo(f.n_total, row, col, val, f.slack_idx, f.v_slack, Sw, Sd)
-    V, it, cv = net.solve(dev(Sw), dev(Sd), precision="tree")
+    V, it, cv = net.solve(dev(Sw), dev(Sd), precision=mode)
     np.testing.assert_array_equal(cv.cpu().numpy(), ref["converged"])
     assert np.abs(V.cpu().numpy() - ref["V"]).max() <= 1e-6
     mm = net.power_mismatch(V, dev(Sw), dev(Sd)).cpu().numpy()
@@ -93,7 +95,7 @@ def test_sizes_and_block_shapes(N, B):
     Sw, Sd = F.make_scenarios(f, B, 0.8, 1.2)
     ref = O.solve_coo(f.n_total, f.Y_row, f.Y_col, f.Y_val, f.slack_idx, f.v_slack, Sw, Sd)
     net = zbus.Network.from_feeder(f)
-    V, it, cv = net.solve(dev(Sw), dev(Sd), precision="tree")
+    V, it, cv = net.solve(dev(Sw), dev(Sd), precision=mode)
     np.testing.assert_array_equal(cv.cpu().numpy(), ref["converged"])
     m = ref["converged"] == 1
     assert np.abs(V.cpu().numpy()[m] - ref["V"][m]).max(initial=0.0) <= 1e-6
