@@ -216,6 +216,28 @@ def parity_vs_oracle(ref, out, form):
                                              (dit == 0 if form == "fp64" else dit <= 1))}
 
 
+def feeder_config(workload, wl, n, B, precision, ws, phased=False):
+    """The `config` of a feeder workload's line, the same in both arms."""
+    cfg = {"workload": workload, "feeder_buses": wl.N, "unknowns": n,
+           "scenarios_per_gpu": B, "tol": wl.tol, "max_iter": wl.max_iter,
+           "precision": precision, "l2": "flushed between steps (512 MiB write)",
+           "parallelism": f"replicas x{ws}"}
+    if phased:
+        # the device solves the network padded to three phase slots per bus
+        cfg["padded_unknowns"] = 3 * (wl.N - 1)
+    return cfg
+
+
+def grid_config(workload, g, wl, B, precision, ws):
+    """The `config` of a Newton-Raphson workload's line, the same in both arms."""
+    return {"workload": workload, "method": "batched Newton-Raphson, "
+            "preconditioned GMRES (Sec. II-A)", "buses": g.N,
+            "branches": g.n_branch, "scenarios_per_gpu": B, "tol": wl.tol,
+            "max_iter": wl.max_iter, "gmres": "restart 30, tol 1e-6", "precision": precision,
+            "l2": "flushed between steps (512 MiB write)",
+            "parallelism": f"replicas x{ws}"}
+
+
 def run_reference(args):
     """The oracle (numpy FP64) as the reference arm, on the host cores."""
     ws = int(os.environ.get("WORLD_SIZE", "1"))
@@ -249,8 +271,8 @@ def run_reference(args):
            "n_gpus": ws, "steps": args.steps, "warmup": args.warmup,
            "ms_per_step": 1e3 * total / args.steps, "higher_is_better": True,
            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-           "config": {"workload": workload, "feeder_buses": wl.N, "unknowns": int(Sw.shape[1]),
-                      "scenarios_per_step": bs, "tol": wl.tol, "max_iter": wl.max_iter},
+           "config": feeder_config(workload, wl, int(Sw.shape[1]), wl.B, args.precision, ws,
+                                    getattr(f, "bus_phase", None) is not None),
            "cpu_baseline": {"value": value, "unit": UNIT, "cores": cpu_cores(), "kind": "oracle",
                             "sample": f"{bs} scenarios of the {wl.B}-scenario workload per step "
                                       "(same generator, consecutive slices)"},
@@ -280,8 +302,9 @@ def run_reference_nr(args, ws):
            "n_gpus": ws, "steps": args.steps, "warmup": args.warmup,
            "ms_per_step": 1e3 * sum(times) / args.steps, "higher_is_better": True,
            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-           "config": {"workload": args.workload, "buses": g.N, "scenarios_per_step": per,
-                      "tol": wl.tol},
+           "config": grid_config(args.workload, g, wl, wl.B,
+                                  args.precision if args.precision in ("fp64", "mixed")
+                                  else "fp64", ws),
            "cpu_baseline": {"value": value, "unit": UNIT, "cores": cpu_cores(), "kind": "oracle",
                             "sample": f"{per} scenarios of the {wl.B}-scenario batch per step "
                                       "(dense Newton-Raphson)"},
@@ -668,11 +691,7 @@ def run_ours(args):
                "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
                "dtype": DTYPE[args.precision],
                "data": "synthetic",
-               "config": {"workload": args.workload, "feeder_buses": wl.N, "unknowns": n,
-                          "scenarios_per_gpu": B, "tol": wl.tol, "max_iter": wl.max_iter,
-                          "precision": args.precision,
-                          "l2": "flushed between steps (512 MiB write)",
-                          "parallelism": f"replicas x{ws}"},
+               "config": feeder_config(args.workload, wl, n, B, args.precision, ws, phased),
                "converged_per_step": head["converged_per_step"], "max_iters": head["max_iters"],
                "mean_iters": head["mean_iters"], "gpu_launches": head["gpu_launches"],
                "vs_plain_fp64": forms_out[args.precision]["vs_plain_fp64"],
@@ -687,9 +706,6 @@ def run_ours(args):
                "peaks": {"src": peaks["src"], "fp64_tflops": peaks["fp64_tflops"],
                          "fp64_src": peaks["fp64_src"]},
                "forms": forms_out}
-        if phased:
-            # the device solves the network padded to three phase slots per bus
-            out["config"]["padded_unknowns"] = 3 * (wl.N - 1)
         if grad is not None:
             for k in ("fp64", "tree"):
                 if "ms_per_step" in grad.get(k, {}):
@@ -1163,12 +1179,7 @@ def run_nr(args):
                 "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * t_max / args.steps,
                 "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
                 "dtype": dtype_line, "data": "synthetic",
-                "config": {"workload": args.workload, "method": "batched Newton-Raphson, "
-                           "preconditioned GMRES (Sec. II-A)", "buses": g.N,
-                           "branches": g.n_branch, "scenarios_per_gpu": B, "tol": wl.tol,
-                           "max_iter": wl.max_iter, "gmres": "restart 30, tol 1e-6", "precision": prec,
-                           "l2": "flushed between steps (512 MiB write)",
-                           "parallelism": f"replicas x{ws}"},
+                "config": grid_config(args.workload, g, wl, B, prec, ws),
                 "precision": prec, "forms": forms,
                 "converged_per_step": good, "newton_steps_mean": float(it.mean()),
                 "gmres_iters_mean": float(gm.mean()), "max_mismatch": float(mm.max()),

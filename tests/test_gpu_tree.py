@@ -95,7 +95,7 @@ def test_sizes_and_block_shapes(N, B):
     Sw, Sd = F.make_scenarios(f, B, 0.8, 1.2)
     ref = O.solve_coo(f.n_total, f.Y_row, f.Y_col, f.Y_val, f.slack_idx, f.v_slack, Sw, Sd)
     net = zbus.Network.from_feeder(f)
-    V, it, cv = net.solve(dev(Sw), dev(Sd), precision=mode)
+    V, it, cv = net.solve(dev(Sw), dev(Sd), precision="tree")
     np.testing.assert_array_equal(cv.cpu().numpy(), ref["converged"])
     m = ref["converged"] == 1
     assert np.abs(V.cpu().numpy()[m] - ref["V"][m]).max(initial=0.0) <= 1e-6
