@@ -38,6 +38,9 @@ constexpr int64_t FUSE_DECIDE = 1024;   // slots up to which the stop test joins
 // output of the residual: scaled FP16 / BF16 rows of R (tensor-core
 // contraction) or FP32 values, scenario-minor (tree sweep)
 constexpr int RES_FP16 = 0, RES_BF16 = 1, RES_F32 = 2;
+// a cold start's sweeps stay on the FP32 residual while its max |r| exceeds
+// this fraction of the largest line or load current (decide_slot)
+constexpr float F32_SWITCH = 0x1p-13f;
 constexpr int TREE_BATCH = 4;   // buses whose state a tree-sweep warp loads at once
 constexpr size_t TREE_ONCHIP_MAX = 200 * 1024;   // shared memory of an on-chip tree block
 
@@ -742,7 +745,7 @@ __device__ __forceinline__ void decide_slot(const GroupState* __restrict__ gs, c
       // falls, and the step is above the stop tolerance; once off, the slot
       // runs double-float to its stop
       const float g = it.amax[2 * it.Bp + b];
-      const bool more = keep && am > 0x1p-13f * g && am < prev && delta > gs->tol;
+      const bool more = keep && am > F32_SWITCH * g && am < prev && delta > gs->tol;
       it.amax[3 * it.Bp + b] = more ? 1.f : 0.f;
       it.amax[2 * it.Bp + b] = 0.f;
     }
@@ -1025,7 +1028,7 @@ k_tree_group(GroupState* __restrict__ gs, const ItemDesc* __restrict__ items,
       if (!keep) it.st[b] = SLOT_DONE;
       if (lp) {
         const float am = it.amax[it.Bp + b], prev = it.amax[b], g = it.amax[2 * it.Bp + b];
-        const bool more = keep && am > 0x1p-13f * g && am < prev && delta > gs->tol;
+        const bool more = keep && am > F32_SWITCH * g && am < prev && delta > gs->tol;
         it.amax[3 * it.Bp + b] = more ? 1.f : 0.f;
         it.amax[b] = am;
         it.amax[it.Bp + b] = 0.f;
