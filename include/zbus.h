@@ -96,7 +96,7 @@ typedef struct {
                               first sweeps form the defect residual in FP32
                               (block products with the FP32 part of Y, load
                               currents at the FP32 voltage) as long as its max
-                              |r| exceeds 2^-13 of its largest line or load
+                              |r| exceeds 2^-20 of its largest line or load
                               current, falls from sweep to sweep and its step
                               exceeds tol, then double-float to the stop; no
                               scenario stops on an FP32 sweep, so the fixed

@@ -39,8 +39,14 @@ constexpr int64_t FUSE_DECIDE = 1024;   // slots up to which the stop test joins
 // contraction) or FP32 values, scenario-minor (tree sweep)
 constexpr int RES_FP16 = 0, RES_BF16 = 1, RES_F32 = 2;
 // a cold start's sweeps stay on the FP32 residual while its max |r| exceeds
-// this fraction of the largest line or load current (decide_slot)
-constexpr float F32_SWITCH = 0x1p-13f;
+// this fraction of the largest line or load current (decide_slot).  The FP32
+// rounding of the block products, a few 2^-24 of those currents, then stays
+// below about 2^-3 of the residual, so an FP32 sweep still removes most of
+// it; the double-float sweeps that follow remove the rest.  Measured: at
+// 2^-20 the fifth of the eight sweeps of the 1024-bus workload runs on FP32
+// with the iteration counts unchanged; at 2^-22 the rounding stalls the
+// FP32 sweeps and scenarios need up to two more double-float sweeps.
+constexpr float F32_SWITCH = 0x1p-20f;
 constexpr int TREE_BATCH = 4;   // buses whose state a tree-sweep warp loads at once
 constexpr size_t TREE_ONCHIP_MAX = 200 * 1024;   // shared memory of an on-chip tree block
 
@@ -211,7 +217,7 @@ k_residual_group(GroupState* __restrict__ gs, const ItemDesc* __restrict__ items
   const bool act = it.st[b] == SLOT_ACTIVE;
   if (!__syncthreads_or(act)) return;   // all 32 slots of this group are idle
   // FP32 sweep for this slot (its flag, set at a cold start and kept by the
-  // stop test while the residual stays above 2^-13 of the largest line
+  // stop test while the residual stays above F32_SWITCH of the largest line
   // current); lanes of a warp may differ and then take both paths
   const bool lp = act && it.amax[3 * it.Bp + b] != 0.f;
   float c = 1.f;
@@ -738,12 +744,10 @@ __device__ __forceinline__ void decide_slot(const GroupState* __restrict__ gs, c
     it.amax[b] = am;
     it.amax[it.Bp + b] = 0.f;
     if (lp) {
-      // the next sweep stays on FP32 while max |r| exceeds 2^-13 of the
-      // largest line current or load current of this one (the FP32 rounding
-      // of the block products, a few ulps of those currents, is then below
-      // 2^-8 of the residual, under 1/30 of what one sweep removes), still
-      // falls, and the step is above the stop tolerance; once off, the slot
-      // runs double-float to its stop
+      // the next sweep stays on FP32 while max |r| exceeds F32_SWITCH of
+      // the largest line current or load current of this one, still falls,
+      // and the step is above the stop tolerance; once off, the slot runs
+      // double-float to its stop
       const float g = it.amax[2 * it.Bp + b];
       const bool more = keep && am > F32_SWITCH * g && am < prev && delta > gs->tol;
       it.amax[3 * it.Bp + b] = more ? 1.f : 0.f;
