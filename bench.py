@@ -504,14 +504,21 @@ def measure(net, form, Sw, Sd, wl, n, steps, warmup, flush, ws, peaks, extra_lau
 TRAFFIC = {
     ("feeder128_b4096", 4096, "fp64", "k_gemm3m_f64"): 66.403584e6 + 1.091584e6,
     ("feeder1024_b16384", 16384, "fp16_scaled", "k_residual_group"):
-        4.0 * (404.387840e6 + 49.560320e6),
+        4.0 * (404.311040e6 + 49.283840e6),
+    ("feeder1024_b16384", 16384, "fp16_scaled", "k_contract_group"):
+        2.0 * (1047.367168e6 + 368.998144e6),
 }
 TRAFFIC_SRC = {
     ("feeder128_b4096", 4096, "fp64", "k_gemm3m_f64"):
         "ncu capture of this launch configuration (sweep 3, all scenarios active)",
     ("feeder1024_b16384", 16384, "fp16_scaled", "k_residual_group"):
-        "ncu capture of a double-float sweep at 4096 scenarios x 4 (bytes scale with the "
-        "scenarios: measured 453.9 MB = algorithmic 452.6 MB; an FP32 start sweep 454.2 MB)",
+        "ncu capture of an FP32 start sweep at 4096 scenarios x 4 (bytes scale with the "
+        "scenarios: measured 453.6 MB = algorithmic 452.6 MB; a double-float sweep 453.9 MB)",
+    ("feeder1024_b16384", 16384, "fp16_scaled", "k_contract_group"):
+        "ncu capture (dram__bytes_read/write.sum, one pass) of sweep 3 at 8192 scenarios x 2: "
+        "past one group of 128-slot tiles the bytes grow with the scenarios (4096: 681 MB, "
+        "8192: 1416 MB); algorithmic 1886 MB per 16384-scenario launch (Z 75 MB, R rows "
+        "201 MB, double-float v read and written 1609 MB)",
 }
 
 

@@ -1243,19 +1243,24 @@ k_slot_merge(const ItemDesc* __restrict__ items, int k, int s0, int B,
 
 // 1 / d: a single-precision reciprocal refined by two Newton-Raphson steps
 // r <- r (2 - d r) (quadratic convergence, 24 -> 48 -> beyond 53 bits);
-// plain division outside the single-precision range.  The conversions to
-// and from float are the integer ones (the FP64 units stay on the FMAs).
+// plain division outside [2^-99, 2^100), well inside the single-precision
+// range (zero, infinities and NaNs included).  The range test reads the
+// exponent field and the conversions to and from float are the integer
+// ones, so the FP64 units only do the FMAs.
 __device__ __forceinline__ double recip64(double d) {
-  if (!(d > 1e-30 && d < 1e30)) return 1.0 / d;
+  const unsigned ex = (unsigned)((unsigned long long)__double_as_longlong(d) >> 52) & 0x7FFu;
+  if (ex < 1023u - 99u || ex >= 1023u + 100u) return 1.0 / d;
   double r = f2d_exact(__frcp_rn(d2f_rn(d)));
   r = r * fma(-d, r, 2.0);
   r = r * fma(-d, r, 2.0);
   return r;
 }
 
-// conj(S / v), zero for an absent load.
+// conj(S / v), zero for an absent load (both parts +-0, tested on the
+// integer units).
 __device__ __forceinline__ double2 draw64(double2 S, double2 v) {
-  if (S.x == 0.0 && S.y == 0.0) return make_double2(0.0, 0.0);
+  if (((unsigned long long)(__double_as_longlong(S.x) | __double_as_longlong(S.y)) << 1) == 0ull)
+    return make_double2(0.0, 0.0);
   const double inv = recip64(fma(v.x, v.x, v.y * v.y));
   return make_double2(fma(S.x, v.x, S.y * v.y) * inv, fma(S.x, v.y, -S.y * v.x) * inv);
 }
