@@ -752,7 +752,8 @@ def bench_latency(solves=200):
     f, Sw_h, Sd_h, wl = F.make_workload("feeder13_b8")
     Sw, Sd = torch.from_numpy(Sw_h).cuda(), torch.from_numpy(Sd_h).cuda()
     net = zbus.Network.from_feeder(f)
-    res = {"what": "device time of one zbus_solve of 8 scenarios (CUDA events), "
+    res = {"what": "time of one zbus_solve call of 8 scenarios from Python (CUDA events "
+                   "around the call, so the host's call overhead is included), "
                    f"{solves} solves after 10 warm-up"}
     for form in ("fp64", "fp16_scaled", "tree"):
         out = (torch.empty((8, f.n), dtype=torch.complex128, device="cuda"),

@@ -589,6 +589,16 @@ zbus_status solve_device(zbus_network net, int64_t B, const double* S_wye, const
   }
 
   net->last_group = nullptr;   // the plain method has no device-side waits
+  if (o.profile != 1 && B <= F64_BM && net->n_pad <= FUSED_MAX_NPAD) {
+    // a small feeder and at most one tile of scenarios: the whole solve in
+    // one launch (bitwise the results of the sweep-per-launch path below)
+    launch_solve_fused_f64(net->Zr, net->Zi, net->Zs, net->w, (const double2*)V_init,
+                           (const double2*)S_wye, (const double2*)S_delta, net->n, net->n_pad,
+                           (int)B, tol, max_iter, o.conv_rule, (double2*)V_out, iters, converged,
+                           st);
+    ZB_CUDA(cudaGetLastError());
+    return ZBUS_OK;
+  }
   SolveCtx h;
   std::memset(&h, 0, sizeof(h));
   h.S_wye = (const double2*)S_wye;

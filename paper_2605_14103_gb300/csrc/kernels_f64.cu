@@ -313,6 +313,132 @@ k_gemm3m_f64_small(const SolveCtx* __restrict__ ctx, const double* __restrict__ 
 }
 
 // ---------------------------------------------------------------------------
+// The whole solve of one small feeder in one launch, for the latency case
+// (n_pad <= FUSED_MAX_NPAD unknowns, at most one 32-scenario tile): one block
+// per scenario keeps v and the 3M operands in shared memory and runs every
+// sweep (K1, K2, K3) itself, so a solve costs one launch instead of four
+// kernel nodes per sweep.  The arithmetic is that of the sweep kernels in
+// the same order: the currents of k_currents_f64, each output's three
+// products summed over k in sequence and the tile partials grouped as in
+// k_gemm3m_f64_small, the tiles reduced and the stop rule applied as in
+// k_decide, so the results are bitwise those of the sweep-per-launch path.
+// ---------------------------------------------------------------------------
+__global__ void __launch_bounds__(FUSED_THREADS)
+k_solve_fused_f64(const double* __restrict__ Zr, const double* __restrict__ Zi,
+                  const double* __restrict__ Zs, const double2* __restrict__ w,
+                  const double2* __restrict__ V_init, const double2* __restrict__ Sw,
+                  const double2* __restrict__ Sd, int n, int n_pad, double tol, int max_iter,
+                  int rule, double2* __restrict__ V, int32_t* __restrict__ iters,
+                  uint8_t* __restrict__ conv) {
+  __shared__ double2 sv[FUSED_MAX_NPAD];
+  __shared__ double sIr[FUSED_MAX_NPAD], sIi[FUSED_MAX_NPAD], sIs[FUSED_MAX_NPAD];
+  __shared__ double sdm[FUSED_MAX_NPAD], sds[FUSED_MAX_NPAD];
+  __shared__ int sok[FUSED_MAX_NPAD];
+  __shared__ int sdone;
+  const int b = blockIdx.x, t = threadIdx.x;
+  const int64_t row = (int64_t)b * n;
+  const int nbp = n_pad / 3, ntn = n_pad / F64_BN;
+  for (int i = t; i < n; i += blockDim.x) sv[i] = V_init ? V_init[row + i] : w[i];
+  __syncthreads();
+  for (int it = 1;; ++it) {
+    // K1: the currents of every bus
+    for (int k = t; k < nbp; k += blockDim.x) {
+      const int j0 = 3 * k;
+      double2 inj[3] = {make_double2(0.0, 0.0), make_double2(0.0, 0.0), make_double2(0.0, 0.0)};
+      if (j0 < n) {
+        const int m = min(3, n - j0);
+        double2 vv[3], sw[3], sd[3];
+#pragma unroll
+        for (int p = 0; p < 3; ++p) {
+          vv[p] = p < m ? sv[j0 + p] : make_double2(1.0, 0.0);
+          sw[p] = (Sw && p < m) ? Sw[row + j0 + p] : make_double2(0.0, 0.0);
+          sd[p] = (Sd && p < m) ? Sd[row + j0 + p] : make_double2(0.0, 0.0);
+        }
+        bus_injection(vv, Sw ? sw : nullptr, Sd ? sd : nullptr, m, inj);
+        for (int p = m; p < 3; ++p) inj[p] = make_double2(0.0, 0.0);
+      }
+#pragma unroll
+      for (int p = 0; p < 3; ++p) {
+        sIr[j0 + p] = inj[p].x;
+        sIi[j0 + p] = inj[p].y;
+        sIs[j0 + p] = inj[p].x + inj[p].y;
+      }
+    }
+    __syncthreads();
+    // K2: one output per thread, v <- w + D in place (the currents are read
+    // from shared memory only)
+    for (int i = t; i < n_pad; i += blockDim.x) {
+      const double* zr = Zr + (int64_t)i * n_pad;
+      const double* zi = Zi + (int64_t)i * n_pad;
+      const double* zs = Zs + (int64_t)i * n_pad;
+      double a1 = 0.0, a2 = 0.0, a3 = 0.0;
+      for (int k = 0; k < n_pad; ++k) {
+        a1 = fma(zr[k], sIr[k], a1);
+        a2 = fma(zi[k], sIi[k], a2);
+        a3 = fma(zs[k], sIs[k], a3);
+      }
+      int ok = 0;
+      double dm = 0.0, ds = 0.0;
+      if (i < n) {
+        const double dr = a1 - a2;
+        const double di = a3 - a1 - a2;
+        const double2 vo = sv[i];
+        const double2 wi = w[i];
+        const double2 vn = make_double2(wi.x + dr, wi.y + di);
+        sv[i] = vn;
+        double step = hypot(vn.x - vo.x, vn.y - vo.y);
+        if (step != step) step = INFINITY;
+        dm = step;
+        ds = hypot(vn.x, vn.y) - hypot(vo.x, vo.y);
+        ok = 1;
+      }
+      sdm[i] = dm;
+      sds[i] = ds;
+      sok[i] = ok;
+    }
+    __syncthreads();
+    // K3: the tile partials and the stop rule
+    if (t == 0) {
+      double dmax = 0.0, dsum = 0.0;
+      for (int nt = 0; nt < ntn; ++nt) {
+        double tm = 0.0, tu = 0.0;
+        for (int tn = 0; tn < F64_BN / 4; ++tn) {
+          double m = 0.0, u = 0.0;
+          for (int c = 0; c < 4; ++c) {
+            const int o = nt * F64_BN + tn + (F64_BN / 4) * c;
+            if (sok[o]) {
+              m = fmax(m, sdm[o]);
+              u += sds[o];
+            }
+          }
+          tm = fmax(tm, m);
+          tu += u;
+        }
+        dmax = fmax(dmax, tm);
+        dsum += tu;
+      }
+      const double delta = rule == ZBUS_CONV_SUMMAG ? fabs(dsum) : dmax;
+      int done = 1;
+      if (!isfinite(delta)) {
+        conv[b] = 0;
+      } else if (delta <= tol) {
+        conv[b] = 1;
+      } else if (it < max_iter) {
+        done = 0;
+      } else {
+        conv[b] = 0;
+      }
+      if (done) iters[b] = it;
+      sdone = done;
+    }
+    __syncthreads();
+    if (sdone) break;
+    __syncthreads();
+  }
+  for (int i = t; i < n; i += blockDim.x) V[row + i] = sv[i];
+}
+
+// ---------------------------------------------------------------------------
 // K3a: stop test per active scenario (many blocks): reduce the per-tile
 // partials in a fixed order, record iters / flags, mark the slots to keep.
 // ---------------------------------------------------------------------------
@@ -533,6 +659,15 @@ void launch_gemm_f64(SolveCtx* ctx, const double* Zr, const double* Zi, const do
                                                                              n, n_pad);
   else
     k_gemm3m_f64<<<grid, GEMM_THREADS, 0, st>>>(ctx, Zr, Zi, Zs, w, n, n_pad);
+}
+
+void launch_solve_fused_f64(const double* Zr, const double* Zi, const double* Zs,
+                            const double2* w, const double2* V_init, const double2* S_wye,
+                            const double2* S_del, int n, int n_pad, int B, double tol,
+                            int max_iter, int rule, double2* V, int32_t* iters, uint8_t* conv,
+                            cudaStream_t st) {
+  k_solve_fused_f64<<<B, FUSED_THREADS, 0, st>>>(Zr, Zi, Zs, w, V_init, S_wye, S_del, n, n_pad,
+                                                  tol, max_iter, rule, V, iters, conv);
 }
 
 void launch_converge(SolveCtx* ctx, int B, cudaGraphConditionalHandle h, bool use_handle,

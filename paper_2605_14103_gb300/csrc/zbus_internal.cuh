@@ -37,6 +37,10 @@ zbus_status cuda_fail(cudaError_t e, const char* what, const char* file, int lin
 // ---------------------------------------------------------------------------
 constexpr int F64_BM = 32;   // scenarios per tile
 constexpr int F64_BN = 48;   // outputs (16 buses) per tile
+// whole-solve kernel of the latency case: up to 96 padded unknowns, one
+// block of 96 threads per scenario, batches of one tile at most
+constexpr int FUSED_MAX_NPAD = 96;
+constexpr int FUSED_THREADS = 96;
 constexpr int F64_BK = 16;   // k step
 constexpr int F64_PAD = 48;  // n is padded to a multiple of this
 
@@ -325,6 +329,11 @@ void launch_gemm_f64(SolveCtx* ctx, const double* Zr, const double* Zi, const do
 int gemm_f64_grid(int B, int n_pad);
 void launch_converge(SolveCtx* ctx, int B, cudaGraphConditionalHandle h, bool use_handle,
                      cudaStream_t st);
+void launch_solve_fused_f64(const double* Zr, const double* Zi, const double* Zs,
+                            const double2* w, const double2* V_init, const double2* S_wye,
+                            const double2* S_del, int n, int n_pad, int B, double tol,
+                            int max_iter, int rule, double2* V, int32_t* iters, uint8_t* conv,
+                            cudaStream_t st);
 void launch_mismatch(const double2* V, const double2* S_wye, const double2* S_del,
                      const int32_t* ptr, const int32_t* col, const double2* val,
                      const double2* ys, int n, int B, double* out, cudaStream_t st);

@@ -230,3 +230,50 @@ def test_1024bus_small_batch():
     ref = oracle(f, Sw, Sd, tol=w.tol, max_iter=w.max_iter)
     compare(V, it, cv, ref, tight=False)
     assert np.abs(V.cpu().numpy() - ref["V"]).max() <= 1e-9
+
+
+def _bits(V):
+    """Bit patterns of a complex128 tensor (NaNs compare equal by their bits)."""
+    return V.view(torch.float64).view(torch.int64)
+
+
+@pytest.mark.parametrize("N,B,delta,seed", [(2, 1, 0.0, 5), (13, 8, 0.4, 101), (25, 32, 0.5, 7),
+                                             (33, 17, 1.0, 9)])
+def test_one_launch_solve_equals_the_sweep_per_launch_path(N, B, delta, seed):
+    """Feeders of at most 96 padded unknowns with at most 32 scenarios solve in
+    one launch (a block per scenario runs every sweep); the profile mode
+    launches the sweep kernels one by one.  Both give the same bits
+    (voltages, counts, flags) under both stop rules, cold and warm, with
+    scenarios that diverge and with the iteration cap reached; the one-launch
+    results also match the oracle."""
+    f = F.make_feeder(N, seed, delta_frac=delta, mult_hi=1.5)
+    Sw, Sd = F.make_scenarios(f, B, 0.5, 1.5)
+    if B > 2:   # one scenario far beyond what the feeder can carry
+        Sw[1] *= 500.0
+        Sd[1] *= 500.0
+    net = zbus.Network.from_feeder(f)
+    for rule in ("maxabs", "summag"):
+        for tol, max_iter in ((1e-8, 50), (1e-13, 3)):
+            kw = dict(tol=tol, max_iter=max_iter, rule=rule)
+            V1, it1, cv1 = net.solve(dev(Sw), dev(Sd), **kw)
+            V2, it2, cv2 = net.solve(dev(Sw), dev(Sd), profile=True, **kw)
+            assert torch.equal(_bits(V1), _bits(V2))
+            assert torch.equal(it1, it2) and torch.equal(cv1, cv2)
+            if max_iter == 50:
+                compare(V1, it1, cv1, oracle(f, Sw, Sd, tol=tol, rule=rule), tight=False)
+            # warm start from a perturbed solution, the output aliasing the start
+            V0 = V1 * (1.0 - 1e-3)
+            Va = V0.clone()
+            ita = torch.empty_like(it1)
+            cva = torch.empty_like(cv1)
+            net.solve(dev(Sw), dev(Sd), V_init=Va, out=(Va, ita, cva), **kw)
+            Vb, itb, cvb = net.solve(dev(Sw), dev(Sd), V_init=V0, profile=True, **kw)
+            assert torch.equal(_bits(Va), _bits(Vb))
+            assert torch.equal(ita, itb) and torch.equal(cva, cvb)
+    # wye-only and delta-only pointers
+    for a, b in ((Sw, None), (None, Sd)):
+        args = (dev(a) if a is not None else None, dev(b) if b is not None else None)
+        V1, it1, cv1 = net.solve(*args)
+        V2, it2, cv2 = net.solve(*args, profile=True)
+        assert torch.equal(_bits(V1), _bits(V2))
+        assert torch.equal(it1, it2) and torch.equal(cv1, cv2)
