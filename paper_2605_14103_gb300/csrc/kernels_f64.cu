@@ -317,11 +317,14 @@ k_gemm3m_f64_small(const SolveCtx* __restrict__ ctx, const double* __restrict__ 
 // (n_pad <= FUSED_MAX_NPAD unknowns, at most one 32-scenario tile): one block
 // per scenario keeps v and the 3M operands in shared memory and runs every
 // sweep (K1, K2, K3) itself, so a solve costs one launch instead of four
-// kernel nodes per sweep.  The arithmetic is that of the sweep kernels in
-// the same order: the currents of k_currents_f64, each output's three
-// products summed over k in sequence and the tile partials grouped as in
-// k_gemm3m_f64_small, the tiles reduced and the stop rule applied as in
-// k_decide, so the results are bitwise those of the sweep-per-launch path.
+// kernel nodes per sweep.  Every value is formed with the arithmetic of the
+// sweep kernels: the load currents of bus_injection (a thread per unknown
+// draws its wye current and its bus's delta branch, then adds the branches
+// into its phase as bus_injection does), each output's three products summed
+// over k in sequence, the step partials grouped as in k_gemm3m_f64_small and
+// reduced over the tiles as in k_decide (maxima in any order, which is exact;
+// the sums of the sum-of-magnitudes rule in the same order), so the results
+// are bitwise those of the sweep-per-launch path.
 // ---------------------------------------------------------------------------
 __global__ void __launch_bounds__(FUSED_THREADS)
 k_solve_fused_f64(const double* __restrict__ Zr, const double* __restrict__ Zi,
@@ -330,47 +333,72 @@ k_solve_fused_f64(const double* __restrict__ Zr, const double* __restrict__ Zi,
                   const double2* __restrict__ Sd, int n, int n_pad, double tol, int max_iter,
                   int rule, double2* __restrict__ V, int32_t* __restrict__ iters,
                   uint8_t* __restrict__ conv) {
+  static_assert(FUSED_THREADS >= FUSED_MAX_NPAD && FUSED_THREADS == 128,
+                "one thread per padded unknown; four warps share the outputs");
   __shared__ double2 sv[FUSED_MAX_NPAD];
+  __shared__ double2 sdw[FUSED_MAX_NPAD], sib[FUSED_MAX_NPAD];   // wye draws, delta branches
   __shared__ double sIr[FUSED_MAX_NPAD], sIi[FUSED_MAX_NPAD], sIs[FUSED_MAX_NPAD];
-  __shared__ double sdm[FUSED_MAX_NPAD], sds[FUSED_MAX_NPAD];
+  __shared__ double sds[FUSED_MAX_NPAD], su[FUSED_MAX_NPAD / 4];
+  __shared__ double swm[FUSED_THREADS / 32];
   __shared__ int sok[FUSED_MAX_NPAD];
   __shared__ int sdone;
-  const int b = blockIdx.x, t = threadIdx.x;
+  const int b = blockIdx.x, t = threadIdx.x, lane = t & 31, wid = t >> 5;
   const int64_t row = (int64_t)b * n;
-  const int nbp = n_pad / 3, ntn = n_pad / F64_BN;
-  for (int i = t; i < n; i += blockDim.x) sv[i] = V_init ? V_init[row + i] : w[i];
+  const int ntn = n_pad / F64_BN;
+  const bool summag = rule == ZBUS_CONV_SUMMAG;
+  if (t < n) sv[t] = V_init ? V_init[row + t] : w[t];
+  // this thread's unknown: bus j0 / 3, phase p, m valid phases in the bus
+  const int j0 = 3 * (t / 3), p = t % 3, m = min(3, n - j0);
+  const bool own = t < n;
+  const bool delta = Sd != nullptr && m == 3 && own;
+  const double2 swj = (Sw && own) ? Sw[row + t] : make_double2(0.0, 0.0);
+  const double2 sdj = delta ? Sd[row + t] : make_double2(0.0, 0.0);
   __syncthreads();
   for (int it = 1;; ++it) {
-    // K1: the currents of every bus
-    for (int k = t; k < nbp; k += blockDim.x) {
-      const int j0 = 3 * k;
-      double2 inj[3] = {make_double2(0.0, 0.0), make_double2(0.0, 0.0), make_double2(0.0, 0.0)};
-      if (j0 < n) {
-        const int m = min(3, n - j0);
-        double2 vv[3], sw[3], sd[3];
-#pragma unroll
-        for (int p = 0; p < 3; ++p) {
-          vv[p] = p < m ? sv[j0 + p] : make_double2(1.0, 0.0);
-          sw[p] = (Sw && p < m) ? Sw[row + j0 + p] : make_double2(0.0, 0.0);
-          sd[p] = (Sd && p < m) ? Sd[row + j0 + p] : make_double2(0.0, 0.0);
+    // K1a: the wye current of this unknown and the delta branch p of its bus
+    // (branch p joins phases p and p + 1), as load_draw inside bus_injection
+    if (t < n_pad) {
+      double2 dw = make_double2(0.0, 0.0), ib = make_double2(0.0, 0.0);
+      if (own) {
+        if (Sw) dw = load_draw(swj, sv[t]);
+        if (delta) {
+          const double2 va = sv[t], vb = sv[j0 + (p == 2 ? 0 : p + 1)];
+          ib = load_draw(sdj, make_double2(va.x - vb.x, va.y - vb.y));
         }
-        bus_injection(vv, Sw ? sw : nullptr, Sd ? sd : nullptr, m, inj);
-        for (int p = m; p < 3; ++p) inj[p] = make_double2(0.0, 0.0);
       }
-#pragma unroll
-      for (int p = 0; p < 3; ++p) {
-        sIr[j0 + p] = inj[p].x;
-        sIi[j0 + p] = inj[p].y;
-        sIs[j0 + p] = inj[p].x + inj[p].y;
+      sdw[t] = dw;
+      sib[t] = ib;
+    }
+    __syncthreads();
+    // K1b: phase p draws branch p and returns branch p - 1; injection = -drawn
+    if (t < n_pad) {
+      double2 inj = make_double2(0.0, 0.0);
+      if (own) {
+        double2 d = sdw[t];
+        if (delta) {
+          const double2 ib = sib[t], iw = sib[j0 + (p == 0 ? 2 : p - 1)];
+          d.x += ib.x - iw.x;
+          d.y += ib.y - iw.y;
+        }
+        inj = make_double2(-d.x, -d.y);
       }
+      sIr[t] = inj.x;
+      sIi[t] = inj.y;
+      sIs[t] = inj.x + inj.y;
     }
     __syncthreads();
     // K2: one output per thread, v <- w + D in place (the currents are read
-    // from shared memory only)
-    for (int i = t; i < n_pad; i += blockDim.x) {
-      const double* zr = Zr + (int64_t)i * n_pad;
-      const double* zi = Zi + (int64_t)i * n_pad;
-      const double* zs = Zs + (int64_t)i * n_pad;
+    // from shared memory only).  The outputs are dealt to the four warps in
+    // equal parts (n_pad / 4 lanes each), so each SM sub-partition's FP64
+    // pipe carries a quarter of the products.
+    double dm = 0.0;
+    const int per = n_pad / 4;
+    const int o = lane < per ? wid * per + lane : -1;
+    if (o >= 0) {
+      const bool out_own = o < n;
+      const double* zr = Zr + (int64_t)o * n_pad;
+      const double* zi = Zi + (int64_t)o * n_pad;
+      const double* zs = Zs + (int64_t)o * n_pad;
       double a1 = 0.0, a2 = 0.0, a3 = 0.0;
       for (int k = 0; k < n_pad; ++k) {
         a1 = fma(zr[k], sIr[k], a1);
@@ -378,50 +406,54 @@ k_solve_fused_f64(const double* __restrict__ Zr, const double* __restrict__ Zi,
         a3 = fma(zs[k], sIs[k], a3);
       }
       int ok = 0;
-      double dm = 0.0, ds = 0.0;
-      if (i < n) {
+      double ds = 0.0;
+      if (out_own) {
         const double dr = a1 - a2;
         const double di = a3 - a1 - a2;
-        const double2 vo = sv[i];
-        const double2 wi = w[i];
+        const double2 vo = sv[o];
+        const double2 wi = w[o];
         const double2 vn = make_double2(wi.x + dr, wi.y + di);
-        sv[i] = vn;
+        sv[o] = vn;
         double step = hypot(vn.x - vo.x, vn.y - vo.y);
         if (step != step) step = INFINITY;
         dm = step;
         ds = hypot(vn.x, vn.y) - hypot(vo.x, vo.y);
         ok = 1;
       }
-      sdm[i] = dm;
-      sds[i] = ds;
-      sok[i] = ok;
+      sds[o] = ds;
+      sok[o] = ok;
+    }
+    // K3: the largest step (maxima are exact in any order; every step is >= 0)
+    for (int o = 16; o > 0; o >>= 1) dm = fmax(dm, __shfl_xor_sync(0xffffffffu, dm, o));
+    if (lane == 0) swm[wid] = dm;
+    __syncthreads();
+    // the sum-of-magnitudes rule: per tile and thread column tn the outputs
+    // tn, tn + 12, tn + 24, tn + 36 in order, then tn = 0..11, then the tiles
+    if (summag && t < ntn * (F64_BN / 4)) {
+      const int nt = t / (F64_BN / 4), tn = t % (F64_BN / 4);
+      double u = 0.0;
+      for (int c = 0; c < 4; ++c) {
+        const int o = nt * F64_BN + tn + (F64_BN / 4) * c;
+        if (sok[o]) u += sds[o];
+      }
+      su[t] = u;
     }
     __syncthreads();
-    // K3: the tile partials and the stop rule
     if (t == 0) {
-      double dmax = 0.0, dsum = 0.0;
-      for (int nt = 0; nt < ntn; ++nt) {
-        double tm = 0.0, tu = 0.0;
-        for (int tn = 0; tn < F64_BN / 4; ++tn) {
-          double m = 0.0, u = 0.0;
-          for (int c = 0; c < 4; ++c) {
-            const int o = nt * F64_BN + tn + (F64_BN / 4) * c;
-            if (sok[o]) {
-              m = fmax(m, sdm[o]);
-              u += sds[o];
-            }
-          }
-          tm = fmax(tm, m);
-          tu += u;
+      double dmax = 0.0;
+      for (int x = 0; x < FUSED_THREADS / 32; ++x) dmax = fmax(dmax, swm[x]);
+      double dsum = 0.0;
+      if (summag)
+        for (int nt = 0; nt < ntn; ++nt) {
+          double tu = 0.0;
+          for (int tn = 0; tn < F64_BN / 4; ++tn) tu += su[nt * (F64_BN / 4) + tn];
+          dsum += tu;
         }
-        dmax = fmax(dmax, tm);
-        dsum += tu;
-      }
-      const double delta = rule == ZBUS_CONV_SUMMAG ? fabs(dsum) : dmax;
+      const double delta_v = summag ? fabs(dsum) : dmax;
       int done = 1;
-      if (!isfinite(delta)) {
+      if (!isfinite(delta_v)) {
         conv[b] = 0;
-      } else if (delta <= tol) {
+      } else if (delta_v <= tol) {
         conv[b] = 1;
       } else if (it < max_iter) {
         done = 0;
@@ -435,7 +467,7 @@ k_solve_fused_f64(const double* __restrict__ Zr, const double* __restrict__ Zi,
     if (sdone) break;
     __syncthreads();
   }
-  for (int i = t; i < n; i += blockDim.x) V[row + i] = sv[i];
+  if (t < n) V[row + t] = sv[t];
 }
 
 // ---------------------------------------------------------------------------

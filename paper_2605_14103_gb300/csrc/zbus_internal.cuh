@@ -38,9 +38,9 @@ zbus_status cuda_fail(cudaError_t e, const char* what, const char* file, int lin
 constexpr int F64_BM = 32;   // scenarios per tile
 constexpr int F64_BN = 48;   // outputs (16 buses) per tile
 // whole-solve kernel of the latency case: up to 96 padded unknowns, one
-// block of 96 threads per scenario, batches of one tile at most
+// block of four warps per scenario, batches of one tile at most
 constexpr int FUSED_MAX_NPAD = 96;
-constexpr int FUSED_THREADS = 96;
+constexpr int FUSED_THREADS = 128;
 constexpr int F64_BK = 16;   // k step
 constexpr int F64_PAD = 48;  // n is padded to a multiple of this
 
