@@ -4,7 +4,9 @@
 //       v <- w + D and per-tile step partials,
 //   K3  per-scenario stop test, freeze and stable compaction of the active
 //       list; sets the graph's loop condition.
-// Plus the run start (v^0) and the FP64 power-mismatch check.
+// Plus the run start (v^0), the whole solve of a small feeder in one launch
+// (K1-K3 of every sweep in one block per scenario, the latency case) and the
+// FP64 power-mismatch check.
 #include <cmath>
 
 #include "loads.cuh"
