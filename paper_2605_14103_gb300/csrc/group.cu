@@ -70,13 +70,15 @@ __device__ __forceinline__ int find_item(const ItemDesc* items, int n_items, int
 // Admission: slots [s0, s0 + B) of item k take v^0 (V0 with row stride
 // v0_stride, 0 broadcasting one row; else w) and the loads (FP64, [B][n]),
 // transposed to the scenario-minor state through 32 x 32 shared-memory tiles.
-// Admitted slots become active.
+// Admitted slots become active.  WARM: a start V0 is given (a cold start
+// needs no tile for it, which leaves room for more blocks per SM).
 // ---------------------------------------------------------------------------
+template <bool WARM>
 __global__ void k_slot_init(GroupState* __restrict__ gs, const ItemDesc* __restrict__ items, int k,
                             int s0, int B, const double2* __restrict__ V0, int v0_stride,
                             const float4* __restrict__ w_df, const double2* __restrict__ Sw,
                             const double2* __restrict__ Sd, int fp32_start) {
-  __shared__ double2 tv[32][33];
+  __shared__ double2 tv[WARM ? 32 : 1][33];
   __shared__ double2 tw[32][33];
   __shared__ double2 td[32][33];
   const ItemDesc it = items[k];
@@ -88,11 +90,11 @@ __global__ void k_slot_init(GroupState* __restrict__ gs, const ItemDesc* __restr
     double2 v = make_double2(0.0, 0.0), a = v, d = v;
     if (b < B && j < n) {
       const int64_t g = (int64_t)b * n + j;
-      if (V0) v = V0[(int64_t)b * v0_stride + j];
+      if (WARM) v = V0[(int64_t)b * v0_stride + j];
       if (Sw) a = Sw[g];
       if (Sd) d = Sd[g];
     }
-    tv[r][tx] = v;
+    if (WARM) tv[r][tx] = v;
     tw[r][tx] = a;
     td[r][tx] = d;
   }
@@ -101,7 +103,7 @@ __global__ void k_slot_init(GroupState* __restrict__ gs, const ItemDesc* __restr
     const int j = j0 + r, b = b0 + tx;
     if (j < n && b < B) {
       const int64_t g = (int64_t)j * Bp + s0 + b;
-      if (V0) {
+      if (WARM) {
         const double2 v = tv[tx][r];
         const float2 xr = df_split(v.x), xi = df_split(v.y);
         it.Vh[g] = make_float2(xr.x, xi.x);
@@ -127,7 +129,7 @@ __global__ void k_slot_init(GroupState* __restrict__ gs, const ItemDesc* __restr
       it.amax[slot] = 1.0f;
       it.amax[Bp + slot] = 0.0f;
       it.amax[2 * Bp + slot] = 0.0f;
-      it.amax[3 * Bp + slot] = (fp32_start && !V0) ? 1.0f : 0.0f;
+      it.amax[3 * Bp + slot] = (fp32_start && !WARM) ? 1.0f : 0.0f;
     }
   }
 }
@@ -2055,9 +2057,15 @@ zbus_status group_admit(Group* g, int k, int64_t s0, int64_t B, const double* V0
                         bool v0_broadcast, bool fp32_start) {
   if (B <= 0) return ZBUS_OK;
   const ItemDesc& d = g->h_items[k];
-  k_slot_init<<<dim3((d.n + 31) / 32, (unsigned)((B + 31) / 32)), dim3(32, 8), 0, st>>>(
-      g->d_state, g->d_items, k, (int)s0, (int)B, (const double2*)V0, v0_broadcast ? 0 : d.n,
-      g->nets[k]->w_df, (const double2*)S_wye, (const double2*)S_delta, fp32_start ? 1 : 0);
+  const dim3 grid((d.n + 31) / 32, (unsigned)((B + 31) / 32)), block(32, 8);
+  if (V0)
+    k_slot_init<true><<<grid, block, 0, st>>>(
+        g->d_state, g->d_items, k, (int)s0, (int)B, (const double2*)V0, v0_broadcast ? 0 : d.n,
+        g->nets[k]->w_df, (const double2*)S_wye, (const double2*)S_delta, fp32_start ? 1 : 0);
+  else
+    k_slot_init<false><<<grid, block, 0, st>>>(
+        g->d_state, g->d_items, k, (int)s0, (int)B, nullptr, 0, g->nets[k]->w_df,
+        (const double2*)S_wye, (const double2*)S_delta, fp32_start ? 1 : 0);
   ZB_CUDA(cudaGetLastError());
   return ZBUS_OK;
 }
