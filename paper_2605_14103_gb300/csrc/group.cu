@@ -2095,11 +2095,13 @@ void launch_residual(Group* g, cudaStream_t st) {
   const int out = tree ? RES_F32 : (bf ? RES_BF16 : RES_FP16);
   if (g->max_n > 1024) {
     // the tree sweep's FP32 rows: 8 blocks (64 registers) beat 6 and 7
-    // (17.50 / 17.90 / 17.54 ms per 1024-bus x 16384 step); the FP16 and
-    // BF16 rows: 6 (18.91) against 7 (18.85) and 8 (18.93), within noise
+    // (17.50 / 17.90 / 17.54 ms per 1024-bus x 16384 step); the FP16 rows,
+    // with six of the eight sweeps on the FP32 path: 7 blocks (17.14 ms)
+    // against 6 (17.25) and 8 (17.42); the BF16 rows: 7 (24.09) against 6
+    // (24.22)
     if (out == RES_F32) ZB_RES(RES_F32, 8);
-    else if (out == RES_BF16) ZB_RES(RES_BF16, 6);
-    else ZB_RES(RES_FP16, 6);
+    else if (out == RES_BF16) ZB_RES(RES_BF16, 7);
+    else ZB_RES(RES_FP16, 7);
   } else {
     if (out == RES_F32) ZB_RES(RES_F32, 4);
     else if (out == RES_BF16) ZB_RES(RES_BF16, 4);
